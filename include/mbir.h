@@ -1,0 +1,207 @@
+/*
+ * mbir.h - C ABI of the GB300 multi-layer collimated-beam MBIR library.
+ *
+ * The library applies the physics-based forward model A of Alanazi et al.,
+ * "Model-Based Reconstruction for Collimated Beam Ultrasound Systems"
+ * (Section 2, eq. 1-13), its adjoint, the direct-arrival term of eq. 1 and the
+ * QGGMRF prior of eq. 14-17, and minimises the MAP cost of eq. 18, all in
+ * hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *   - SI units (m, s, m/s, kg/m^3).  Attenuation alpha is given in
+ *     Np / (MHz m) (the paper's "/Hz m" read with f in MHz, Section 3).
+ *   - Image pixel v = r * img_w + c; row r is depth, column c is lateral.
+ *     Pixel centre: (img_x0_m + (c + 0.5) pitch_m, img_z0_m + (r + 0.5) pitch_m).
+ *     Transducers sit at depth 0 in layer 1.
+ *   - A-scan k = i * n_rx + j: transmitter position i (lateral tx_x_m[i]),
+ *     receiver j (lateral tx_x_m[i] + rx_offset_m[j]).  y is K x M row-major,
+ *     K = n_tx * n_rx, M = n_samples, sample n at time n / fs_hz.
+ *   - Device pointers are owned by the caller (e.g. a torch tensor's
+ *     data_ptr) and must stay valid until the stream reaches the call.  All
+ *     device work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and is asynchronous unless stated otherwise.
+ *   - Every call returns MBIR_OK (0) or a negative MBIR_ERR_* code; outputs
+ *     are untouched on an argument error.  mbir_error_string gives the text.
+ *   - A geometry handle may be used from one host thread at a time; calls
+ *     that share a handle must be ordered on one stream (the handle owns the
+ *     reconstruction workspace).
+ */
+#ifndef MBIR_H
+#define MBIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MBIR_OK               0
+#define MBIR_ERR_INVALID_ARG (-1)  /* bad size, pointer, layer or prior value */
+#define MBIR_ERR_OOM         (-2)  /* device or host allocation failed */
+#define MBIR_ERR_CUDA        (-3)  /* a CUDA runtime call or launch failed */
+#define MBIR_ERR_NONFINITE   (-4)  /* the data or an iterate is NaN/Inf */
+#define MBIR_ERR_TIMEOUT     (-5)  /* a bounded wait gave up */
+#define MBIR_ERR_BUSY        (-6)  /* admission refused: over the memory budget */
+#define MBIR_ERR_UNSUPPORTED (-7)  /* option not available for this geometry */
+#define MBIR_ERR_CANCELLED   (-8)  /* a request was cancelled */
+#define MBIR_ERR_NOT_READY   (-9)  /* a request has not finished yet */
+
+#define MBIR_MAX_LAYERS 8
+
+typedef enum {
+    MBIR_PREC_FP32 = 0,          /* y, residual and pulse table in FP32 */
+    MBIR_PREC_BF16 = 1           /* y / residual copy and pulse table stored BF16, FP32 math */
+} mbir_precision;
+
+typedef enum {
+    MBIR_MODE_AUTO = 0,          /* TAB when the leg table fits, else OTF */
+    MBIR_MODE_OTF = 1,           /* travel times solved in registers on every apply */
+    MBIR_MODE_TAB = 2            /* legs solved once per geometry, kept in device memory */
+} mbir_mode;
+
+/*
+ * Geometry of one scan (Section 2 "Multi-layered structures", eq. 3-6, and the
+ * acquisition of Section 3).  Arrays are host memory and are copied.
+ *   thickness_m[l], speed_mps[l], atten_np_per_mhz_m[l], density_kgm3[l]:
+ *       layer l from the transducer plane down; the last layer extends below
+ *       its thickness.  Density only enters the interface transmittance tau.
+ *   pulse: Gaussian-modulated cosine at fc_hz whose envelope FWHM spans
+ *       n_cycles periods; its window t0 (eq. 10) is ceil(8 sigma fs) samples.
+ *   beta: apodization power of eq. 12.
+ *   direct_arrival: 1 adds one direct-arrival column per A-scan (eq. 1).
+ *   gamma_max_s: top of the pulse table's attenuation axis (s); 0 selects
+ *       4 * sum_l alpha_l eta_l down to the deepest pixel centre.
+ *   gamma_bins (G), phases (Q): pulse table of G attenuation bins and Q
+ *       phases per sample, read by bilinear interpolation (0 selects 16, 16).
+ */
+typedef struct {
+    int n_layers;
+    double thickness_m[MBIR_MAX_LAYERS];
+    double speed_mps[MBIR_MAX_LAYERS];
+    double atten_np_per_mhz_m[MBIR_MAX_LAYERS];
+    double density_kgm3[MBIR_MAX_LAYERS];
+    int img_w, img_h;
+    double pitch_m, img_x0_m, img_z0_m;
+    int n_tx;
+    const double* tx_x_m;
+    int n_rx;
+    const double* rx_offset_m;
+    double fs_hz;
+    int n_samples;
+    double fc_hz, n_cycles;
+    double beta;
+    int direct_arrival;
+    double gamma_max_s;
+    int gamma_bins, phases;
+    int precision;               /* mbir_precision */
+    int mode;                    /* mbir_mode */
+} mbir_geometry_desc;
+
+/* QGGMRF prior (eq. 15-17) and the noise sigma of eq. 2.
+ * Requires 1 < p < q = 2 (Section 2, "Prior model"), T > 0, sigma0 > 0,
+ * m > 0, a >= 0 and sigma_noise > 0. */
+typedef struct {
+    double p, q, T, sigma0, m, a;
+    double sigma_noise;
+} mbir_prior;
+
+/* Per-call statistics (host memory).  cost may be NULL; when given it
+ * receives min(cost_len, n_iter) values of the eq. 18 cost after each
+ * iteration (this adds one device-to-host read per iteration). */
+typedef struct {
+    double* cost;
+    int cost_len;
+    int iterations;
+    double grad_norm_first;
+    double grad_norm_last;
+} mbir_stats;
+
+typedef struct {
+    int64_t n_pixels, n_ascans, n_samples;
+    int pulse_support;           /* T_w samples */
+    int gamma_bins, phases;
+    double gamma_max_s;
+    int mode;                    /* resolved mbir_mode (OTF or TAB) */
+    int precision;
+    int64_t device_bytes;        /* tables + workspace held by the handle */
+} mbir_geometry_info;
+
+typedef struct mbir_geometry mbir_geometry;
+
+/* Validate `d`, build the pulse table (eq. 9-10) on the host in FP64, copy
+ * the layer, transducer and table data to the current device, and (TAB mode)
+ * solve every leg once (the paper's "compute only once", Section 3).
+ * Errors: MBIR_ERR_INVALID_ARG (n_layers outside 1..8, non-positive
+ * thickness, speed, density, pitch, fs, fc, n_cycles, beta < 0, negative
+ * attenuation, img_z0_m < 0, sizes < 1, NULL arrays, K*M or N above 2^31),
+ * MBIR_ERR_OOM, MBIR_ERR_CUDA.  *out is untouched on error.  Synchronises
+ * `stream` before returning. */
+int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometry** out);
+
+/* Free the handle and its device memory.  Accepts NULL.  The caller must
+ * have finished every call that uses the handle. */
+int mbir_destroy_geometry(mbir_geometry* g);
+
+/* Bytes of device memory held by the handle (tables and workspace). */
+size_t mbir_geometry_bytes(const mbir_geometry* g);
+
+int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info);
+
+/* y = A x (eq. 11-13 summed over voxels).  x_dev: N floats.  y_dev: K x M,
+ * float (FP32) or bfloat16 (BF16 precision).  Every output sample is written
+ * (no accumulation into y). */
+int mbir_forward(const mbir_geometry* g, const float* x_dev, void* y_dev, void* stream);
+
+/* x = A^T r (adjoint of eq. 13).  r_dev: K x M, float (FP32) or bfloat16
+ * (BF16 precision).  x_dev: N floats, overwritten. */
+int mbir_backproject(const mbir_geometry* g, const void* r_dev, float* x_dev, void* stream);
+
+/* Direct-arrival projection (eq. 1): per A-scan k, g_k = <d_k, r_k>/|d_k|^2
+ * and e_k = r_k - g_k d_k, with d_k the unattenuated pulse delayed by
+ * |rx_offset_m[j]| / speed_mps[0].  r_dev, e_dev: K x M floats (may alias);
+ * gk_dev: K floats or NULL.  Without direct arrivals e = r and g = 0. */
+int mbir_project(const mbir_geometry* g, const float* r_dev, float* e_dev, float* gk_dev,
+                 void* stream);
+
+/* Gradient of the prior of eq. 14-17 at x: out_s = sum_r b_sr rho'(x_s - x_r).
+ * x_dev, out_dev: N floats. */
+int mbir_prior_gradient(const mbir_geometry* g, const mbir_prior* pr, const float* x_dev,
+                        float* out_dev, void* stream);
+
+/* MAP estimate of eq. 18.  y_dev: K x M (float, or bfloat16 in BF16
+ * precision).  x_dev: N floats, the start when x_given != 0 (else zeros), the
+ * estimate on return.  g_dev: K floats (direct-arrival gains) or NULL.
+ * Iteration: Polak-Ribiere+ conjugate directions with the majorize-minimize
+ * step of the exact data term plus the symmetric quadratic bound of the prior.
+ * Synchronises `stream` before returning (it reads the convergence scalars).
+ * Errors: MBIR_ERR_INVALID_ARG (prior outside 1 < p < q = 2 and friends,
+ * n_iter < 0), MBIR_ERR_NONFINITE (the data or cost is NaN/Inf), MBIR_ERR_CUDA. */
+int mbir_reconstruct(const mbir_geometry* g, const void* y_dev, const mbir_prior* pr,
+                     int n_iter, float* x_dev, int x_given, float* g_dev, mbir_stats* st,
+                     void* stream);
+
+/* mbir_reconstruct on host buffers: copies y_host (K x M float) in, runs, and
+ * copies x_host (N floats) and g_host (K floats, may be NULL) out, all on
+ * `stream`.  Synchronises the stream. */
+int mbir_reconstruct_host(const mbir_geometry* g, const float* y_host, const mbir_prior* pr,
+                          int n_iter, float* x_host, float* g_host, mbir_stats* st,
+                          void* stream);
+
+/* Diagnostics for parity tests: per requested (pixel, A-scan) pair, the
+ * device's travel time in samples (double, from its compensated FP32 pair),
+ * total attenuation gamma (s) and weight w = tau * phi (eq. 12).
+ * pix_host, k_host: n ints (host).  Outputs: n values each (host). */
+int mbir_pair_quantities(const mbir_geometry* g, const int32_t* pix_host, const int32_t* k_host,
+                         int n, double* T_samples_host, float* gamma_host, float* w_host);
+
+/* Copy the pulse table used by the kernels (G x (Q*T_w + 1) doubles,
+ * as built on the host) to host memory. */
+int mbir_pulse_table(const mbir_geometry* g, double* out_host, size_t n);
+
+const char* mbir_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBIR_H */

@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle against mathematics the paper fixes (no GPU).
+
+Each test checks the oracle against something other than itself: closed forms,
+brute force, an independent Fermat minimisation, the Faddeeva closed form of
+the attenuated pulse, invariants (adjointness, projection, majorization) and a
+dense linear solve.  A plausible slip anywhere in the oracle (a dropped term, a
+wrong sign or index, a transposed operand) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import wofz
+
+from oracle import oracle as O
+from paper_2202_09703_gb300 import synth as S
+
+
+def _scene_layers(speeds, thicknesses, atten=None, w=8, h=8, pitch=0.5e-3):
+    s = S.small_scene(n_layers=1, w=w, h=h)
+    atten = atten if atten is not None else [0.0] * len(speeds)
+    s.layers = [S.Layer(t, c, a, 1000.0 + 500 * i)
+                for i, (t, c, a) in enumerate(zip(thicknesses, speeds, atten))]
+    s.pitch = pitch
+    return s
+
+
+# --------------------------------------------------------------------------
+# travel time of one leg (Section 2, eq. 4-6)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("h,z", [(0.0, 1e-3), (2e-3, 1.7e-3), (1e-2, 3e-3), (3e-2, 0.4e-3)])
+def test_leg_one_layer_closed_form(h, z):
+    s = _scene_layers([1480.0], [50e-3], atten=[0.7])
+    T, gm, Th, t1 = O.Geometry(s).leg(h, z)
+    dist = math.hypot(h, z)
+    assert T == pytest.approx(dist / 1480.0, rel=1e-13)
+    assert gm == pytest.approx(0.7e-6 * dist, rel=1e-13)      # gamma = alpha * path
+    assert Th == pytest.approx(math.atan2(h, z), abs=1e-12)
+
+
+def test_leg_equal_speed_split_is_invariant():
+    a = _scene_layers([2000.0], [40e-3])
+    b = _scene_layers([2000.0, 2000.0, 2000.0], [3e-3, 4e-3, 33e-3])
+    for h, z in [(1e-3, 2e-3), (5e-3, 9e-3), (2e-2, 30e-3)]:
+        Ta = O.Geometry(a).leg(h, z)[0]
+        Tb = O.Geometry(b).leg(h, z)[0]
+        assert Tb == pytest.approx(Ta, rel=1e-12)
+
+
+def test_leg_zero_offset_is_vertical():
+    s = _scene_layers([1480.0, 5900.0, 3000.0], [2e-3, 1.5e-3, 20e-3])
+    z = 6e-3
+    T, gm, Th, t1 = O.Geometry(s).leg(0.0, z)
+    assert T == pytest.approx(2e-3 / 1480 + 1.5e-3 / 5900 + 2.5e-3 / 3000, rel=1e-14)
+    assert t1 == 0.0 and Th == 0.0
+
+
+def _fermat_time(speeds, eta, h):
+    """Minimum of sum sqrt((x_l - x_{l-1})^2 + eta_l^2) / c_l over crossings."""
+    L = len(eta)
+    if L == 1:
+        return math.hypot(h, eta[0]) / speeds[0]
+    c = np.asarray(speeds, float)
+    e = np.asarray(eta, float)
+    x = h * np.cumsum(e)[:-1] / e.sum()              # straight-line start
+
+    def total(xi):
+        pts = np.concatenate([[0.0], xi, [h]])
+        return float(np.sum(np.sqrt(np.diff(pts) ** 2 + e ** 2) / c))
+
+    for _ in range(200):
+        pts = np.concatenate([[0.0], x, [h]])
+        u = np.diff(pts)
+        d = np.sqrt(u * u + e * e)
+        g1 = u / (c * d)                              # d/du of each segment
+        g2 = e * e / (c * d ** 3)                     # d2/du2
+        grad = g1[:-1] - g1[1:]
+        Hm = np.diag(g2[:-1] + g2[1:]) - np.diag(g2[1:-1], 1) - np.diag(g2[1:-1], -1)
+        step = np.linalg.solve(Hm, grad)
+        t0 = total(x)
+        lam = 1.0
+        while total(x - lam * step) > t0 and lam > 1e-12:
+            lam *= 0.5
+        x = x - lam * step
+        if np.max(np.abs(lam * step)) < 1e-18:
+            break
+    return total(x)
+
+
+@pytest.mark.parametrize("speeds,thick", [
+    ([1480.0, 5900.0], [2e-3, 10e-3]),
+    ([1480.0, 5900.0, 3000.0], [2e-3, 1.5e-3, 20e-3]),
+    ([3000.0, 1500.0, 4500.0], [1e-3, 2e-3, 20e-3]),
+])
+@pytest.mark.parametrize("h,z", [(1e-3, 4.5e-3), (6e-3, 8e-3), (2.5e-2, 12e-3)])
+def test_leg_matches_fermat_minimum(speeds, thick, h, z):
+    s = _scene_layers(speeds, thick)
+    T = O.Geometry(s).leg(h, z)[0]
+    eta, top = [], 0.0
+    for t in thick:
+        if z <= top + t or len(eta) == len(thick) - 1:
+            eta.append(z - top)
+            break
+        eta.append(t)
+        top += t
+    used = speeds[:len(eta)]
+    assert T == pytest.approx(_fermat_time(used, eta, h), rel=1e-12)
+
+
+def test_leg_binary_search_bracket_brute_force():
+    speeds, thick = [1480.0, 5900.0, 3000.0], [2e-3, 1.5e-3, 20e-3]
+    s = _scene_layers(speeds, thick)
+    h, z = 7e-3, 9e-3
+    eta = np.array([2e-3, 1.5e-3, 9e-3 - 3.5e-3])
+    c = np.array(speeds)
+    crit = math.asin(c[0] / c.max())
+    th1 = np.linspace(0.0, crit, 1_000_001)[:-1]
+    sl = np.sin(th1)[:, None] * c[None, :] / c[0]     # Snell in closed form
+    height = np.sum(eta[None, :] * sl / np.sqrt(1.0 - sl * sl), axis=1)
+    i = np.searchsorted(height, h)                    # height is increasing
+    _, _, _, t1 = O.Geometry(s).leg(h, z)
+    assert th1[i - 1] <= t1 <= th1[i]
+    assert np.all(np.diff(height) > 0)
+
+
+def test_leg_calculus_and_monotonicity():
+    speeds, thick = [1480.0, 5900.0, 3000.0, 4500.0], [2e-3, 1.2e-3, 4e-3, 10e-3]
+    g = O.Geometry(_scene_layers(speeds, thick))
+    h, z = 6e-3, 6e-3                                  # voxel in the cement layer
+    T, _, _, t1 = g.leg(h, z)
+    p = math.sin(t1) / speeds[0]                      # ray parameter
+    dh = 1e-7
+    dT_dh = (g.leg(h + dh, z)[0] - g.leg(h - dh, z)[0]) / (2 * dh)
+    dT_dz = (g.leg(h, z + dh)[0] - g.leg(h, z - dh)[0]) / (2 * dh)
+    assert dT_dh == pytest.approx(p, rel=1e-6)
+    assert dT_dz == pytest.approx(math.sqrt(speeds[2] ** -2 - p * p), rel=1e-6)
+    hs = np.linspace(0, 3e-2, 40)
+    Ts = [g.leg(x, z)[0] for x in hs]
+    assert np.all(np.diff(Ts) > 0)
+    # depth: increasing inside each layer (dT/dz = sqrt(c^-2 - p^2) > 0); at a
+    # boundary into a faster layer the Snell path may run along the fast layer
+    # and the time drops, so monotonicity holds per layer only
+    tops = np.cumsum([0.0] + thick)
+    for lo, hi in zip(tops[:-1], tops[1:]):
+        zs = np.linspace(lo + 1e-6, hi - 1e-6, 25)
+        Tz = [g.leg(h, x)[0] for x in zs]
+        assert np.all(np.diff(Tz) > 0)
+    assert g.leg(h, 2e-3 + 1e-6)[0] < g.leg(h, 2e-3 - 1e-6)[0]
+
+
+def test_transmission_two_way_normal_incidence():
+    s = _scene_layers([1480.0, 5900.0, 3000.0], [2e-3, 1.5e-3, 20e-3])
+    g = O.Geometry(s)
+    Z = [L.density * L.speed for L in s.layers]
+    t12 = 4 * Z[0] * Z[1] / (Z[0] + Z[1]) ** 2
+    t23 = 4 * Z[1] * Z[2] / (Z[1] + Z[2]) ** 2
+    assert g.transmission(1e-3) == 1.0
+    assert g.transmission(3e-3) == pytest.approx(t12, rel=1e-15)
+    assert g.transmission(10e-3) == pytest.approx(t12 * t23, rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# pulse family (eq. 9-10)
+# --------------------------------------------------------------------------
+def _h_closed_form(scene, gamma, tau):
+    """h(gamma, tau) through the Faddeeva function (scipy.special.wofz)."""
+    sg = scene.n_cycles / (2 * math.sqrt(2 * math.log(2)) * scene.fc)
+    Tw = math.ceil(8 * sg * scene.fs)
+    tc = 0.5 * Tw / scene.fs
+    A = 2 * math.pi ** 2 * sg ** 2
+    beta = -gamma + 1j * 2 * math.pi * (tau - tc)
+    tot = 0.0
+    for a in (scene.fc, -scene.fc):
+        b = a + beta / (2 * A)
+        I = 0.5 * math.sqrt(math.pi / A) * math.exp(-A * a * a) * wofz(-1j * math.sqrt(A) * b)
+        tot += I
+    return (sg * math.sqrt(2 * math.pi) * tot).real
+
+
+def test_pulse_table_no_attenuation_is_the_pulse():
+    s = S.cfg0().copy(layers=[S.Layer(10e-3, 1480, 0.0, 1000), S.Layer(10e-3, 5900, 0.0, 7850)])
+    g = O.Geometry(s)
+    assert g.effective_G() == 1
+    tab = g.pulse_table()
+    Tw = g.pulse_support()
+    assert Tw == 68
+    taus = np.arange(s.Q * Tw + 1) / (s.fs * s.Q)
+    ref = np.array([g.pulse(t) for t in taus])
+    assert np.max(np.abs(tab[0] - ref)) < 1e-12
+
+
+def test_pulse_table_matches_faddeeva_closed_form():
+    s = S.cfg1()
+    g = O.Geometry(s)
+    tab = g.pulse_table()
+    G = g.effective_G()
+    gmax = g.gamma_max()
+    nq = tab.shape[1]
+    for gi in (0, 3, G - 1):
+        gam = gi * gmax / (G - 1)
+        for q in range(0, nq, 37):
+            ref = _h_closed_form(s, gam, q / (s.fs * s.Q))
+            assert abs(tab[gi, q] - ref) < 1e-11
+
+
+def test_pulse_table_quadrature_converged_and_energy_decreases():
+    s = S.cfg1()
+    g = O.Geometry(s)
+    t1 = g.pulse_table(1)
+    t2 = g.pulse_table(2)
+    assert np.max(np.abs(t1 - t2)) < 1e-12
+    energy = np.sum(t1 * t1, axis=1)
+    assert np.all(np.diff(energy) < 0)
+
+
+# --------------------------------------------------------------------------
+# operator (eq. 11, 13): dense matrix, adjointness, impulse response
+# --------------------------------------------------------------------------
+def _tiny(direct=False, layers=2, atten=True):
+    return S.small_scene(n_layers=layers, w=8, h=10, n_tx=2, n_rx=2, M=160,
+                         direct=direct, atten=atten)
+
+
+def test_dense_matrix_matches_operators_and_adjoint():
+    s = _tiny(layers=3)
+    p = O.Plan(s, nthreads=2)
+    A = p.dense_A()
+    x = S.random_vector(s.N, 1)
+    y = S.random_vector(s.K * s.M, 2)
+    Ax = p.forward(x).reshape(-1)
+    ATy = p.backproject(y)
+    assert np.linalg.norm(A @ x - Ax) <= 1e-13 * np.linalg.norm(Ax)
+    assert np.linalg.norm(A.T @ y - ATy) <= 1e-13 * np.linalg.norm(ATy)
+    lhs, rhs = float(Ax @ y), float(x @ ATy)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    assert np.count_nonzero(A) > 0.05 * A.size
+
+
+def test_impulse_response_single_layer_on_node():
+    c, fs = 1500.0, 10e6
+    s = S.small_scene(n_layers=1, w=4, h=4, n_tx=1, n_rx=1, M=128, atten=False)
+    s.layers = [S.Layer(20e-3, c, 0.0, 1000.0)]
+    s.rx_offset = np.array([0.0])
+    col = 1
+    s.tx_x = np.array([(col + 0.5) * s.pitch])
+    p = O.Plan(s, nthreads=1)
+    x = np.zeros((s.img_h, s.img_w))
+    x[1, col] = 1.0                                 # depth 0.75 mm: 2d/c = 1 us = 10 samples
+    y = p.forward(x)[0]
+    g = O.Geometry(s)
+    ref = np.array([g.pulse((n - 10) / fs) if 0 < n - 10 < 68 else 0.0 for n in range(s.M)])
+    assert np.max(np.abs(y - ref)) < 1e-12
+
+
+def test_pair_weight_is_transmission_times_apodization():
+    s = _tiny(layers=2)
+    p = O.Plan(s, nthreads=1)
+    g = O.Geometry(s)
+    v = 7 * s.img_w + 3
+    r, cc = divmod(v, s.img_w)
+    xc, zr = (cc + 0.5) * s.pitch, (r + 0.5) * s.pitch
+    k = 3
+    i, j = divmod(k, s.n_rx)
+    T, gm, w = p.pair(v, k)
+    lt = g.leg(xc - s.tx_x[i], zr)
+    lr = g.leg(xc - s.tx_x[i] - s.rx_offset[j], zr)
+    assert T == pytest.approx(lt[0] + lr[0], rel=1e-15)
+    assert gm == pytest.approx(lt[1] + lr[1], rel=1e-15)
+    ref_w = g.transmission(zr) * max(math.cos(lt[2]), 0) ** s.beta * max(math.cos(lr[2]), 0) ** s.beta
+    assert w == pytest.approx(ref_w, rel=1e-14)
+
+
+def test_projection_removes_direct_arrivals():
+    s = _tiny(direct=True)
+    p = O.Plan(s, nthreads=1)
+    d = p.direct_columns()
+    r = S.random_vector(s.K * s.M, 5).reshape(s.K, s.M)
+    e, gk = p.project(r)
+    for k in range(s.K):
+        dj = d[k % s.n_rx]
+        assert abs(dj @ e[k]) < 1e-12 * np.linalg.norm(dj) * np.linalg.norm(r[k])
+        assert np.allclose(r[k] - gk[k] * dj, e[k], atol=1e-15)
+
+
+def test_direct_only_data_reconstructs_zero_image_and_gains():
+    s = _tiny(direct=True)
+    p = O.Plan(s, nthreads=1)
+    d = p.direct_columns()
+    g_true = S.direct_gains(s, 3)
+    y = np.stack([g_true[k] * d[k % s.n_rx] for k in range(s.K)])
+    x, gk, cost, gn = p.reconstruct(y, sigma_noise=0.05, n_iter=5)
+    assert np.max(np.abs(x)) < 1e-12
+    assert np.allclose(gk, g_true, rtol=1e-12, atol=0)
+
+
+# --------------------------------------------------------------------------
+# prior (eq. 14-17)
+# --------------------------------------------------------------------------
+def test_potential_derivative_and_curvature():
+    s = S.cfg1()
+    for sigma in (0.3, 0.05):
+        for delta in (-0.7, -1e-3, 2e-4, 0.05, 1.3):
+            h = 1e-7 * max(abs(delta), 1e-3)
+            fd = (O.rho(s, delta + h, sigma) - O.rho(s, delta - h, sigma)) / (2 * h)
+            assert O.drho(s, delta, sigma) == pytest.approx(fd, rel=1e-6)
+            assert O.kappa(s, delta, sigma) == pytest.approx(O.drho(s, delta, sigma) / delta, rel=1e-14)
+        # the curvature is continuous at 0 and non-increasing in |delta|
+        k0 = O.kappa(s, 0.0, sigma)
+        assert O.kappa(s, 1e-14, sigma) == pytest.approx(k0, rel=1e-9)
+        ks = [O.kappa(s, d, sigma) for d in np.linspace(1e-6, 2.0, 50)]
+        assert np.all(np.diff(ks) <= 0)
+
+
+def test_prior_gradient_matches_finite_differences():
+    s = S.small_scene(w=6, h=5).copy(prior=S.Prior(m=0.2, a=1.5))
+    x = S.random_vector(s.N, 9, -0.5, 0.5)
+    gr = O.prior_grad(s, x)
+    h = 1e-6
+    for v in range(s.N):
+        xp, xm = x.copy(), x.copy()
+        xp[v] += h
+        xm[v] -= h
+        fd = (O.prior_cost(s, xp) - O.prior_cost(s, xm)) / (2 * h)
+        assert gr[v] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_prior_weights_follow_depth_rule():
+    # with p = q = 2 the potential is delta^2 / (4 sigma^2): a two-pixel image
+    # isolates sigma_g = sigma0 sqrt(m_s m_r) with m_s = 1 + (m-1)(z/zmax)^a
+    s = S.small_scene(w=1, h=2).copy(prior=S.Prior(p=2.0, q=2.0, sigma0=0.4, m=0.25, a=2.0))
+    x = np.array([0.3, -0.1])
+    z = (np.arange(2) + 0.5) * s.pitch
+    m = 1 + (0.25 - 1) * (z / z[-1]) ** 2.0
+    sg = 0.4 * math.sqrt(m[0] * m[1])
+    b_edge = 1.0 / (4 + 4 / math.sqrt(2))
+    assert O.prior_cost(s, x) == pytest.approx(b_edge * 0.4 ** 2 / (4 * sg * sg), rel=1e-14)
+
+
+def test_symmetric_bound_majorizes_prior():
+    s = S.small_scene(w=7, h=6).copy(prior=S.Prior(m=0.3))
+    x = S.random_vector(s.N, 11, -0.3, 0.3)
+    d = S.random_vector(s.N, 12, -0.2, 0.2)
+    r0 = O.prior_cost(s, x)
+    g = O.prior_grad(s, x)
+    cv = O.prior_curv(s, x, d)
+    for t in (-3.0, -0.5, 0.01, 0.3, 1.0, 4.0):
+        bound = r0 + t * float(g @ d) + 0.5 * t * t * cv
+        assert O.prior_cost(s, x + t * d) <= bound + 1e-12
+
+
+# --------------------------------------------------------------------------
+# MAP iteration (eq. 18)
+# --------------------------------------------------------------------------
+def _noisy_data(s, seed=0, snr_db=20.0):
+    p = O.Plan(s, nthreads=2)
+    x_true = S.phantom(s, seed)
+    y0 = p.forward(x_true)
+    if s.direct_arrival:
+        d = p.direct_columns()
+        g = S.direct_gains(s, seed) * np.max(np.abs(y0))
+        y0 = y0 + np.stack([g[k] * d[k % s.n_rx] for k in range(s.K)])
+    sig = math.sqrt(np.sum(y0 ** 2) / (10 ** (snr_db / 10) * s.K * s.M))
+    return p, x_true, y0 + sig * S.unit_noise(s, seed), sig
+
+
+def test_map_cost_is_non_increasing():
+    s = _tiny(direct=True, layers=3).copy(prior=S.Prior(m=0.2))
+    p, _, y, sig = _noisy_data(s)
+    x, gk, cost, gn = p.reconstruct(y, sig, 30)
+    assert np.all(np.diff(cost) <= 1e-12 * abs(cost[0]))
+    assert cost[-1] < cost[0]
+
+
+def test_quadratic_prior_map_matches_dense_solve():
+    s = S.small_scene(n_layers=2, w=6, h=6, n_tx=2, n_rx=2, M=96, direct=True)
+    s = s.copy(prior=S.Prior(p=2.0, q=2.0, sigma0=0.5, m=0.5))
+    p, _, y, sig = _noisy_data(s, seed=4)
+    A = p.dense_A()
+    d = p.direct_columns()
+    K, M, N = s.K, s.M, s.N
+    P = np.eye(K * M)
+    for k in range(K):
+        dj = d[k % s.n_rx]
+        sl = slice(k * M, (k + 1) * M)
+        P[sl, sl] -= np.outer(dj, dj) / (dj @ dj)
+    # Hessian of sum b (x_s - x_r)^2 / (4 sigma_sr^2) assembled by brute force
+    Hr = np.zeros((N, N))
+    for v in range(N):
+        e = np.zeros(N)
+        e[v] = 1.0
+        Hr[:, v] = O.prior_grad(s, e)
+    lhs = A.T @ P @ A / sig ** 2 + Hr
+    rhs = A.T @ P @ y.reshape(-1) / sig ** 2
+    x_ref = np.linalg.solve(lhs, rhs)
+    x, gk, cost, gn = p.reconstruct(y, sig, 3000)
+    assert np.linalg.norm(x.reshape(-1) - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+
+
+def test_gradient_vanishes_at_convergence():
+    s = S.small_scene(n_layers=2, w=6, h=6, n_tx=2, n_rx=2, M=96, direct=False)
+    s = s.copy(prior=S.Prior(sigma0=0.5, m=0.5, T=0.5))
+    p, _, y, sig = _noisy_data(s, seed=2)
+    x, gk, cost, gn = p.reconstruct(y, sig, 4000)
+    assert gn[-1] / gn[0] < 1e-9
