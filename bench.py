@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: MAP reconstructions per second of the layered collimated-beam
+model on one GB300 (and N independent replicas under torchrun).
+
+Workload (one step = one full reconstruction): the 4-layer scan of 256 x 512
+pixels at 0.5 mm (water 20 mm / steel 12 mm / cement 40 mm / rock), 64 Tx x
+16 receivers, 2048 samples at 20 MHz, 2 MHz 2-cycle pulse, direct arrivals on,
+depth-varying QGGMRF prior, 50 iterations in FP32.  Synthetic data
+y = A x + D g + w (SNR 20 dB) is made on the device by the library itself.
+
+Reported: recons/s (device time of the timed steps, L2 flushed between steps),
+p50/p99 latency, an end-to-end figure through the host-buffer C ABI call, the
+roofline of the dominant kernel, GPU clocks sampled during the timed region,
+and (rank 0, one GPU) the FP64 oracle timed on a bounded sample on the host
+cores.  ``--impl reference`` times only the oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
+WORKLOAD = ("4-layer water/steel/cement/rock, 256x512 image @0.5 mm, 64 Tx x 16 Rx, 2048 samples "
+            "@20 MHz, 2 MHz pulse, direct arrivals, depth-varying QGGMRF prior, 50 MAP iterations")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "otf", "tab"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--apply-only", type=int, default=0,
+                    help="run only A x and A^T r this many times (for profiler captures) and exit")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# FP64 oracle on the host (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(scene, budget_s: float, x_img, gpu_rows=None):
+    """Times the oracle on a bounded sample and extrapolates one reconstruction.
+
+    Sample: the forward operator on a few A-scans (legs cached separately) and
+    the adjoint on a block of pixels.  Returns (seconds per reconstruction,
+    description, threads, rel. L2 of the GPU's sampled A-scans vs the oracle)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2202_09703_gb300 import synth as S
+
+    nthreads = os.cpu_count() or 1
+    plan = O.Plan(scene, nthreads=nthreads)
+    K, N = scene.K, scene.N
+    ks = [0, K // 2, K - 1]
+    t0 = time.perf_counter()
+    yk = [plan.forward(x_img, k, k + 1)[0] for k in ks]       # legs for these positions + taps
+    t_first = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for k in ks:
+        plan.forward(x_img, k, k + 1)
+    t_fwd = (time.perf_counter() - t0) / len(ks)              # one A-scan, legs cached
+    legs_first = max(t_first - t_fwd * len(ks), 0.0)
+    n_pos_first = len({i for k in ks for i in (k // scene.n_rx,)}) + len(ks)
+    t_leg_per_pos = legs_first / max(n_pos_first, 1)          # all pixels, one position
+    # adjoint on a block of pixels inside the record, sized to the budget
+    rng = S.SplitMix64(7)
+    npix = 256
+    while True:
+        pix = np.unique(rng.integers(0, min(N, 300 * scene.img_w) - 1, npix))
+        bp = O.Plan(scene, pix=pix, nthreads=nthreads)
+        r = S.random_vector(K * scene.M, 3)
+        t0 = time.perf_counter()
+        bp.backproject(r)                                      # legs for these pixels + taps
+        t_b1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        bp.backproject(r)
+        t_b2 = time.perf_counter() - t0
+        bp.close()
+        if t_b1 + t_b2 > 0.3 * budget_s or npix >= N:
+            break
+        npix = min(N, npix * 4)
+    active = min(N, 344 * scene.img_w)                        # rows whose vertical time is inside the record
+    t_bwd = t_b2 * active / len(pix)
+    legs_all = (t_b1 - t_b2) * active / len(pix)               # every position, every active pixel
+    t_fwd_full = t_fwd * K
+    n_iter = scene.n_iter
+    recon = legs_all + (n_iter + 1) * t_fwd_full + n_iter * t_bwd
+    desc = (f"oracle A on {len(ks)} A-scans and A^T on {len(pix)} pixels of the workload, "
+            f"extrapolated to one {n_iter}-iteration reconstruction (legs once, {n_iter + 1} A, {n_iter} A^T); "
+            f"{nthreads} OpenMP threads")
+    err = None
+    if gpu_rows is not None:
+        num = sum(float(np.sum((gpu_rows[i] - yk[i]) ** 2)) for i in range(len(ks)))
+        den = sum(float(np.sum(yk[i] ** 2)) for i in range(len(ks)))
+        err = math.sqrt(num / den)
+    plan.close()
+    return recon, desc, nthreads, err, ks
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2202_09703_gb300 import synth as S
+    scene = S.cfg1()
+    x_img = S.phantom(scene, 0)
+    times = []
+    desc, nth = "", 1
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        recon, desc, nth, _, _ = oracle_sample(scene, args.cpu_seconds / 3, x_img)
+        if step >= args.warmup:
+            times.append(recon)
+    val = len(times) / sum(times)
+    out = {"impl": "reference", "metric": "recons/s", "value": val, "unit": "recons/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": val, "unit": "recons/s", "cores": nth, "kind": "oracle", "sample": desc},
+           "e2e": {"value": val, "unit": "recons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2202_09703_gb300 import build as B
+    B.build()
+    from paper_2202_09703_gb300 import mbir as M
+    from paper_2202_09703_gb300 import synth as S
+
+    scene = S.cfg1()
+    stream = torch.cuda.current_stream()
+    geo = M.Geometry(scene, mode=args.mode)
+    K, Mn, N = scene.K, scene.M, scene.N
+
+    # synthetic scan: y = A x_true + D g + w at 20 dB SNR, made by the library
+    x_true = torch.as_tensor(S.phantom(scene, rank).reshape(-1), dtype=torch.float32, device=dev)
+    y = torch.empty(K * Mn, dtype=torch.float32, device=dev)
+    geo.forward(x_true, y)
+    g_true = torch.as_tensor(S.direct_gains(scene, rank), dtype=torch.float32, device=dev) * y.abs().max()
+    geo.add_direct(g_true, y)
+    noise = torch.as_tensor(S.unit_noise(scene, rank).reshape(-1), dtype=torch.float32, device=dev)
+    sigma = math.sqrt(float((y.double() ** 2).sum()) / (100.0 * K * Mn))
+    y += sigma * noise
+    x = torch.empty(N, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    def step():
+        geo.reconstruct(y, sigma, scene.n_iter, x)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    geo.set_profiling(True)
+    geo.kernel_times(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    kt = geo.kernel_times(reset=True)
+    geo.set_profiling(False)
+    lat = [a.elapsed_time(b) for a, b in ev]                 # ms per reconstruction
+    t_dev = sum(lat) / 1e3
+    if dist:
+        tt = torch.tensor([t_dev, wall], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, wall = float(tt[0]), float(tt[1])
+    value = args.steps * world / t_dev
+
+    # end to end through the host-buffer call: H2D of y, D2H of x and g
+    y_h = y.cpu().pin_memory()
+    x_h = torch.empty(N, dtype=torch.float32).pin_memory()
+    g_h = torch.empty(K, dtype=torch.float32).pin_memory()
+    geo.reconstruct_host(y_h, sigma, scene.n_iter, x_h, g_h)
+    if dist:
+        dist.barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        geo.reconstruct_host(y_h, sigma, scene.n_iter, x_h, g_h)
+    e_wall = time.perf_counter() - e0
+    if dist:
+        tt = torch.tensor([e_wall], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_wall = float(tt[0])
+    e2e = {"value": args.steps * world / e_wall, "unit": "recons/s",
+           "h2d_bytes_per_step": y_h.numel() * 4, "d2h_bytes_per_step": (x_h.numel() + g_h.numel()) * 4}
+
+    # roofline of the dominant apply kernel
+    pk, src = peaks()
+    pairs, taps = geo.count_taps()
+    fwd_ms = kt["forward_ms"] / max(kt["forward_launches"], 1)
+    bwd_ms = kt["backproject_ms"] / max(kt["backproject_launches"], 1)
+    dom, dom_ms = ("forward", fwd_ms) if fwd_ms >= bwd_ms else ("backproject", bwd_ms)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+    flops = 8.0 * taps                                   # 4 FMA per tap (bilinear table read)
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    algo_bytes = 4.0 * (N + K * Mn)                      # x and one A-scan array
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_mhz:.0f} MHz "
+                               f"(sm_max_mhz, {src})",
+                "algorithmic_flops_per_launch": flops, "taps_per_launch": taps, "active_pairs": pairs,
+                "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
+                "hbm": {"algorithmic_bytes_per_launch": algo_bytes,
+                        "achieved_gbs": algo_bytes / (dom_ms * 1e-3) / 1e9,
+                        "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),
+                        "frac": algo_bytes / (dom_ms * 1e-3) / 1e9 / float(pk.get("hbm_gbs", 6800.0))}}
+    launches = args.steps * (2 + 8 * scene.n_iter)
+
+    out = {"metric": "recons/s", "value": value, "unit": "recons/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "mode": geo.mode, "iterations": scene.n_iter,
+                      "l2": "flushed between steps (256 MB write); device time from CUDA events per step",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)),
+                          "wall_s": wall},
+           "e2e": e2e, "roofline": roofline, "clocks": clk, "gpu_launches": launches}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        xr = S.phantom(scene, 0)
+        yg = torch.empty(K * Mn, dtype=torch.float32, device=dev)
+        geo.forward(torch.as_tensor(xr.reshape(-1), dtype=torch.float32, device=dev), yg)
+        ygn = yg.cpu().numpy().reshape(K, Mn)
+        ks = [0, K // 2, K - 1]
+        recon, desc, nth, err, _ = oracle_sample(scene, args.cpu_seconds, xr, gpu_rows=[ygn[k] for k in ks])
+        out["cpu_baseline"] = {"value": 1.0 / recon, "unit": "recons/s", "cores": nth, "kind": "oracle",
+                               "sample": desc}
+        out["oracle_rel_l2_sampled_A"] = err
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_apply_only(args):
+    import torch
+    from paper_2202_09703_gb300 import build as B
+    B.build()
+    from paper_2202_09703_gb300 import mbir as M
+    from paper_2202_09703_gb300 import synth as S
+    scene = S.cfg1()
+    dev = torch.device("cuda:0")
+    geo = M.Geometry(scene, mode=args.mode)
+    x = torch.as_tensor(S.phantom(scene, 0).reshape(-1), dtype=torch.float32, device=dev)
+    y = torch.empty(scene.K * scene.M, dtype=torch.float32, device=dev)
+    b = torch.empty(scene.N, dtype=torch.float32, device=dev)
+    for _ in range(args.apply_only):
+        geo.forward(x, y)
+        geo.backproject(y, b)
+    torch.cuda.synchronize()
+    print(json.dumps({"apply_only": args.apply_only, "mode": geo.mode, "y_norm": float(y.norm()),
+                      "b_norm": float(b.norm())}))
+
+
+def main():
+    args = parse()
+    if args.apply_only:
+        run_apply_only(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,10 @@ int mbir_backproject(const mbir_geometry* g, const void* r_dev, float* x_dev, vo
 int mbir_project(const mbir_geometry* g, const float* r_dev, float* e_dev, float* gk_dev,
                  void* stream);
 
+/* y += D g (eq. 1): adds g_k times the direct-arrival column of A-scan k to
+ * every A-scan.  gk_dev: K floats; y_dev: K x M floats, updated in place. */
+int mbir_add_direct(const mbir_geometry* g, const float* gk_dev, float* y_dev, void* stream);
+
 /* Gradient of the prior of eq. 14-17 at x: out_s = sum_r b_sr rho'(x_s - x_r).
  * x_dev, out_dev: N floats. */
 int mbir_prior_gradient(const mbir_geometry* g, const mbir_prior* pr, const float* x_dev,
@@ -198,6 +202,24 @@ int mbir_pair_quantities(const mbir_geometry* g, const int32_t* pix_host, const 
 /* Copy the pulse table used by the kernels (G x (Q*T_w + 1) doubles,
  * as built on the host) to host memory. */
 int mbir_pulse_table(const mbir_geometry* g, double* out_host, size_t n);
+
+/* Per-kernel device time of the A x and A^T r launches made inside
+ * mbir_reconstruct while profiling is on (CUDA events on the call's stream,
+ * read when the call synchronises).  Enabling adds two event records per
+ * launch; it does not change results. */
+typedef struct {
+    int64_t forward_launches, backproject_launches;
+    double forward_ms, backproject_ms;
+} mbir_kernel_times;
+
+int mbir_set_profiling(mbir_geometry* g, int enable);
+int mbir_get_kernel_times(mbir_geometry* g, mbir_kernel_times* t, int reset);
+
+/* Algorithmic work of one apply of A (or A^T): the number of (pixel, A-scan)
+ * pairs with a non-zero weight and a tap inside the record, and the number of
+ * taps (samples n with 0 < n - T < t0, n < M) over those pairs.  Computed on
+ * the device from the geometry alone; synchronises the legacy stream. */
+int mbir_count_taps(const mbir_geometry* g, int64_t* active_pairs, int64_t* taps);
 
 const char* mbir_error_string(int code);
 

@@ -1,0 +1,209 @@
+// A x (eq. 11-13 summed over voxels) as a gather: one CTA per A-scan.  The CTA
+// walks the image in blocks of columns.  For each block it writes one record
+// per (column, row) pair - first tap sample, table row, bilinear weights times
+// x - into shared memory.  Inside one layer the travel time grows with depth,
+// so each (column, layer) segment of records is sorted by first sample; for
+// every 32-sample span of the A-scan the rows whose 68-tap window reaches the
+// span form one contiguous run.  The run bounds of every (segment, span) are
+// written by a conflict-free scatter (each bound is owned by exactly one row),
+// then each warp produces its spans with counted loops over those runs.
+// Every output sample is owned by one lane: no atomics, a fixed summation
+// order, bitwise reproducible results.
+#include <algorithm>
+
+#include "device_common.cuh"
+
+namespace mbir {
+
+constexpr int kKeyShift = 13;                  // record key: n0 << 13 | table row << 1 | flag0
+constexpr int kKeyBeyond = (1 << 18) - 1;      // n0 of rows that cannot reach the record
+
+__device__ __forceinline__ int key_n0(int key) { return key >> kKeyShift; }
+
+template <int NL, int MODE, bool BF16, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+    forward_kernel(GeomParams P, DevPtrs D, const typename TabT<BF16>::type* __restrict__ tab_g,
+                   const float* __restrict__ x, float* __restrict__ y_f32, __nv_bfloat16* __restrict__ y_bf16,
+                   int out_stride, int CB)
+{
+    using Tab = typename TabT<BF16>::type;
+    constexpr int WARPS = THREADS / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int S = table_stride(P.Tw4);
+    const int R = P.Q + 1;
+    const int nspan = (P.M + 31) >> 5;
+    const int nseg = P.n_seg;
+    const size_t tab_bytes = ((size_t)P.Gt * R * S * sizeof(Tab) + 127) & ~(size_t)127;
+    const size_t ybytes = ((size_t)P.Mp * 4 + 127) & ~(size_t)127;
+    const int nrec = CB * P.H;
+    Tab* tab = reinterpret_cast<Tab*>(smem);
+    float* yacc = reinterpret_cast<float*>(smem + tab_bytes);
+    float4* wrec = reinterpret_cast<float4*>(smem + tab_bytes + ybytes);
+    int* keys = reinterpret_cast<int*>(wrec + nrec);
+    // run bounds: [first, end) rows of (column, segment) for each span
+    short* fb = reinterpret_cast<short*>(keys + nrec);
+    short* eb = fb + (size_t)CB * nseg * nspan;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int k = blockIdx.x;
+    const int i = k / P.n_rx;
+    const int txp = __ldg(D.txpos + i), rxp = __ldg(D.rxpos + k);
+
+    {
+        const int4* src = reinterpret_cast<const int4*>(tab_g);
+        int4* dst = reinterpret_cast<int4*>(tab);
+        const int n16 = (int)(tab_bytes / 16);
+        for (int t = tid; t < n16; t += THREADS) dst[t] = __ldg(src + t);
+    }
+    for (int t = tid; t < P.Mp; t += THREADS) yacc[t] = 0.0f;
+
+    for (int c0 = 0; c0 < P.W; c0 += CB) {
+        __syncthreads();
+        // ---- records of this column block
+        for (int idx = tid; idx < nrec; idx += THREADS) {
+            const int cl = idx / P.H, row = idx - cl * P.H;
+            const int col = c0 + cl;
+            int key = kKeyBeyond << kKeyShift;
+            float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col < P.W) {
+                RowInfo ri = load_row(D.rows, row);
+                if (ri.tvert < (float)(P.M - 1)) {
+                    Leg tx = get_leg<NL, MODE>(P, D, ri, row, col, txp);
+                    Leg rx = get_leg<NL, MODE>(P, D, ri, row, col, rxp);
+                    Pair pr = make_pair(P, tx, rx, ri.tau);
+                    const int n0 = min(max(pr.n0, -1), kKeyBeyond);
+                    key = (n0 << kKeyShift) | ((pr.gi * R + pr.r) << 1) | (pr.flag0 ? 1 : 0);
+                    const float wx = pr.w * __ldg(x + (size_t)row * P.W + col);
+                    const float p1 = pr.psi, p0 = 1.0f - pr.psi;
+                    wv = make_float4(wx * pr.w0 * p0, wx * pr.w0 * p1, wx * pr.w1 * p0, wx * pr.w1 * p1);
+                }
+            }
+            keys[idx] = key;
+            wrec[idx] = wv;
+        }
+        __syncthreads();
+        // ---- run bounds by scatter: span s needs rows with s*32-Tw <= n0 <= s*32+30.
+        // Within a segment n0 is non-decreasing, so row r is the first row of
+        // span s for exactly the spans whose threshold falls in (n0[r-1], n0[r]];
+        // the segment's last row also closes every later span at rb.
+        for (int idx = tid; idx < nrec; idx += THREADS) {
+            const int cl = idx / P.H, row = idx - cl * P.H;
+            int sg = 0;
+            while (sg + 1 < nseg && row >= P.seg_row[sg + 1]) ++sg;
+            const int ra = P.seg_row[sg], rb = P.seg_row[sg + 1];
+            const int n0 = key_n0(keys[idx]);
+            const int prev = (row > ra) ? key_n0(keys[idx - 1]) : -(1 << 20);
+            short* F = fb + ((size_t)cl * nseg + sg) * nspan;
+            short* E = eb + ((size_t)cl * nseg + sg) * nspan;
+            // first row with n0 >= 32 s - Tw  <=>  32 s in (prev + Tw, n0 + Tw]
+            const int s_lo = (prev + P.Tw < 0) ? 0 : (prev + P.Tw) / 32 + 1;
+            const int s_hi = min((n0 + P.Tw) >> 5, nspan - 1);
+            for (int s = s_lo; s <= s_hi; ++s) F[s] = (short)row;
+            // first row with n0 >= 32 s + 31  <=>  32 s in (prev - 31, n0 - 31]
+            const int e_lo = (prev - 31 < 0) ? 0 : (prev - 31) / 32 + 1;
+            const int e_hi = (n0 - 31 < 0) ? -1 : min((n0 - 31) >> 5, nspan - 1);
+            for (int s = e_lo; s <= e_hi; ++s) E[s] = (short)row;
+            if (row == rb - 1) {
+                const int s_f = (n0 + P.Tw < 0) ? 0 : ((n0 + P.Tw) >> 5) + 1;
+                for (int s = s_f; s < nspan; ++s) F[s] = (short)rb;
+                const int s_e = (n0 - 31 < 0) ? 0 : ((n0 - 31) >> 5) + 1;
+                for (int s = s_e; s < nspan; ++s) E[s] = (short)rb;
+            }
+        }
+        __syncthreads();
+        // ---- gather: warp-owned spans of 32 samples, counted loops over runs
+        for (int sp = warp; sp < nspan; sp += WARPS) {
+            const int n = sp * 32 + lane;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int cl = 0; cl < CB; ++cl) {
+                const int* kc = keys + cl * P.H;
+                const float4* wc = wrec + cl * P.H;
+                for (int sg = 0; sg < nseg; ++sg) {
+                    const size_t o = ((size_t)cl * nseg + sg) * nspan + sp;
+                    const int r0 = fb[o], r1 = eb[o];
+#pragma unroll 4
+                    for (int rr = r0; rr < r1; ++rr) {
+                        const int key = kc[rr];
+                        const int m = n - key_n0(key) - 1;
+                        const bool edge = (key & 1) && m == P.Tw - 1;   // tau = t0 exactly: outside
+                        if ((unsigned)m < (unsigned)P.Tw && !edge) {
+                            const float4 wv = wc[rr];
+                            const Tab* A = tab + (size_t)((key >> 1) & 0xfff) * S + m;
+                            acc = __ffma2_rn(TabT<BF16>::ld(A), make_float2(wv.x, wv.y), acc);
+                            acc = __ffma2_rn(TabT<BF16>::ld(A + S), make_float2(wv.z, wv.w), acc);
+                        }
+                    }
+                }
+            }
+            if (n < P.M) yacc[n] += acc.x + acc.y;
+        }
+    }
+    __syncthreads();
+    if (y_f32) {
+        float* yo = y_f32 + (size_t)k * out_stride;
+        for (int t = tid; t < out_stride; t += THREADS) yo[t] = (t < P.M) ? yacc[t] : 0.0f;
+    } else {
+        __nv_bfloat16* yo = y_bf16 + (size_t)k * out_stride;
+        for (int t = tid; t < out_stride; t += THREADS) yo[t] = __float2bfloat16_rn((t < P.M) ? yacc[t] : 0.0f);
+    }
+}
+
+// shared memory: table + accumulator + CB columns of records (20 B per row)
+// + run bounds (2 x 2 B per (column, segment, span))
+size_t forward_smem(const mbir_geometry* g, int* cb_out)
+{
+    const GeomParams& P = g->P;
+    size_t tsz = P.precision == MBIR_PREC_BF16 ? 4 : 8;
+    size_t tab = ((size_t)P.Gt * (P.Q + 1) * table_stride(P.Tw4) * tsz + 127) & ~(size_t)127;
+    size_t yb = ((size_t)P.Mp * 4 + 127) & ~(size_t)127;
+    const size_t nspan = (P.M + 31) / 32;
+    const size_t per_col = (size_t)P.H * 20 + (size_t)P.n_seg * nspan * 4;
+    const size_t budget = 222 * 1024;
+    long avail = (long)budget - (long)(tab + yb);
+    int cb = avail > 0 ? (int)(avail / per_col) : 0;
+    cb = std::min(cb, 16);
+    if (cb_out) *cb_out = cb;
+    return tab + yb + (size_t)std::max(cb, 1) * per_col + 16;
+}
+
+template <int NL, int MODE, bool BF16, int THREADS>
+static cudaError_t launch_fwd_t(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
+                                cudaStream_t st)
+{
+    int cb = 0;
+    size_t sm = forward_smem(g, &cb);
+    if (cb < 1) return cudaErrorInvalidConfiguration;
+    auto kern = forward_kernel<NL, MODE, BF16, THREADS>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce != cudaSuccess) return ce;
+    using Tab = typename TabT<BF16>::type;
+    const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
+    kern<<<g->P.K, THREADS, sm, st>>>(g->P, dev_ptrs(g), tab, x, yf, yb, stride, cb);
+    return cudaGetLastError();
+}
+
+template <int MODE, bool BF16>
+static cudaError_t launch_fwd_nl(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
+                                 cudaStream_t st)
+{
+    if constexpr (MODE == kModeTAB) {
+        return launch_fwd_t<1, MODE, BF16, 1024>(g, x, yf, yb, stride, st);
+    } else {
+        if (g->P.L <= 2) return launch_fwd_t<2, MODE, BF16, 512>(g, x, yf, yb, stride, st);
+        if (g->P.L <= 4) return launch_fwd_t<4, MODE, BF16, 512>(g, x, yf, yb, stride, st);
+        return launch_fwd_t<8, MODE, BF16, 512>(g, x, yf, yb, stride, st);
+    }
+}
+
+cudaError_t launch_forward(const mbir_geometry* g, const float* x, float* y_f32, __nv_bfloat16* y_bf16,
+                           int out_stride, cudaStream_t st)
+{
+    const bool bf = g->P.precision == MBIR_PREC_BF16;
+    if (g->P.mode == MBIR_MODE_TAB)
+        return bf ? launch_fwd_nl<kModeTAB, true>(g, x, y_f32, y_bf16, out_stride, st)
+                  : launch_fwd_nl<kModeTAB, false>(g, x, y_f32, y_bf16, out_stride, st);
+    return bf ? launch_fwd_nl<kModeOTF, true>(g, x, y_f32, y_bf16, out_stride, st)
+              : launch_fwd_nl<kModeOTF, false>(g, x, y_f32, y_bf16, out_stride, st);
+}
+
+}  // namespace mbir

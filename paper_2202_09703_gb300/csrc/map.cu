@@ -1,0 +1,720 @@
+// The MAP iteration of eq. 18 and the remaining C ABI entry points.
+//
+// Per iteration, all on the device with no host round trip:
+//   b = A^T e                                  (backproject kernel)
+//   grad = -b / sigma^2 + grad R(x)             (prior stencil, FP64 partials)
+//   beta (Polak-Ribiere+), d = -grad + beta d   (direction + prior curvature)
+//   q = P A d                                   (forward kernel + projection)
+//   alpha = -<grad,d> / (|q|^2/sigma^2 + sum b kappa (d_s-d_r)^2)
+//   x += alpha d, e -= alpha q
+// FP64 appears only in the reductions (costs, norms and the step scalars);
+// partial sums are combined in a fixed order, so runs are reproducible.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace mbir {
+
+constexpr int kRedThreads = 256;
+
+struct PriorParams {
+    float p, q, T, sigma0;
+    float inv_s2;        // 1 / sigma_noise^2
+    float kappa0_base;   // 2 / (p T^(2-p)) : kappa(0) * sigma^2
+};
+
+// scalar slots (doubles)
+enum {
+    S_GG = 0, S_GGP, S_GDP, S_GGPREV, S_BETA, S_GD, S_QQ, S_CURV, S_ALPHA, S_EE, S_PRIOR, S_BAD,
+    S_COUNT = 16
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+    return r;   // valid in thread 0
+}
+
+// QGGMRF potential (eq. 15) and its derivatives, in FP32 through log2/exp2.
+// rho'(d) = sign(d) |d|^(p-1) / s^p * u/(1+u) * (1 + (q-p)/(p(1+u))),
+// u = |d/(T s)|^(q-p); kappa = rho'(d)/d (limit 2/(p s^2 T^(2-p)) at d = 0).
+__device__ __forceinline__ void qggmrf(const PriorParams& pr, float d, float s, float* drho, float* kappa,
+                                       float* rho)
+{
+    float ad = fabsf(d);
+    float ls = log2f(s);
+    float r = ad / (pr.T * s);
+    if (!(r > 1e-12f)) {
+        if (drho) *drho = 0.0f;
+        if (kappa) *kappa = pr.kappa0_base / (s * s);
+        if (rho) *rho = 0.0f;
+        return;
+    }
+    float la = log2f(ad);
+    float u = exp2f((pr.q - pr.p) * log2f(r));
+    float f = u / (1.0f + u);
+    float corr = 1.0f + (pr.q - pr.p) / (pr.p * (1.0f + u));
+    float base = exp2f((pr.p - 2.0f) * la - pr.p * ls);   // |d|^(p-2) / s^p
+    float kap = base * f * corr;
+    if (kappa) *kappa = kap;
+    if (drho) *drho = kap * d;
+    if (rho) *rho = base * ad * ad * f / pr.p;
+}
+
+__constant__ int c_nb_dr[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+__constant__ int c_nb_dc[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+
+__device__ __forceinline__ float nb_weight(int dr, int dc)
+{
+    const float be = 1.0f / (4.0f + 4.0f / 1.41421356237309515f);
+    return (dr == 0 || dc == 0) ? be : be * 0.70710678118654752f;
+}
+
+// grad = -b/sigma^2 + grad R(x); partials of <g,g>, <g,gprev>, <g,dprev>
+__global__ void grad_kernel(GeomParams P, PriorParams pr, const float* __restrict__ x, const float* __restrict__ b,
+                            const float* __restrict__ msq, const float* __restrict__ gprev,
+                            const float* __restrict__ dprev, float* __restrict__ grad, double* __restrict__ part,
+                            int with_data)
+{
+    __shared__ double sh[32];
+    const int N = P.W * P.H;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double a0 = 0, a1 = 0, a2 = 0;
+    if (v < N) {
+        const int r = v / P.W, c = v - r * P.W;
+        const float xs = x[v];
+        const float ms = msq[r];
+        float gr = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int r2 = r + c_nb_dr[t], c2 = c + c_nb_dc[t];
+            if (r2 < 0 || r2 >= P.H || c2 < 0 || c2 >= P.W) continue;
+            float dr;
+            qggmrf(pr, xs - x[r2 * P.W + c2], pr.sigma0 * ms * msq[r2], &dr, nullptr, nullptr);
+            gr += nb_weight(c_nb_dr[t], c_nb_dc[t]) * dr;
+        }
+        const float g = with_data ? -b[v] * pr.inv_s2 + gr : gr;
+        grad[v] = g;
+        a0 = (double)g * g;
+        a1 = (double)g * gprev[v];
+        a2 = (double)g * dprev[v];
+    }
+    double s0 = block_sum(a0, sh);
+    double s1 = block_sum(a1, sh);
+    double s2 = block_sum(a2, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = s0;
+        part[3 * blockIdx.x + 1] = s1;
+        part[3 * blockIdx.x + 2] = s2;
+    }
+}
+
+// Polak-Ribiere+ coefficient with a descent restart
+__global__ void finalize_dir_kernel(const double* __restrict__ part, int nb, int it, double* __restrict__ sc,
+                                    double* __restrict__ gnorm_hist)
+{
+    __shared__ double sh[32];
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        a0 += part[3 * t];
+        a1 += part[3 * t + 1];
+        a2 += part[3 * t + 2];
+    }
+    double gg = block_sum(a0, sh), ggp = block_sum(a1, sh), gdp = block_sum(a2, sh);
+    if (threadIdx.x == 0) {
+        double beta = 0.0;
+        if (it > 0 && sc[S_GGPREV] > 0.0) beta = fmax((gg - ggp) / sc[S_GGPREV], 0.0);
+        double gd = -gg + beta * gdp;
+        if (!(gd < 0.0)) { beta = 0.0; gd = -gg; }
+        sc[S_GG] = gg;
+        sc[S_BETA] = beta;
+        sc[S_GD] = gd;
+        sc[S_GGPREV] = gg;
+        if (!isfinite(gg)) sc[S_BAD] = 1.0;
+        if (gnorm_hist) gnorm_hist[it] = sqrt(gg);
+    }
+}
+
+// d = -grad + beta dprev; gprev = grad; partial of sum b kappa(x_s - x_r) (d_s - d_r)^2
+__global__ void dir_kernel(GeomParams P, PriorParams pr, const float* __restrict__ x, const float* __restrict__ grad,
+                           const float* __restrict__ dprev, const float* __restrict__ msq, const double* __restrict__ sc,
+                           float* __restrict__ dnew, float* __restrict__ gprev, double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    const int N = P.W * P.H;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const float beta = (float)sc[S_BETA];
+    double acc = 0.0;
+    if (v < N) {
+        const int r = v / P.W, c = v - r * P.W;
+        const float gv = grad[v];
+        const float dv = -gv + beta * dprev[v];
+        dnew[v] = dv;
+        gprev[v] = gv;
+        const float xs = x[v], ms = msq[r];
+        // forward cliques E, SW, S, SE: each unordered pair once
+        const int dr4[4] = {0, 1, 1, 1}, dc4[4] = {1, -1, 0, 1};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int r2 = r + dr4[t], c2 = c + dc4[t];
+            if (r2 >= P.H || c2 < 0 || c2 >= P.W) continue;
+            const int v2 = r2 * P.W + c2;
+            const float d2 = -grad[v2] + beta * dprev[v2];
+            float kap;
+            qggmrf(pr, xs - x[v2], pr.sigma0 * ms * msq[r2], nullptr, &kap, nullptr);
+            const float dd = dv - d2;
+            acc += (double)(nb_weight(dr4[t], dc4[t]) * kap) * (double)dd * (double)dd;
+        }
+    }
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Per A-scan direct-arrival projection (eq. 1): g = <d,r>/|d|^2, out = r - g d.
+// src rows of stride `sin` (float or bf16, optional subtraction of `sub`),
+// dst rows of stride `sout` padded with zeros; FP64 partial |out|^2 per row.
+__global__ void project_kernel(GeomParams P, const void* __restrict__ src, int src_bf16, int sin,
+                               const float* __restrict__ sub, int ssub, const float* __restrict__ direct,
+                               const float* __restrict__ dinv, int use_direct, float* __restrict__ dst, int sout,
+                               float* __restrict__ gk, double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    const int k = blockIdx.x;
+    const int j = k % P.n_rx;
+    const float* dj = direct + (size_t)j * P.Mp;
+    auto val = [&](int n) -> float {
+        size_t s = (size_t)k * sin + n;
+        float v = src_bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(src)[s])
+                           : reinterpret_cast<const float*>(src)[s];
+        if (sub) v -= sub[(size_t)k * ssub + n];
+        return v;
+    };
+    double dr = 0.0;
+    if (use_direct)
+        for (int n = threadIdx.x; n < P.M; n += blockDim.x) dr += (double)dj[n] * (double)val(n);
+    double tot = block_sum(dr, sh);
+    __shared__ float gsh;
+    if (threadIdx.x == 0) gsh = use_direct ? (float)(tot * (double)dinv[j]) : 0.0f;
+    __syncthreads();
+    const float g = gsh;
+    double ee = 0.0;
+    for (int n = threadIdx.x; n < sout; n += blockDim.x) {
+        float o = 0.0f;
+        if (n < P.M) o = val(n) - g * dj[n];
+        dst[(size_t)k * sout + n] = o;
+        ee += (double)o * o;
+    }
+    double e2 = block_sum(ee, sh);
+    if (threadIdx.x == 0) {
+        if (gk) gk[k] = g;
+        if (part) part[k] = e2;
+    }
+}
+
+__global__ void finalize_step_kernel(const double* __restrict__ qpart, int nq, const double* __restrict__ cpart,
+                                     int nc, float inv_s2, double* __restrict__ sc)
+{
+    __shared__ double sh[32];
+    double a = 0, b = 0;
+    for (int t = threadIdx.x; t < nq; t += blockDim.x) a += qpart[t];
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) b += cpart[t];
+    double qq = block_sum(a, sh), cv = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        double den = qq * (double)inv_s2 + cv;
+        double alpha = den > 0.0 ? -sc[S_GD] / den : 0.0;
+        if (!isfinite(alpha)) { alpha = 0.0; sc[S_BAD] = 1.0; }
+        sc[S_QQ] = qq;
+        sc[S_CURV] = cv;
+        sc[S_ALPHA] = alpha;
+    }
+}
+
+// x += alpha d (first N threads), e -= alpha q (next K*Mp), optional BF16 copy
+__global__ void update_kernel(int N, long long KM, const double* __restrict__ sc, float* __restrict__ x,
+                              const float* __restrict__ d, float* __restrict__ e, const float* __restrict__ q,
+                              __nv_bfloat16* __restrict__ ebf)
+{
+    const float a = (float)sc[S_ALPHA];
+    const long long tot = N + KM;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < N) {
+            x[t] = fmaf(a, d[t], x[t]);
+        } else {
+            long long u = t - N;
+            float ev = fmaf(-a, q[u], e[u]);
+            e[u] = ev;
+            if (ebf) ebf[u] = __float2bfloat16_rn(ev);
+        }
+    }
+}
+
+// cost of eq. 18 after an iteration: |e|^2 / (2 sigma^2) + sum b rho
+__global__ void cost_part_kernel(GeomParams P, PriorParams pr, const float* __restrict__ x,
+                                 const float* __restrict__ msq, const float* __restrict__ e, long long KM,
+                                 double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    const int N = P.W * P.H;
+    double acc = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < KM; t += stride) {
+        double ev = e[t];
+        acc += ev * ev * 0.5 * (double)pr.inv_s2;
+    }
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += stride) {
+        const int r = (int)(v / P.W), c = (int)(v - (long long)r * P.W);
+        const int dr4[4] = {0, 1, 1, 1}, dc4[4] = {1, -1, 0, 1};
+        for (int t = 0; t < 4; ++t) {
+            const int r2 = r + dr4[t], c2 = c + dc4[t];
+            if (r2 >= P.H || c2 < 0 || c2 >= P.W) continue;
+            float rho;
+            qggmrf(pr, x[v] - x[r2 * P.W + c2], pr.sigma0 * msq[r] * msq[r2], nullptr, nullptr, &rho);
+            acc += (double)(nb_weight(dr4[t], dc4[t]) * rho);
+        }
+    }
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void finalize_cost_kernel(const double* __restrict__ part, int nb, int it, double* __restrict__ sc,
+                                     double* __restrict__ cost_hist)
+{
+    __shared__ double sh[32];
+    double a = 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) a += part[t];
+    double s = block_sum(a, sh);
+    if (threadIdx.x == 0) {
+        cost_hist[it] = s;
+        if (!isfinite(s)) sc[S_BAD] = 1.0;
+    }
+}
+
+__global__ void add_direct_kernel(GeomParams P, const float* __restrict__ gk, const float* __restrict__ direct,
+                                  float* __restrict__ y)
+{
+    const int k = blockIdx.x;
+    const float g = gk[k];
+    const float* dj = direct + (size_t)(k % P.n_rx) * P.Mp;
+    for (int n = threadIdx.x; n < P.M; n += blockDim.x) y[(size_t)k * P.M + n] += g * dj[n];
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, long long n)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        dst[t] = __float2bfloat16_rn(src[t]);
+}
+
+__global__ void residual_sum_kernel(const double* __restrict__ part, int nb, double* __restrict__ sc)
+{
+    __shared__ double sh[32];
+    double a = 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) a += part[t];
+    double s = block_sum(a, sh);
+    if (threadIdx.x == 0) {
+        sc[S_EE] = s;
+        if (!isfinite(s)) sc[S_BAD] = 1.0;
+    }
+}
+
+}  // namespace mbir
+
+using namespace mbir;
+
+namespace {
+
+int cerr_code(cudaError_t e) { return e == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA; }
+
+#define CK(expr)                                           \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return cerr_code(_e);       \
+    } while (0)
+
+template <typename T>
+cudaError_t grow(T** p, size_t count, size_t* bytes)
+{
+    if (*p) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+    if (e == cudaSuccess) *bytes += sizeof(T) * std::max<size_t>(count, 1);
+    return e;
+}
+
+int ensure_workspace(mbir_geometry* g, int hist)
+{
+    const GeomParams& P = g->P;
+    const size_t N = (size_t)P.W * P.H, KMp = (size_t)P.K * P.Mp;
+    const size_t nbpix = (N + kRedThreads - 1) / kRedThreads;
+    size_t& B = g->bytes;
+    CK(grow(&g->w_e, KMp, &B));
+    CK(grow(&g->w_q, KMp, &B));
+    CK(grow(&g->w_b, N, &B));
+    CK(grow(&g->w_grad, N, &B));
+    CK(grow(&g->w_gprev, N, &B));
+    CK(grow(&g->w_d, N, &B));
+    CK(grow(&g->w_d2, N, &B));
+    CK(grow(&g->w_msq, (size_t)P.H, &B));
+    g->part_len = std::max<size_t>(3 * nbpix, (size_t)P.K) + 4096;
+    CK(grow(&g->w_part, g->part_len * 2, &B));
+    CK(grow(&g->w_scal, (size_t)S_COUNT, &B));
+    if (P.precision == MBIR_PREC_BF16) CK(grow(&g->w_ebf, KMp, &B));
+    if (hist > g->hist_len) {
+        if (g->w_hist) { cudaFree(g->w_hist); g->bytes -= sizeof(double) * 2 * g->hist_len; g->w_hist = nullptr; }
+        CK(cudaMalloc((void**)&g->w_hist, sizeof(double) * 2 * hist));
+        g->bytes += sizeof(double) * 2 * hist;
+        g->hist_len = hist;
+    }
+    return MBIR_OK;
+}
+
+bool prior_ok(const mbir_prior* pr)
+{
+    return pr && pr->p > 1.0 && pr->p < pr->q && pr->q == 2.0 && pr->T > 0 && pr->sigma0 > 0 && pr->m > 0 &&
+           pr->a >= 0 && pr->sigma_noise > 0 && std::isfinite(pr->sigma_noise);
+}
+
+PriorParams prior_params(const mbir_prior* pr)
+{
+    PriorParams q;
+    q.p = (float)pr->p;
+    q.q = (float)pr->q;
+    q.T = (float)pr->T;
+    q.sigma0 = (float)pr->sigma0;
+    q.inv_s2 = (float)(1.0 / (pr->sigma_noise * pr->sigma_noise));
+    q.kappa0_base = (float)(2.0 / (pr->p * std::pow(pr->T, 2.0 - pr->p)));
+    return q;
+}
+
+// sqrt(m_s) of eq. 17 per row (depth of the pixel centre from the transducer plane)
+cudaError_t upload_msq(mbir_geometry* g, const mbir_prior* pr, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    std::vector<float> m(P.H);
+    double zmax = g->z0 + (P.H - 0.5) * g->pitch;
+    for (int r = 0; r < P.H; ++r) {
+        double z = g->z0 + (r + 0.5) * g->pitch;
+        double ms = 1.0 + (pr->m - 1.0) * std::pow(z / zmax, pr->a);
+        m[r] = (float)std::sqrt(ms);
+    }
+    cudaError_t e = cudaMemcpyAsync(g->w_msq, m.data(), sizeof(float) * P.H, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+struct ProfState {
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, int>> pending;   // (kind, index of start event)
+    size_t used = 0;
+};
+
+cudaEvent_t prof_event(mbir_geometry* g)
+{
+    ProfState* ps = (ProfState*)g->prof_state;
+    if (ps->used == ps->pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ps->pool.push_back(e);
+    }
+    return ps->pool[ps->used++];
+}
+
+// record a start event before an apply launch (kind 0 = forward, 1 = backproject)
+void prof_begin(mbir_geometry* g, int kind, cudaStream_t st)
+{
+    if (!g->prof) return;
+    ProfState* ps = (ProfState*)g->prof_state;
+    size_t idx = ps->used;
+    cudaEventRecord(prof_event(g), st);
+    ps->pending.push_back({kind, (int)idx});
+}
+
+void prof_end(mbir_geometry* g, cudaStream_t st)
+{
+    if (!g->prof) return;
+    cudaEventRecord(prof_event(g), st);
+}
+
+// after the stream is synchronised: accumulate and recycle the events
+void prof_collect(mbir_geometry* g)
+{
+    if (!g->prof) return;
+    ProfState* ps = (ProfState*)g->prof_state;
+    for (auto& pe : ps->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ps->pool[pe.second], ps->pool[pe.second + 1]);
+        if (pe.first == 0) { g->prof_fms += ms; ++g->prof_nf; }
+        else { g->prof_bms += ms; ++g->prof_nb; }
+    }
+    ps->pending.clear();
+    ps->used = 0;
+}
+
+int reconstruct_core(mbir_geometry* g, const void* y_dev, int y_bf16, const mbir_prior* pr, int n_iter,
+                     float* x, int x_given, float* g_dev, mbir_stats* st_out, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const int N = P.W * P.H;
+    const long long KMp = (long long)P.K * P.Mp;
+    const int nbpix = (N + kRedThreads - 1) / kRedThreads;
+    const bool want_cost = st_out && st_out->cost && st_out->cost_len > 0;
+    int rc = ensure_workspace(g, std::max(n_iter, 1));
+    if (rc != MBIR_OK) return rc;
+    PriorParams pp = prior_params(pr);
+    CK(upload_msq(g, pr, st));
+    double* sc = g->w_scal;
+    double* part = g->w_part;
+    double* part2 = g->w_part + g->part_len;
+    const int use_direct = 1;
+    CK(cudaMemsetAsync(sc, 0, sizeof(double) * S_COUNT, st));
+    CK(cudaMemsetAsync(g->w_gprev, 0, sizeof(float) * N, st));
+    CK(cudaMemsetAsync(g->w_d, 0, sizeof(float) * N, st));
+    CK(cudaMemsetAsync(g->w_d2, 0, sizeof(float) * N, st));
+    CK(cudaMemsetAsync(g->w_hist, 0, sizeof(double) * 2 * g->hist_len, st));
+    if (!x_given) CK(cudaMemsetAsync(x, 0, sizeof(float) * N, st));
+    __nv_bfloat16* ebf = P.precision == MBIR_PREC_BF16 ? g->w_ebf : nullptr;
+
+    // e = P (y - A x)
+    if (x_given) {
+        CK(launch_forward(g, x, g->w_q, nullptr, P.Mp, st));
+        project_kernel<<<P.K, kRedThreads, 0, st>>>(P, y_dev, y_bf16, P.M, g->w_q, P.Mp, g->d_direct, g->d_dinv,
+                                                    use_direct, g->w_e, P.Mp, nullptr, part);
+    } else {
+        project_kernel<<<P.K, kRedThreads, 0, st>>>(P, y_dev, y_bf16, P.M, nullptr, 0, g->d_direct, g->d_dinv,
+                                                    use_direct, g->w_e, P.Mp, nullptr, part);
+    }
+    CK(cudaGetLastError());
+    residual_sum_kernel<<<1, kRedThreads, 0, st>>>(part, P.K, sc);
+    if (ebf) to_bf16_kernel<<<1024, 256, 0, st>>>(g->w_e, ebf, KMp);
+    CK(cudaGetLastError());
+    double bad = 0;
+    CK(cudaMemcpyAsync(&bad, sc + S_BAD, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (bad != 0.0) return MBIR_ERR_NONFINITE;
+
+    float* dcur = g->w_d;    // previous direction
+    float* dnxt = g->w_d2;
+    const int ublocks = (int)std::min<long long>((N + KMp + 255) / 256, 152LL * 32);
+    const int cblocks = 152 * 4;
+    for (int it = 0; it < n_iter; ++it) {
+        prof_begin(g, 1, st);
+        CK(launch_backproject(g, g->w_e, ebf, g->w_b, st));
+        prof_end(g, st);
+        grad_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, x, g->w_b, g->w_msq, g->w_gprev, dcur, g->w_grad, part, 1);
+        finalize_dir_kernel<<<1, kRedThreads, 0, st>>>(part, nbpix, it, sc, g->w_hist + g->hist_len);
+        dir_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, x, g->w_grad, dcur, g->w_msq, sc, dnxt, g->w_gprev, part2);
+        CK(cudaGetLastError());
+        prof_begin(g, 0, st);
+        CK(launch_forward(g, dnxt, g->w_q, nullptr, P.Mp, st));
+        prof_end(g, st);
+        project_kernel<<<P.K, kRedThreads, 0, st>>>(P, g->w_q, 0, P.Mp, nullptr, 0, g->d_direct, g->d_dinv,
+                                                    use_direct, g->w_q, P.Mp, nullptr, part);
+        finalize_step_kernel<<<1, kRedThreads, 0, st>>>(part, P.K, part2, nbpix, pp.inv_s2, sc);
+        update_kernel<<<ublocks, 256, 0, st>>>(N, KMp, sc, x, dnxt, g->w_e, g->w_q, ebf);
+        if (want_cost) {
+            cost_part_kernel<<<cblocks, kRedThreads, 0, st>>>(P, pp, x, g->w_msq, g->w_e, KMp, part);
+            finalize_cost_kernel<<<1, kRedThreads, 0, st>>>(part, cblocks, it, sc, g->w_hist);
+        }
+        CK(cudaGetLastError());
+        std::swap(dcur, dnxt);
+    }
+    if (g_dev) {
+        CK(launch_forward(g, x, g->w_q, nullptr, P.Mp, st));
+        project_kernel<<<P.K, kRedThreads, 0, st>>>(P, y_dev, y_bf16, P.M, g->w_q, P.Mp, g->d_direct, g->d_dinv,
+                                                    use_direct, g->w_q, P.Mp, g_dev, nullptr);
+        CK(cudaGetLastError());
+    }
+    std::vector<double> scal(S_COUNT);
+    CK(cudaMemcpyAsync(scal.data(), sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+    std::vector<double> hist(2 * (size_t)g->hist_len);
+    if (st_out && n_iter > 0)
+        CK(cudaMemcpyAsync(hist.data(), g->w_hist, sizeof(double) * 2 * g->hist_len, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    prof_collect(g);
+    int status = 0;
+    CK(cudaMemcpy(&status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        int zero = 0;
+        cudaMemcpy(g->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return MBIR_ERR_TIMEOUT;
+    }
+    if (st_out) {
+        st_out->iterations = n_iter;
+        st_out->grad_norm_first = n_iter > 0 ? hist[g->hist_len] : 0.0;
+        st_out->grad_norm_last = n_iter > 0 ? hist[g->hist_len + n_iter - 1] : 0.0;
+        if (want_cost)
+            for (int t = 0; t < std::min(n_iter, st_out->cost_len); ++t) st_out->cost[t] = hist[t];
+    }
+    if (scal[S_BAD] != 0.0) return MBIR_ERR_NONFINITE;
+    return MBIR_OK;
+}
+
+}  // namespace
+
+void mbir::prof_release(mbir_geometry* g)
+{
+    ProfState* ps = (ProfState*)g->prof_state;
+    if (!ps) return;
+    for (cudaEvent_t e : ps->pool) cudaEventDestroy(e);
+    delete ps;
+    g->prof_state = nullptr;
+}
+
+namespace {
+
+int check_status(mbir_geometry* g)
+{
+    int status = 0;
+    if (cudaMemcpy(&status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MBIR_ERR_CUDA;
+    return status ? MBIR_ERR_TIMEOUT : MBIR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mbir_forward(const mbir_geometry* g, const float* x_dev, void* y_dev, void* stream)
+{
+    if (!g || !x_dev || !y_dev) return MBIR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (g->P.precision == MBIR_PREC_BF16)
+        e = launch_forward(g, x_dev, nullptr, (__nv_bfloat16*)y_dev, g->P.M, st);
+    else
+        e = launch_forward(g, x_dev, (float*)y_dev, nullptr, g->P.M, st);
+    return e == cudaSuccess ? MBIR_OK : cerr_code(e);
+}
+
+int mbir_backproject(const mbir_geometry* gc, const void* r_dev, float* x_dev, void* stream)
+{
+    if (!gc || !r_dev || !x_dev) return MBIR_ERR_INVALID_ARG;
+    mbir_geometry* g = const_cast<mbir_geometry*>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_workspace(g, 1);
+    if (rc != MBIR_OK) return rc;
+    const bool bf = g->P.precision == MBIR_PREC_BF16;
+    CK(launch_pad_rows(g, r_dev, bf ? 1 : 0, g->w_e, st));
+    if (bf) {
+        // BF16 storage: the kernel streams a BF16 copy of the padded rows
+        to_bf16_kernel<<<1024, 256, 0, st>>>(g->w_e, g->w_ebf, (long long)g->P.K * g->P.Mp);
+        CK(cudaGetLastError());
+    }
+    CK(launch_backproject(g, g->w_e, g->w_ebf, x_dev, st));
+    return MBIR_OK;
+}
+
+int mbir_project(const mbir_geometry* g, const float* r_dev, float* e_dev, float* gk_dev, void* stream)
+{
+    if (!g || !r_dev || !e_dev) return MBIR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // rows are processed one block each; in-place use is safe (a block reads
+    // its row fully before writing it)
+    project_kernel<<<g->P.K, kRedThreads, 0, st>>>(g->P, r_dev, 0, g->P.M, nullptr, 0, g->d_direct, g->d_dinv, 1,
+                                                   e_dev, g->P.M, gk_dev, nullptr);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBIR_OK : cerr_code(e);
+}
+
+int mbir_add_direct(const mbir_geometry* g, const float* gk_dev, float* y_dev, void* stream)
+{
+    if (!g || !gk_dev || !y_dev) return MBIR_ERR_INVALID_ARG;
+    add_direct_kernel<<<g->P.K, kRedThreads, 0, (cudaStream_t)stream>>>(g->P, gk_dev, g->d_direct, y_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBIR_OK : cerr_code(e);
+}
+
+int mbir_prior_gradient(const mbir_geometry* gc, const mbir_prior* pr, const float* x_dev, float* out_dev,
+                        void* stream)
+{
+    if (!gc || !x_dev || !out_dev || !pr) return MBIR_ERR_INVALID_ARG;
+    mbir_prior tmp = *pr;
+    tmp.sigma_noise = tmp.sigma_noise > 0 ? tmp.sigma_noise : 1.0;
+    if (!prior_ok(&tmp)) return MBIR_ERR_INVALID_ARG;
+    mbir_geometry* g = const_cast<mbir_geometry*>(gc);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_workspace(g, 1);
+    if (rc != MBIR_OK) return rc;
+    CK(upload_msq(g, &tmp, st));
+    const int N = g->P.W * g->P.H;
+    const int nb = (N + kRedThreads - 1) / kRedThreads;
+    CK(cudaMemsetAsync(g->w_gprev, 0, sizeof(float) * N, st));
+    grad_kernel<<<nb, kRedThreads, 0, st>>>(g->P, prior_params(&tmp), x_dev, nullptr, g->w_msq, g->w_gprev,
+                                           g->w_gprev, out_dev, g->w_part, 0);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MBIR_OK : cerr_code(e);
+}
+
+int mbir_reconstruct(const mbir_geometry* gc, const void* y_dev, const mbir_prior* pr, int n_iter, float* x_dev,
+                     int x_given, float* g_dev, mbir_stats* st, void* stream)
+{
+    if (!gc || !y_dev || !x_dev || n_iter < 0 || !prior_ok(pr)) return MBIR_ERR_INVALID_ARG;
+    mbir_geometry* g = const_cast<mbir_geometry*>(gc);
+    return reconstruct_core(g, y_dev, g->P.precision == MBIR_PREC_BF16 ? 1 : 0, pr, n_iter, x_dev, x_given, g_dev,
+                            st, (cudaStream_t)stream);
+}
+
+int mbir_reconstruct_host(const mbir_geometry* gc, const float* y_host, const mbir_prior* pr, int n_iter,
+                          float* x_host, float* g_host, mbir_stats* st, void* stream)
+{
+    if (!gc || !y_host || !x_host || n_iter < 0 || !prior_ok(pr)) return MBIR_ERR_INVALID_ARG;
+    mbir_geometry* g = const_cast<mbir_geometry*>(gc);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t KM = (size_t)g->P.K * g->P.M, N = (size_t)g->P.W * g->P.H;
+    size_t& B = g->bytes;
+    CK(grow(&g->w_y, KM, &B));
+    CK(grow(&g->w_x, N, &B));
+    CK(grow(&g->w_g, (size_t)g->P.K, &B));
+    CK(cudaMemcpyAsync(g->w_y, y_host, sizeof(float) * KM, cudaMemcpyHostToDevice, s));
+    int rc = reconstruct_core(g, g->w_y, 0, pr, n_iter, g->w_x, 0, g_host ? g->w_g : nullptr, st, s);
+    if (rc != MBIR_OK) return rc;
+    CK(cudaMemcpyAsync(x_host, g->w_x, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+    if (g_host) CK(cudaMemcpyAsync(g_host, g->w_g, sizeof(float) * g->P.K, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MBIR_OK;
+}
+
+int mbir_set_profiling(mbir_geometry* g, int enable)
+{
+    if (!g) return MBIR_ERR_INVALID_ARG;
+    if (enable && !g->prof_state) g->prof_state = new ProfState();
+    g->prof = enable ? 1 : 0;
+    return MBIR_OK;
+}
+
+int mbir_get_kernel_times(mbir_geometry* g, mbir_kernel_times* t, int reset)
+{
+    if (!g || !t) return MBIR_ERR_INVALID_ARG;
+    t->forward_launches = g->prof_nf;
+    t->backproject_launches = g->prof_nb;
+    t->forward_ms = g->prof_fms;
+    t->backproject_ms = g->prof_bms;
+    if (reset) { g->prof_nf = g->prof_nb = 0; g->prof_fms = g->prof_bms = 0.0; }
+    return MBIR_OK;
+}
+
+int mbir_count_taps(const mbir_geometry* g, int64_t* active_pairs, int64_t* taps)
+{
+    if (!g || !active_pairs || !taps) return MBIR_ERR_INVALID_ARG;
+    unsigned long long* d = nullptr;
+    CK(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = launch_count_taps(g, d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cerr_code(e);
+    *active_pairs = (int64_t)h[0];
+    *taps = (int64_t)h[1];
+    return MBIR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,311 @@
+// Internal definitions shared by the library's host setup and CUDA kernels.
+//
+// Device units: time in samples (1 / fs), lengths in metres.  A leg's ray
+// parameter p is in samples per metre, so sin(theta_l) = p * k_l with
+// k_l = c_l / fs, and the slowness of layer l is s_l = fs / c_l.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/mbir.h"
+
+namespace mbir {
+
+constexpr int kMaxLayers = MBIR_MAX_LAYERS;
+constexpr int kBisect = 22;          // FP32 bisection steps on p (bracket / 2^22)
+
+// Per-geometry constants, passed to kernels by value.
+struct GeomParams {
+    int L, W, H, n_tx, n_rx, K, M, Mp;
+    int Tw, Tw4, Q, G, Gt;           // Gt = table gamma planes (max(G-1, 1))
+    int mode, precision;
+    int npos, nh;                     // distinct transducer positions, distinct |h| (TAB)
+    int beta_int;                     // >= 0: beta is this integer; -1: use powf
+    float beta;
+    float gscale;                     // (G-1) / gamma_max (gamma bins per second)
+    float inv_gscale;
+    float k[kMaxLayers];              // c_l / fs  (m per sample)
+    float2 s2[kMaxLayers];            // (fs / c_l)^2 as double-float
+    float2 eta[kMaxLayers];           // full layer thickness as double-float
+    float alpha_c[kMaxLayers];        // alpha_l (s/m) * gscale: gamma-bin units per metre
+    int n_seg;                        // layer segments among image rows
+    int seg_row[kMaxLayers + 1];      // first row of each segment, seg_row[n_seg] = H
+};
+
+// Per image row.
+struct RowInfo {
+    int nl;                           // layers crossed (eta > 0)
+    float pmax;                       // fs / max crossed speed
+    float2 eta_last;                  // eta of the deepest crossed layer (double-float)
+    float tau;                        // interface transmittance product
+    float tvert;                      // two-way vertical time (lower bound of T), samples
+    float mrow;                       // unused by the operator (prior weight slot)
+    int pad;
+};
+
+struct Leg {
+    float Th, Tl;                     // travel time (double-float, samples)
+    float g;                          // attenuation in gamma-bin units
+    float phi;                        // cos^beta of the summed refraction angles
+};
+
+// ---------------------------------------------------------------------------
+// Error-free transformations (Knuth TwoSum, FMA TwoProduct) and double-float
+// arithmetic.  Intrinsics keep the compiler from contracting or reordering.
+// ---------------------------------------------------------------------------
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    df s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
+
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    df p = two_prod(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b)
+{
+    df p = two_prod(a.hi, b);
+    float e = __fmaf_rn(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, e);
+}
+
+// sqrt of a non-negative double-float: IEEE sqrt of the head, one Newton step
+__device__ __forceinline__ df df_sqrt(df a)
+{
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    float r = __fsqrt_rn(a.hi);
+    float e = __fadd_rn(__fmaf_rn(-r, r, a.hi), a.lo);
+    return fast_two_sum(r, __fmul_rn(e, __fdividef(0.5f, r)));
+}
+
+__device__ __forceinline__ float pow_beta(float c, int beta_int, float beta)
+{
+    if (!(c > 0.0f)) return 0.0f;
+    if (beta_int >= 0) {
+        float r = 1.0f, b = c;
+        int e = beta_int;
+        while (e) {
+            if (e & 1) r *= b;
+            b *= b;
+            e >>= 1;
+        }
+        return r;
+    }
+    return powf(c, beta);
+}
+
+// |x_c - u| as double-float from double-float operands
+__device__ __forceinline__ df abs_diff(float2 xc, float2 u)
+{
+    df s = two_sum(xc.x, -u.x);
+    float e = __fadd_rn(s.lo, __fsub_rn(xc.y, u.y));
+    df h = fast_two_sum(s.hi, e);
+    if (h.hi < 0.0f) { h.hi = -h.hi; h.lo = -h.lo; }
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// One leg (Section 2, eq. 4-6) from a transducer at depth 0 to a voxel of row
+// `ri` at lateral offset h >= 0.  The paper's binary search on theta_1 runs
+// here on the ray parameter p = sin(theta_1) / c_1 (monotone in theta_1), in
+// FP32 with a fixed step count so a warp stays in lockstep.  The travel time
+// then uses the Legendre form T = p h + sum_l eta_l sqrt(s_l^2 - p^2), which is
+// stationary in p, so the FP32 bracket error enters T only at second order;
+// it is evaluated in double-float arithmetic.
+// ---------------------------------------------------------------------------
+template <int NL>
+__device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri, df h)
+{
+    float eta[NL], kk[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        bool act = l < ri.nl;
+        eta[l] = (l < ri.nl - 1) ? P.eta[l].x : (l == ri.nl - 1 ? ri.eta_last.x : 0.0f);
+        kk[l] = act ? P.k[l] : 0.0f;
+    }
+    float lo = 0.0f, hi = ri.pmax;
+#pragma unroll 2
+    for (int it = 0; it < kBisect; ++it) {
+        float mid = 0.5f * (lo + hi);
+        float X = 0.0f;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            float t = mid * kk[l];
+            float c2 = __fmaf_rn(-t, t, 1.0f);
+            X = __fmaf_rn(eta[l] * t, rsqrtf(c2), X);
+        }
+        bool below = X < h.hi;
+        lo = below ? mid : lo;
+        hi = below ? hi : mid;
+    }
+    float p = 0.5f * (lo + hi);
+
+    df T = df_mul_f(h, p);
+    df p2 = two_prod(p, p);
+    float g = 0.0f, C = 1.0f, S = 0.0f;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        if (l < ri.nl) {
+            float2 e2 = (l < ri.nl - 1) ? P.eta[l] : ri.eta_last;
+            df e = {e2.x, e2.y};
+            df s2 = {P.s2[l].x, P.s2[l].y};
+            df sq = df_sqrt(df_sub(s2, p2));
+            T = df_add(T, df_mul(e, sq));
+            float t = p * kk[l];
+            float c2 = fmaxf(__fmaf_rn(-t, t, 1.0f), 0.0f);
+            float rc = rsqrtf(c2);
+            g = __fmaf_rn(P.alpha_c[l] * eta[l], rc, g);     // alpha * path length
+            float cth = c2 * rc;                               // cos(theta_l)
+            float Cn = C * cth - S * t;                        // cos, sin of the angle sum
+            S = S * cth + C * t;
+            C = Cn;
+        }
+    }
+    Leg out;
+    out.Th = T.hi;
+    out.Tl = T.lo;
+    out.g = g;
+    out.phi = pow_beta(C, P.beta_int, P.beta);
+    return out;
+}
+
+// Tap parameters of one (pixel, A-scan) pair.  Taps are samples
+// n = n0 + 1 + m, m = 0..Tw-1, at table coordinate q = m*Q + r with weight
+// (1 - w1) on node q and w1 on node q + 1.  flag0 marks T exactly on a sample
+// (the tap m = Tw-1 then sits at tau = t0 and is outside the open window).
+struct Pair {
+    int n0;
+    int r, gi;
+    float w0, w1;        // tau weights of nodes q and q + 1
+    float psi;           // gamma weight of plane gi + 1
+    float w;             // tau(l_v) * phi_tx * phi_rx
+    bool flag0;
+};
+
+__device__ __forceinline__ Pair make_pair(const GeomParams& P, const Leg& tx, const Leg& rx, float tau)
+{
+    Pair o;
+    df T = df_add({tx.Th, tx.Tl}, {rx.Th, rx.Tl});
+    float n0f = floorf(T.hi);
+    float f = __fadd_rn(__fsub_rn(T.hi, n0f), T.lo);
+    if (f < 0.0f) { f += 1.0f; n0f -= 1.0f; }
+    if (f >= 1.0f) { f -= 1.0f; n0f += 1.0f; }
+    float a = f * (float)P.Q;
+    if (a >= (float)P.Q) { n0f += 1.0f; f = 0.0f; a = 0.0f; }
+    o.n0 = (int)n0f;
+    float fl = floorf(a);
+    int ia = (int)fl;
+    float fa = a - fl;
+    o.r = P.Q - 1 - ia;
+    o.w1 = 1.0f - fa;
+    o.w0 = fa;
+    o.flag0 = (f == 0.0f);
+    float gam = fminf(fmaxf(tx.g + rx.g, 0.0f), (float)(P.G - 1));
+    int gi = (P.G > 1) ? min((int)gam, P.G - 2) : 0;
+    o.gi = gi;
+    o.psi = (P.G > 1) ? gam - (float)gi : 0.0f;
+    o.w = tau * tx.phi * rx.phi;
+    return o;
+}
+
+// Host-side launchers (apply.cu / map.cu)
+struct GeomDev;
+}  // namespace mbir
+
+// The geometry handle (opaque in the C ABI).
+struct mbir_geometry {
+    int device;
+    mbir::GeomParams P;
+    mbir::RowInfo* d_rows;
+    float2* d_colx;        // W pixel-centre laterals (double-float)
+    float2* d_pos;         // npos distinct transducer laterals (double-float)
+    int* d_txpos;          // n_tx position index per Tx
+    int* d_rxpos;          // K position index per A-scan receiver
+    float2* d_tab;         // Gt x (Q+1) x Tw4 pulse table, float2 = (plane g, plane g+1)
+    __nv_bfloat162* d_tab_bf16;
+    float4* d_legs;        // TAB: H x nh legs
+    int* d_hidx;           // TAB: npos x W index into the |h| list
+    float* d_direct;       // n_rx x Mp direct-arrival columns (eq. 1)
+    float* d_dinv;         // n_rx: 1 / |d_j|^2 (0 if empty)
+    int* d_status;         // device error flag (bounded waits)
+    // reconstruction workspace (grown on demand)
+    float* w_e;            // K x Mp projected residual
+    float* w_q;            // K x Mp P A d
+    float* w_b;            // N
+    float* w_grad;         // N
+    float* w_gprev;        // N
+    float* w_d;            // N
+    double* w_part;        // reduction partials
+    double* w_scal;        // scalar slots
+    __nv_bfloat16* w_ebf;  // K x Mp BF16 copy of e (BF16 precision)
+    size_t part_len;
+    size_t bytes;
+    double* tab_host;
+    size_t tab_len;
+    float* w_msq;          // H: sqrt(m_s) of eq. 17 for the current prior
+    float* w_d2;           // N: second direction buffer (ping-pong)
+    float* w_y;            // K x M staging for host-buffer calls
+    float* w_x;            // N staging for host-buffer calls
+    float* w_g;            // K staging for host-buffer calls
+    double* w_hist;        // 2 x hist_len: cost and gradient norm per iteration
+    int hist_len;
+    double gamma_max;
+    double fs;
+    double z0, pitch;
+    // profiling of the apply kernels inside mbir_reconstruct
+    int prof;
+    void* prof_state;      // host-side event lists (see map.cu)
+    long long prof_nf, prof_nb;
+    double prof_fms, prof_bms;
+};
+
+namespace mbir {
+// launchers implemented in apply.cu
+cudaError_t launch_build_legs(const mbir_geometry* g, const double* hvals_dev_unused, const float2* d_hvals,
+                              cudaStream_t st);
+cudaError_t launch_backproject(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
+                               float* b, cudaStream_t st);
+cudaError_t launch_forward(const mbir_geometry* g, const float* x, float* y_f32, __nv_bfloat16* y_bf16,
+                           int out_stride, cudaStream_t st);
+cudaError_t launch_pad_rows(const mbir_geometry* g, const void* src, int src_bf16, float* dst_pad,
+                            cudaStream_t st);
+cudaError_t launch_pair_quantities(const mbir_geometry* g, const int* pix, const int* k, int n,
+                                   double* T, float* gam, float* w, cudaStream_t st);
+void prof_release(mbir_geometry* g);
+cudaError_t launch_count_taps(const mbir_geometry* g, unsigned long long* d_out, cudaStream_t st);
+size_t backproject_smem(const mbir_geometry* g);
+size_t forward_smem(const mbir_geometry* g, int* cb_out);
+}  // namespace mbir
