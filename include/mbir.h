@@ -74,6 +74,7 @@ typedef enum {
  *       4 * sum_l alpha_l eta_l down to the deepest pixel centre.
  *   gamma_bins (G), phases (Q): pulse table of G attenuation bins and Q
  *       phases per sample, read by bilinear interpolation (0 selects 16, 16).
+ *   flags: MBIR_FLAG_* below (0 for the defaults).
  */
 typedef struct {
     int n_layers;
@@ -96,7 +97,14 @@ typedef struct {
     int gamma_bins, phases;
     int precision;               /* mbir_precision */
     int mode;                    /* mbir_mode */
+    int flags;                   /* MBIR_FLAG_* */
 } mbir_geometry_desc;
+
+/* TAB mode normally also stores every A-scan's active pairs as records
+ * sorted by first tap sample (the system matrix of Section 3, about 24 bytes
+ * per active pair) so that A x streams them; this flag keeps the on-the-fly
+ * record path of A x instead (less memory, slower). */
+#define MBIR_FLAG_NO_RECORDS 1
 
 /* QGGMRF prior (eq. 15-17) and the noise sigma of eq. 2.
  * Requires 1 < p < q = 2 (Section 2, "Prior model"), T > 0, sigma0 > 0,

@@ -1,141 +1,191 @@
-// A^T r (adjoint of eq. 13): one thread per pixel, one CTA per tile of
-// kRows x 32 pixels.  The CTA walks the A-scans in (Tx, receiver) order,
-// keeping the pixel's transmit leg while the receiver changes.  Each A-scan's
-// residual row is staged in shared memory by a 1-D bulk copy (TMA engine)
-// into a double buffer guarded by mbarriers, so the next row streams in while
-// the current one is consumed.  The pulse table sits in shared memory.
-// Every tap of a pair shares one table phase, so a pair costs two packed FP32
-// FMAs per tap (four dot products, combined once per pair); per-pair partial
-// sums are added across A-scans with Neumaier compensation.
+// A^T r (adjoint of eq. 13).  Thread = pixel.  A persistent grid of one CTA
+// per SM holds the pulse table in shared memory once; each CTA runs two
+// independent tile workers (16 x 32 pixels each, synchronised by their own
+// named barrier) that take work items = (pixel tile, group of transmitter
+// positions).  A worker walks its A-scans in (Tx, receiver) order, keeping
+// the pixel's transmit leg while the receiver changes.  Residual rows are
+// staged in shared memory by 1-D bulk copies (TMA engine) into a 3-stage ring
+// guarded by mbarriers with bounded waits.  Every tap of a pair shares one
+// table phase, so the tap loop is two packed FP32 FMAs over four dot products,
+// combined once per pair; per-pair sums are added across A-scans with
+// Neumaier compensation.  Each item writes its own partial image; a second
+// kernel adds the groups in a fixed order, so results are reproducible.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace mbir {
 
-constexpr int kBwdRows = 16;
-constexpr int kBwdThreads = kBwdRows * 32;
+constexpr int kBwdRows = 16;                       // rows per tile (one warp per row)
+constexpr int kBwdHalves = 2;                      // tile workers per CTA
+constexpr int kBwdHalfThreads = kBwdRows * 32;
+constexpr int kBwdThreads = kBwdHalves * kBwdHalfThreads;
+constexpr int kBwdStages = 3;
 
-__device__ __forceinline__ uint32_t bar_of(int k, uint32_t b0, uint32_t b1) { return (k & 1) ? b1 : b0; }
+__device__ __forceinline__ void half_barrier(int h)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "n"(kBwdHalfThreads) : "memory");
+}
 
 template <int NL, int MODE, bool BF16>
 __global__ void __launch_bounds__(kBwdThreads, 1)
     backproject_kernel(GeomParams P, DevPtrs D, const typename TabT<BF16>::type* __restrict__ tab_g,
-                       const typename ET<BF16>::type* __restrict__ e_g, float* __restrict__ b_out)
+                       const typename ET<BF16>::type* __restrict__ e_g, const int4* __restrict__ items,
+                       int nitems, float* __restrict__ partial)
 {
     using Tab = typename TabT<BF16>::type;
     using E = typename ET<BF16>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = table_stride(P.Tw4);
     const int R = P.Q + 1;
-    const size_t tab_elems = (size_t)P.Gt * R * S;
-    const size_t tab_bytes = (tab_elems * sizeof(Tab) + 127) & ~(size_t)127;
+    const size_t tab_bytes = ((size_t)P.Gt * R * S * sizeof(Tab) + 127) & ~(size_t)127;
     const size_t ebytes = ((size_t)P.Mp * sizeof(E) + 127) & ~(size_t)127;
     Tab* tab = reinterpret_cast<Tab*>(smem);
-    E* ebuf0 = reinterpret_cast<E*>(smem + tab_bytes);
-    E* ebuf1 = reinterpret_cast<E*>(smem + tab_bytes + ebytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tab_bytes + 2 * ebytes);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int h = warp / kBwdRows, hw = warp % kBwdRows, ht = tid % kBwdHalfThreads;
+    E* ering = reinterpret_cast<E*>(smem + tab_bytes + (size_t)h * kBwdStages * ebytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tab_bytes + (size_t)kBwdHalves * kBwdStages * ebytes);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + kBwdHalves * kBwdStages) + h;
+    const uint32_t bar0 = smem_u32(bars + h * kBwdStages);
+    const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
+    const int N = P.W * P.H;
 
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int col = blockIdx.x * 32 + lane;
-    const int row = blockIdx.y * kBwdRows + warp;
-    const int row0 = blockIdx.y * kBwdRows;
-
-    // rows are ordered by depth, so the vertical time grows with the row:
-    // a tile whose first row cannot reach the record has nothing to do
-    if (__ldg(&D.rows[row0].tvert) >= (float)(P.M - 1)) {
-        if (col < P.W && row < P.H) b_out[(size_t)row * P.W + col] = 0.0f;
-        return;
-    }
-    const bool pix_ok = col < P.W && row < P.H;
-    RowInfo ri = load_row(D.rows, pix_ok ? row : row0);
-    const bool row_ok = pix_ok && ri.tvert < (float)(P.M - 1);
-
-    // pulse table -> shared
     {
         const int4* src = reinterpret_cast<const int4*>(tab_g);
         int4* dst = reinterpret_cast<int4*>(tab);
         const int n16 = (int)(tab_bytes / 16);
-        for (int t = tid; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
+        for (int t = tid; t < n16; t += kBwdThreads) dst[t] = __ldg(src + t);
     }
-    const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
-    const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
     if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        *abort_flag = 0;
+        for (int b = 0; b < kBwdHalves * kBwdStages; ++b) mbar_init(smem_u32(bars + b), 1);
+        for (int b = 0; b < kBwdHalves; ++b) reinterpret_cast<volatile int*>(bars + kBwdHalves * kBwdStages)[b] = 0;
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar0, rowbytes);
-        bulk_g2s(smem_u32(ebuf0), e_g, rowbytes, bar0);
-        if (P.K > 1) {
-            mbar_arrive_expect_tx(bar1, rowbytes);
-            bulk_g2s(smem_u32(ebuf1), e_g + (size_t)P.Mp, rowbytes, bar1);
-        }
-    }
 
-    float sum = 0.0f, comp = 0.0f;
-    Leg tx = {0.f, 0.f, 0.f, 0.f};
-    int i = 0, j = 0;
-    for (int k = 0; k < P.K; ++k) {
-        if (row_ok) {
-            if (j == 0) tx = get_leg<NL, MODE>(P, D, ri, row, col, __ldg(D.txpos + i));
-            Leg rx = get_leg<NL, MODE>(P, D, ri, row, col, __ldg(D.rxpos + k));
-            Pair pr = make_pair(P, tx, rx, ri.tau);
-            const bool act = pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M;
-            const uint32_t bar = (k & 1) ? bar1 : bar0;
-            bool ok = mbar_wait_bounded(bar, (uint32_t)((k >> 1) & 1), D.status);
+    uint32_t par = 0;                    // expected phase parity per stage (bit s)
+    bool aborted = false;
+    for (int it = blockIdx.x * kBwdHalves + h; it < nitems && !aborted; it += gridDim.x * kBwdHalves) {
+        const int4 item = __ldg(items + it);
+        const int row = item.x * kBwdRows + hw, col = item.y * 32 + lane;
+        const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
+        const bool pix_ok = col < P.W && row < P.H;
+        const RowInfo ri = load_row(D.rows, min(row, P.H - 1));
+        const bool row_ok = pix_ok && ri.tvert < (float)(P.M - 1);
+        const int colc = min(col, P.W - 1);
+        const int ka = tx0 * P.n_rx, kb = tx1 * P.n_rx;
+        if (ht == 0) {
+            for (int s = 0; s < kBwdStages && ka + s < kb; ++s) {
+                mbar_arrive_expect_tx(bar0 + 8 * s, rowbytes);
+                bulk_g2s(smem_u32(ering + (size_t)s * (ebytes / sizeof(E))), e_g + (size_t)(ka + s) * P.Mp,
+                         rowbytes, bar0 + 8 * s);
+            }
+        }
+        float sum = 0.0f, comp = 0.0f;
+        Leg tx = {0.f, 0.f, 0.f, 0.f}, rx_cur = tx, rx_nxt = tx;
+        int hx_nxt = 0;
+        if constexpr (MODE == kModeTAB) {
+            if (row_ok) {
+                rx_cur = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + ka));
+                if (ka + 1 < kb) hx_nxt = __ldg(D.hidx + (size_t)__ldg(D.rxpos + ka + 1) * P.W + colc);
+            }
+        }
+        int i = tx0, j = 0, stage = 0, k = ka;
+        for (; k < kb; ++k) {
+            if constexpr (MODE == kModeTAB) {
+                // legs of the next A-scan stream in while this one is consumed
+                if (row_ok && k + 1 < kb) {
+                    float4 v = __ldg(D.legs + (size_t)row * P.nh + hx_nxt);
+                    rx_nxt = Leg{v.x, v.y, v.z, v.w};
+                    if (k + 2 < kb) hx_nxt = __ldg(D.hidx + (size_t)__ldg(D.rxpos + k + 2) * P.W + colc);
+                }
+            }
+            if (row_ok) {
+                if (j == 0) tx = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.txpos + i));
+                if constexpr (MODE != kModeTAB) rx_cur = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + k));
+            }
+            const Pair pr = make_pair(P, tx, rx_cur, ri.tau);
+            const bool act = row_ok && pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M;
+            const bool ok = mbar_wait_bounded(bar0 + 8 * stage, (par >> stage) & 1u, D.status);
+            par ^= 1u << stage;
             if (!ok) *abort_flag = 1;
             if (act && ok) {
-                const E* ev = ((k & 1) ? ebuf1 : ebuf0) + pr.n0 + 1;
+                const E* ev = ering + (size_t)stage * (ebytes / sizeof(E)) + pr.n0 + 1;
                 const Tab* A = tab + (size_t)(pr.gi * R + pr.r) * S;
                 const Tab* B = A + S;
                 float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
                 for (int m = 0; m < P.Tw4; m += 4) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        float e = ET<BF16>::ld(ev + m + u);
-                        float2 ee = make_float2(e, e);
+                        const float e = ET<BF16>::ld(ev + m + u);
+                        const float2 ee = make_float2(e, e);
                         sa = __ffma2_rn(TabT<BF16>::ld(A + m + u), ee, sa);
                         sb = __ffma2_rn(TabT<BF16>::ld(B + m + u), ee, sb);
                     }
                 }
                 const float p1 = pr.psi, p0 = 1.0f - pr.psi;
-                float h = pr.w0 * (p0 * sa.x + p1 * sa.y) + pr.w1 * (p0 * sb.x + p1 * sb.y);
+                float hv = pr.w0 * (p0 * sa.x + p1 * sa.y) + pr.w1 * (p0 * sb.x + p1 * sb.y);
                 if (pr.flag0) {
                     // tau = t0 exactly: outside the open window of eq. 10
-                    float2 bl = TabT<BF16>::ld(B + P.Tw - 1);
-                    h -= pr.w1 * (p0 * bl.x + p1 * bl.y) * ET<BF16>::ld(ev + P.Tw - 1);
+                    const float2 bl = TabT<BF16>::ld(B + P.Tw - 1);
+                    hv -= pr.w1 * (p0 * bl.x + p1 * bl.y) * ET<BF16>::ld(ev + P.Tw - 1);
                 }
-                float val = pr.w * h;
-                float t = sum + val;
+                const float val = pr.w * hv;
+                const float t = sum + val;
                 comp += (fabsf(sum) >= fabsf(val)) ? (sum - t) + val : (val - t) + sum;
                 sum = t;
             }
-        } else {
-            const uint32_t bar = (k & 1) ? bar1 : bar0;
-            if (!mbar_wait_bounded(bar, (uint32_t)((k >> 1) & 1), D.status)) *abort_flag = 1;
+            half_barrier(h);
+            if (*abort_flag) {
+                aborted = true;
+                break;
+            }
+            if (ht == 0 && k + kBwdStages < kb) {
+                mbar_arrive_expect_tx(bar0 + 8 * stage, rowbytes);
+                bulk_g2s(smem_u32(ering + (size_t)stage * (ebytes / sizeof(E))),
+                         e_g + (size_t)(k + kBwdStages) * P.Mp, rowbytes, bar0 + 8 * stage);
+            }
+            if constexpr (MODE == kModeTAB) rx_cur = rx_nxt;
+            if (++stage == kBwdStages) stage = 0;
+            if (++j == P.n_rx) { j = 0; ++i; }
         }
-        __syncthreads();
-        if (*abort_flag) {
-            if (tid == 0) {
-                // drain the copies still in flight (rows k and k+1) before exiting
-                mbar_wait_bounded(bar_of(k, bar0, bar1), (uint32_t)((k >> 1) & 1), D.status);
-                if (k + 1 < P.K)
-                    mbar_wait_bounded(bar_of(k + 1, bar0, bar1), (uint32_t)(((k + 1) >> 1) & 1), D.status);
+        if (aborted) {
+            // drain this item's copies still in flight (bounded) before leaving
+            if (ht == 0) {
+                for (int q = k + 1; q < kb && q < k + kBwdStages; ++q) {
+                    const int s = (q - ka) % kBwdStages;
+                    mbar_wait_bounded(bar0 + 8 * s, (par >> s) & 1u, D.status);
+                    par ^= 1u << s;
+                }
             }
             break;
         }
-        if (tid == 0 && k + 2 < P.K) {
-            const uint32_t bar = (k & 1) ? bar1 : bar0;
-            mbar_arrive_expect_tx(bar, rowbytes);
-            bulk_g2s(smem_u32((k & 1) ? ebuf1 : ebuf0), e_g + (size_t)(k + 2) * P.Mp, rowbytes, bar);
-        }
-        if (++j == P.n_rx) { j = 0; ++i; }
+        if (pix_ok) partial[(size_t)grp * N + (size_t)row * P.W + col] = sum + comp;
     }
-    if (pix_ok) b_out[(size_t)row * P.W + col] = sum + comp;
+}
+
+// b = sum over transmitter groups of the partial images (fixed order,
+// compensated); pixels of tiles that cannot reach the record are zero.
+__global__ void backproject_reduce_kernel(GeomParams P, const RowInfo* __restrict__ rows,
+                                          const float* __restrict__ partial, int ngroups, float* __restrict__ b)
+{
+    const int N = P.W * P.H;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const int row = v / P.W;
+    const int row0 = (row / kBwdRows) * kBwdRows;
+    if (__ldg(&rows[row0].tvert) >= (float)(P.M - 1)) {
+        b[v] = 0.0f;
+        return;
+    }
+    float s = 0.0f, c = 0.0f;
+    for (int g = 0; g < ngroups; ++g) {
+        const float val = partial[(size_t)g * N + v];
+        const float t = s + val;
+        c += (fabsf(s) >= fabsf(val)) ? (s - t) + val : (val - t) + s;
+        s = t;
+    }
+    b[v] = s + c;
 }
 
 size_t backproject_smem(const mbir_geometry* g)
@@ -145,8 +195,10 @@ size_t backproject_smem(const mbir_geometry* g)
     size_t tsz = P.precision == MBIR_PREC_BF16 ? 4 : 8;
     size_t tab = ((size_t)P.Gt * (P.Q + 1) * table_stride(P.Tw4) * tsz + 127) & ~(size_t)127;
     size_t eb = ((size_t)P.Mp * esz + 127) & ~(size_t)127;
-    return tab + 2 * eb + 64;
+    return tab + (size_t)kBwdHalves * kBwdStages * eb + 8 * kBwdHalves * kBwdStages + 16;
 }
+
+int backproject_tile_rows() { return kBwdRows; }
 
 template <int NL, int MODE, bool BF16>
 static cudaError_t launch_bwd_t(const mbir_geometry* g, const DevPtrs& D, const void* e, float* b, cudaStream_t st)
@@ -156,10 +208,17 @@ static cudaError_t launch_bwd_t(const mbir_geometry* g, const DevPtrs& D, const 
     auto kern = backproject_kernel<NL, MODE, BF16>;
     cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (ce != cudaSuccess) return ce;
-    dim3 grid((P.W + 31) / 32, (P.H + kBwdRows - 1) / kBwdRows);
     using Tab = typename TabT<BF16>::type;
     const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
-    kern<<<grid, kBwdThreads, sm, st>>>(P, D, tab, (const typename ET<BF16>::type*)e, b);
+    if (g->n_items > 0) {
+        int grid = std::min(g->n_sm, (g->n_items + kBwdHalves - 1) / kBwdHalves);
+        kern<<<grid, kBwdThreads, sm, st>>>(P, D, tab, (const typename ET<BF16>::type*)e, g->d_items, g->n_items,
+                                            g->w_bpart);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return ce;
+    }
+    const int N = P.W * P.H;
+    backproject_reduce_kernel<<<(N + 255) / 256, 256, 0, st>>>(P, g->d_rows, g->w_bpart, g->n_groups, b);
     return cudaGetLastError();
 }
 

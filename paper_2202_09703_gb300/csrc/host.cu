@@ -80,7 +80,7 @@ int validate(const mbir_geometry_desc* d)
     if (d->img_w < 1 || d->img_h < 1 || d->img_h > 32767 || !(d->pitch_m > 0) || !(d->img_z0_m >= 0) ||
         !std::isfinite(d->img_x0_m))
         return MBIR_ERR_INVALID_ARG;
-    if (d->n_tx < 1 || d->n_rx < 1 || !d->tx_x_m || !d->rx_offset_m) return MBIR_ERR_INVALID_ARG;
+    if (d->n_tx < 1 || d->n_rx < 1 || d->n_tx > 65535 || !d->tx_x_m || !d->rx_offset_m) return MBIR_ERR_INVALID_ARG;
     if (!(d->fs_hz > 0) || d->n_samples < 1 || !(d->fc_hz > 0) || !(d->n_cycles > 0) || !(d->beta >= 0))
         return MBIR_ERR_INVALID_ARG;
     if (d->gamma_max_s < 0 || d->gamma_bins < 0 || d->gamma_bins == 1 || d->phases < 0 ||
@@ -168,7 +168,8 @@ void free_geometry(mbir_geometry* g)
     void* ptrs[] = {g->d_rows, g->d_colx, g->d_pos, g->d_txpos, g->d_rxpos, g->d_tab, g->d_tab_bf16,
                     g->d_legs, g->d_hidx, g->d_direct, g->d_dinv, g->d_status, g->w_e, g->w_q,
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
-                    g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist};
+                    g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
+                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::prof_release(g);
     free(g->tab_host);
@@ -419,7 +420,48 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
         cudaFree(d_hv);
         if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
     }
+    {
+        // A^T r work list: active 16-row tiles x 32-column tiles x transmitter groups,
+        // enough items for a few rounds of two workers per SM
+        cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, g->device);
+        if (g->n_sm < 1) g->n_sm = 1;
+        const int TR = mbir::backproject_tile_rows();
+        const int ntr = (P.H + TR - 1) / TR, ntc = (P.W + 31) / 32;
+        int active_tiles = 0;
+        for (int tr = 0; tr < ntr; ++tr)
+            if (rows[tr * TR].tvert < (float)(P.M - 1)) active_tiles += ntc;
+        int ngroups = 1;
+        if (active_tiles > 0) {
+            ngroups = (8 * g->n_sm + active_tiles - 1) / active_tiles;
+            ngroups = std::max(1, std::min(ngroups, P.n_tx));
+        }
+        const int txg = (P.n_tx + ngroups - 1) / ngroups;
+        ngroups = (P.n_tx + txg - 1) / txg;
+        std::vector<int4> items;
+        for (int tr = 0; tr < ntr; ++tr) {
+            if (!(rows[tr * TR].tvert < (float)(P.M - 1))) continue;
+            for (int tc = 0; tc < ntc; ++tc)
+                for (int gi = 0; gi < ngroups; ++gi) {
+                    int t0 = gi * txg, t1 = std::min(P.n_tx, t0 + txg);
+                    items.push_back(make_int4(tr, tc, t0 | (t1 << 16), gi));
+                }
+        }
+        g->n_items = (int)items.size();
+        g->n_groups = ngroups;
+        UP(g->d_items, items);
+        ce = cudaMalloc((void**)&g->w_bpart, sizeof(float) * (size_t)ngroups * P.W * P.H);
+        if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
+        bytes += sizeof(float) * (size_t)ngroups * P.W * P.H;
+    }
 #undef UP
+    if (P.mode == MBIR_MODE_TAB && !(d->flags & MBIR_FLAG_NO_RECORDS)) {
+        size_t freeb = 0, totalb = 0;
+        cudaMemGetInfo(&freeb, &totalb);
+        size_t cap = std::min<size_t>(freeb / 2, (size_t)64 << 30);
+        ce = mbir::build_sorted_records(g, st, cap);
+        if (ce == cudaErrorNotSupported) ce = cudaSuccess;     // keep the on-the-fly record path
+        if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
+    }
     ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
     g->bytes = bytes;

@@ -285,6 +285,17 @@ struct mbir_geometry {
     double gamma_max;
     double fs;
     double z0, pitch;
+    // A^T r work list: (tile row, tile column, Tx range, group) and per-group partial images
+    int n_sm;
+    int n_items, n_groups;
+    int4* d_items;
+    float* w_bpart;
+    // TAB-mode A x records sorted by first tap sample (see forward_tab.cu)
+    long long* d_rec_off;
+    int2* d_rec_key;
+    float4* d_rec_w;
+    int2* d_runs;
+    long long n_records;
     // profiling of the apply kernels inside mbir_reconstruct
     int prof;
     void* prof_state;      // host-side event lists (see map.cu)
@@ -306,6 +317,10 @@ cudaError_t launch_pair_quantities(const mbir_geometry* g, const int* pix, const
                                    double* T, float* gam, float* w, cudaStream_t st);
 void prof_release(mbir_geometry* g);
 cudaError_t launch_count_taps(const mbir_geometry* g, unsigned long long* d_out, cudaStream_t st);
+cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_bytes);
+cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
+                                  cudaStream_t st);
 size_t backproject_smem(const mbir_geometry* g);
+int backproject_tile_rows();
 size_t forward_smem(const mbir_geometry* g, int* cb_out);
 }  // namespace mbir

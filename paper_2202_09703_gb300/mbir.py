@@ -42,8 +42,11 @@ class GeometryDesc(C.Structure):
         ("fc_hz", C.c_double), ("n_cycles", C.c_double),
         ("beta", C.c_double), ("direct_arrival", C.c_int),
         ("gamma_max_s", C.c_double), ("gamma_bins", C.c_int), ("phases", C.c_int),
-        ("precision", C.c_int), ("mode", C.c_int),
+        ("precision", C.c_int), ("mode", C.c_int), ("flags", C.c_int),
     ]
+
+
+FLAG_NO_RECORDS = 1
 
 
 class Prior(C.Structure):
@@ -128,7 +131,7 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def desc_from_scene(scene, mode: str = "auto", precision: str | None = None):
+def desc_from_scene(scene, mode: str = "auto", precision: str | None = None, flags: int = 0):
     d = GeometryDesc()
     n = len(scene.layers)
     d.n_layers = n
@@ -149,6 +152,7 @@ def desc_from_scene(scene, mode: str = "auto", precision: str | None = None):
     d.gamma_max_s, d.gamma_bins, d.phases = scene.gamma_max, scene.G, scene.Q
     d.precision = PRECISIONS[precision or scene.precision]
     d.mode = MODES[mode]
+    d.flags = flags
     return d, (tx, rx)
 
 
@@ -160,10 +164,11 @@ def prior_struct(scene, sigma_noise: float) -> Prior:
 class Geometry:
     """A geometry handle: device tables of one scan (see include/mbir.h)."""
 
-    def __init__(self, scene, mode: str = "auto", precision: str | None = None, stream=None):
+    def __init__(self, scene, mode: str = "auto", precision: str | None = None, stream=None,
+                 records: bool = True):
         self.scene = scene
         self._lib = lib()
-        desc, self._keep = desc_from_scene(scene, mode, precision)
+        desc, self._keep = desc_from_scene(scene, mode, precision, 0 if records else FLAG_NO_RECORDS)
         h = C.c_void_p()
         _check(self._lib.mbir_create_geometry(C.byref(desc), _stream_ptr(stream), C.byref(h)),
                "mbir_create_geometry")

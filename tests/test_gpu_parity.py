@@ -26,7 +26,14 @@ B.build()
 from paper_2202_09703_gb300 import mbir as M  # noqa: E402
 
 DEV = torch.device("cuda:0")
-MODES = ["otf", "tab"]
+MODES = ["otf", "tab", "tab-norec"]
+
+
+def make_geo(s, mode="auto", **kw):
+    """'tab-norec' is TAB mode without the sorted record list (on-the-fly A x records)."""
+    if mode == "tab-norec":
+        return M.Geometry(s, mode="tab", records=False, **kw)
+    return M.Geometry(s, mode=mode, **kw)
 
 
 def to_dev(a, dtype=torch.float32):
@@ -67,7 +74,7 @@ def test_pulse_table_matches_oracle(cfg):
 @pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene])
 def test_pair_delays_weights_attenuation(mode, scene_fn):
     s = scene_fn()
-    geo = M.Geometry(s, mode=mode)
+    geo = make_geo(s, mode)
     plan = O.Plan(s)
     pix = np.repeat(np.arange(s.N), s.K)
     ks = np.tile(np.arange(s.K), s.N)
@@ -87,7 +94,7 @@ def test_pair_delays_weights_attenuation(mode, scene_fn):
                                       lambda: S.small_scene(n_layers=1, w=32, h=16, n_tx=2, n_rx=3, M=200)])
 def test_forward_parity(mode, scene_fn):
     s = scene_fn()
-    geo = M.Geometry(s, mode=mode)
+    geo = make_geo(s, mode)
     plan = O.Plan(s)
     for x in (S.phantom(s, 1), S.random_vector(s.N, 2).reshape(s.img_h, s.img_w)):
         y_ref = plan.forward(x)
@@ -99,7 +106,7 @@ def test_forward_parity(mode, scene_fn):
 @pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene])
 def test_backproject_parity(mode, scene_fn):
     s = scene_fn()
-    geo = M.Geometry(s, mode=mode)
+    geo = make_geo(s, mode)
     plan = O.Plan(s)
     r = S.random_vector(s.K * s.M, 3)
     b_ref = plan.backproject(r)
@@ -110,7 +117,7 @@ def test_backproject_parity(mode, scene_fn):
 @pytest.mark.parametrize("mode", MODES)
 def test_adjoint_identity_on_gpu(mode):
     s = S.cfg0()
-    geo = M.Geometry(s, mode=mode)
+    geo = make_geo(s, mode)
     x = S.random_vector(s.N, 4)
     r = S.random_vector(s.K * s.M, 5)
     Ax = gpu_forward(geo, x).reshape(-1)
@@ -119,21 +126,26 @@ def test_adjoint_identity_on_gpu(mode):
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
-def test_outputs_are_bitwise_reproducible():
+@pytest.mark.parametrize("mode", MODES)
+def test_outputs_are_bitwise_reproducible(mode):
     s = S.cfg0()
-    geo = M.Geometry(s, mode="tab")
+    geo = make_geo(s, mode)
     x = S.phantom(s, 0)
     r = S.random_vector(s.K * s.M, 6)
     assert np.array_equal(gpu_forward(geo, x), gpu_forward(geo, x))
     assert np.array_equal(gpu_backproject(geo, r), gpu_backproject(geo, r))
+    # a second handle of the same geometry gives the same bits
+    geo2 = make_geo(s, mode)
+    assert np.array_equal(gpu_forward(geo, x), gpu_forward(geo2, x))
 
 
 def test_otf_and_tab_modes_agree():
     s = S.cfg0()
     x = S.phantom(s, 3)
-    a = gpu_forward(M.Geometry(s, mode="otf"), x)
-    b = gpu_forward(M.Geometry(s, mode="tab"), x)
-    assert rel_l2(a, b) <= 2e-6
+    a = gpu_forward(make_geo(s, "otf"), x)
+    b = gpu_forward(make_geo(s, "tab"), x)
+    c = gpu_forward(make_geo(s, "tab-norec"), x)
+    assert rel_l2(a, b) <= 2e-6 and rel_l2(c, b) <= 2e-6
 
 
 def test_bf16_storage_within_stated_error():
@@ -150,23 +162,26 @@ def test_bf16_storage_within_stated_error():
 # full-size cfg1 (the benchmark's launch configuration) on sampled outputs
 # --------------------------------------------------------------------------
 @pytest.fixture(scope="module")
-def cfg1_geo():
+def cfg1_plan():
     s = S.cfg1()
-    return s, M.Geometry(s)
+    return s, O.Plan(s)
 
 
-def test_cfg1_forward_sampled_ascans(cfg1_geo):
-    s, geo = cfg1_geo
-    x = S.phantom(s, 0)
-    y = gpu_forward(geo, x)
-    plan = O.Plan(s)
-    for k in (0, 517, s.K - 1):
-        y_ref = plan.forward(x, k, k + 1)[0]
-        assert rel_l2(y[k], y_ref) <= 1e-5
+@pytest.mark.parametrize("mode", MODES)
+def test_cfg1_forward_sampled_ascans(cfg1_plan, mode):
+    s, plan = cfg1_plan
+    geo = make_geo(s, mode)
+    for x in (S.phantom(s, 0), S.random_vector(s.N, 12).reshape(s.img_h, s.img_w)):
+        y = gpu_forward(geo, x)
+        for k in (0, 517, s.K - 1):
+            y_ref = plan.forward(x, k, k + 1)[0]
+            assert rel_l2(y[k], y_ref) <= 1e-5
 
 
-def test_cfg1_backproject_sampled_pixels(cfg1_geo):
-    s, geo = cfg1_geo
+@pytest.mark.parametrize("mode", MODES)
+def test_cfg1_backproject_sampled_pixels(mode):
+    s = S.cfg1()
+    geo = make_geo(s, mode)
     r = S.random_vector(s.K * s.M, 8)
     b = gpu_backproject(geo, r)
     rng = S.SplitMix64(99)
