@@ -8,9 +8,11 @@
 // window reaches the span are then one contiguous range, stored as run bounds.
 //
 // The apply kernel is a persistent, barrier-free gather: every warp takes
-// whole spans, stages 32 records at a time in its own shared-memory slot
-// (multiplying in x), and each lane accumulates the taps that land on its
-// sample.  Output samples are owned by one lane: no atomics, fixed order.
+// whole spans (largest first, from a counter), decodes 32 records at a time
+// into its own shared-memory slot (first tap, tap count, table offset, and
+// weights times x) while the next 32 stream into registers, and each lane
+// accumulates the taps that land on its sample.  Output samples are owned by
+// one lane and summed in record order: no atomics on data, fixed order.
 #include <algorithm>
 #include <vector>
 
@@ -134,7 +136,8 @@ template <bool BF16>
 __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     forward_sorted_kernel(GeomParams P, const typename TabT<BF16>::type* __restrict__ tab_g,
                           const long long* __restrict__ off, const int2* __restrict__ rkey,
-                          const float4* __restrict__ rw, const int2* __restrict__ runs, const float* __restrict__ x,
+                          const float4* __restrict__ rw, const int2* __restrict__ runs,
+                          const int* __restrict__ order, int* __restrict__ next_span, const float* __restrict__ x,
                           float* __restrict__ y_f32, __nv_bfloat16* __restrict__ y_bf16, int out_stride)
 {
     using Tab = typename TabT<BF16>::type;
@@ -144,8 +147,9 @@ __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     const size_t tab_bytes = ((size_t)P.Gt * (P.Q + 1) * S * sizeof(Tab) + 127) & ~(size_t)127;
     Tab* tab = reinterpret_cast<Tab*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float4* sw = reinterpret_cast<float4*>(smem + tab_bytes) + warp * 32;
-    int* sk = reinterpret_cast<int*>(reinterpret_cast<float4*>(smem + tab_bytes) + WARPS * 32) + warp * 32;
+    // per-warp staging of 32 decoded records: {first tap, tap count, table offset - first tap} and weights * x
+    int4* sr = reinterpret_cast<int4*>(smem + tab_bytes) + warp * 32;
+    float4* sw = reinterpret_cast<float4*>(smem + tab_bytes) + WARPS * 32 + warp * 32;
     {
         const int4* src = reinterpret_cast<const int4*>(tab_g);
         int4* dst = reinterpret_cast<int4*>(tab);
@@ -154,34 +158,52 @@ __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     }
     __syncthreads();
     const int nspan = (P.M + 31) >> 5;
-    const long long total = (long long)P.K * nspan;
-    for (long long gs = (long long)blockIdx.x * WARPS + warp; gs < total; gs += (long long)gridDim.x * WARPS) {
-        const int k = (int)(gs / nspan), sp = (int)(gs - (long long)k * nspan);
+    const int total = P.K * nspan;
+    for (;;) {
+        // spans are handed out largest-first through a counter, one per warp
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(next_span, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= total) break;
+        const int gs = __ldg(order + idx);
+        const int k = gs / nspan, sp = gs - k * nspan;
         const int n = sp * 32 + lane;
         const long long base = __ldg(off + k);
         const int2 rb = __ldg(runs + gs);
         float sum = 0.0f, comp = 0.0f;
+        // register prefetch of the next batch of records
+        int2 kv = make_int2(0, 0);
+        float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+        float xv = 0.0f;
+        if (rb.x + lane < rb.y) {
+            kv = __ldg(rkey + base + rb.x + lane);
+            wv = __ldg(rw + base + rb.x + lane);
+            xv = __ldg(x + kv.x);
+        }
         for (int r0 = rb.x; r0 < rb.y; r0 += 32) {
             const int cnt = min(32, rb.y - r0);
             if (lane < cnt) {
-                const int2 kv = __ldg(rkey + base + r0 + lane);
-                const float4 wv = __ldg(rw + base + r0 + lane);
-                const float xv = __ldg(x + kv.x);
-                sk[lane] = kv.y;
+                const int key = kv.y;
+                const int lo = (key >> kRecShift) + 1;
+                const int len = P.Tw - (key & 1);             // tau = t0 exactly lies outside
+                sr[lane] = make_int4(lo, len, ((key >> 1) & 0xfff) * S - lo, 0);
                 sw[lane] = make_float4(wv.x * xv, wv.y * xv, wv.z * xv, wv.w * xv);
             }
             __syncwarp();
+            if (r0 + 32 + lane < rb.y) {
+                kv = __ldg(rkey + base + r0 + 32 + lane);
+                wv = __ldg(rw + base + r0 + 32 + lane);
+                xv = __ldg(x + kv.x);
+            }
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
             for (int j = 0; j < cnt; ++j) {
-                const int key = sk[j];
-                const int m = n - (key >> kRecShift) - 1;
-                const bool edge = (key & 1) && m == P.Tw - 1;   // tau = t0 exactly: outside
-                if ((unsigned)m < (unsigned)P.Tw && !edge) {
-                    const float4 wv = sw[j];
-                    const Tab* A = tab + (size_t)((key >> 1) & 0xfff) * S + m;
-                    acc = __ffma2_rn(TabT<BF16>::ld(A), make_float2(wv.x, wv.y), acc);
-                    acc = __ffma2_rn(TabT<BF16>::ld(A + S), make_float2(wv.z, wv.w), acc);
+                const int4 d = sr[j];
+                if ((unsigned)(n - d.x) < (unsigned)d.y) {
+                    const float4 w4 = sw[j];
+                    const Tab* A = tab + (d.z + n);
+                    acc = __ffma2_rn(TabT<BF16>::ld(A), make_float2(w4.x, w4.y), acc);
+                    acc = __ffma2_rn(TabT<BF16>::ld(A + S), make_float2(w4.z, w4.w), acc);
                 }
             }
             __syncwarp();
@@ -239,6 +261,21 @@ cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_b
     rec_fill_kernel<<<P.K, kSortThreads, sm, st>>>(P, D, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    // spans in decreasing order of work, so the last spans handed out are short
+    std::vector<int2> runs((size_t)P.K * nspan);
+    e = cudaMemcpy(runs.data(), g->d_runs, sizeof(int2) * runs.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    std::vector<int> order(runs.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return runs[a].y - runs[a].x > runs[b].y - runs[b].x;
+    });
+    e = cudaMalloc((void**)&g->d_span_order, sizeof(int) * order.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_span_order, order.data(), sizeof(int) * order.size(),
+                                         cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->d_span_counter, sizeof(int));
+    if (e == cudaSuccess) g->bytes += sizeof(int) * (order.size() + 1);
     return e;
 }
 
@@ -247,7 +284,7 @@ size_t forward_sorted_smem(const mbir_geometry* g)
     const GeomParams& P = g->P;
     size_t tsz = P.precision == MBIR_PREC_BF16 ? 4 : 8;
     size_t tab = ((size_t)P.Gt * (P.Q + 1) * table_stride(P.Tw4) * tsz + 127) & ~(size_t)127;
-    return tab + (size_t)kFwdSortedThreads * (sizeof(float4) + sizeof(int));
+    return tab + (size_t)kFwdSortedThreads * (sizeof(float4) + sizeof(int4));
 }
 
 cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
@@ -257,18 +294,20 @@ cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float*
     const int nspan = (g->P.M + 31) / 32;
     const long long spans = (long long)g->P.K * nspan;
     const int grid = (int)std::max<long long>(1, std::min<long long>(g->n_sm, (spans + 31) / 32));
+    cudaError_t me = cudaMemsetAsync(g->d_span_counter, 0, sizeof(int), st);
+    if (me != cudaSuccess) return me;
     if (g->P.precision == MBIR_PREC_BF16) {
         auto kern = forward_sorted_kernel<true>;
         cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (ce != cudaSuccess) return ce;
         kern<<<grid, kFwdSortedThreads, sm, st>>>(g->P, g->d_tab_bf16, g->d_rec_off, g->d_rec_key, g->d_rec_w,
-                                                  g->d_runs, x, yf, yb, stride);
+                                                  g->d_runs, g->d_span_order, g->d_span_counter, x, yf, yb, stride);
     } else {
         auto kern = forward_sorted_kernel<false>;
         cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (ce != cudaSuccess) return ce;
         kern<<<grid, kFwdSortedThreads, sm, st>>>(g->P, g->d_tab, g->d_rec_off, g->d_rec_key, g->d_rec_w,
-                                                  g->d_runs, x, yf, yb, stride);
+                                                  g->d_runs, g->d_span_order, g->d_span_counter, x, yf, yb, stride);
     }
     return cudaGetLastError();
 }

@@ -169,7 +169,7 @@ void free_geometry(mbir_geometry* g)
                     g->d_legs, g->d_hidx, g->d_direct, g->d_dinv, g->d_status, g->w_e, g->w_q,
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
                     g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
-                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs};
+                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_span_order, g->d_span_counter};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::prof_release(g);
     free(g->tab_host);
@@ -238,11 +238,13 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
         if (l < d->n_layers) {
             double c = d->speed_mps[l];
             P.k[l] = (float)(c / d->fs_hz);
+            P.kd[l] = split_df(c / d->fs_hz);
             P.s2[l] = split_df((d->fs_hz / c) * (d->fs_hz / c));
             P.eta[l] = split_df(d->thickness_m[l]);
             P.alpha_c[l] = (float)(d->atten_np_per_mhz_m[l] * 1e-6 * gscale);
         } else {
             P.k[l] = 0.f;
+            P.kd[l] = make_float2(0.f, 0.f);
             P.s2[l] = make_float2(0.f, 0.f);
             P.eta[l] = make_float2(0.f, 0.f);
             P.alpha_c[l] = 0.f;

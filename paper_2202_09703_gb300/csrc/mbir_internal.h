@@ -27,6 +27,7 @@ struct GeomParams {
     float gscale;                     // (G-1) / gamma_max (gamma bins per second)
     float inv_gscale;
     float k[kMaxLayers];              // c_l / fs  (m per sample)
+    float2 kd[kMaxLayers];            // c_l / fs as double-float
     float2 s2[kMaxLayers];            // (fs / c_l)^2 as double-float
     float2 eta[kMaxLayers];           // full layer thickness as double-float
     float alpha_c[kMaxLayers];        // alpha_l (s/m) * gscale: gamma-bin units per metre
@@ -111,6 +112,31 @@ __device__ __forceinline__ df df_sqrt(df a)
     return fast_two_sum(r, __fmul_rn(e, __fdividef(0.5f, r)));
 }
 
+__device__ __forceinline__ df df_div(df a, df b)
+{
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df r = df_sub(a, df_mul_f(b, q1));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return fast_two_sum(q1, q2);
+}
+
+// c^beta in double-float for integer beta (binary powering), FP32 otherwise
+__device__ __forceinline__ float pow_beta_df(df c, int beta_int, float beta)
+{
+    if (!(c.hi > 0.0f)) return 0.0f;
+    if (beta_int >= 0) {
+        df r = {1.0f, 0.0f}, b = c;
+        int e = beta_int;
+        while (e) {
+            if (e & 1) r = df_mul(r, b);
+            b = df_mul(b, b);
+            e >>= 1;
+        }
+        return __fadd_rn(r.hi, r.lo);
+    }
+    return powf(c.hi, beta);
+}
+
 __device__ __forceinline__ float pow_beta(float c, int beta_int, float beta)
 {
     if (!(c > 0.0f)) return 0.0f;
@@ -141,10 +167,13 @@ __device__ __forceinline__ df abs_diff(float2 xc, float2 u)
 // One leg (Section 2, eq. 4-6) from a transducer at depth 0 to a voxel of row
 // `ri` at lateral offset h >= 0.  The paper's binary search on theta_1 runs
 // here on the ray parameter p = sin(theta_1) / c_1 (monotone in theta_1), in
-// FP32 with a fixed step count so a warp stays in lockstep.  The travel time
-// then uses the Legendre form T = p h + sum_l eta_l sqrt(s_l^2 - p^2), which is
-// stationary in p, so the FP32 bracket error enters T only at second order;
-// it is evaluated in double-float arithmetic.
+// FP32 with a fixed step count so a warp stays in lockstep; one Newton step on
+// X(p) = sum_l eta_l tan(theta_l) = h in double-float arithmetic then brings p
+// to ~1e-13 relative.  The travel time uses the Legendre form
+// T = p h + sum_l eta_l sqrt(s_l^2 - p^2) (stationary in p), the apodization
+// cos^beta(sum theta_l) is built from the layer angles' cosines and sines by
+// complex multiplication, all in double-float: beta = 8 multiplies the
+// relative error of the cosine by eight.
 // ---------------------------------------------------------------------------
 template <int NL>
 __device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri, df h)
@@ -171,11 +200,36 @@ __device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri,
         lo = below ? mid : lo;
         hi = below ? hi : mid;
     }
-    float p = 0.5f * (lo + hi);
+    df p = {0.5f * (lo + hi), 0.0f};
 
-    df T = df_mul_f(h, p);
-    df p2 = two_prod(p, p);
-    float g = 0.0f, C = 1.0f, S = 0.0f;
+    // Newton step in double-float: p -= (X(p) - h) / X'(p)
+    if (h.hi > 0.0f) {
+        df X = {0.0f, 0.0f};
+        float dX = 0.0f;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            if (l < ri.nl) {
+                float2 e2 = (l < ri.nl - 1) ? P.eta[l] : ri.eta_last;
+                df e = {e2.x, e2.y};
+                df t = df_mul(p, {P.kd[l].x, P.kd[l].y});
+                df c = df_sqrt(df_sub({1.0f, 0.0f}, df_mul(t, t)));
+                if (c.hi > 0.0f) {
+                    X = df_add(X, df_mul(e, df_div(t, c)));
+                    dX += e.hi * P.k[l] / (c.hi * c.hi * c.hi);
+                }
+            }
+        }
+        df diff = df_sub(X, h);
+        if (dX > 0.0f && isfinite(diff.hi)) {
+            float dp = __fdiv_rn(diff.hi, dX);
+            if (fabsf(dp) < 1e-5f * p.hi + 1e-30f) p = df_add(p, {-dp, 0.0f});
+        }
+    }
+
+    df T = df_mul(h, p);
+    df p2 = df_mul(p, p);
+    float g = 0.0f;
+    df C = {1.0f, 0.0f}, Sn = {0.0f, 0.0f};
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         if (l < ri.nl) {
@@ -184,13 +238,11 @@ __device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri,
             df s2 = {P.s2[l].x, P.s2[l].y};
             df sq = df_sqrt(df_sub(s2, p2));
             T = df_add(T, df_mul(e, sq));
-            float t = p * kk[l];
-            float c2 = fmaxf(__fmaf_rn(-t, t, 1.0f), 0.0f);
-            float rc = rsqrtf(c2);
-            g = __fmaf_rn(P.alpha_c[l] * eta[l], rc, g);     // alpha * path length
-            float cth = c2 * rc;                               // cos(theta_l)
-            float Cn = C * cth - S * t;                        // cos, sin of the angle sum
-            S = S * cth + C * t;
+            df t = df_mul(p, {P.kd[l].x, P.kd[l].y});            // sin(theta_l)
+            df c = df_sqrt(df_sub({1.0f, 0.0f}, df_mul(t, t)));   // cos(theta_l)
+            g = __fmaf_rn(P.alpha_c[l] * eta[l], __frcp_rn(fmaxf(c.hi, 1e-30f)), g);  // alpha * path
+            df Cn = df_sub(df_mul(C, c), df_mul(Sn, t));          // cos, sin of the angle sum
+            Sn = df_add(df_mul(Sn, c), df_mul(C, t));
             C = Cn;
         }
     }
@@ -198,7 +250,7 @@ __device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri,
     out.Th = T.hi;
     out.Tl = T.lo;
     out.g = g;
-    out.phi = pow_beta(C, P.beta_int, P.beta);
+    out.phi = pow_beta_df(C, P.beta_int, P.beta);
     return out;
 }
 
@@ -295,6 +347,8 @@ struct mbir_geometry {
     int2* d_rec_key;
     float4* d_rec_w;
     int2* d_runs;
+    int* d_span_order;     // spans by decreasing record count
+    int* d_span_counter;   // work counter of the A x launch
     long long n_records;
     // profiling of the apply kernels inside mbir_reconstruct
     int prof;
@@ -322,5 +376,7 @@ cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float*
                                   cudaStream_t st);
 size_t backproject_smem(const mbir_geometry* g);
 int backproject_tile_rows();
+cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
+                                        float* b, float* partial, cudaStream_t st);
 size_t forward_smem(const mbir_geometry* g, int* cb_out);
 }  // namespace mbir
