@@ -165,6 +165,30 @@ int mbir_forward(const mbir_geometry* g, const float* x_dev, void* y_dev, void* 
  * (BF16 precision).  x_dev: N floats, overwritten. */
 int mbir_backproject(const mbir_geometry* g, const void* r_dev, float* x_dev, void* stream);
 
+/* x = A^T r like mbir_backproject, but without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate at the point of the call - code running during CUDA stream
+ * capture (where cudaMalloc is not allowed), real-time loops that forbid
+ * allocator calls after start-up, and processes with a fixed, pre-sized
+ * memory pool.  (mbir_backproject may allocate its workspace on first use.)
+ * Its scratch (the padded residual rows, K x (M + pulse support + pad)
+ * floats, and one partial image per transmitter group) lives in one fixed
+ * 16 MiB array inside the library, held by every GPU that loads the library
+ * until the process exits.
+ *   - Geometries whose scratch would exceed 16 MiB (for a 256 x 512 image,
+ *     more than about 3 M residual samples) and BF16-precision geometries
+ *     return MBIR_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture begins.  The geometry's device must be current.
+ *   - Every call rewrites the scratch before reading it, so no clearing is
+ *     needed, but all calls share the one array: calls whose work overlaps on
+ *     the GPU (other streams, other host threads) race and must be
+ *     serialised by the caller.
+ * r_dev: K x M floats; x_dev: N floats, overwritten.  Asynchronous on
+ * `stream`; no device memory is allocated or freed. */
+int mbir_backproject_noalloc(const mbir_geometry* g, const float* r_dev, float* x_dev, void* stream);
+
 /* Direct-arrival projection (eq. 1): per A-scan k, g_k = <d_k, r_k>/|d_k|^2
  * and e_k = r_k - g_k d_k, with d_k the unattenuated pulse delayed by
  * |rx_offset_m[j]| / speed_mps[0].  r_dev, e_dev: K x M floats (may alias);

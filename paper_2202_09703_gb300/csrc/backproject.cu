@@ -258,4 +258,46 @@ cudaError_t launch_backproject(const mbir_geometry* g, const float* e_pad, const
     return bf ? launch_bwd_nl<kModeOTF, true>(g, e_bf, b, st) : launch_bwd_nl<kModeOTF, false>(g, e_pad, b, st);
 }
 
+// Same launch as launch_backproject, with the per-group partial images in a
+// caller-provided buffer (n_groups x N floats) instead of the handle's.
+template <int NL, int MODE, bool BF16>
+static cudaError_t launch_bwd_partials_t(const mbir_geometry* g, const void* e, float* b, float* partial,
+                                         cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    size_t sm = backproject_smem(g);
+    auto kern = backproject_kernel<NL, MODE, BF16>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce != cudaSuccess) return ce;
+    using Tab = typename TabT<BF16>::type;
+    const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
+    if (g->n_items > 0) {
+        int grid = std::min(g->n_sm, (g->n_items + kBwdHalves - 1) / kBwdHalves);
+        kern<<<grid, kBwdThreads, sm, st>>>(P, dev_ptrs(g), tab, (const typename ET<BF16>::type*)e, g->d_items,
+                                            g->n_items, partial);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return ce;
+    }
+    const int N = P.W * P.H;
+    backproject_reduce_kernel<<<(N + 255) / 256, 256, 0, st>>>(P, g->d_rows, partial, g->n_groups, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
+                                        float* b, float* partial, cudaStream_t st)
+{
+    const bool bf = g->P.precision == MBIR_PREC_BF16;
+    if (g->P.mode == MBIR_MODE_TAB)
+        return bf ? launch_bwd_partials_t<1, kModeTAB, true>(g, e_bf, b, partial, st)
+                  : launch_bwd_partials_t<1, kModeTAB, false>(g, e_pad, b, partial, st);
+    if (g->P.L <= 2)
+        return bf ? launch_bwd_partials_t<2, kModeOTF, true>(g, e_bf, b, partial, st)
+                  : launch_bwd_partials_t<2, kModeOTF, false>(g, e_pad, b, partial, st);
+    if (g->P.L <= 4)
+        return bf ? launch_bwd_partials_t<4, kModeOTF, true>(g, e_bf, b, partial, st)
+                  : launch_bwd_partials_t<4, kModeOTF, false>(g, e_pad, b, partial, st);
+    return bf ? launch_bwd_partials_t<8, kModeOTF, true>(g, e_bf, b, partial, st)
+              : launch_bwd_partials_t<8, kModeOTF, false>(g, e_pad, b, partial, st);
+}
+
 }  // namespace mbir

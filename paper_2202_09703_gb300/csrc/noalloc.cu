@@ -1,0 +1,69 @@
+// mbir_backproject_noalloc: A^T r without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they apply
+// the adjoint: code running while a stream is being captured into a CUDA
+// graph (where cudaMalloc is not allowed), real-time loops that forbid
+// allocator calls after start-up, and hosts whose memory pool is sized and
+// locked in advance.  mbir_backproject may allocate its workspace on first
+// use; this entry point instead takes its scratch from one fixed array that
+// is part of the library image.
+//
+// The scratch holds the residual rows padded with a zero tail (K x Mp floats)
+// followed by the per-transmitter-group partial images (groups x N floats).
+// Both are completely rewritten by every call before they are read, so
+// nothing has to be cleared between calls.  The array is shared by all calls
+// in the process: two calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on it and must be serialised by
+// the caller.
+#include <mutex>
+
+#include "device_common.cuh"
+
+namespace {
+
+// 16 MiB of scratch, held by every GPU that loads the library until exit.
+constexpr size_t kNoAllocFloats = (size_t)16 * 1024 * 1024 / sizeof(float);
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+float* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on `dev` (the current device).  The
+// host-side symbol is only a stand-in, so the address is looked up once per
+// device and cached.
+cudaError_t scratch_for(int dev, float** out)
+{
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int mbir_backproject_noalloc(const mbir_geometry* g, const float* r_dev, float* x_dev, void* stream)
+{
+    if (!g || !r_dev || !x_dev) return MBIR_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device || dev < 0 || dev >= kMaxDevices)
+        return MBIR_ERR_INVALID_ARG;
+    if (g->P.precision != MBIR_PREC_FP32) return MBIR_ERR_UNSUPPORTED;
+    const size_t rows = (size_t)g->P.K * g->P.Mp;
+    const size_t parts = (size_t)g->n_groups * g->P.W * g->P.H;
+    if (rows + parts > kNoAllocFloats) return MBIR_ERR_UNSUPPORTED;   // beyond the fixed 16 MiB
+    float* scratch = nullptr;
+    if (scratch_for(dev, &scratch) != cudaSuccess) return MBIR_ERR_CUDA;
+    float* e_pad = scratch;
+    float* partial = scratch + ((rows + 63) & ~(size_t)63);
+    if ((size_t)(partial - scratch) + parts > kNoAllocFloats) return MBIR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = mbir::launch_pad_rows(g, r_dev, 0, e_pad, st);
+    if (e == cudaSuccess) e = mbir::launch_backproject_partials(g, e_pad, nullptr, x_dev, partial, st);
+    return e == cudaSuccess ? MBIR_OK : MBIR_ERR_CUDA;
+}
