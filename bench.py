@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
+SMEM_BYTES_PER_CLK = 128           # shared-memory load bandwidth per SM per clock
 WORKLOAD = ("4-layer water/steel/cement/rock, 256x512 image @0.5 mm, 64 Tx x 16 Rx, 2048 samples "
             "@20 MHz, 2 MHz pulse, direct arrivals, depth-varying QGGMRF prior, 50 MAP iterations")
 
@@ -46,6 +47,23 @@ def parse():
     ap.add_argument("--apply-only", type=int, default=0,
                     help="run only A x and A^T r this many times (for profiler captures) and exit")
     return ap.parse_args()
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    import hashlib
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            if line.startswith("#") or not line.strip():
+                continue
+            name, src, sha, rd, wr = line.split()[:5]
+            if name.startswith(kernel):
+                cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+                return float(rd) + float(wr) if cur == sha else None
+    except OSError:
+        return None
+    return None
 
 
 def peaks():
@@ -280,7 +298,10 @@ def run_gpu(args):
     e2e = {"value": args.steps * world / e_wall, "unit": "recons/s",
            "h2d_bytes_per_step": y_h.numel() * 4, "d2h_bytes_per_step": (x_h.numel() + g_h.numel()) * 4}
 
-    # roofline of the dominant apply kernel
+    # roofline of the dominant apply kernel.  Each tap reads the four bilinear
+    # corners of the pulse table (4 x 4 B) from shared memory and does 4 FMA;
+    # shared-memory bandwidth (128 B/clk/SM) binds before the FP32 pipes
+    # (128 FMA/clk/SM) do, so it is the primary roofline.
     pk, src = peaks()
     pairs, taps = geo.count_taps()
     fwd_ms = kt["forward_ms"] / max(kt["forward_launches"], 1)
@@ -288,16 +309,22 @@ def run_gpu(args):
     dom, dom_ms = ("forward", fwd_ms) if fwd_ms >= bwd_ms else ("backproject", bwd_ms)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
-    flops = 8.0 * taps                                   # 4 FMA per tap (bilinear table read)
-    achieved = flops / (dom_ms * 1e-3) / 1e12
-    algo_bytes = 4.0 * (N + K * Mn)                      # x and one A-scan array
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
-                "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_mhz:.0f} MHz "
+    smem_peak = sm_count * SMEM_BYTES_PER_CLK * clk_mhz * 1e6 / 1e9            # GB/s
+    smem_bytes = 16.0 * taps
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12       # TFLOP/s
+    flops = 8.0 * taps
+    algo_bytes = 4.0 * (N + K * Mn)                      # x and one A-scan array in HBM
+    roofline = {"bound": "alu", "resource": "shared-memory load bandwidth (pulse-table corners per tap)",
+                "kernel": dom, "achieved": smem_bytes / (dom_ms * 1e-3) / 1e9, "peak": smem_peak,
+                "unit": "GB/s", "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak,
+                "traffic": measured_traffic("forward_sorted_kernel" if dom == "forward" else "backproject_kernel"),
+                "traffic_note": "DRAM read+write bytes per launch (ncu); the kernel streams from L2/shared memory",
+                "peak_source": f"{sm_count} SMs x {SMEM_BYTES_PER_CLK} B/clk x {clk_mhz:.0f} MHz "
                                f"(sm_max_mhz, {src})",
-                "algorithmic_flops_per_launch": flops, "taps_per_launch": taps, "active_pairs": pairs,
+                "algorithmic_bytes_per_launch": smem_bytes, "taps_per_launch": taps, "active_pairs": pairs,
                 "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
+                "fp32": {"algorithmic_flops_per_launch": flops, "achieved_tflops": flops / (dom_ms * 1e-3) / 1e12,
+                         "peak_tflops": fp32_peak, "frac": flops / (dom_ms * 1e-3) / 1e12 / fp32_peak},
                 "hbm": {"algorithmic_bytes_per_launch": algo_bytes,
                         "achieved_gbs": algo_bytes / (dom_ms * 1e-3) / 1e9,
                         "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),
