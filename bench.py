@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--apply-only", type=int, default=0,
                     help="run only A x and A^T r this many times (for profiler captures) and exit")
+    ap.add_argument("--workload", default="cfg1", choices=["cfg1", "batched", "served"],
+                    help="cfg1: the headline workload; batched: uneven scenes through the engine vs serial "
+                         "solves; served: Poisson arrivals of mixed sizes through the engine vs a serial queue")
+    ap.add_argument("--requests", type=int, default=0, help="requests for the batched / served workloads")
     return ap.parse_args()
 
 
@@ -377,8 +381,145 @@ def run_apply_only(args):
                       "b_norm": float(b.norm())}))
 
 
+def _synth_request(M, S, torch, scene, seed, dev, precision=None):
+    """Geometry + synthetic y = A x + D g + w (20 dB) made with the library."""
+    geo = M.Geometry(scene, mode="tab", precision=precision)
+    K, Mn = scene.K, scene.M
+    xt = torch.as_tensor(S.phantom(scene, seed).reshape(-1), dtype=torch.float32, device=dev)
+    y = torch.empty(K * Mn, dtype=torch.float32, device=dev)
+    geo_f = geo if geo.precision == "fp32" else M.Geometry(scene, mode="tab", precision="fp32", records=False)
+    geo_f.forward(xt, y)
+    if scene.direct_arrival:
+        gt = torch.as_tensor(S.direct_gains(scene, seed), dtype=torch.float32, device=dev) * y.abs().max()
+        geo_f.add_direct(gt, y)
+    sig = math.sqrt(float((y.double() ** 2).sum()) / (100.0 * K * Mn)) + 1e-12
+    y += sig * torch.as_tensor(S.unit_noise(scene, seed).reshape(-1), dtype=torch.float32, device=dev)
+    if geo.precision == "bf16":
+        y = y.to(torch.bfloat16)
+    return geo, y, sig
+
+
+def run_batched(args):
+    """Uneven scenes (image sides 64-512, 2-5 layers, 8-32 receivers, 512-4096
+    samples): all submitted at once to the engine, against the same solves run
+    one after another through mbir_reconstruct."""
+    import numpy as np
+    import torch
+    from paper_2202_09703_gb300 import build as B
+    B.build()
+    from paper_2202_09703_gb300 import mbir as M
+    from paper_2202_09703_gb300 import synth as S
+    dev = torch.device("cuda:0")
+    n = args.requests or 96
+    scenes = S.cfg3_scenes(n, seed=0)
+    out = {"workload": f"batched: {n} uneven scenes (cfg3 recipe), 50 iterations each"}
+    for prec in ("fp32", "bf16"):
+        reqs = [_synth_request(M, S, torch, sc, i, dev, precision=prec) for i, sc in enumerate(scenes)]
+        xs = [torch.empty(sc.N, device=dev) for sc in scenes]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if prec == "fp32":
+            for (geo, y, sig), x, sc in zip(reqs, xs, scenes):
+                geo.reconstruct(y, sig, sc.n_iter, x)
+            torch.cuda.synchronize()
+            t_serial = time.perf_counter() - t0
+            x_serial = [x.clone() for x in xs]
+        eng = M.Engine(120 << 30)
+        xe = [torch.empty(sc.N, device=dev) for sc in scenes]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (geo, y, sig), x, sc in zip(reqs, xe, scenes):
+            eng.submit(geo, y, sig, sc.n_iter, x)
+        eng.run_until_idle()
+        torch.cuda.synchronize()
+        t_eng = time.perf_counter() - t0
+        err = max(float((a - b).norm() / max(float(b.norm()), 1e-30)) for a, b in zip(xe, x_serial))
+        out[prec] = {"engine_recons_per_s": n / t_eng, "engine_s": t_eng, "max_rel_diff_vs_serial_fp32": err}
+        if prec == "fp32":
+            out[prec]["serial_recons_per_s"] = n / t_serial
+            out[prec]["serial_s"] = t_serial
+        eng.close()
+        del reqs
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "recons/s", "value": out["bf16"]["engine_recons_per_s"], "unit": "recons/s",
+                      "higher_is_better": True, "data": "synthetic", "config": out}), flush=True)
+
+
+def run_served(args):
+    """Poisson arrivals mixing the three workload sizes (60/30/10 %), each a
+    50-iteration reconstruction, served by the engine (admission capped at
+    120 GB) against a serial FIFO of mbir_reconstruct calls on the same GPU."""
+    import numpy as np
+    import torch
+    from paper_2202_09703_gb300 import build as B
+    B.build()
+    from paper_2202_09703_gb300 import mbir as M
+    from paper_2202_09703_gb300 import synth as S
+    dev = torch.device("cuda:0")
+    n = args.requests or 24
+    classes = [S.cfg0(), S.cfg1(), S.cfg2().copy(precision="fp32")]
+    for c in classes:
+        c.n_iter = 50
+    pool = {ci: _synth_request(M, S, torch, c, ci, dev) for ci, c in enumerate(classes)}
+    rng = S.SplitMix64(4242)
+    results = {}
+    for rate in (20.0, 200.0):
+        u = rng.uniform(n)
+        kinds = np.where(u < 0.6, 0, np.where(u < 0.9, 1, 2))
+        gaps = -np.log(1.0 - rng.uniform(n)) / rate
+        arrive = np.cumsum(gaps)
+        res = {}
+        for mode in ("engine", "serial"):
+            xs = [torch.empty(classes[k].N, device=dev) for k in kinds]
+            done = [None] * n
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "engine":
+                eng = M.Engine(120 << 30)
+                tickets = {}
+                nxt = 0
+                while True:
+                    now = time.perf_counter() - t0
+                    while nxt < n and arrive[nxt] <= now:
+                        geo, y, sig = pool[kinds[nxt]]
+                        tickets[nxt] = eng.submit(geo, y, sig, classes[kinds[nxt]].n_iter, xs[nxt])
+                        nxt += 1
+                    na, nq = eng.step()
+                    for i, t in tickets.items():
+                        if done[i] is None and eng.poll(t) == M.Engine.DONE:
+                            done[i] = time.perf_counter() - t0
+                    if nxt >= n and na == 0 and nq == 0 and all(d is not None for d in done):
+                        break
+                    if na == 0 and nq == 0 and nxt < n:
+                        time.sleep(max(0.0, arrive[nxt] - (time.perf_counter() - t0)))
+                eng.close()
+            else:
+                for i in range(n):
+                    wait = arrive[i] - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(wait)
+                    geo, y, sig = pool[kinds[i]]
+                    geo.reconstruct(y, sig, classes[kinds[i]].n_iter, xs[i])
+                    done[i] = time.perf_counter() - t0
+            lat = np.array(done) - arrive
+            res[mode] = {"recons_per_s": n / max(done), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "makespan_s": float(max(done))}
+        results[f"{rate:g}_req_per_s"] = res
+    cfg = {"workload": f"served: {n} Poisson requests per rate, sizes 64x64 / 256x512 / 512x1024 at 60/30/10 %",
+           "rates": results}
+    best = results["200_req_per_s"]["engine"]["recons_per_s"]
+    print(json.dumps({"metric": "recons/s", "value": best, "unit": "recons/s", "higher_is_better": True,
+                      "data": "synthetic", "config": cfg}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "served":
+        run_served(args)
+        return
     if args.apply_only:
         run_apply_only(args)
     elif args.impl == "reference":

@@ -143,8 +143,10 @@ typedef struct mbir_geometry mbir_geometry;
  * Errors: MBIR_ERR_INVALID_ARG (n_layers outside 1..8, non-positive
  * thickness, speed, density, pitch, fs, fc, n_cycles, beta < 0, negative
  * attenuation, img_z0_m < 0, sizes < 1, NULL arrays, K*M or N above 2^31),
- * MBIR_ERR_OOM, MBIR_ERR_CUDA.  *out is untouched on error.  Synchronises
- * `stream` before returning. */
+ * MBIR_ERR_OOM, MBIR_ERR_CUDA, MBIR_ERR_UNSUPPORTED (the pulse table and two
+ * padded residual rows exceed shared memory: with the default 16 x 16 FP32
+ * table about 11,000 samples per A-scan, twice that in BF16).  *out is
+ * untouched on error.  Synchronises `stream` before returning. */
 int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometry** out);
 
 /* Free the handle and its device memory.  Accepts NULL.  The caller must
@@ -223,6 +225,62 @@ int mbir_reconstruct(const mbir_geometry* g, const void* y_dev, const mbir_prior
 int mbir_reconstruct_host(const mbir_geometry* g, const float* y_host, const mbir_prior* pr,
                           int n_iter, float* x_host, float* g_host, mbir_stats* st,
                           void* stream);
+
+/*
+ * Batched and served reconstructions (continuous batching).
+ *
+ * An engine advances many independent MAP problems (eq. 18) of uneven size
+ * together, one iteration per step; each step is one launch of a captured
+ * CUDA graph of grouped kernels over every active request.  Requests enter
+ * and leave between steps: a queued request is admitted when its device
+ * state fits the engine's byte budget, and retires after its own n_iter
+ * iterations.  A request's result does not depend on which other requests
+ * share its steps.  Geometries must be TAB mode with records (the default for
+ * grid-aligned transducers); all active requests of one engine share one
+ * precision.  An engine and its requests belong to the device current at
+ * creation and are driven from one host thread and one stream.
+ */
+typedef struct mbir_engine mbir_engine;
+
+/* budget_bytes: cap on the device state of admitted requests (their
+ * geometries are owned by the caller and not counted); max_active: cap on
+ * requests per step.  Errors: MBIR_ERR_INVALID_ARG, MBIR_ERR_CUDA. */
+int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out);
+
+/* Waits for the device, frees every request's state and the engine. */
+int mbir_engine_destroy(mbir_engine* e);
+
+/* Queues one reconstruction of y_dev (K x M, float or bfloat16 per the
+ * geometry's precision; must stay valid until the request is done) with
+ * prior `pr` and n_iter iterations.  x_dev (N floats) is the iterate, written
+ * in place from zero; g_dev (K floats, may be NULL) receives the
+ * direct-arrival gains at the end.  *ticket identifies the request.
+ * Errors: MBIR_ERR_INVALID_ARG, MBIR_ERR_UNSUPPORTED (geometry not TAB with
+ * records, table or record length beyond the engine's limits, other device),
+ * MBIR_ERR_BUSY (the request alone exceeds the budget). */
+int mbir_engine_submit(mbir_engine* e, const mbir_geometry* g, const void* y_dev, const mbir_prior* pr, int n_iter,
+                       float* x_dev, float* g_dev, int64_t* ticket);
+
+/* One engine step on `stream`: retire requests that finished, admit queued
+ * requests that fit the budget (arrival order), then one MAP iteration of
+ * every active request.  Asynchronous except for retirement, which reads each
+ * finishing request's status.  *n_active / *n_queued (may be NULL) report the
+ * engine's load after admission. */
+int mbir_engine_step(mbir_engine* e, void* stream, int* n_active, int* n_queued);
+
+/* *state: 0 queued, 1 running, 3 done; a negative MBIR_ERR_* if the request
+ * failed (also returned). */
+int mbir_engine_poll(mbir_engine* e, int64_t ticket, int* state);
+
+/* Steps the engine until the request is done; MBIR_ERR_TIMEOUT if timeout_ms
+ * of host time pass first (the request keeps running). */
+int mbir_engine_wait(mbir_engine* e, int64_t ticket, int timeout_ms, void* stream);
+
+/* Removes a queued or running request (state becomes MBIR_ERR_CANCELLED). */
+int mbir_engine_cancel(mbir_engine* e, int64_t ticket, void* stream);
+
+/* Device bytes of request state currently admitted. */
+size_t mbir_engine_bytes_in_use(const mbir_engine* e);
 
 /* Diagnostics for parity tests: per requested (pixel, A-scan) pair, the
  * device's travel time in samples (double, from its compensated FP32 pair),

@@ -12,15 +12,15 @@
 // kernel adds the groups in a fixed order, so results are reproducible.
 #include <algorithm>
 
-#include "device_common.cuh"
+#include "apply_common.cuh"
 
 namespace mbir {
 
 constexpr int kBwdRows = 16;                       // rows per tile (one warp per row)
-constexpr int kBwdHalves = 2;                      // tile workers per CTA
-constexpr int kBwdHalfThreads = kBwdRows * 32;
-constexpr int kBwdThreads = kBwdHalves * kBwdHalfThreads;
-constexpr int kBwdStages = 3;
+constexpr int kBwdHalfThreads = kBwdRows * 32;     // threads per tile worker
+constexpr int kBwdThreads = 2 * kBwdHalfThreads;   // at most two workers per CTA
+constexpr int kBwdMaxStages = 3;
+constexpr size_t kSmemLimit = 227 * 1024;
 
 __device__ __forceinline__ void half_barrier(int h)
 {
@@ -31,7 +31,7 @@ template <int NL, int MODE, bool BF16>
 __global__ void __launch_bounds__(kBwdThreads, 1)
     backproject_kernel(GeomParams P, DevPtrs D, const typename TabT<BF16>::type* __restrict__ tab_g,
                        const typename ET<BF16>::type* __restrict__ e_g, const int4* __restrict__ items,
-                       int nitems, float* __restrict__ partial)
+                       int nitems, float* __restrict__ partial, int nst)
 {
     using Tab = typename TabT<BF16>::type;
     using E = typename ET<BF16>::type;
@@ -43,10 +43,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
     Tab* tab = reinterpret_cast<Tab*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int h = warp / kBwdRows, hw = warp % kBwdRows, ht = tid % kBwdHalfThreads;
-    E* ering = reinterpret_cast<E*>(smem + tab_bytes + (size_t)h * kBwdStages * ebytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tab_bytes + (size_t)kBwdHalves * kBwdStages * ebytes);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + kBwdHalves * kBwdStages) + h;
-    const uint32_t bar0 = smem_u32(bars + h * kBwdStages);
+    const int halves = blockDim.x / kBwdHalfThreads;
+    E* ering = reinterpret_cast<E*>(smem + tab_bytes + (size_t)h * nst * ebytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tab_bytes + (size_t)halves * nst * ebytes);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + halves * nst) + h;
+    const uint32_t bar0 = smem_u32(bars + h * nst);
     const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
     const int N = P.W * P.H;
 
@@ -54,18 +55,19 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         const int4* src = reinterpret_cast<const int4*>(tab_g);
         int4* dst = reinterpret_cast<int4*>(tab);
         const int n16 = (int)(tab_bytes / 16);
-        for (int t = tid; t < n16; t += kBwdThreads) dst[t] = __ldg(src + t);
+        for (int t = tid; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
     }
     if (tid == 0) {
-        for (int b = 0; b < kBwdHalves * kBwdStages; ++b) mbar_init(smem_u32(bars + b), 1);
-        for (int b = 0; b < kBwdHalves; ++b) reinterpret_cast<volatile int*>(bars + kBwdHalves * kBwdStages)[b] = 0;
+        uint64_t* all_bars = reinterpret_cast<uint64_t*>(smem + tab_bytes + (size_t)halves * nst * ebytes);
+        for (int b = 0; b < halves * nst; ++b) mbar_init(smem_u32(all_bars + b), 1);
+        for (int b = 0; b < halves; ++b) reinterpret_cast<volatile int*>(all_bars + halves * nst)[b] = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
     uint32_t par = 0;                    // expected phase parity per stage (bit s)
     bool aborted = false;
-    for (int it = blockIdx.x * kBwdHalves + h; it < nitems && !aborted; it += gridDim.x * kBwdHalves) {
+    for (int it = blockIdx.x * halves + h; it < nitems && !aborted; it += gridDim.x * halves) {
         const int4 item = __ldg(items + it);
         const int row = item.x * kBwdRows + hw, col = item.y * 32 + lane;
         const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         const int colc = min(col, P.W - 1);
         const int ka = tx0 * P.n_rx, kb = tx1 * P.n_rx;
         if (ht == 0) {
-            for (int s = 0; s < kBwdStages && ka + s < kb; ++s) {
+            for (int s = 0; s < nst && ka + s < kb; ++s) {
                 mbar_arrive_expect_tx(bar0 + 8 * s, rowbytes);
                 bulk_g2s(smem_u32(ering + (size_t)s * (ebytes / sizeof(E))), e_g + (size_t)(ka + s) * P.Mp,
                          rowbytes, bar0 + 8 * s);
@@ -112,48 +114,27 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
             if (act && ok) {
                 const E* ev = ering + (size_t)stage * (ebytes / sizeof(E)) + pr.n0 + 1;
                 const Tab* A = tab + (size_t)(pr.gi * R + pr.r) * S;
-                const Tab* B = A + S;
-                float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
-                for (int m = 0; m < P.Tw4; m += 4) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float e = ET<BF16>::ld(ev + m + u);
-                        const float2 ee = make_float2(e, e);
-                        sa = __ffma2_rn(TabT<BF16>::ld(A + m + u), ee, sa);
-                        sb = __ffma2_rn(TabT<BF16>::ld(B + m + u), ee, sb);
-                    }
-                }
-                const float p1 = pr.psi, p0 = 1.0f - pr.psi;
-                float hv = pr.w0 * (p0 * sa.x + p1 * sa.y) + pr.w1 * (p0 * sb.x + p1 * sb.y);
-                if (pr.flag0) {
-                    // tau = t0 exactly: outside the open window of eq. 10
-                    const float2 bl = TabT<BF16>::ld(B + P.Tw - 1);
-                    hv -= pr.w1 * (p0 * bl.x + p1 * bl.y) * ET<BF16>::ld(ev + P.Tw - 1);
-                }
-                const float val = pr.w * hv;
-                const float t = sum + val;
-                comp += (fabsf(sum) >= fabsf(val)) ? (sum - t) + val : (val - t) + sum;
-                sum = t;
+                neumaier_add(sum, comp, pair_taps<BF16>(A, S, P.Tw, P.Tw4, ev, pr));
             }
             half_barrier(h);
             if (*abort_flag) {
                 aborted = true;
                 break;
             }
-            if (ht == 0 && k + kBwdStages < kb) {
+            if (ht == 0 && k + nst < kb) {
                 mbar_arrive_expect_tx(bar0 + 8 * stage, rowbytes);
                 bulk_g2s(smem_u32(ering + (size_t)stage * (ebytes / sizeof(E))),
-                         e_g + (size_t)(k + kBwdStages) * P.Mp, rowbytes, bar0 + 8 * stage);
+                         e_g + (size_t)(k + nst) * P.Mp, rowbytes, bar0 + 8 * stage);
             }
             if constexpr (MODE == kModeTAB) rx_cur = rx_nxt;
-            if (++stage == kBwdStages) stage = 0;
+            if (++stage == nst) stage = 0;
             if (++j == P.n_rx) { j = 0; ++i; }
         }
         if (aborted) {
             // drain this item's copies still in flight (bounded) before leaving
             if (ht == 0) {
-                for (int q = k + 1; q < kb && q < k + kBwdStages; ++q) {
-                    const int s = (q - ka) % kBwdStages;
+                for (int q = k + 1; q < kb && q < k + nst; ++q) {
+                    const int s = (q - ka) % nst;
                     mbar_wait_bounded(bar0 + 8 * s, (par >> s) & 1u, D.status);
                     par ^= 1u << s;
                 }
@@ -188,15 +169,32 @@ __global__ void backproject_reduce_kernel(GeomParams P, const RowInfo* __restric
     b[v] = s + c;
 }
 
-size_t backproject_smem(const mbir_geometry* g)
+// Shared memory of a (workers, stages) configuration; 0 if it exceeds the limit.
+static size_t bwd_smem_for(const GeomParams& P, int halves, int nst)
 {
-    const GeomParams& P = g->P;
     size_t esz = P.precision == MBIR_PREC_BF16 ? 2 : 4;
     size_t tsz = P.precision == MBIR_PREC_BF16 ? 4 : 8;
     size_t tab = ((size_t)P.Gt * (P.Q + 1) * table_stride(P.Tw4) * tsz + 127) & ~(size_t)127;
     size_t eb = ((size_t)P.Mp * esz + 127) & ~(size_t)127;
-    return tab + (size_t)kBwdHalves * kBwdStages * eb + 8 * kBwdHalves * kBwdStages + 16;
+    size_t total = tab + (size_t)halves * nst * eb + 8 * halves * nst + 16;
+    return total <= kSmemLimit ? total : 0;
 }
+
+// Picks two tile workers with a 3-deep ring if it fits, else 2-deep, else one
+// worker; false if even that exceeds shared memory.
+bool backproject_config(const GeomParams& P, int* halves, int* stages)
+{
+    const int opts[3][2] = {{2, 3}, {2, 2}, {1, 2}};
+    for (auto& o : opts)
+        if (bwd_smem_for(P, o[0], o[1])) {
+            *halves = o[0];
+            *stages = o[1];
+            return true;
+        }
+    return false;
+}
+
+size_t backproject_smem(const mbir_geometry* g) { return bwd_smem_for(g->P, g->bwd_halves, g->bwd_stages); }
 
 int backproject_tile_rows() { return kBwdRows; }
 
@@ -211,9 +209,9 @@ static cudaError_t launch_bwd_t(const mbir_geometry* g, const DevPtrs& D, const 
     using Tab = typename TabT<BF16>::type;
     const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
     if (g->n_items > 0) {
-        int grid = std::min(g->n_sm, (g->n_items + kBwdHalves - 1) / kBwdHalves);
-        kern<<<grid, kBwdThreads, sm, st>>>(P, D, tab, (const typename ET<BF16>::type*)e, g->d_items, g->n_items,
-                                            g->w_bpart);
+        int grid = std::min(g->n_sm, (g->n_items + g->bwd_halves - 1) / g->bwd_halves);
+        kern<<<grid, g->bwd_halves * kBwdHalfThreads, sm, st>>>(P, D, tab, (const typename ET<BF16>::type*)e,
+                                                                g->d_items, g->n_items, g->w_bpart, g->bwd_stages);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return ce;
     }
@@ -272,9 +270,10 @@ static cudaError_t launch_bwd_partials_t(const mbir_geometry* g, const void* e, 
     using Tab = typename TabT<BF16>::type;
     const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
     if (g->n_items > 0) {
-        int grid = std::min(g->n_sm, (g->n_items + kBwdHalves - 1) / kBwdHalves);
-        kern<<<grid, kBwdThreads, sm, st>>>(P, dev_ptrs(g), tab, (const typename ET<BF16>::type*)e, g->d_items,
-                                            g->n_items, partial);
+        int grid = std::min(g->n_sm, (g->n_items + g->bwd_halves - 1) / g->bwd_halves);
+        kern<<<grid, g->bwd_halves * kBwdHalfThreads, sm, st>>>(P, dev_ptrs(g), tab,
+                                                                (const typename ET<BF16>::type*)e, g->d_items,
+                                                                g->n_items, partial, g->bwd_stages);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return ce;
     }

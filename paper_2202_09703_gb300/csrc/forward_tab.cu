@@ -16,11 +16,10 @@
 #include <algorithm>
 #include <vector>
 
-#include "device_common.cuh"
+#include "apply_common.cuh"
 
 namespace mbir {
 
-constexpr int kRecShift = 13;                     // key: n0 << 13 | table row << 1 | flag0
 constexpr int kSortThreads = 512;
 constexpr int kFwdSortedThreads = 1024;
 
@@ -150,12 +149,7 @@ __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     // per-warp staging of 32 decoded records: {first tap, tap count, table offset - first tap} and weights * x
     int4* sr = reinterpret_cast<int4*>(smem + tab_bytes) + warp * 32;
     float4* sw = reinterpret_cast<float4*>(smem + tab_bytes) + WARPS * 32 + warp * 32;
-    {
-        const int4* src = reinterpret_cast<const int4*>(tab_g);
-        int4* dst = reinterpret_cast<int4*>(tab);
-        const int n16 = (int)(tab_bytes / 16);
-        for (int t = tid; t < n16; t += kFwdSortedThreads) dst[t] = __ldg(src + t);
-    }
+    load_table_smem(tab, tab_g, tab_bytes, tid, kFwdSortedThreads);
     __syncthreads();
     const int nspan = (P.M + 31) >> 5;
     const int total = P.K * nspan;
@@ -170,49 +164,8 @@ __global__ void __launch_bounds__(kFwdSortedThreads, 1)
         const int n = sp * 32 + lane;
         const long long base = __ldg(off + k);
         const int2 rb = __ldg(runs + gs);
-        float sum = 0.0f, comp = 0.0f;
-        // register prefetch of the next batch of records
-        int2 kv = make_int2(0, 0);
-        float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
-        float xv = 0.0f;
-        if (rb.x + lane < rb.y) {
-            kv = __ldg(rkey + base + rb.x + lane);
-            wv = __ldg(rw + base + rb.x + lane);
-            xv = __ldg(x + kv.x);
-        }
-        for (int r0 = rb.x; r0 < rb.y; r0 += 32) {
-            const int cnt = min(32, rb.y - r0);
-            if (lane < cnt) {
-                const int key = kv.y;
-                const int lo = (key >> kRecShift) + 1;
-                const int len = P.Tw - (key & 1);             // tau = t0 exactly lies outside
-                sr[lane] = make_int4(lo, len, ((key >> 1) & 0xfff) * S - lo, 0);
-                sw[lane] = make_float4(wv.x * xv, wv.y * xv, wv.z * xv, wv.w * xv);
-            }
-            __syncwarp();
-            if (r0 + 32 + lane < rb.y) {
-                kv = __ldg(rkey + base + r0 + 32 + lane);
-                wv = __ldg(rw + base + r0 + 32 + lane);
-                xv = __ldg(x + kv.x);
-            }
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-            for (int j = 0; j < cnt; ++j) {
-                const int4 d = sr[j];
-                if ((unsigned)(n - d.x) < (unsigned)d.y) {
-                    const float4 w4 = sw[j];
-                    const Tab* A = tab + (d.z + n);
-                    acc = __ffma2_rn(TabT<BF16>::ld(A), make_float2(w4.x, w4.y), acc);
-                    acc = __ffma2_rn(TabT<BF16>::ld(A + S), make_float2(w4.z, w4.w), acc);
-                }
-            }
-            __syncwarp();
-            const float v = acc.x + acc.y;           // compensated across batches
-            const float t = sum + v;
-            comp += (fabsf(sum) >= fabsf(v)) ? (sum - t) + v : (v - t) + sum;
-            sum = t;
-        }
-        const float yv = (n < P.M) ? sum + comp : 0.0f;
+        const float acc = span_gather<BF16>(tab, S, P.Tw, rkey, rw, base, rb.x, rb.y, x, n, lane, sr, sw);
+        const float yv = (n < P.M) ? acc : 0.0f;
         if (n < out_stride) {
             if (y_f32) y_f32[(size_t)k * out_stride + n] = yv;
             else y_bf16[(size_t)k * out_stride + n] = __float2bfloat16_rn(yv);
@@ -266,6 +219,9 @@ cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_b
     std::vector<int2> runs((size_t)P.K * nspan);
     e = cudaMemcpy(runs.data(), g->d_runs, sizeof(int2) * runs.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return e;
+    g->h_span_cost = (int*)malloc(sizeof(int) * runs.size());
+    if (g->h_span_cost)
+        for (size_t t = 0; t < runs.size(); ++t) g->h_span_cost[t] = runs[t].y - runs[t].x;
     std::vector<int> order(runs.size());
     for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {

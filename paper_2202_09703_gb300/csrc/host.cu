@@ -128,7 +128,7 @@ std::vector<double> pulse_table(const mbir_geometry_desc* d, const Derived& D)
     const int nq = D.Q * D.Tw + 1;
     const double dt = 1.0 / (d->fs_hz * D.Q);
     size_t n = 1;
-    while (n < (size_t)64 * nq) n <<= 1;
+    while (n < (size_t)16 * nq) n <<= 1;
     std::vector<std::complex<double>> s(n);
     for (size_t k = 0; k < n; ++k) {
         double t = (k < n / 2) ? k * dt : ((double)k - (double)n) * dt;
@@ -173,6 +173,8 @@ void free_geometry(mbir_geometry* g)
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::prof_release(g);
     free(g->tab_host);
+    free(g->h_span_cost);
+    free(g->h_tvert);
     delete g;
 }
 
@@ -286,6 +288,9 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
         ri.pad = 0;
     }
     P.seg_row[P.n_seg] = P.H;
+    g->h_tvert = (float*)malloc(sizeof(float) * P.H);
+    if (!g->h_tvert) { free_geometry(g); return MBIR_ERR_OOM; }
+    for (int r = 0; r < P.H; ++r) g->h_tvert[r] = rows[r].tvert;
 
     // pixel-centre laterals and distinct transducer positions
     std::vector<float2> colx(P.W);
@@ -422,6 +427,11 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
         cudaFree(d_hv);
         if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
     }
+    if (!mbir::backproject_config(P, &g->bwd_halves, &g->bwd_stages)) {
+        // the pulse table plus two residual rows do not fit in shared memory
+        free_geometry(g);
+        return MBIR_ERR_UNSUPPORTED;
+    }
     {
         // A^T r work list: active 16-row tiles x 32-column tiles x transmitter groups,
         // enough items for a few rounds of two workers per SM
@@ -434,7 +444,7 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
             if (rows[tr * TR].tvert < (float)(P.M - 1)) active_tiles += ntc;
         int ngroups = 1;
         if (active_tiles > 0) {
-            ngroups = (8 * g->n_sm + active_tiles - 1) / active_tiles;
+            ngroups = (4 * g->bwd_halves * g->n_sm + active_tiles - 1) / active_tiles;
             ngroups = std::max(1, std::min(ngroups, P.n_tx));
         }
         const int txg = (P.n_tx + ngroups - 1) / ngroups;

@@ -339,6 +339,7 @@ struct mbir_geometry {
     double z0, pitch;
     // A^T r work list: (tile row, tile column, Tx range, group) and per-group partial images
     int n_sm;
+    int bwd_halves, bwd_stages;   // A^T r tile workers per CTA and residual ring depth
     int n_items, n_groups;
     int4* d_items;
     float* w_bpart;
@@ -348,6 +349,8 @@ struct mbir_geometry {
     float4* d_rec_w;
     int2* d_runs;
     int* d_span_order;     // spans by decreasing record count
+    int* h_span_cost;      // host copy: records per span (K x nspan), for work partitioning
+    float* h_tvert;        // host copy: vertical two-way time per image row (samples)
     int* d_span_counter;   // work counter of the A x launch
     long long n_records;
     // profiling of the apply kernels inside mbir_reconstruct
@@ -370,11 +373,16 @@ cudaError_t launch_pad_rows(const mbir_geometry* g, const void* src, int src_bf1
 cudaError_t launch_pair_quantities(const mbir_geometry* g, const int* pix, const int* k, int n,
                                    double* T, float* gam, float* w, cudaStream_t st);
 void prof_release(mbir_geometry* g);
+cudaError_t launch_project_rows(const mbir_geometry* g, const void* src, int src_bf16, int sin, const float* sub,
+                                int ssub, float* dst, int sout, float* gk, double* part, cudaStream_t st);
+cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, long long n, cudaStream_t st);
+void compute_msq(const mbir_geometry* g, const mbir_prior* pr, float* out);
 cudaError_t launch_count_taps(const mbir_geometry* g, unsigned long long* d_out, cudaStream_t st);
 cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_bytes);
 cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
                                   cudaStream_t st);
 size_t backproject_smem(const mbir_geometry* g);
+bool backproject_config(const GeomParams& P, int* halves, int* stages);
 int backproject_tile_rows();
 cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
                                         float* b, float* partial, cudaStream_t st);

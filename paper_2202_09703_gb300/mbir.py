@@ -102,6 +102,13 @@ def lib(path: str | None = None):
         "mbir_set_profiling": [_V, C.c_int],
         "mbir_get_kernel_times": [_V, C.POINTER(KernelTimes), C.c_int],
         "mbir_count_taps": [_V, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+        "mbir_engine_create": [C.c_size_t, C.c_int, C.POINTER(_V)],
+        "mbir_engine_destroy": [_V],
+        "mbir_engine_submit": [_V, _V, _V, Pp, C.c_int, _V, _V, C.POINTER(C.c_int64)],
+        "mbir_engine_step": [_V, _V, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "mbir_engine_poll": [_V, C.c_int64, C.POINTER(C.c_int)],
+        "mbir_engine_wait": [_V, C.c_int64, C.c_int, _V],
+        "mbir_engine_cancel": [_V, C.c_int64, _V],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -109,6 +116,8 @@ def lib(path: str | None = None):
         f.restype = C.c_int
     L.mbir_geometry_bytes.argtypes = [_V]
     L.mbir_geometry_bytes.restype = C.c_size_t
+    L.mbir_engine_bytes_in_use.argtypes = [_V]
+    L.mbir_engine_bytes_in_use.restype = C.c_size_t
     L.mbir_error_string.argtypes = [C.c_int]
     L.mbir_error_string.restype = C.c_char_p
     _lib = L
@@ -268,3 +277,64 @@ class Geometry:
         out = np.zeros(G * (Q * Tw + 1))
         _check(self._lib.mbir_pulse_table(self.h, out.ctypes.data, out.size), "mbir_pulse_table")
         return out.reshape(G, Q * Tw + 1)
+
+
+class Engine:
+    """Batched / served reconstructions (continuous batching, see include/mbir.h)."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 3
+
+    def __init__(self, budget_bytes: int, max_active: int = 256):
+        self._lib = lib()
+        h = C.c_void_p()
+        _check(self._lib.mbir_engine_create(budget_bytes, max_active, C.byref(h)), "mbir_engine_create")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.mbir_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, geo: "Geometry", y, sigma_noise: float, n_iter: int, x, g=None) -> int:
+        pr = prior_struct(geo.scene, sigma_noise)
+        t = C.c_int64()
+        _check(self._lib.mbir_engine_submit(self.h, geo.h, _ptr(y), C.byref(pr), n_iter, _ptr(x), _ptr(g),
+                                            C.byref(t)), "mbir_engine_submit")
+        self._keep[t.value] = (geo, y, x, g)
+        return t.value
+
+    def step(self, stream=None):
+        na, nq = C.c_int(), C.c_int()
+        _check(self._lib.mbir_engine_step(self.h, _stream_ptr(stream), C.byref(na), C.byref(nq)), "mbir_engine_step")
+        return na.value, nq.value
+
+    def poll(self, ticket: int) -> int:
+        st = C.c_int()
+        rc = self._lib.mbir_engine_poll(self.h, ticket, C.byref(st))
+        if rc not in (0,) and st.value >= 0:
+            _check(rc, "mbir_engine_poll")
+        return st.value
+
+    def wait(self, ticket: int, timeout_ms: int = 600000, stream=None):
+        _check(self._lib.mbir_engine_wait(self.h, ticket, timeout_ms, _stream_ptr(stream)), "mbir_engine_wait")
+
+    def cancel(self, ticket: int, stream=None):
+        _check(self._lib.mbir_engine_cancel(self.h, ticket, _stream_ptr(stream)), "mbir_engine_cancel")
+
+    def run_until_idle(self, stream=None, max_steps: int = 1_000_000):
+        for _ in range(max_steps):
+            na, nq = self.step(stream)
+            if na == 0 and nq == 0:
+                return
+        raise RuntimeError("engine did not drain")
+
+    @property
+    def bytes_in_use(self) -> int:
+        return int(self._lib.mbir_engine_bytes_in_use(self.h))

@@ -1,0 +1,142 @@
+"""Batched / served engine on a GB300: results against the single-request path
+and the oracle, bitwise equality alone vs in a mix, admission by budget,
+cancellation and BF16 storage."""
+import numpy as np
+import pytest
+
+from paper_2202_09703_gb300 import synth as S
+from tests.helpers import oracle_data, ragged_scene, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2202_09703_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2202_09703_gb300 import mbir as M  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32).reshape(-1), device=DEV)
+
+
+@pytest.fixture(scope="module")
+def problems():
+    """Three uneven problems with oracle data and reference reconstructions."""
+    out = []
+    for fn, seed in ((S.cfg0, 1), (ragged_scene, 2),
+                     (lambda: S.small_scene(n_layers=2, w=48, h=40, n_tx=5, n_rx=6, M=384, direct=True,
+                                            name="tiny_mid"), 3)):
+        s = fn()
+        plan, x_true, g_true, y, sig = oracle_data(s, seed=seed)
+        geo = M.Geometry(s, mode="tab")
+        out.append((s, geo, dev(y), sig, plan, y))
+    return out
+
+
+def single(geo, y, sig, n_iter):
+    s = geo.scene
+    x = torch.empty(s.N, device=DEV)
+    g = torch.empty(s.K, device=DEV)
+    geo.reconstruct(y, sig, n_iter, x, g=g)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), g.cpu().numpy()
+
+
+def test_engine_matches_single_request_path_and_oracle(problems):
+    s, geo, y, sig, plan, y_np = problems[0]
+    eng = M.Engine(1 << 30)
+    x = torch.empty(s.N, device=DEV)
+    g = torch.empty(s.K, device=DEV)
+    t = eng.submit(geo, y, sig, s.n_iter, x, g)
+    eng.wait(t)
+    torch.cuda.synchronize()
+    assert eng.poll(t) == M.Engine.DONE
+    xs, gs = single(geo, y, sig, s.n_iter)
+    assert rel_l2(x.cpu().numpy(), xs) <= 1e-5
+    x_ref, g_ref, _, _ = plan.reconstruct(y_np, sig, s.n_iter)
+    assert rel_l2(x.cpu().numpy(), x_ref) <= 1e-4
+
+
+def test_engine_result_is_identical_alone_and_in_a_mix(problems):
+    n_iters = [12, 7, 9]
+    alone = []
+    for (s, geo, y, sig, _, _), n in zip(problems, n_iters):
+        eng = M.Engine(1 << 30)
+        x = torch.empty(s.N, device=DEV)
+        eng.wait(eng.submit(geo, y, sig, n, x))
+        torch.cuda.synchronize()
+        alone.append(x.cpu().numpy())
+        eng.close()
+    # the mix: staggered arrivals, so requests join while others are mid-run
+    eng = M.Engine(1 << 30)
+    xs = [torch.empty(p[0].N, device=DEV) for p in problems]
+    t0 = eng.submit(problems[0][1], problems[0][2], problems[0][3], n_iters[0], xs[0])
+    eng.step()
+    eng.step()
+    t1 = eng.submit(problems[1][1], problems[1][2], problems[1][3], n_iters[1], xs[1])
+    eng.step()
+    t2 = eng.submit(problems[2][1], problems[2][2], problems[2][3], n_iters[2], xs[2])
+    eng.run_until_idle()
+    torch.cuda.synchronize()
+    for t in (t0, t1, t2):
+        assert eng.poll(t) == M.Engine.DONE
+    for a, x in zip(alone, xs):
+        assert np.array_equal(a, x.cpu().numpy())
+
+
+def test_admission_waits_for_memory_and_refuses_oversize(problems):
+    s, geo, y, sig, _, _ = problems[0]
+    x1 = torch.empty(s.N, device=DEV)
+    x2 = torch.empty(s.N, device=DEV)
+    # a budget that fits one request of this size at a time
+    probe = M.Engine(1 << 30)
+    probe.submit(geo, y, sig, 2, x1)
+    probe.step()
+    one = probe.bytes_in_use
+    probe.run_until_idle()
+    probe.close()
+    eng = M.Engine(int(one * 1.5))
+    ta = eng.submit(geo, y, sig, 3, x1)
+    tb = eng.submit(geo, y, sig, 3, x2)
+    na, nq = eng.step()
+    assert (na, nq) == (1, 1)
+    assert eng.poll(tb) == M.Engine.QUEUED
+    eng.run_until_idle()
+    assert eng.poll(ta) == M.Engine.DONE and eng.poll(tb) == M.Engine.DONE
+    assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    small = M.Engine(1024)
+    with pytest.raises(M.MbirError) as ei:
+        small.submit(geo, y, sig, 3, x1)
+    assert ei.value.code == -6
+
+
+def test_cancel_removes_a_running_request(problems):
+    s, geo, y, sig, _, _ = problems[1]
+    eng = M.Engine(1 << 30)
+    x = torch.empty(s.N, device=DEV)
+    t = eng.submit(geo, y, sig, 50, x)
+    eng.step()
+    eng.cancel(t)
+    assert eng.poll(t) == -8
+    assert eng.bytes_in_use == 0
+    na, nq = eng.step()
+    assert (na, nq) == (0, 0)
+
+
+def test_engine_bf16_storage(problems):
+    s, _, y, sig, _, y_np = problems[0]
+    sb = s.copy(precision="bf16")
+    geo_b = M.Geometry(sb, mode="tab")
+    yb = torch.as_tensor(y_np.reshape(-1), dtype=torch.bfloat16, device=DEV)
+    eng = M.Engine(1 << 30)
+    x = torch.empty(s.N, device=DEV)
+    eng.wait(eng.submit(geo_b, yb, sig, s.n_iter, x))
+    torch.cuda.synchronize()
+    xs, _ = single(problems[0][1], y, sig, s.n_iter)
+    assert rel_l2(x.cpu().numpy(), xs) <= 3e-2

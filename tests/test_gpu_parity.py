@@ -269,3 +269,43 @@ def test_invalid_prior_is_rejected():
     with pytest.raises(M.MbirError) as ei:
         geo.reconstruct(torch.zeros(s.K * s.M, device=DEV), 0.1, 3, x)
     assert ei.value.code == -1
+
+
+# --------------------------------------------------------------------------
+# precision form at full size: 512 x 1024 image, 128 Tx x 32 Rx, 4096 samples
+# --------------------------------------------------------------------------
+def test_cfg2_bf16_sampled_ascans_and_pixels():
+    s = S.cfg2()
+    assert s.precision == "bf16"
+    geo = M.Geometry(s)
+    plan = O.Plan(s)
+    x = S.random_vector(s.N, 14).reshape(s.img_h, s.img_w)
+    y = gpu_forward(geo, x)
+    for k in (0, s.K // 2 + 7):
+        assert rel_l2(y[k], plan.forward(x, k, k + 1)[0]) <= 1e-2
+    r = S.random_vector(s.K * s.M, 15)
+    b = gpu_backproject(geo, r)
+    rng = S.SplitMix64(5)
+    pix = np.unique(rng.integers(0, s.N - 1, 48))
+    bp = O.Plan(s, pix=pix)
+    assert rel_l2(b[pix], bp.backproject(r)) <= 1e-2
+
+
+@pytest.mark.parametrize("M_len", [4096, 9000])
+def test_long_records_use_smaller_adjoint_configurations(M_len):
+    """Long A-scans shrink the adjoint's residual ring (two workers x two
+    stages, then one worker) to fit shared memory; results are unchanged."""
+    s = S.small_scene(n_layers=2, w=40, h=24, n_tx=2, n_rx=3, M=M_len, direct=True, name="tiny_long")
+    geo = make_geo(s, "tab")
+    plan = O.Plan(s)
+    r = S.random_vector(s.K * s.M, 16)
+    assert rel_l2(gpu_backproject(geo, r), plan.backproject(r)) <= 1e-5
+    x = S.random_vector(s.N, 17)
+    assert rel_l2(gpu_forward(geo, x), plan.forward(x)) <= 1e-5
+
+
+def test_records_too_long_for_shared_memory_are_refused():
+    s = S.small_scene(n_layers=2, w=16, h=8, n_tx=1, n_rx=1, M=16000, name="tiny_toolong")
+    with pytest.raises(M.MbirError) as ei:
+        M.Geometry(s, mode="tab")
+    assert ei.value.code == -7
