@@ -311,6 +311,13 @@ int mbir_get_kernel_times(mbir_geometry* g, mbir_kernel_times* t, int reset);
  * the device from the geometry alone; synchronises the legacy stream. */
 int mbir_count_taps(const mbir_geometry* g, int64_t* active_pairs, int64_t* taps);
 
+/* Failure-detection self-test: launches a kernel whose bounded wait can never
+ * be satisfied (an mbarrier that no arrival completes) and returns
+ * MBIR_ERR_TIMEOUT once the wait gives up after max_cycles SM clocks
+ * (1 .. 4e9), leaving the context usable.  The apply kernels use the same
+ * bounded waits for their bulk copies. */
+int mbir_selftest_bounded_wait(long long max_cycles);
+
 const char* mbir_error_string(int code);
 
 #ifdef __cplusplus

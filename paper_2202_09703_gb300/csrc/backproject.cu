@@ -2,7 +2,7 @@
 // per SM holds the pulse table in shared memory once; each CTA runs two
 // independent tile workers (16 x 32 pixels each, synchronised by their own
 // named barrier) that take work items = (pixel tile, group of transmitter
-// positions).  A worker walks its A-scans in (Tx, receiver) order, keeping
+// positions) from a shared counter, longest estimated item first.  A worker walks its A-scans in (Tx, receiver) order, keeping
 // the pixel's transmit leg while the receiver changes.  Residual rows are
 // staged in shared memory by 1-D bulk copies (TMA engine) into a 3-stage ring
 // guarded by mbarriers with bounded waits.  Every tap of a pair shares one
@@ -31,7 +31,7 @@ template <int NL, int MODE, bool BF16>
 __global__ void __launch_bounds__(kBwdThreads, 1)
     backproject_kernel(GeomParams P, DevPtrs D, const typename TabT<BF16>::type* __restrict__ tab_g,
                        const typename ET<BF16>::type* __restrict__ e_g, const int4* __restrict__ items,
-                       int nitems, float* __restrict__ partial, int nst)
+                       int nitems, int* __restrict__ counter, float* __restrict__ partial, int nst)
 {
     using Tab = typename TabT<BF16>::type;
     using E = typename ET<BF16>::type;
@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
     E* ering = reinterpret_cast<E*>(smem + tab_bytes + (size_t)h * nst * ebytes);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tab_bytes + (size_t)halves * nst * ebytes);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + halves * nst) + h;
+    volatile int* next_item = reinterpret_cast<volatile int*>(bars + halves * nst) + 2 + h;
     const uint32_t bar0 = smem_u32(bars + h * nst);
     const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
     const int N = P.W * P.H;
@@ -67,7 +68,12 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
 
     uint32_t par = 0;                    // expected phase parity per stage (bit s)
     bool aborted = false;
-    for (int it = blockIdx.x * halves + h; it < nitems && !aborted; it += gridDim.x * halves) {
+    while (!aborted) {
+        if (ht == 0) *next_item = atomicAdd(counter, 1);
+        half_barrier(h);
+        const int it = *next_item;
+        half_barrier(h);                 // every thread has read the slot before it is reused
+        if (it >= nitems) break;
         const int4 item = __ldg(items + it);
         const int row = item.x * kBwdRows + hw, col = item.y * 32 + lane;
         const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
@@ -169,6 +175,75 @@ __global__ void backproject_reduce_kernel(GeomParams P, const RowInfo* __restric
     b[v] = s + c;
 }
 
+// Estimated A^T r cost per (16 x 32 pixel tile, transmitter position), in
+// warp tap iterations: a warp runs the whole tap loop (Tw4 taps) for an
+// A-scan as soon as one of its pixels has an active pair, and every warp pays
+// a fixed overhead per A-scan (leg loads, pair set-up, ring wait, barrier).
+constexpr float kBwdAscanOverhead = 16.0f;
+
+template <int NL, int MODE>
+__global__ void __launch_bounds__(kBwdHalfThreads)
+    bwd_tile_cost_kernel(GeomParams P, DevPtrs D, int ntc, float* __restrict__ cost)
+{
+    __shared__ int s_active[kBwdRows];
+    const int tile = blockIdx.x;
+    const int tr = tile / ntc, tc = tile - tr * ntc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = tr * kBwdRows + warp, col = tc * 32 + lane;
+    const bool pix_ok = col < P.W && row < P.H;
+    const RowInfo ri = load_row(D.rows, min(row, P.H - 1));
+    const bool row_ok = pix_ok && ri.tvert < (float)(P.M - 1);
+    const int colc = min(col, P.W - 1);
+    for (int i = 0; i < P.n_tx; ++i) {
+        Leg tx = {0.f, 0.f, 0.f, 0.f};
+        if (row_ok) tx = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.txpos + i));
+        int na = 0;
+        for (int j = 0; j < P.n_rx; ++j) {
+            const int k = i * P.n_rx + j;
+            bool act = false;
+            if (row_ok) {
+                const Leg rx = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + k));
+                const Pair pr = make_pair(P, tx, rx, ri.tau);
+                act = pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M;
+            }
+            na += __any_sync(0xffffffffu, act) ? 1 : 0;
+        }
+        if (lane == 0) s_active[warp] = na;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kBwdRows; ++w) tot += s_active[w];
+            cost[(size_t)tile * P.n_tx + i] = (float)tot * P.Tw4 + kBwdAscanOverhead * kBwdRows * P.n_rx;
+        }
+        __syncthreads();
+    }
+}
+
+// Fills h_cost (ntr x ntc x n_tx, host) with the estimates above; synchronous.
+cudaError_t backproject_tile_costs(const mbir_geometry* g, int ntr, int ntc, float* h_cost, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const size_t n = (size_t)ntr * ntc * P.n_tx;
+    float* d = nullptr;
+    cudaError_t ce = cudaMalloc((void**)&d, sizeof(float) * std::max<size_t>(n, 1));
+    if (ce != cudaSuccess) return ce;
+    DevPtrs D = dev_ptrs(g);
+    const int blocks = ntr * ntc;
+    if (P.mode == MBIR_MODE_TAB)
+        bwd_tile_cost_kernel<1, kModeTAB><<<blocks, kBwdHalfThreads, 0, st>>>(P, D, ntc, d);
+    else if (P.L <= 2)
+        bwd_tile_cost_kernel<2, kModeOTF><<<blocks, kBwdHalfThreads, 0, st>>>(P, D, ntc, d);
+    else if (P.L <= 4)
+        bwd_tile_cost_kernel<4, kModeOTF><<<blocks, kBwdHalfThreads, 0, st>>>(P, D, ntc, d);
+    else
+        bwd_tile_cost_kernel<8, kModeOTF><<<blocks, kBwdHalfThreads, 0, st>>>(P, D, ntc, d);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_cost, d, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    cudaFree(d);
+    return ce;
+}
+
 // Shared memory of a (workers, stages) configuration; 0 if it exceeds the limit.
 static size_t bwd_smem_for(const GeomParams& P, int halves, int nst)
 {
@@ -176,7 +251,7 @@ static size_t bwd_smem_for(const GeomParams& P, int halves, int nst)
     size_t tsz = P.precision == MBIR_PREC_BF16 ? 4 : 8;
     size_t tab = ((size_t)P.Gt * (P.Q + 1) * table_stride(P.Tw4) * tsz + 127) & ~(size_t)127;
     size_t eb = ((size_t)P.Mp * esz + 127) & ~(size_t)127;
-    size_t total = tab + (size_t)halves * nst * eb + 8 * halves * nst + 16;
+    size_t total = tab + (size_t)halves * nst * eb + 8 * halves * nst + 32;   // + abort flags, item slots
     return total <= kSmemLimit ? total : 0;
 }
 
@@ -209,9 +284,12 @@ static cudaError_t launch_bwd_t(const mbir_geometry* g, const DevPtrs& D, const 
     using Tab = typename TabT<BF16>::type;
     const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
     if (g->n_items > 0) {
+        ce = cudaMemsetAsync(g->d_bwd_counter, 0, sizeof(int), st);
+        if (ce != cudaSuccess) return ce;
         int grid = std::min(g->n_sm, (g->n_items + g->bwd_halves - 1) / g->bwd_halves);
         kern<<<grid, g->bwd_halves * kBwdHalfThreads, sm, st>>>(P, D, tab, (const typename ET<BF16>::type*)e,
-                                                                g->d_items, g->n_items, g->w_bpart, g->bwd_stages);
+                                                                g->d_items, g->n_items, g->d_bwd_counter,
+                                                                g->w_bpart, g->bwd_stages);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return ce;
     }
@@ -270,10 +348,13 @@ static cudaError_t launch_bwd_partials_t(const mbir_geometry* g, const void* e, 
     using Tab = typename TabT<BF16>::type;
     const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
     if (g->n_items > 0) {
+        ce = cudaMemsetAsync(g->d_bwd_counter, 0, sizeof(int), st);
+        if (ce != cudaSuccess) return ce;
         int grid = std::min(g->n_sm, (g->n_items + g->bwd_halves - 1) / g->bwd_halves);
         kern<<<grid, g->bwd_halves * kBwdHalfThreads, sm, st>>>(P, dev_ptrs(g), tab,
                                                                 (const typename ET<BF16>::type*)e, g->d_items,
-                                                                g->n_items, partial, g->bwd_stages);
+                                                                g->n_items, g->d_bwd_counter, partial,
+                                                                g->bwd_stages);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return ce;
     }

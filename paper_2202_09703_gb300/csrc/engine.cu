@@ -649,7 +649,13 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
                     const int t0 = gi * txg, t1 = std::min(P.n_tx, t0 + txg);
                     if (t0 >= t1) continue;
                     bwd.push_back(make_int4((int)ri, (tr << 16) | tc, t0 | (t1 << 16), gi));
-                    bwd_cost.push_back((double)(t1 - t0) * P.n_rx * kEngTile * kEngTile * (P.Tw4 + 8));
+                    // the geometry's estimates per 16-row tile and transmitter position
+                    const int TR = backproject_tile_rows(), ntr16 = (P.H + TR - 1) / TR;
+                    double c = 0;
+                    for (int r16 = tr * kEngTile / TR; r16 < std::min(ntr16, (tr + 1) * kEngTile / TR); ++r16)
+                        for (int t = t0; t < t1; ++t)
+                            c += r->g->h_bwd_cost[((size_t)r16 * r->g->bwd_ntc + tc) * P.n_tx + t];
+                    bwd_cost.push_back(c);
                 }
         }
         const int nspan = (P.M + 31) / 32;

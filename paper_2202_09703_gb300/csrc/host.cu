@@ -169,12 +169,14 @@ void free_geometry(mbir_geometry* g)
                     g->d_legs, g->d_hidx, g->d_direct, g->d_dinv, g->d_status, g->w_e, g->w_q,
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
                     g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
-                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_span_order, g->d_span_counter};
+                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_span_order, g->d_span_counter,
+                    g->d_bwd_counter};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::prof_release(g);
     free(g->tab_host);
     free(g->h_span_cost);
     free(g->h_tvert);
+    free(g->h_bwd_cost);
     delete g;
 }
 
@@ -434,36 +436,53 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
     }
     {
         // A^T r work list: active 16-row tiles x 32-column tiles x transmitter groups,
-        // enough items for a few rounds of two workers per SM
+        // about eight items per tile worker, ordered by decreasing estimated cost so
+        // that the persistent workers, taking items from a shared counter, finish together
         cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, g->device);
         if (g->n_sm < 1) g->n_sm = 1;
         const int TR = mbir::backproject_tile_rows();
         const int ntr = (P.H + TR - 1) / TR, ntc = (P.W + 31) / 32;
+        g->bwd_ntc = ntc;
         int active_tiles = 0;
         for (int tr = 0; tr < ntr; ++tr)
             if (rows[tr * TR].tvert < (float)(P.M - 1)) active_tiles += ntc;
         int ngroups = 1;
         if (active_tiles > 0) {
-            ngroups = (4 * g->bwd_halves * g->n_sm + active_tiles - 1) / active_tiles;
+            ngroups = (8 * g->bwd_halves * g->n_sm + active_tiles - 1) / active_tiles;
             ngroups = std::max(1, std::min(ngroups, P.n_tx));
         }
         const int txg = (P.n_tx + ngroups - 1) / ngroups;
         ngroups = (P.n_tx + txg - 1) / txg;
+        g->h_bwd_cost = (float*)malloc(sizeof(float) * (size_t)ntr * ntc * P.n_tx);
+        if (!g->h_bwd_cost) { free_geometry(g); return MBIR_ERR_OOM; }
+        ce = mbir::backproject_tile_costs(g, ntr, ntc, g->h_bwd_cost, st);
+        if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
         std::vector<int4> items;
+        std::vector<double> cost;
         for (int tr = 0; tr < ntr; ++tr) {
             if (!(rows[tr * TR].tvert < (float)(P.M - 1))) continue;
             for (int tc = 0; tc < ntc; ++tc)
                 for (int gi = 0; gi < ngroups; ++gi) {
                     int t0 = gi * txg, t1 = std::min(P.n_tx, t0 + txg);
+                    double c = 0;
+                    for (int t = t0; t < t1; ++t) c += g->h_bwd_cost[((size_t)tr * ntc + tc) * P.n_tx + t];
                     items.push_back(make_int4(tr, tc, t0 | (t1 << 16), gi));
+                    cost.push_back(c);
                 }
         }
-        g->n_items = (int)items.size();
+        std::vector<int> order(items.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::vector<int4> sorted(items.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        g->n_items = (int)sorted.size();
         g->n_groups = ngroups;
-        UP(g->d_items, items);
+        UP(g->d_items, sorted);
+        ce = cudaMalloc((void**)&g->d_bwd_counter, sizeof(int));
+        if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
         ce = cudaMalloc((void**)&g->w_bpart, sizeof(float) * (size_t)ngroups * P.W * P.H);
         if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
-        bytes += sizeof(float) * (size_t)ngroups * P.W * P.H;
+        bytes += sizeof(float) * (size_t)ngroups * P.W * P.H + sizeof(int);
     }
 #undef UP
     if (P.mode == MBIR_MODE_TAB && !(d->flags & MBIR_FLAG_NO_RECORDS)) {

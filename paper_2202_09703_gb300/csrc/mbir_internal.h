@@ -341,8 +341,11 @@ struct mbir_geometry {
     int n_sm;
     int bwd_halves, bwd_stages;   // A^T r tile workers per CTA and residual ring depth
     int n_items, n_groups;
-    int4* d_items;
+    int4* d_items;         // ordered by decreasing estimated cost
     float* w_bpart;
+    int* d_bwd_counter;    // work counter of the A^T r launch
+    float* h_bwd_cost;     // host copy: estimated A^T r cost per (16-row tile, 32-column tile, Tx position)
+    int bwd_ntc;           // 32-column tiles per row of tiles
     // TAB-mode A x records sorted by first tap sample (see forward_tab.cu)
     long long* d_rec_off;
     int2* d_rec_key;
@@ -384,6 +387,7 @@ cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float*
 size_t backproject_smem(const mbir_geometry* g);
 bool backproject_config(const GeomParams& P, int* halves, int* stages);
 int backproject_tile_rows();
+cudaError_t backproject_tile_costs(const mbir_geometry* g, int ntr, int ntc, float* h_cost, cudaStream_t st);
 cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
                                         float* b, float* partial, cudaStream_t st);
 size_t forward_smem(const mbir_geometry* g, int* cb_out);

@@ -144,4 +144,41 @@ cudaError_t launch_pad_rows(const mbir_geometry* g, const void* src, int src_bf1
     return cudaGetLastError();
 }
 
+// A wait that nothing completes: the mbarrier expects one arrival that never
+// comes.  The bounded wait gives up after max_cycles, records the failure and
+// returns, exactly as the apply kernels do when a bulk copy never lands.
+__global__ void bounded_wait_selftest_kernel(long long max_cycles, int* status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const uint32_t b = smem_u32(&bar);
+    long long start = clock64();
+    bool ok = false;
+    while (!(ok = mbar_try_wait(b, 0))) {
+        if (clock64() - start > max_cycles) break;
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(status, 1);
+}
+
 }  // namespace mbir
+
+extern "C" int mbir_selftest_bounded_wait(long long max_cycles)
+{
+    if (max_cycles <= 0 || max_cycles > 4000000000LL) return MBIR_ERR_INVALID_ARG;
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return MBIR_ERR_OOM;
+    int h = 0;
+    cudaError_t e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        mbir::bounded_wait_selftest_kernel<<<1, 32>>>(max_cycles, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return MBIR_ERR_CUDA;
+    return h ? MBIR_ERR_TIMEOUT : MBIR_OK;
+}

@@ -140,3 +140,32 @@ def test_engine_bf16_storage(problems):
     torch.cuda.synchronize()
     xs, _ = single(problems[0][1], y, sig, s.n_iter)
     assert rel_l2(x.cpu().numpy(), xs) <= 3e-2
+
+
+def test_engine_wait_times_out_and_the_request_keeps_running(problems):
+    s, geo, y, sig, _, _ = problems[0]
+    eng = M.Engine(1 << 30)
+    x = torch.empty(s.N, device=DEV)
+    t = eng.submit(geo, y, sig, 400, x)
+    with pytest.raises(M.MbirError) as ei:
+        eng.wait(t, timeout_ms=0)
+    assert ei.value.code == -5
+    assert eng.poll(t) == M.Engine.RUNNING
+    eng.cancel(t)
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives(problems):
+    import ctypes as C
+    L = M.lib()
+    f = L.mbir_selftest_bounded_wait
+    f.argtypes = [C.c_longlong]
+    f.restype = C.c_int
+    assert f(2_000_000) == -5            # about a millisecond of spinning, then the error status
+    # the context is still usable: a normal apply runs and matches itself
+    s, geo, y, sig, _, _ = problems[0]
+    b1 = torch.empty(s.N, device=DEV)
+    b2 = torch.empty(s.N, device=DEV)
+    geo.backproject(y, b1)
+    geo.backproject(y, b2)
+    torch.cuda.synchronize()
+    assert torch.equal(b1, b2)
