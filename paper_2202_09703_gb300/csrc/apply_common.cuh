@@ -103,4 +103,112 @@ __device__ __forceinline__ float span_gather(const typename TabT<BF16>::type* __
     return sum + comp;
 }
 
+
+constexpr int kBwdTileRows = 16;                       // A^T r tile: 16 rows (one warp each) x 32 columns
+constexpr int kBwdWorkerThreads = kBwdTileRows * 32;   // threads of one tile worker
+
+// Named barrier of tile worker h (ids 1 and 2; id 0 is __syncthreads).
+__device__ __forceinline__ void worker_barrier(int h)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "n"(kBwdWorkerThreads) : "memory");
+}
+
+// One A^T r work item {tile row, tile column, tx0 | tx1 << 16, group} for tile
+// worker h: every pixel of the tile sums its pairs with the A-scans of
+// transmitter positions [tx0, tx1) (transmitter outer, receiver inner, the
+// transmit leg kept) and writes the sum to its partial image `grp`.  Residual
+// rows stream through the worker's nst-stage ring `ering` (rows of ebytes)
+// guarded by the mbarriers at bar0.  A wait that gives up sets *abort_flag
+// and the function drains the copies still in flight (bounded) and returns
+// false; every thread of the worker returns the same value.
+template <int NL, int MODE, bool BF16>
+__device__ __forceinline__ bool backproject_item(const GeomParams& P, const DevPtrs& D,
+                                                 const typename TabT<BF16>::type* __restrict__ tab,
+                                                 const typename ET<BF16>::type* __restrict__ e_g, const int4 item,
+                                                 float* __restrict__ partial, typename ET<BF16>::type* ering,
+                                                 uint32_t bar0, int nst, size_t ebytes, volatile int* abort_flag,
+                                                 uint32_t& par, int h, int hw, int lane, int ht)
+{
+    using Tab = typename TabT<BF16>::type;
+    using E = typename ET<BF16>::type;
+    const int S = table_stride(P.Tw4);
+    const int R = P.Q + 1;
+    const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
+    const size_t estride = ebytes / sizeof(E);
+    const int row = item.x * kBwdTileRows + hw, col = item.y * 32 + lane;
+    const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
+    const bool pix_ok = col < P.W && row < P.H;
+    const RowInfo ri = load_row(D.rows, min(row, P.H - 1));
+    const bool row_ok = pix_ok && ri.tvert < (float)(P.M - 1);
+    const int colc = min(col, P.W - 1);
+    const int ka = tx0 * P.n_rx, kb = tx1 * P.n_rx;
+    if (ht == 0) {
+        for (int s = 0; s < nst && ka + s < kb; ++s) {
+            mbar_arrive_expect_tx(bar0 + 8 * s, rowbytes);
+            bulk_g2s(smem_u32(ering + (size_t)s * estride), e_g + (size_t)(ka + s) * P.Mp, rowbytes, bar0 + 8 * s);
+        }
+    }
+    float sum = 0.0f, comp = 0.0f;
+    Leg tx = {0.f, 0.f, 0.f, 0.f}, rx_cur = tx, rx_nxt = tx;
+    int hx_nxt = 0;
+    if constexpr (MODE == kModeTAB) {
+        if (row_ok) {
+            rx_cur = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + ka));
+            if (ka + 1 < kb) hx_nxt = __ldg(D.hidx + (size_t)__ldg(D.rxpos + ka + 1) * P.W + colc);
+        }
+    }
+    int i = tx0, j = 0, stage = 0, k = ka;
+    bool aborted = false;
+    for (; k < kb; ++k) {
+        if constexpr (MODE == kModeTAB) {
+            // legs of the next A-scan stream in while this one is consumed
+            if (row_ok && k + 1 < kb) {
+                float4 v = __ldg(D.legs + (size_t)row * P.nh + hx_nxt);
+                rx_nxt = Leg{v.x, v.y, v.z, v.w};
+                if (k + 2 < kb) hx_nxt = __ldg(D.hidx + (size_t)__ldg(D.rxpos + k + 2) * P.W + colc);
+            }
+        }
+        if (row_ok) {
+            if (j == 0) tx = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.txpos + i));
+            if constexpr (MODE != kModeTAB) rx_cur = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + k));
+        }
+        const Pair pr = make_pair(P, tx, rx_cur, ri.tau);
+        const bool act = row_ok && pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M;
+        const bool ok = mbar_wait_bounded(bar0 + 8 * stage, (par >> stage) & 1u, D.status);
+        par ^= 1u << stage;
+        if (!ok) *abort_flag = 1;
+        if (act && ok) {
+            const E* ev = ering + (size_t)stage * estride + pr.n0 + 1;
+            const Tab* A = tab + (size_t)(pr.gi * R + pr.r) * S;
+            neumaier_add(sum, comp, pair_taps<BF16>(A, S, P.Tw, P.Tw4, ev, pr));
+        }
+        worker_barrier(h);
+        if (*abort_flag) {
+            aborted = true;
+            break;
+        }
+        if (ht == 0 && k + nst < kb) {
+            mbar_arrive_expect_tx(bar0 + 8 * stage, rowbytes);
+            bulk_g2s(smem_u32(ering + (size_t)stage * estride), e_g + (size_t)(k + nst) * P.Mp, rowbytes,
+                     bar0 + 8 * stage);
+        }
+        if constexpr (MODE == kModeTAB) rx_cur = rx_nxt;
+        if (++stage == nst) stage = 0;
+        if (++j == P.n_rx) { j = 0; ++i; }
+    }
+    if (aborted) {
+        // drain this item's copies still in flight (bounded) before leaving
+        if (ht == 0) {
+            for (int q = k + 1; q < kb && q < k + nst; ++q) {
+                const int s = (q - ka) % nst;
+                mbar_wait_bounded(bar0 + 8 * s, (par >> s) & 1u, D.status);
+                par ^= 1u << s;
+            }
+        }
+        return false;
+    }
+    if (pix_ok) partial[(size_t)grp * P.W * P.H + (size_t)row * P.W + col] = sum + comp;
+    return true;
+}
+
 }  // namespace mbir

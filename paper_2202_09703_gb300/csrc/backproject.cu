@@ -16,16 +16,11 @@
 
 namespace mbir {
 
-constexpr int kBwdRows = 16;                       // rows per tile (one warp per row)
-constexpr int kBwdHalfThreads = kBwdRows * 32;     // threads per tile worker
-constexpr int kBwdThreads = 2 * kBwdHalfThreads;   // at most two workers per CTA
+constexpr int kBwdRows = kBwdTileRows;
+constexpr int kBwdHalfThreads = kBwdWorkerThreads;   // threads per tile worker
+constexpr int kBwdThreads = 2 * kBwdHalfThreads;     // at most two workers per CTA
 constexpr int kBwdMaxStages = 3;
 constexpr size_t kSmemLimit = 227 * 1024;
-
-__device__ __forceinline__ void half_barrier(int h)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "n"(kBwdHalfThreads) : "memory");
-}
 
 template <int NL, int MODE, bool BF16>
 __global__ void __launch_bounds__(kBwdThreads, 1)
@@ -49,105 +44,25 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + halves * nst) + h;
     volatile int* next_item = reinterpret_cast<volatile int*>(bars + halves * nst) + 2 + h;
     const uint32_t bar0 = smem_u32(bars + h * nst);
-    const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
-    const int N = P.W * P.H;
 
-    {
-        const int4* src = reinterpret_cast<const int4*>(tab_g);
-        int4* dst = reinterpret_cast<int4*>(tab);
-        const int n16 = (int)(tab_bytes / 16);
-        for (int t = tid; t < n16; t += blockDim.x) dst[t] = __ldg(src + t);
-    }
+    load_table_smem(tab, tab_g, tab_bytes, tid, blockDim.x);
     if (tid == 0) {
-        uint64_t* all_bars = reinterpret_cast<uint64_t*>(smem + tab_bytes + (size_t)halves * nst * ebytes);
-        for (int b = 0; b < halves * nst; ++b) mbar_init(smem_u32(all_bars + b), 1);
-        for (int b = 0; b < halves; ++b) reinterpret_cast<volatile int*>(all_bars + halves * nst)[b] = 0;
+        for (int b = 0; b < halves * nst; ++b) mbar_init(smem_u32(bars + b), 1);
+        for (int b = 0; b < halves; ++b) reinterpret_cast<volatile int*>(bars + halves * nst)[b] = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
     uint32_t par = 0;                    // expected phase parity per stage (bit s)
-    bool aborted = false;
-    while (!aborted) {
+    for (;;) {
         if (ht == 0) *next_item = atomicAdd(counter, 1);
-        half_barrier(h);
+        worker_barrier(h);
         const int it = *next_item;
-        half_barrier(h);                 // every thread has read the slot before it is reused
+        worker_barrier(h);               // every thread has read the slot before it is reused
         if (it >= nitems) break;
-        const int4 item = __ldg(items + it);
-        const int row = item.x * kBwdRows + hw, col = item.y * 32 + lane;
-        const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
-        const bool pix_ok = col < P.W && row < P.H;
-        const RowInfo ri = load_row(D.rows, min(row, P.H - 1));
-        const bool row_ok = pix_ok && ri.tvert < (float)(P.M - 1);
-        const int colc = min(col, P.W - 1);
-        const int ka = tx0 * P.n_rx, kb = tx1 * P.n_rx;
-        if (ht == 0) {
-            for (int s = 0; s < nst && ka + s < kb; ++s) {
-                mbar_arrive_expect_tx(bar0 + 8 * s, rowbytes);
-                bulk_g2s(smem_u32(ering + (size_t)s * (ebytes / sizeof(E))), e_g + (size_t)(ka + s) * P.Mp,
-                         rowbytes, bar0 + 8 * s);
-            }
-        }
-        float sum = 0.0f, comp = 0.0f;
-        Leg tx = {0.f, 0.f, 0.f, 0.f}, rx_cur = tx, rx_nxt = tx;
-        int hx_nxt = 0;
-        if constexpr (MODE == kModeTAB) {
-            if (row_ok) {
-                rx_cur = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + ka));
-                if (ka + 1 < kb) hx_nxt = __ldg(D.hidx + (size_t)__ldg(D.rxpos + ka + 1) * P.W + colc);
-            }
-        }
-        int i = tx0, j = 0, stage = 0, k = ka;
-        for (; k < kb; ++k) {
-            if constexpr (MODE == kModeTAB) {
-                // legs of the next A-scan stream in while this one is consumed
-                if (row_ok && k + 1 < kb) {
-                    float4 v = __ldg(D.legs + (size_t)row * P.nh + hx_nxt);
-                    rx_nxt = Leg{v.x, v.y, v.z, v.w};
-                    if (k + 2 < kb) hx_nxt = __ldg(D.hidx + (size_t)__ldg(D.rxpos + k + 2) * P.W + colc);
-                }
-            }
-            if (row_ok) {
-                if (j == 0) tx = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.txpos + i));
-                if constexpr (MODE != kModeTAB) rx_cur = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + k));
-            }
-            const Pair pr = make_pair(P, tx, rx_cur, ri.tau);
-            const bool act = row_ok && pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M;
-            const bool ok = mbar_wait_bounded(bar0 + 8 * stage, (par >> stage) & 1u, D.status);
-            par ^= 1u << stage;
-            if (!ok) *abort_flag = 1;
-            if (act && ok) {
-                const E* ev = ering + (size_t)stage * (ebytes / sizeof(E)) + pr.n0 + 1;
-                const Tab* A = tab + (size_t)(pr.gi * R + pr.r) * S;
-                neumaier_add(sum, comp, pair_taps<BF16>(A, S, P.Tw, P.Tw4, ev, pr));
-            }
-            half_barrier(h);
-            if (*abort_flag) {
-                aborted = true;
-                break;
-            }
-            if (ht == 0 && k + nst < kb) {
-                mbar_arrive_expect_tx(bar0 + 8 * stage, rowbytes);
-                bulk_g2s(smem_u32(ering + (size_t)stage * (ebytes / sizeof(E))),
-                         e_g + (size_t)(k + nst) * P.Mp, rowbytes, bar0 + 8 * stage);
-            }
-            if constexpr (MODE == kModeTAB) rx_cur = rx_nxt;
-            if (++stage == nst) stage = 0;
-            if (++j == P.n_rx) { j = 0; ++i; }
-        }
-        if (aborted) {
-            // drain this item's copies still in flight (bounded) before leaving
-            if (ht == 0) {
-                for (int q = k + 1; q < kb && q < k + nst; ++q) {
-                    const int s = (q - ka) % nst;
-                    mbar_wait_bounded(bar0 + 8 * s, (par >> s) & 1u, D.status);
-                    par ^= 1u << s;
-                }
-            }
+        if (!backproject_item<NL, MODE, BF16>(P, D, tab, e_g, __ldg(items + it), partial, ering, bar0, nst, ebytes,
+                                              abort_flag, par, h, hw, lane, ht))
             break;
-        }
-        if (pix_ok) partial[(size_t)grp * N + (size_t)row * P.W + col] = sum + comp;
     }
 }
 

@@ -1,21 +1,25 @@
 // Batched and served reconstructions: many independent MAP problems of
 // uneven size advance together, one iteration per engine step.
 //
-// Every step is one captured CUDA graph of eight grouped kernels.  Their grids
-// are fixed (persistent or grid-stride), and they read the current set of
-// active requests from device-side work lists that the host rewrites between
-// steps, so the graph is captured once and replayed as requests come and go
+// Every step is one captured CUDA graph of grouped kernels.  Their grids are
+// fixed (persistent or grid-stride), and they read the current set of active
+// requests from device-side work lists that the host rewrites between steps,
+// so the graph is captured once and replayed as requests come and go
 // (continuous batching):
-//   A^T e   persistent, 32 x 32 pixel tiles x transmitter groups of every
-//           request, split into contiguous cost-balanced ranges per CTA; a CTA
-//           reloads the pulse table only when its next item belongs to
-//           another request
+//   A^T e   persistent, two tile workers per CTA; each request's own work
+//           items (pixel tile x transmitter group, longest first) form a pool
+//           drained through a per-request counter.  A CTA starts at the
+//           request its share of the total cost falls on and walks on through
+//           the others until every pool is empty, loading a request's pulse
+//           table only when it joins that request's pool
 //   grad    prior gradient + FP64 partials per (request, pixel block)
 //   dir     Polak-Ribiere+ scalars per request, then directions + curvature
-//   A d     persistent span gather over each request's sorted records, in
-//           chunks of spans assigned to CTAs by cost; warps share a chunk
+//   A d     persistent span gather over each request's sorted records, spans
+//           largest first, pools and CTA placement as for A^T e
 //   P q     direct-arrival projection per (request, A-scan) with FP64 norms
 //   step    majorize-minimize step per request; x and e updated
+// The apply kernels run the same per-item and per-span code as the
+// single-request kernels, on the geometry's own work decomposition.
 // Each request's arithmetic depends only on its own data and its own fixed
 // work decomposition, so a result is bitwise the same alone and in any mix.
 // Admission is by device memory: a request is admitted when its state fits
@@ -41,10 +45,10 @@ using namespace mbir;
 
 namespace {
 
-constexpr int kEngThreads = 1024;          // apply kernels: 32 warps
-constexpr int kEngStages = 3;              // residual-row ring of A^T e
-constexpr int kEngTile = 32;               // 32 x 32 pixel tiles
-constexpr int kSpanChunk = 64;             // spans per A d work chunk
+constexpr int kEngThreads = 1024;          // apply kernels: 32 warps (A^T e: two tile workers)
+constexpr int kEngStages = 3;              // residual-row ring of A^T e, per worker (2 if 3 do not fit)
+constexpr size_t kEngHdr = 128;            // mbarriers and flags at the start of shared memory
+constexpr size_t kEngSmem = 227 * 1024;
 constexpr int kUpdChunk = 4096;            // elements per update item
 constexpr size_t kTableMaxBytes = 160 * 1024;
 constexpr int kMpMax = 4224;
@@ -74,18 +78,20 @@ struct ReqDesc {
     const float* msq;
     double* sc;
     double* part;          // [3 nblk grad | nblk curvature | K projection]
+    const int* span_order; // A d spans, largest first
+    const int4* items;     // A^T e work items, longest first
     PriorParams pr;
     int it;                // iteration index of this step
-    int ngroups;
+    int ngroups;           // transmitter groups (partial images) of the A^T e items
+    int n_items;
+    int nsp;               // K x 32-sample spans
     int nblk;              // pixel blocks of kRedThreads
 };
 
 struct EngLists {
     ReqDesc* desc;
-    int4* bwd_items;       // {req, tile_r << 16 | tile_c, tx0 | tx1 << 16, group}
-    int* bwd_cta;          // per-CTA item ranges (gridDim + 1)
-    int4* fwd_chunks;      // {req, first span, end span, 0}
-    int* fwd_cta;
+    int* pool;             // per request: next A d span, next A^T e item (zeroed every step)
+    int* start;            // per CTA: first request of A^T e [0, G), of A d [G, 2G)
     int2* pixblk;          // {req, pixel block}
     int2* rowblk;          // {req, A-scan}
     int4* upd;             // {req, kind (0 x, 1 e), start, 0}
@@ -98,99 +104,76 @@ __device__ __forceinline__ float* dnew_of(const ReqDesc& R) { return (R.it & 1) 
 // ---------------------------------------------------------------------------
 // A^T e over every active request
 // ---------------------------------------------------------------------------
+// Shared-memory geometry of one request in the apply kernels.
+template <typename Tab, typename E>
+__device__ __forceinline__ void eng_layout(const GeomParams& P, size_t* tab_bytes, size_t* ebytes, int* nst)
+{
+    *tab_bytes = ((size_t)P.Gt * (P.Q + 1) * table_stride(P.Tw4) * sizeof(Tab) + 127) & ~(size_t)127;
+    *ebytes = ((size_t)P.Mp * sizeof(E) + 127) & ~(size_t)127;
+    *nst = (kEngHdr + *tab_bytes + 2 * kEngStages * *ebytes <= kEngSmem) ? kEngStages : 2;
+}
+
+// Whether request rq's pool (slot 0: A d spans, 1: A^T e items) still has
+// work; the answer is the same for every thread of the CTA.
+__device__ __forceinline__ bool eng_pool_live(const int* pool, int rq, int slot, int total, volatile int* flag)
+{
+    if (threadIdx.x == 0) *flag = *reinterpret_cast<const volatile int*>(pool + 2 * rq + slot) < total;
+    __syncthreads();
+    const bool live = *flag != 0;
+    __syncthreads();
+    return live;
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(kEngThreads, 1) eng_bwd_kernel(EngLists L)
 {
     using Tab = typename TabT<BF16>::type;
     using E = typename ET<BF16>::type;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + kEngStages);
-    Tab* tab = reinterpret_cast<Tab*>(smem + 128);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);                               // [2][kEngStages]
+    volatile int* flags = reinterpret_cast<volatile int*>(bars + 2 * kEngStages);     // abort[2], next[2], live
+    Tab* tab = reinterpret_cast<Tab*>(smem + kEngHdr);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int h = warp / kBwdTileRows, hw = warp % kBwdTileRows, ht = tid % kBwdWorkerThreads;
     if (tid == 0) {
-        for (int s = 0; s < kEngStages; ++s) mbar_init(smem_u32(bars + s), 1);
-        *abort_flag = 0;
+        for (int b = 0; b < 2 * kEngStages; ++b) mbar_init(smem_u32(bars + b), 1);
+        flags[0] = flags[1] = 0;
         fence_mbar_init();
     }
     __syncthreads();
-    const uint32_t bar0 = smem_u32(bars);
+    const uint32_t bar0 = smem_u32(bars + h * kEngStages);
     uint32_t par = 0;
+    const int nreq = L.counts[0];
+    if (nreq <= 0) return;
+    const int r0 = L.start[blockIdx.x] % nreq;
     int cur = -1;
-    size_t tab_bytes = 0, ebytes = 0;
-    E* ring = nullptr;
-    const int i0 = L.bwd_cta[blockIdx.x], i1 = L.bwd_cta[blockIdx.x + 1];
-    for (int it = i0; it < i1; ++it) {
-        const int4 item = L.bwd_items[it];
-        const ReqDesc& R = L.desc[item.x];
+    for (int t = 0; t < nreq; ++t) {
+        const int rq = (r0 + t) % nreq;
+        const ReqDesc& R = L.desc[rq];
+        if (!eng_pool_live(L.pool, rq, 1, R.n_items, flags + 4)) continue;
         const GeomParams& P = R.P;
-        const int S = table_stride(P.Tw4), Q1 = P.Q + 1;
-        if (item.x != cur) {
-            __syncthreads();
-            tab_bytes = ((size_t)P.Gt * Q1 * S * sizeof(Tab) + 127) & ~(size_t)127;
-            ebytes = ((size_t)P.Mp * sizeof(E) + 127) & ~(size_t)127;
-            ring = reinterpret_cast<E*>(smem + 128 + tab_bytes);
+        size_t tab_bytes, ebytes;
+        int nst;
+        eng_layout<Tab, E>(P, &tab_bytes, &ebytes, &nst);
+        if (rq != cur) {
             load_table_smem(tab, BF16 ? (const void*)R.tab_bf : (const void*)R.tab, tab_bytes, tid, kEngThreads);
-            cur = item.x;
+            cur = rq;
             __syncthreads();
         }
+        E* ering = reinterpret_cast<E*>(smem + kEngHdr + tab_bytes + (size_t)h * nst * ebytes);
         const E* e_g = BF16 ? (const E*)(const void*)R.ebf : (const E*)(const void*)R.e;
-        const int row = (item.y >> 16) * kEngTile + warp, col = (item.y & 0xffff) * kEngTile + lane;
-        const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
-        const bool pix_ok = col < P.W && row < P.H;
-        const RowInfo ri = load_row(R.D.rows, min(row, P.H - 1));
-        const bool row_ok = pix_ok && ri.tvert < (float)(P.M - 1);
-        const int colc = min(col, P.W - 1);
-        const int ka = tx0 * P.n_rx, kb = tx1 * P.n_rx;
-        const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
-        if (tid == 0) {
-            for (int s = 0; s < kEngStages && ka + s < kb; ++s) {
-                mbar_arrive_expect_tx(bar0 + 8 * s, rowbytes);
-                bulk_g2s(smem_u32(ring + (size_t)s * (ebytes / sizeof(E))), e_g + (size_t)(ka + s) * P.Mp,
-                         rowbytes, bar0 + 8 * s);
-            }
+        for (;;) {
+            if (ht == 0) flags[2 + h] = atomicAdd(L.pool + 2 * rq + 1, 1);
+            worker_barrier(h);
+            const int it = flags[2 + h];
+            worker_barrier(h);
+            if (it >= R.n_items) break;
+            if (!backproject_item<1, kModeTAB, BF16>(P, R.D, tab, e_g, __ldg(R.items + it), R.bpart, ering, bar0, nst,
+                                                     ebytes, flags + h, par, h, hw, lane, ht))
+                break;
         }
-        float sum = 0.0f, comp = 0.0f;
-        Leg tx = {0.f, 0.f, 0.f, 0.f};
-        int i = tx0, j = 0, stage = 0;
-        bool aborted = false;
-        int k = ka;
-        for (; k < kb; ++k) {
-            Leg rx = tx;
-            if (row_ok) {
-                if (j == 0) tx = get_leg<1, kModeTAB>(P, R.D, ri, row, colc, __ldg(R.D.txpos + i));
-                rx = get_leg<1, kModeTAB>(P, R.D, ri, row, colc, __ldg(R.D.rxpos + k));
-            }
-            const Pair pr = make_pair(P, tx, rx, ri.tau);
-            const bool act = row_ok && pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M;
-            const bool ok = mbar_wait_bounded(bar0 + 8 * stage, (par >> stage) & 1u, R.D.status);
-            par ^= 1u << stage;
-            if (!ok) *abort_flag = 1;
-            if (act && ok) {
-                const E* ev = ring + (size_t)stage * (ebytes / sizeof(E)) + pr.n0 + 1;
-                const Tab* A = tab + (size_t)(pr.gi * Q1 + pr.r) * S;
-                neumaier_add(sum, comp, pair_taps<BF16>(A, S, P.Tw, P.Tw4, ev, pr));
-            }
-            __syncthreads();
-            if (*abort_flag) { aborted = true; break; }
-            if (tid == 0 && k + kEngStages < kb) {
-                mbar_arrive_expect_tx(bar0 + 8 * stage, rowbytes);
-                bulk_g2s(smem_u32(ring + (size_t)stage * (ebytes / sizeof(E))),
-                         e_g + (size_t)(k + kEngStages) * P.Mp, rowbytes, bar0 + 8 * stage);
-            }
-            if (++stage == kEngStages) stage = 0;
-            if (++j == P.n_rx) { j = 0; ++i; }
-        }
-        if (aborted) {
-            if (tid == 0)
-                for (int q = k + 1; q < kb && q < k + kEngStages; ++q) {
-                    const int s = (q - ka) % kEngStages;
-                    mbar_wait_bounded(bar0 + 8 * s, (par >> s) & 1u, R.D.status);
-                    par ^= 1u << s;
-                }
-            return;
-        }
-        if (pix_ok) R.bpart[(size_t)grp * P.W * P.H + (size_t)row * P.W + col] = sum + comp;
+        __syncthreads();                 // both workers are done before the table is replaced
+        if (flags[0] | flags[1]) return; // a residual copy never landed (status set)
     }
 }
 
@@ -207,7 +190,7 @@ __global__ void eng_bwd_reduce_kernel(EngLists L)
         const int v = rb.y * kRedThreads + threadIdx.x;
         if (v >= N) continue;
         const int row = v / P.W;
-        const int row0 = (row / kEngTile) * kEngTile;
+        const int row0 = (row / kBwdTileRows) * kBwdTileRows;
         float s = 0.0f, c = 0.0f;
         if (R.D.rows[row0].tvert < (float)(P.M - 1))
             for (int g = 0; g < R.ngroups; ++g) neumaier_add(s, c, R.bpart[(size_t)g * N + v]);
@@ -324,40 +307,43 @@ __global__ void eng_dir_kernel(EngLists L)
     }
 }
 
-// q = A d over every active request (span chunks, table reloaded per request)
+// q = A d over every active request: warps take spans of a request's pool,
+// largest first; the CTA moves on when the pool is empty
 template <bool BF16>
 __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
 {
     using Tab = typename TabT<BF16>::type;
     constexpr int WARPS = kEngThreads / 32;
     extern __shared__ __align__(128) unsigned char smem[];
-    int* counter = reinterpret_cast<int*>(smem);
-    Tab* tab = reinterpret_cast<Tab*>(smem + 128);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem);
+    Tab* tab = reinterpret_cast<Tab*>(smem + kEngHdr);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int4* sr = reinterpret_cast<int4*>(smem + 128 + kTableMaxBytes) + warp * 32;
-    float4* sw = reinterpret_cast<float4*>(smem + 128 + kTableMaxBytes) + WARPS * 32 + warp * 32;
+    int4* sr = reinterpret_cast<int4*>(smem + kEngHdr + kTableMaxBytes) + warp * 32;
+    float4* sw = reinterpret_cast<float4*>(smem + kEngHdr + kTableMaxBytes) + WARPS * 32 + warp * 32;
+    const int nreq = L.counts[0];
+    if (nreq <= 0) return;
+    const int r0 = L.start[gridDim.x + blockIdx.x] % nreq;
     int cur = -1;
-    const int c0 = L.fwd_cta[blockIdx.x], c1 = L.fwd_cta[blockIdx.x + 1];
-    for (int ch = c0; ch < c1; ++ch) {
-        const int4 cd = L.fwd_chunks[ch];
-        const ReqDesc& R = L.desc[cd.x];
+    for (int t = 0; t < nreq; ++t) {
+        const int rq = (r0 + t) % nreq;
+        const ReqDesc& R = L.desc[rq];
+        if (!eng_pool_live(L.pool, rq, 0, R.nsp, flag)) continue;
         const GeomParams& P = R.P;
         const int S = table_stride(P.Tw4);
-        __syncthreads();
-        if (cd.x != cur) {
+        if (rq != cur) {
             const size_t tab_bytes = ((size_t)P.Gt * (P.Q + 1) * S * sizeof(Tab) + 127) & ~(size_t)127;
             load_table_smem(tab, BF16 ? (const void*)R.tab_bf : (const void*)R.tab, tab_bytes, tid, kEngThreads);
-            cur = cd.x;
+            cur = rq;
+            __syncthreads();
         }
-        if (tid == 0) *counter = cd.y;
-        __syncthreads();
         const int nspan = (P.M + 31) >> 5;
         const float* x = dnew_of(R);
         for (;;) {
-            int s = 0;
-            if (lane == 0) s = atomicAdd(counter, 1);
-            s = __shfl_sync(0xffffffffu, s, 0);
-            if (s >= cd.z) break;
+            int idx = 0;
+            if (lane == 0) idx = atomicAdd(L.pool + 2 * rq, 1);
+            idx = __shfl_sync(0xffffffffu, idx, 0);
+            if (idx >= R.nsp) break;
+            const int s = __ldg(R.span_order + idx);
             const int k = s / nspan, sp = s - k * nspan;
             const int n = sp * 32 + lane;
             const int2 rb = __ldg(R.runs + s);
@@ -366,8 +352,9 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
             float* qo = R.q + (size_t)k * P.Mp;
             if (n < P.Mp) qo[n] = (n < P.M) ? acc : 0.0f;
             if (sp == nspan - 1)
-                for (int t = nspan * 32 + lane; t < P.Mp; t += 32) qo[t] = 0.0f;
+                for (int u = nspan * 32 + lane; u < P.Mp; u += 32) qo[u] = 0.0f;
         }
+        __syncthreads();                 // every warp is done before the table is replaced
     }
 }
 
@@ -482,12 +469,6 @@ size_t request_bytes(const mbir_geometry* g, int ngroups)
     return b;
 }
 
-int groups_for(const mbir_geometry* g)
-{
-    // about 64 A-scans per work item
-    const int txg = std::max(1, std::min(g->P.n_tx, 64 / std::max(1, g->P.n_rx)));
-    return (g->P.n_tx + txg - 1) / txg;
-}
 
 }  // namespace
 
@@ -502,7 +483,7 @@ struct mbir_engine {
     bool dirty = true;                   // work lists must be rebuilt
     // device work lists (fixed capacity; growing them re-captures the graph)
     EngLists L{};
-    size_t cap_desc = 0, cap_bwd = 0, cap_fwd = 0, cap_pix = 0, cap_row = 0, cap_upd = 0;
+    size_t cap_desc = 0, cap_pool = 0, cap_pix = 0, cap_row = 0, cap_upd = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_bf16 = -1;
     size_t smem_bwd = 0, smem_fwd = 0;
@@ -558,7 +539,7 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     const mbir_geometry* g = r->g;
     const GeomParams& P = g->P;
     const size_t N = (size_t)P.W * P.H, KMp = (size_t)P.K * P.Mp;
-    r->ngroups = groups_for(g);
+    r->ngroups = g->n_groups;
     r->nblk = (int)((N + kRedThreads - 1) / kRedThreads);
     cudaError_t e = cudaSuccess;
 #define AL(ptr, n) if (e == cudaSuccess) e = cudaMallocAsync((void**)&(ptr), sizeof(*(ptr)) * std::max<size_t>((n), 1), st)
@@ -623,85 +604,86 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.part = r->part;
     d.pr = make_prior_params(&r->prior);
     d.it = r->it;
+    d.span_order = g->d_span_order;
+    d.items = g->d_items;
     d.ngroups = r->ngroups;
+    d.n_items = g->n_items;
+    d.nsp = g->P.K * ((g->P.M + 31) / 32);
     d.nblk = r->nblk;
+}
+
+// First request of each CTA: the requests' costs laid end to end and cut into
+// G equal shares; CTA c starts at the request its share begins in.
+std::vector<int> start_requests(const std::vector<double>& cost, int G)
+{
+    std::vector<int> st(G, 0);
+    double total = 0;
+    for (double c : cost) total += c;
+    double acc = 0;
+    size_t r = 0;
+    for (int c = 0; c < G; ++c) {
+        const double at = total * c / G;
+        while (r + 1 < cost.size() && acc + cost[r] <= at) acc += cost[r++];
+        st[c] = (int)r;
+    }
+    return st;
 }
 
 // Rebuilds the per-epoch work lists for the active set.
 int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 {
     const int G = E->n_sm;
-    std::vector<int4> bwd;
-    std::vector<double> bwd_cost;
-    std::vector<int4> fwd;
-    std::vector<double> fwd_cost;
+    std::vector<double> bwd_cost, fwd_cost;
     std::vector<int2> pix, rows;
     std::vector<int4> upd;
     for (size_t ri = 0; ri < E->active.size(); ++ri) {
         const Request* r = E->active[ri];
-        const GeomParams& P = r->g->P;
-        const int ntr = (P.H + kEngTile - 1) / kEngTile, ntc = (P.W + kEngTile - 1) / kEngTile;
-        const int txg = (P.n_tx + r->ngroups - 1) / r->ngroups;
+        const mbir_geometry* g = r->g;
+        const GeomParams& P = g->P;
+        // A^T e: the geometry's estimates of its items (tile x transmitter group)
+        const int TR = backproject_tile_rows(), ntr = (P.H + TR - 1) / TR;
+        double cb = 0;
         for (int tr = 0; tr < ntr; ++tr) {
-            if (!(r->g->h_tvert[tr * kEngTile] < (float)(P.M - 1))) continue;
-            for (int tc = 0; tc < ntc; ++tc)
-                for (int gi = 0; gi < r->ngroups; ++gi) {
-                    const int t0 = gi * txg, t1 = std::min(P.n_tx, t0 + txg);
-                    if (t0 >= t1) continue;
-                    bwd.push_back(make_int4((int)ri, (tr << 16) | tc, t0 | (t1 << 16), gi));
-                    // the geometry's estimates per 16-row tile and transmitter position
-                    const int TR = backproject_tile_rows(), ntr16 = (P.H + TR - 1) / TR;
-                    double c = 0;
-                    for (int r16 = tr * kEngTile / TR; r16 < std::min(ntr16, (tr + 1) * kEngTile / TR); ++r16)
-                        for (int t = t0; t < t1; ++t)
-                            c += r->g->h_bwd_cost[((size_t)r16 * r->g->bwd_ntc + tc) * P.n_tx + t];
-                    bwd_cost.push_back(c);
-                }
+            if (!(g->h_tvert[tr * TR] < (float)(P.M - 1))) continue;
+            for (size_t t = (size_t)tr * g->bwd_ntc * P.n_tx; t < (size_t)(tr + 1) * g->bwd_ntc * P.n_tx; ++t)
+                cb += g->h_bwd_cost[t];
         }
-        const int nspan = (P.M + 31) / 32;
-        const long long nsp = (long long)P.K * nspan;
-        for (long long s0 = 0; s0 < nsp; s0 += kSpanChunk) {
-            const long long s1 = std::min(nsp, s0 + kSpanChunk);
-            double c = 0;
-            for (long long s = s0; s < s1; ++s) c += r->g->h_span_cost[s] + 8;
-            fwd.push_back(make_int4((int)ri, (int)s0, (int)s1, 0));
-            fwd_cost.push_back(c * 32.0);
-        }
+        bwd_cost.push_back(cb);
+        // A d: records per span plus a fixed cost per span, in the same units (warp tap loops)
+        const long long nsp = (long long)P.K * ((P.M + 31) / 32);
+        double cf = 0;
+        for (long long sp = 0; sp < nsp; ++sp) cf += g->h_span_cost[sp] + 8;
+        fwd_cost.push_back(cf);
         for (int b = 0; b < r->nblk; ++b) pix.push_back(make_int2((int)ri, b));
         for (int k = 0; k < P.K; ++k) rows.push_back(make_int2((int)ri, k));
         const long long N = (long long)P.W * P.H, KMp = (long long)P.K * P.Mp;
         for (long long t = 0; t < N; t += kUpdChunk) upd.push_back(make_int4((int)ri, 0, (int)t, 0));
         for (long long t = 0; t < KMp; t += kUpdChunk) upd.push_back(make_int4((int)ri, 1, (int)t, 0));
     }
-    std::vector<int> bcut = balance(bwd_cost, G), fcut = balance(fwd_cost, G);
+    std::vector<int> start = start_requests(bwd_cost, G), fstart = start_requests(fwd_cost, G);
+    start.insert(start.end(), fstart.begin(), fstart.end());
     cudaError_t e = cudaSuccess;
     e = ensure_cap(&E->L.desc, &E->cap_desc, E->active.size(), grew);
-    if (e == cudaSuccess) e = ensure_cap(&E->L.bwd_items, &E->cap_bwd, bwd.size(), grew);
-    if (e == cudaSuccess) e = ensure_cap(&E->L.fwd_chunks, &E->cap_fwd, fwd.size(), grew);
+    if (e == cudaSuccess) e = ensure_cap(&E->L.pool, &E->cap_pool, 2 * E->cap_desc, grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.pixblk, &E->cap_pix, pix.size(), grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.rowblk, &E->cap_row, rows.size(), grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.upd, &E->cap_upd, upd.size(), grew);
     if (e != cudaSuccess) return MBIR_ERR_OOM;
-    if (!E->L.bwd_cta) {
-        e = cudaMalloc((void**)&E->L.bwd_cta, sizeof(int) * (G + 1));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&E->L.fwd_cta, sizeof(int) * (G + 1));
+    if (!E->L.start) {
+        e = cudaMalloc((void**)&E->L.start, sizeof(int) * 2 * G);
         if (e == cudaSuccess) e = cudaMalloc((void**)&E->L.counts, sizeof(int) * 8);
         if (e != cudaSuccess) return MBIR_ERR_OOM;
         *grew = true;
     }
     int counts[8] = {(int)E->active.size(), (int)pix.size(), (int)rows.size(), (int)upd.size(), 0, 0, 0, 0};
     // pageable copies are staged before cudaMemcpyAsync returns, so the host vectors may go away
-    if (!bwd.empty()) e = cudaMemcpyAsync(E->L.bwd_items, bwd.data(), sizeof(int4) * bwd.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !fwd.empty())
-        e = cudaMemcpyAsync(E->L.fwd_chunks, fwd.data(), sizeof(int4) * fwd.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !pix.empty())
+    if (!pix.empty())
         e = cudaMemcpyAsync(E->L.pixblk, pix.data(), sizeof(int2) * pix.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !rows.empty())
         e = cudaMemcpyAsync(E->L.rowblk, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !upd.empty())
         e = cudaMemcpyAsync(E->L.upd, upd.data(), sizeof(int4) * upd.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(E->L.bwd_cta, bcut.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(E->L.fwd_cta, fcut.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E->L.start, start.data(), sizeof(int) * 2 * G, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(E->L.counts, counts, sizeof(counts), cudaMemcpyHostToDevice, st);
     return e == cudaSuccess ? MBIR_OK : MBIR_ERR_CUDA;
 }
@@ -710,6 +692,8 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, cudaStream_t st)
 {
     const int G = E->n_sm, SG = E->n_sm * 8;
+    cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
+    if (e != cudaSuccess) return e;
     if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
     else eng_bwd_kernel<false><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
     eng_bwd_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
@@ -737,8 +721,8 @@ int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out)
     if (E->n_sm < 1) E->n_sm = 1;
     E->budget = budget_bytes;
     E->max_active = max_active;
-    E->smem_bwd = 128 + kTableMaxBytes + (size_t)kEngStages * (((size_t)kMpMax * 4 + 127) & ~(size_t)127);
-    E->smem_fwd = 128 + kTableMaxBytes + (size_t)kEngThreads * (sizeof(int4) + sizeof(float4));
+    E->smem_bwd = kEngSmem;
+    E->smem_fwd = kEngHdr + kTableMaxBytes + (size_t)kEngThreads * (sizeof(int4) + sizeof(float4));
     cudaError_t e = cudaFuncSetAttribute(eng_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_bwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_bwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
@@ -757,8 +741,7 @@ int mbir_engine_destroy(mbir_engine* E)
         if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
     }
     cudaDeviceSynchronize();
-    void* ptrs[] = {E->L.desc, E->L.bwd_items, E->L.bwd_cta, E->L.fwd_chunks, E->L.fwd_cta, E->L.pixblk,
-                    E->L.rowblk, E->L.upd, E->L.counts};
+    void* ptrs[] = {E->L.desc, E->L.pool, E->L.start, E->L.pixblk, E->L.rowblk, E->L.upd, E->L.counts};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (E->graph) cudaGraphExecDestroy(E->graph);
@@ -773,8 +756,10 @@ int mbir_engine_submit(mbir_engine* E, const mbir_geometry* g, const void* y_dev
     if (g->P.mode != MBIR_MODE_TAB || !g->d_rec_key || !g->h_span_cost) return MBIR_ERR_UNSUPPORTED;
     const size_t tsz = g->P.precision == MBIR_PREC_BF16 ? 4 : 8;
     const size_t tab = ((size_t)g->P.Gt * (g->P.Q + 1) * table_stride(g->P.Tw4) * tsz + 127) & ~(size_t)127;
-    if (tab > kTableMaxBytes || g->P.Mp > kMpMax || g->device != E->device) return MBIR_ERR_UNSUPPORTED;
-    const size_t need = request_bytes(g, groups_for(g));
+    const size_t eb = ((size_t)g->P.Mp * (g->P.precision == MBIR_PREC_BF16 ? 2 : 4) + 127) & ~(size_t)127;
+    if (tab > kTableMaxBytes || g->P.Mp > kMpMax || kEngHdr + tab + 2 * 2 * eb > kEngSmem || g->device != E->device)
+        return MBIR_ERR_UNSUPPORTED;
+    const size_t need = request_bytes(g, g->n_groups);
     if (need > E->budget) return MBIR_ERR_BUSY;
     auto r = std::make_unique<Request>();
     r->ticket = E->next_ticket++;
