@@ -50,24 +50,35 @@ def parse():
                     help="cfg1: the headline workload; batched: uneven scenes through the engine vs serial "
                          "solves; served: Poisson arrivals of mixed sizes through the engine vs a serial queue")
     ap.add_argument("--requests", type=int, default=0, help="requests for the batched / served workloads")
+    ap.add_argument("--source-hash", default="",
+                    help="print the hash profiles/traffic.txt records for these comma-separated sources and exit")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="storage precision of the --apply-only geometry")
     return ap.parse_args()
 
 
 def measured_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
-    import hashlib
+    """DRAM bytes per launch from the committed ncu summary, if none of the
+    kernel's source files changed since the capture (else None)."""
     try:
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             if line.startswith("#") or not line.strip():
                 continue
-            name, src, sha, rd, wr = line.split()[:5]
+            name, srcs, sha, rd, wr = line.split()[:5]
             if name.startswith(kernel):
-                cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
-                return float(rd) + float(wr) if cur == sha else None
+                return float(rd) + float(wr) if source_hash(srcs) == sha else None
     except OSError:
         return None
     return None
+
+
+def source_hash(srcs: str) -> str:
+    """sha256 (first 16 hex digits) over comma-separated source files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for src in srcs.split(","):
+        h.update(open(os.path.join(ROOT, src), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -339,6 +350,9 @@ def run_gpu(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "mode": geo.mode, "iterations": scene.n_iter,
+                      "forward_window_spans": geo.info.forward_window_spans,
+                      "forward_window_ms": [round(t, 4) for t in geo.info.forward_window_ms],
+                      "adjoint_groups": geo.info.adjoint_groups,
                       "l2": "flushed between steps (256 MB write); device time from CUDA events per step",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)),
@@ -367,17 +381,19 @@ def run_apply_only(args):
     B.build()
     from paper_2202_09703_gb300 import mbir as M
     from paper_2202_09703_gb300 import synth as S
-    scene = S.cfg1()
+    scene = S.cfg1().copy(precision=args.precision)
     dev = torch.device("cuda:0")
     geo = M.Geometry(scene, mode=args.mode)
     x = torch.as_tensor(S.phantom(scene, 0).reshape(-1), dtype=torch.float32, device=dev)
-    y = torch.empty(scene.K * scene.M, dtype=torch.float32, device=dev)
+    y = torch.empty(scene.K * scene.M, dtype=torch.float32 if args.precision == "fp32" else torch.bfloat16,
+                    device=dev)
     b = torch.empty(scene.N, dtype=torch.float32, device=dev)
     for _ in range(args.apply_only):
         geo.forward(x, y)
         geo.backproject(y, b)
     torch.cuda.synchronize()
-    print(json.dumps({"apply_only": args.apply_only, "mode": geo.mode, "y_norm": float(y.norm()),
+    print(json.dumps({"apply_only": args.apply_only, "mode": geo.mode, "precision": geo.precision,
+                      "y_norm": float(y.float().norm()),
                       "b_norm": float(b.norm())}))
 
 
@@ -514,6 +530,9 @@ def run_served(args):
 
 def main():
     args = parse()
+    if args.source_hash:
+        print(source_hash(args.source_hash))
+        return
     if args.workload == "batched":
         run_batched(args)
         return

@@ -133,6 +133,9 @@ typedef struct {
     int mode;                    /* resolved mbir_mode (OTF or TAB) */
     int precision;
     int64_t device_bytes;        /* tables + workspace held by the handle */
+    int forward_window_spans;    /* TAB records: 32-sample spans per A x work unit (timed at creation), else 0 */
+    double forward_window_ms[3]; /* the A x times measured for windows of 1, 2 and 4 spans (0 if not timed) */
+    int adjoint_groups;          /* transmitter groups of the A^T r work items */
 } mbir_geometry_info;
 
 typedef struct mbir_geometry mbir_geometry;
@@ -157,6 +160,14 @@ int mbir_destroy_geometry(mbir_geometry* g);
 size_t mbir_geometry_bytes(const mbir_geometry* g);
 
 int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info);
+
+/* Override the A x window chosen at creation (TAB records only): every warp of
+ * the A x launch then covers `spans` consecutive 32-sample spans (1, 2 or 4).
+ * A tuning control with no counterpart in the paper; the output bits do not
+ * depend on it.  Synchronises the device; the handle must not be in use by
+ * another call or an engine.  Errors: MBIR_ERR_INVALID_ARG (other values),
+ * MBIR_ERR_UNSUPPORTED (no record list), MBIR_ERR_OOM, MBIR_ERR_CUDA. */
+int mbir_set_forward_window(mbir_geometry* g, int spans);
 
 /* y = A x (eq. 11-13 summed over voxels).  x_dev: N floats.  y_dev: K x M,
  * float (FP32) or bfloat16 (BF16 precision).  Every output sample is written

@@ -52,28 +52,36 @@ __device__ __forceinline__ void neumaier_add(float& sum, float& comp, float v)
     sum = t;
 }
 
-// One 32-sample span of A x from the sorted record list: records [r_lo, r_hi)
-// of A-scan base `base`.  sr / sw are this warp's 32-entry staging slots.
-// Returns the lane's output sample value (compensated across batches).
-template <bool BF16>
-__device__ __forceinline__ float span_gather(const typename TabT<BF16>::type* __restrict__ tab, int S, int Tw,
-                                             const int2* __restrict__ rkey, const float4* __restrict__ rw,
-                                             long long base, int r_lo, int r_hi, const float* __restrict__ x,
-                                             int n, int lane, int4* sr, float4* sw)
+// One window of A x from the sorted record list: SUB sub-spans of 32 samples,
+// the lane's samples being n + 32 s (s < SUB), over the records [r_lo, r_hi)
+// of A-scan base `base` that reach the window.  sr / sw are this warp's
+// 32-entry staging slots.  Records are staged 32 at a time in batches aligned
+// to multiples of 32 in the A-scan's record list, and each lane adds a batch's
+// taps in record order before compensating the batch sum into its total, so a
+// sample's value does not depend on the window size (records of a batch that
+// miss the sample add nothing).
+template <bool BF16, int SUB>
+__device__ __forceinline__ void span_gather(const typename TabT<BF16>::type* __restrict__ tab, int S, int Tw,
+                                            const int2* __restrict__ rkey, const float4* __restrict__ rw,
+                                            long long base, int r_lo, int r_hi, const float* __restrict__ x, int n,
+                                            int lane, int4* sr, float4* sw, float (&out)[SUB])
 {
     using Tab = typename TabT<BF16>::type;
-    float sum = 0.0f, comp = 0.0f;
+    float sum[SUB], comp[SUB];
+#pragma unroll
+    for (int s = 0; s < SUB; ++s) sum[s] = comp[s] = 0.0f;
+    const int r_first = r_lo & ~31;
     int2 kv = make_int2(0, 0);
     float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
     float xv = 0.0f;
-    if (r_lo + lane < r_hi) {
-        kv = __ldg(rkey + base + r_lo + lane);
-        wv = __ldg(rw + base + r_lo + lane);
+    if (r_first + lane >= r_lo && r_first + lane < r_hi) {
+        kv = __ldg(rkey + base + r_first + lane);
+        wv = __ldg(rw + base + r_first + lane);
         xv = __ldg(x + kv.x);
     }
-    for (int r0 = r_lo; r0 < r_hi; r0 += 32) {
-        const int cnt = min(32, r_hi - r0);
-        if (lane < cnt) {
+    for (int r0 = r_first; r0 < r_hi; r0 += 32) {
+        const int j0 = max(0, r_lo - r0), j1 = min(32, r_hi - r0);
+        if (lane >= j0 && lane < j1) {
             const int key = kv.y;
             const int lo = (key >> kRecShift) + 1;
             const int len = Tw - (key & 1);                 // tau = t0 exactly lies outside
@@ -86,23 +94,64 @@ __device__ __forceinline__ float span_gather(const typename TabT<BF16>::type* __
             wv = __ldg(rw + base + r0 + 32 + lane);
             xv = __ldg(x + kv.x);
         }
-        float2 acc = make_float2(0.f, 0.f);
+        float2 acc[SUB];
+#pragma unroll
+        for (int s = 0; s < SUB; ++s) acc[s] = make_float2(0.f, 0.f);
 #pragma unroll 4
-        for (int j = 0; j < cnt; ++j) {
+        for (int j = j0; j < j1; ++j) {
             const int4 d = sr[j];
-            if ((unsigned)(n - d.x) < (unsigned)d.y) {
+            const int m = n - d.x;                           // tap of the lane's first sample
+            if (m < d.y && m + 32 * (SUB - 1) >= 0) {
                 const float4 w4 = sw[j];
-                const Tab* A = tab + (d.z + n);
-                acc = __ffma2_rn(TabT<BF16>::ld(A), make_float2(w4.x, w4.y), acc);
-                acc = __ffma2_rn(TabT<BF16>::ld(A + S), make_float2(w4.z, w4.w), acc);
+#pragma unroll
+                for (int s = 0; s < SUB; ++s) {
+                    if ((unsigned)(m + 32 * s) < (unsigned)d.y) {
+                        const Tab* A = tab + (d.z + n + 32 * s);
+                        acc[s] = __ffma2_rn(TabT<BF16>::ld(A), make_float2(w4.x, w4.y), acc[s]);
+                        acc[s] = __ffma2_rn(TabT<BF16>::ld(A + S), make_float2(w4.z, w4.w), acc[s]);
+                    }
+                }
             }
         }
         __syncwarp();
-        neumaier_add(sum, comp, acc.x + acc.y);
+#pragma unroll
+        for (int s = 0; s < SUB; ++s) neumaier_add(sum[s], comp[s], acc[s].x + acc[s].y);
     }
-    return sum + comp;
+#pragma unroll
+    for (int s = 0; s < SUB; ++s) out[s] = sum[s] + comp[s];
 }
 
+// Record range of window w (sub-spans w SUB .. w SUB + SUB - 1) of A-scan k
+// from the per-span runs (both run bounds grow with the span, so the union of
+// consecutive runs is one range).
+__device__ __forceinline__ int2 window_runs(const int2* __restrict__ runs, int k, int nspan, int w, int sub)
+{
+    const int sp0 = w * sub, sp1 = min(sp0 + sub, nspan) - 1;
+    return make_int2(__ldg(&runs[(size_t)k * nspan + sp0].x), __ldg(&runs[(size_t)k * nspan + sp1].y));
+}
+
+// Writes the window's outputs to row y (stride `stride`: samples >= M are
+// zero), and zeroes the row's tail beyond the last span.
+template <int SUB>
+__device__ __forceinline__ void window_store(float* yf, __nv_bfloat16* yb, int M, int nspan, int stride, int sp0,
+                                             int lane, const float (&v)[SUB])
+{
+#pragma unroll
+    for (int s = 0; s < SUB; ++s) {
+        if (sp0 + s >= nspan) break;
+        const int n = (sp0 + s) * 32 + lane;
+        if (n < stride) {
+            const float val = n < M ? v[s] : 0.0f;
+            if (yf) yf[n] = val;
+            else yb[n] = __float2bfloat16_rn(val);
+        }
+    }
+    if (sp0 + SUB >= nspan)
+        for (int t = nspan * 32 + lane; t < stride; t += 32) {
+            if (yf) yf[t] = 0.0f;
+            else yb[t] = __float2bfloat16_rn(0.0f);
+        }
+}
 
 constexpr int kBwdTileRows = 16;                       // A^T r tile: 16 rows (one warp each) x 32 columns
 constexpr int kBwdWorkerThreads = kBwdTileRows * 32;   // threads of one tile worker

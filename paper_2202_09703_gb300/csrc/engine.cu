@@ -78,13 +78,14 @@ struct ReqDesc {
     const float* msq;
     double* sc;
     double* part;          // [3 nblk grad | nblk curvature | K projection]
-    const int* span_order; // A d spans, largest first
+    const int* win_order;  // A d windows, largest first
     const int4* items;     // A^T e work items, longest first
     PriorParams pr;
     int it;                // iteration index of this step
     int ngroups;           // transmitter groups (partial images) of the A^T e items
     int n_items;
-    int nsp;               // K x 32-sample spans
+    int nwin;              // K x windows of `sub` 32-sample spans
+    int sub;
     int nblk;              // pixel blocks of kRedThreads
 };
 
@@ -307,7 +308,32 @@ __global__ void eng_dir_kernel(EngLists L)
     }
 }
 
-// q = A d over every active request: warps take spans of a request's pool,
+// Warps of the CTA drain request R's A d pool of windows (SUB spans each).
+template <bool BF16, int SUB>
+__device__ __forceinline__ void eng_fwd_pool(const ReqDesc& R, int* pool, const typename TabT<BF16>::type* tab,
+                                             int lane, int4* sr, float4* sw)
+{
+    const GeomParams& P = R.P;
+    const int S = table_stride(P.Tw4);
+    const int nspan = (P.M + 31) >> 5;
+    const int nwin = (nspan + SUB - 1) / SUB;
+    const float* x = dnew_of(R);
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(pool, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= R.nwin) break;
+        const int gw = __ldg(R.win_order + idx);
+        const int k = gw / nwin, w = gw - k * nwin;
+        const int2 rb = window_runs(R.runs, k, nspan, w, SUB);
+        float v[SUB];
+        span_gather<BF16, SUB>(tab, S, P.Tw, R.rkey, R.rw, __ldg(R.rec_off + k), rb.x, rb.y, x, w * SUB * 32 + lane,
+                               lane, sr, sw, v);
+        window_store<SUB>(R.q + (size_t)k * P.Mp, nullptr, P.M, nspan, P.Mp, w * SUB, lane, v);
+    }
+}
+
+// q = A d over every active request: warps take windows of a request's pool,
 // largest first; the CTA moves on when the pool is empty
 template <bool BF16>
 __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
@@ -327,33 +353,18 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
     for (int t = 0; t < nreq; ++t) {
         const int rq = (r0 + t) % nreq;
         const ReqDesc& R = L.desc[rq];
-        if (!eng_pool_live(L.pool, rq, 0, R.nsp, flag)) continue;
+        if (!eng_pool_live(L.pool, rq, 0, R.nwin, flag)) continue;
         const GeomParams& P = R.P;
-        const int S = table_stride(P.Tw4);
         if (rq != cur) {
-            const size_t tab_bytes = ((size_t)P.Gt * (P.Q + 1) * S * sizeof(Tab) + 127) & ~(size_t)127;
+            const size_t tab_bytes =
+                ((size_t)P.Gt * (P.Q + 1) * table_stride(P.Tw4) * sizeof(Tab) + 127) & ~(size_t)127;
             load_table_smem(tab, BF16 ? (const void*)R.tab_bf : (const void*)R.tab, tab_bytes, tid, kEngThreads);
             cur = rq;
             __syncthreads();
         }
-        const int nspan = (P.M + 31) >> 5;
-        const float* x = dnew_of(R);
-        for (;;) {
-            int idx = 0;
-            if (lane == 0) idx = atomicAdd(L.pool + 2 * rq, 1);
-            idx = __shfl_sync(0xffffffffu, idx, 0);
-            if (idx >= R.nsp) break;
-            const int s = __ldg(R.span_order + idx);
-            const int k = s / nspan, sp = s - k * nspan;
-            const int n = sp * 32 + lane;
-            const int2 rb = __ldg(R.runs + s);
-            const float acc = span_gather<BF16>(tab, S, P.Tw, R.rkey, R.rw, __ldg(R.rec_off + k), rb.x, rb.y, x, n,
-                                                lane, sr, sw);
-            float* qo = R.q + (size_t)k * P.Mp;
-            if (n < P.Mp) qo[n] = (n < P.M) ? acc : 0.0f;
-            if (sp == nspan - 1)
-                for (int u = nspan * 32 + lane; u < P.Mp; u += 32) qo[u] = 0.0f;
-        }
+        if (R.sub == 1) eng_fwd_pool<BF16, 1>(R, L.pool + 2 * rq, tab, lane, sr, sw);
+        else if (R.sub == 2) eng_fwd_pool<BF16, 2>(R, L.pool + 2 * rq, tab, lane, sr, sw);
+        else eng_fwd_pool<BF16, 4>(R, L.pool + 2 * rq, tab, lane, sr, sw);
         __syncthreads();                 // every warp is done before the table is replaced
     }
 }
@@ -450,6 +461,8 @@ struct Request {
     int state = 0;          // 0 queued, 1 active, 2 retiring, 3 done, < 0 error code
     int ngroups = 1, nblk = 0;
     size_t bytes = 0;
+    double cost = 0;        // estimated work of one iteration (A^T e estimate, twice)
+    double waited = 0;      // work of the steps that ran while this request was passed over
     float *e = nullptr, *q = nullptr, *b = nullptr, *grad = nullptr, *gprev = nullptr, *d0 = nullptr,
           *d1 = nullptr, *bpart = nullptr, *msq = nullptr;
     __nv_bfloat16* ebf = nullptr;
@@ -478,7 +491,8 @@ struct mbir_engine {
     int max_active = 64;
     int64_t next_ticket = 1;
     std::deque<Request*> queue;
-    std::vector<Request*> active;
+    std::vector<Request*> active;        // admitted: state on the device
+    std::vector<Request*> sel;           // run in the current step (see select_step)
     std::map<int64_t, std::unique_ptr<Request>> all;
     bool dirty = true;                   // work lists must be rebuilt
     // device work lists (fixed capacity; growing them re-captures the graph)
@@ -572,6 +586,13 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     if (e == cudaSuccess && r->ebf) e = mbir::launch_to_bf16(r->e, r->ebf, (long long)KMp, st);
     if (e != cudaSuccess) { free_request_state(r, st); return MBIR_ERR_CUDA; }
     r->it = 0;
+    r->waited = 0;
+    r->cost = 0;
+    const int TR = backproject_tile_rows(), ntr = (P.H + TR - 1) / TR;
+    for (int tr = 0; tr < ntr; ++tr)
+        if (g->h_tvert[tr * TR] < (float)(P.M - 1))
+            for (size_t t = (size_t)tr * g->bwd_ntc * P.n_tx; t < (size_t)(tr + 1) * g->bwd_ntc * P.n_tx; ++t)
+                r->cost += 2.0 * g->h_bwd_cost[t];
     r->state = 1;
     return MBIR_OK;
 }
@@ -604,11 +625,12 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.part = r->part;
     d.pr = make_prior_params(&r->prior);
     d.it = r->it;
-    d.span_order = g->d_span_order;
+    d.win_order = g->d_win_order;
     d.items = g->d_items;
     d.ngroups = r->ngroups;
     d.n_items = g->n_items;
-    d.nsp = g->P.K * ((g->P.M + 31) / 32);
+    d.nwin = (int)g->n_win;
+    d.sub = g->fwd_sub;
     d.nblk = r->nblk;
 }
 
@@ -629,15 +651,47 @@ std::vector<int> start_requests(const std::vector<double>& cost, int G)
     return st;
 }
 
-// Rebuilds the per-epoch work lists for the active set.
+// Requests run in this step.  All admitted requests hold their state on the
+// device, but a step runs one iteration of only some of them, so that small
+// requests are not paced by the long iterations of large ones: in order of
+// remaining work (estimated iteration cost x iterations left) less half the
+// work a request has waited through while passed over (aging, so large
+// requests are not starved), a request joins the step if the step's A^T e
+// items stay within four per tile worker of the GPU (the first always joins).
+constexpr double kAging = 0.5;
+
+void select_step(mbir_engine* E)
+{
+    std::vector<Request*> order(E->active.begin(), E->active.end());
+    auto prio = [](const Request* r) { return r->cost * (r->n_iter - r->it) - kAging * r->waited; };
+    std::stable_sort(order.begin(), order.end(), [&](const Request* a, const Request* b) { return prio(a) < prio(b); });
+    const long long budget = 4LL * 2 * E->n_sm;
+    std::vector<Request*> sel;
+    long long items = 0;
+    double step_cost = 0;
+    for (Request* r : order) {
+        if (!sel.empty() && items + r->g->n_items > budget) continue;
+        sel.push_back(r);
+        items += r->g->n_items;
+        step_cost += r->cost;
+    }
+    for (Request* r : E->active)
+        if (std::find(sel.begin(), sel.end(), r) == sel.end()) r->waited += step_cost;
+    if (sel != E->sel) {
+        E->sel = sel;
+        E->dirty = true;
+    }
+}
+
+// Rebuilds the per-step work lists for the requests run in the step.
 int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 {
     const int G = E->n_sm;
     std::vector<double> bwd_cost, fwd_cost;
     std::vector<int2> pix, rows;
     std::vector<int4> upd;
-    for (size_t ri = 0; ri < E->active.size(); ++ri) {
-        const Request* r = E->active[ri];
+    for (size_t ri = 0; ri < E->sel.size(); ++ri) {
+        const Request* r = E->sel[ri];
         const mbir_geometry* g = r->g;
         const GeomParams& P = g->P;
         // A^T e: the geometry's estimates of its items (tile x transmitter group)
@@ -649,10 +703,9 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
                 cb += g->h_bwd_cost[t];
         }
         bwd_cost.push_back(cb);
-        // A d: records per span plus a fixed cost per span, in the same units (warp tap loops)
-        const long long nsp = (long long)P.K * ((P.M + 31) / 32);
+        // A d: records visited per window plus a fixed cost per window
         double cf = 0;
-        for (long long sp = 0; sp < nsp; ++sp) cf += g->h_span_cost[sp] + 8;
+        for (long long w = 0; w < g->n_win; ++w) cf += g->h_win_cost[w] + 8;
         fwd_cost.push_back(cf);
         for (int b = 0; b < r->nblk; ++b) pix.push_back(make_int2((int)ri, b));
         for (int k = 0; k < P.K; ++k) rows.push_back(make_int2((int)ri, k));
@@ -663,7 +716,7 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
     std::vector<int> start = start_requests(bwd_cost, G), fstart = start_requests(fwd_cost, G);
     start.insert(start.end(), fstart.begin(), fstart.end());
     cudaError_t e = cudaSuccess;
-    e = ensure_cap(&E->L.desc, &E->cap_desc, E->active.size(), grew);
+    e = ensure_cap(&E->L.desc, &E->cap_desc, E->sel.size(), grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.pool, &E->cap_pool, 2 * E->cap_desc, grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.pixblk, &E->cap_pix, pix.size(), grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.rowblk, &E->cap_row, rows.size(), grew);
@@ -675,7 +728,7 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
         if (e != cudaSuccess) return MBIR_ERR_OOM;
         *grew = true;
     }
-    int counts[8] = {(int)E->active.size(), (int)pix.size(), (int)rows.size(), (int)upd.size(), 0, 0, 0, 0};
+    int counts[8] = {(int)E->sel.size(), (int)pix.size(), (int)rows.size(), (int)upd.size(), 0, 0, 0, 0};
     // pageable copies are staged before cudaMemcpyAsync returns, so the host vectors may go away
     if (!pix.empty())
         e = cudaMemcpyAsync(E->L.pixblk, pix.data(), sizeof(int2) * pix.size(), cudaMemcpyHostToDevice, st);
@@ -753,7 +806,7 @@ int mbir_engine_submit(mbir_engine* E, const mbir_geometry* g, const void* y_dev
                        float* x_dev, float* g_dev, int64_t* ticket)
 {
     if (!E || !g || !y_dev || !x_dev || !ticket || n_iter < 1 || !prior_is_valid(pr)) return MBIR_ERR_INVALID_ARG;
-    if (g->P.mode != MBIR_MODE_TAB || !g->d_rec_key || !g->h_span_cost) return MBIR_ERR_UNSUPPORTED;
+    if (g->P.mode != MBIR_MODE_TAB || !g->d_rec_key || !g->h_win_cost) return MBIR_ERR_UNSUPPORTED;
     const size_t tsz = g->P.precision == MBIR_PREC_BF16 ? 4 : 8;
     const size_t tab = ((size_t)g->P.Gt * (g->P.Q + 1) * table_stride(g->P.Tw4) * tsz + 127) & ~(size_t)127;
     const size_t eb = ((size_t)g->P.Mp * (g->P.precision == MBIR_PREC_BF16 ? 2 : 4) + 127) & ~(size_t)127;
@@ -801,6 +854,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         free_request_state(r, st);
         E->used -= r->bytes;
         E->active.erase(E->active.begin() + i);
+        E->sel.erase(std::remove(E->sel.begin(), E->sel.end(), r), E->sel.end());
         E->dirty = true;
     }
     // admit queued requests that fit the budget (in arrival order)
@@ -816,6 +870,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
     if (n_queued) *n_queued = (int)E->queue.size();
     if (n_active) *n_active = (int)E->active.size();
     if (E->active.empty()) return rc;
+    select_step(E);
     // the graph is specialised to one table precision; mixed precisions run in two passes
     bool grew = false;
     if (E->dirty) {
@@ -823,12 +878,12 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         if (lrc != MBIR_OK) return lrc;
         E->dirty = false;
     }
-    E->h_desc.resize(E->active.size());
-    for (size_t i = 0; i < E->active.size(); ++i) fill_desc(E->h_desc[i], E->active[i]);
+    E->h_desc.resize(E->sel.size());
+    for (size_t i = 0; i < E->sel.size(); ++i) fill_desc(E->h_desc[i], E->sel[i]);
     cudaError_t e = cudaMemcpyAsync(E->L.desc, E->h_desc.data(), sizeof(ReqDesc) * E->h_desc.size(),
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;
-    const bool bf16 = E->active[0]->g->P.precision == MBIR_PREC_BF16;
+    const bool bf16 = E->sel[0]->g->P.precision == MBIR_PREC_BF16;
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
     if (grew || !E->graph || E->graph_bf16 != (int)bf16) {
@@ -848,7 +903,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
     }
     e = cudaGraphLaunch(E->graph, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;
-    for (Request* r : E->active) ++r->it;
+    for (Request* r : E->sel) ++r->it;
     return rc;
 }
 
@@ -898,6 +953,7 @@ int mbir_engine_cancel(mbir_engine* E, int64_t ticket, void* stream)
         free_request_state(r, (cudaStream_t)stream);
         E->used -= r->bytes;
         E->active.erase(std::remove(E->active.begin(), E->active.end(), r), E->active.end());
+        E->sel.erase(std::remove(E->sel.begin(), E->sel.end(), r), E->sel.end());
         E->dirty = true;
         r->state = MBIR_ERR_CANCELLED;
     }

@@ -8,11 +8,13 @@
 // window reaches the span are then one contiguous range, stored as run bounds.
 //
 // The apply kernel is a persistent, barrier-free gather: every warp takes
-// whole spans (largest first, from a counter), decodes 32 records at a time
-// into its own shared-memory slot (first tap, tap count, table offset, and
-// weights times x) while the next 32 stream into registers, and each lane
-// accumulates the taps that land on its sample.  Output samples are owned by
-// one lane and summed in record order: no atomics on data, fixed order.
+// whole windows of SUB consecutive spans (largest first, from a counter),
+// decodes 32 records at a time into its own shared-memory slot (first tap,
+// tap count, table offset, and weights times x) while the next 32 stream into
+// registers, and each lane accumulates the taps that land on its SUB samples.
+// Output samples are owned by one lane and summed in record order: no atomics
+// on data, fixed order.  A wider window reads each staged record for more
+// samples; SUB is chosen per geometry by timing the candidates once.
 #include <algorithm>
 #include <vector>
 
@@ -131,12 +133,12 @@ __global__ void __launch_bounds__(kSortThreads)
     }
 }
 
-template <bool BF16>
+template <bool BF16, int SUB>
 __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     forward_sorted_kernel(GeomParams P, const typename TabT<BF16>::type* __restrict__ tab_g,
                           const long long* __restrict__ off, const int2* __restrict__ rkey,
                           const float4* __restrict__ rw, const int2* __restrict__ runs,
-                          const int* __restrict__ order, int* __restrict__ next_span, const float* __restrict__ x,
+                          const int* __restrict__ order, int* __restrict__ next_win, const float* __restrict__ x,
                           float* __restrict__ y_f32, __nv_bfloat16* __restrict__ y_bf16, int out_stride)
 {
     using Tab = typename TabT<BF16>::type;
@@ -152,32 +154,43 @@ __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     load_table_smem(tab, tab_g, tab_bytes, tid, kFwdSortedThreads);
     __syncthreads();
     const int nspan = (P.M + 31) >> 5;
-    const int total = P.K * nspan;
+    const int nwin = (nspan + SUB - 1) / SUB;
+    const int total = P.K * nwin;
     for (;;) {
-        // spans are handed out largest-first through a counter, one per warp
+        // windows are handed out largest-first through a counter, one per warp
         int idx = 0;
-        if (lane == 0) idx = atomicAdd(next_span, 1);
+        if (lane == 0) idx = atomicAdd(next_win, 1);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= total) break;
-        const int gs = __ldg(order + idx);
-        const int k = gs / nspan, sp = gs - k * nspan;
-        const int n = sp * 32 + lane;
-        const long long base = __ldg(off + k);
-        const int2 rb = __ldg(runs + gs);
-        const float acc = span_gather<BF16>(tab, S, P.Tw, rkey, rw, base, rb.x, rb.y, x, n, lane, sr, sw);
-        const float yv = (n < P.M) ? acc : 0.0f;
-        if (n < out_stride) {
-            if (y_f32) y_f32[(size_t)k * out_stride + n] = yv;
-            else y_bf16[(size_t)k * out_stride + n] = __float2bfloat16_rn(yv);
-        }
-        if (sp == nspan - 1) {
-            for (int t = nspan * 32 + lane; t < out_stride; t += 32) {
-                if (y_f32) y_f32[(size_t)k * out_stride + t] = 0.0f;
-                else y_bf16[(size_t)k * out_stride + t] = __float2bfloat16_rn(0.0f);
-            }
-        }
+        const int gw = __ldg(order + idx);
+        const int k = gw / nwin, w = gw - k * nwin;
+        const int2 rb = window_runs(runs, k, nspan, w, SUB);
+        float v[SUB];
+        span_gather<BF16, SUB>(tab, S, P.Tw, rkey, rw, __ldg(off + k), rb.x, rb.y, x, w * SUB * 32 + lane, lane,
+                               sr, sw, v);
+        window_store<SUB>(y_f32 ? y_f32 + (size_t)k * out_stride : nullptr,
+                          y_f32 ? nullptr : y_bf16 + (size_t)k * out_stride, P.M, nspan, out_stride, w * SUB, lane, v);
     }
 }
+
+// Windows of `sub` spans of every A-scan, largest first (records visited).
+static void window_order(const std::vector<int2>& runs, int K, int nspan, int sub, std::vector<int>* order,
+                         std::vector<int>* cost)
+{
+    const int nwin = (nspan + sub - 1) / sub;
+    cost->assign((size_t)K * nwin, 0);
+    for (int k = 0; k < K; ++k)
+        for (int w = 0; w < nwin; ++w) {
+            const int sp0 = w * sub, sp1 = std::min(sp0 + sub, nspan) - 1;
+            (*cost)[(size_t)k * nwin + w] = runs[(size_t)k * nspan + sp1].y - runs[(size_t)k * nspan + sp0].x;
+        }
+    order->resize(cost->size());
+    for (size_t t = 0; t < order->size(); ++t) (*order)[t] = (int)t;
+    std::stable_sort(order->begin(), order->end(), [&](int a, int b) { return (*cost)[a] > (*cost)[b]; });
+}
+
+cudaError_t tune_window(mbir_geometry* g, const std::vector<int2>& runs, cudaStream_t st);
+cudaError_t install_window(mbir_geometry* g, int sub, const std::vector<int>& order, const std::vector<int>& cost);
 
 // Builds the sorted records; returns cudaErrorNotSupported when the record
 // list would not fit the byte cap (the caller then keeps the on-the-fly
@@ -215,24 +228,12 @@ cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_b
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    // spans in decreasing order of work, so the last spans handed out are short
     std::vector<int2> runs((size_t)P.K * nspan);
     e = cudaMemcpy(runs.data(), g->d_runs, sizeof(int2) * runs.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->d_win_counter, sizeof(int));
     if (e != cudaSuccess) return e;
-    g->h_span_cost = (int*)malloc(sizeof(int) * runs.size());
-    if (g->h_span_cost)
-        for (size_t t = 0; t < runs.size(); ++t) g->h_span_cost[t] = runs[t].y - runs[t].x;
-    std::vector<int> order(runs.size());
-    for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return runs[a].y - runs[a].x > runs[b].y - runs[b].x;
-    });
-    e = cudaMalloc((void**)&g->d_span_order, sizeof(int) * order.size());
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_span_order, order.data(), sizeof(int) * order.size(),
-                                         cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&g->d_span_counter, sizeof(int));
-    if (e == cudaSuccess) g->bytes += sizeof(int) * (order.size() + 1);
-    return e;
+    g->bytes += sizeof(int);
+    return tune_window(g, runs, st);
 }
 
 size_t forward_sorted_smem(const mbir_geometry* g)
@@ -243,29 +244,146 @@ size_t forward_sorted_smem(const mbir_geometry* g)
     return tab + (size_t)kFwdSortedThreads * (sizeof(float4) + sizeof(int4));
 }
 
-cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
-                                  cudaStream_t st)
+template <bool BF16, int SUB>
+static cudaError_t launch_sorted_t(const mbir_geometry* g, const int* order, const float* x, float* yf,
+                                   __nv_bfloat16* yb, int stride, cudaStream_t st)
 {
+    using Tab = typename TabT<BF16>::type;
     const size_t sm = forward_sorted_smem(g);
     const int nspan = (g->P.M + 31) / 32;
-    const long long spans = (long long)g->P.K * nspan;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(g->n_sm, (spans + 31) / 32));
-    cudaError_t me = cudaMemsetAsync(g->d_span_counter, 0, sizeof(int), st);
-    if (me != cudaSuccess) return me;
-    if (g->P.precision == MBIR_PREC_BF16) {
-        auto kern = forward_sorted_kernel<true>;
-        cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (ce != cudaSuccess) return ce;
-        kern<<<grid, kFwdSortedThreads, sm, st>>>(g->P, g->d_tab_bf16, g->d_rec_off, g->d_rec_key, g->d_rec_w,
-                                                  g->d_runs, g->d_span_order, g->d_span_counter, x, yf, yb, stride);
-    } else {
-        auto kern = forward_sorted_kernel<false>;
-        cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (ce != cudaSuccess) return ce;
-        kern<<<grid, kFwdSortedThreads, sm, st>>>(g->P, g->d_tab, g->d_rec_off, g->d_rec_key, g->d_rec_w,
-                                                  g->d_runs, g->d_span_order, g->d_span_counter, x, yf, yb, stride);
-    }
+    const long long wins = (long long)g->P.K * ((nspan + SUB - 1) / SUB);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(g->n_sm, (wins + 31) / 32));
+    auto kern = forward_sorted_kernel<BF16, SUB>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_win_counter, 0, sizeof(int), st);
+    if (ce != cudaSuccess) return ce;
+    const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
+    kern<<<grid, kFwdSortedThreads, sm, st>>>(g->P, tab, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, order,
+                                              g->d_win_counter, x, yf, yb, stride);
     return cudaGetLastError();
 }
 
+template <bool BF16>
+static cudaError_t launch_sorted_sub(const mbir_geometry* g, int sub, const int* order, const float* x, float* yf,
+                                     __nv_bfloat16* yb, int stride, cudaStream_t st)
+{
+    switch (sub) {
+    case 1: return launch_sorted_t<BF16, 1>(g, order, x, yf, yb, stride, st);
+    case 2: return launch_sorted_t<BF16, 2>(g, order, x, yf, yb, stride, st);
+    default: return launch_sorted_t<BF16, 4>(g, order, x, yf, yb, stride, st);
+    }
+}
+
+static cudaError_t launch_sorted(const mbir_geometry* g, int sub, const int* order, const float* x, float* yf,
+                                 __nv_bfloat16* yb, int stride, cudaStream_t st)
+{
+    return g->P.precision == MBIR_PREC_BF16 ? launch_sorted_sub<true>(g, sub, order, x, yf, yb, stride, st)
+                                            : launch_sorted_sub<false>(g, sub, order, x, yf, yb, stride, st);
+}
+
+// Window autotuner: times one A x per candidate window (1, 2 or 4 spans per
+// warp) on a random image and keeps the fastest, with its window order and
+// per-window costs.  Results do not depend on the choice (see span_gather).
+cudaError_t tune_window(mbir_geometry* g, const std::vector<int2>& runs, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const int nspan = (P.M + 31) / 32;
+    const int cands[3] = {1, 2, 4};
+    std::vector<int> order[3], cost[3];
+    for (int c = 0; c < 3; ++c) window_order(runs, P.K, nspan, cands[c], &order[c], &cost[c]);
+    int best = 1;                      // two spans per warp unless timing says otherwise
+    const size_t N = (size_t)P.W * P.H, KMp = (size_t)P.K * P.Mp;
+    float *x = nullptr, *y = nullptr;
+    int* d_ord = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc((void**)&x, sizeof(float) * N);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&y, sizeof(float) * KMp);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ord, sizeof(int) * order[0].size());
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        // x = 1 on every pixel: every record is visited as in a real apply
+        std::vector<float> ones(N, 1.0f);
+        e = cudaMemcpy(x, ones.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    }
+    float tbest = 0.0f;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        e = cudaMemcpy(d_ord, order[c].data(), sizeof(int) * order[c].size(), cudaMemcpyHostToDevice);
+        float t = 0.0f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_sorted(g, cands[c], d_ord, x, y, nullptr, P.Mp, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        }
+        if (e == cudaSuccess) g->fwd_tune_ms[c] = t;
+        if (e == cudaSuccess && (c == 0 || t < tbest)) {
+            tbest = t;
+            best = c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(d_ord);
+    if (e != cudaSuccess) return e;
+    return install_window(g, cands[best], order[best], cost[best]);
+}
+
+// Makes `sub` the window of the A x launches, with its order and costs.
+cudaError_t install_window(mbir_geometry* g, int sub, const std::vector<int>& order, const std::vector<int>& cost)
+{
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, sizeof(int) * std::max<size_t>(order.size(), 1));
+    if (e == cudaSuccess) e = cudaMemcpy(d, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice);
+    int* h = (int*)malloc(sizeof(int) * std::max<size_t>(cost.size(), 1));
+    if (e != cudaSuccess || !h) {
+        cudaFree(d);
+        free(h);
+        return e != cudaSuccess ? e : cudaErrorMemoryAllocation;
+    }
+    std::copy(cost.begin(), cost.end(), h);
+    if (g->d_win_order) {
+        cudaFree(g->d_win_order);
+        g->bytes -= sizeof(int) * (size_t)g->n_win;
+    }
+    free(g->h_win_cost);
+    g->d_win_order = d;
+    g->h_win_cost = h;
+    g->fwd_sub = sub;
+    g->n_win = (long long)order.size();
+    g->bytes += sizeof(int) * order.size();
+    return cudaSuccess;
+}
+
+// Replaces the autotuner's window by `sub` spans (1, 2 or 4).  Synchronous.
+cudaError_t set_forward_window(mbir_geometry* g, int sub)
+{
+    const GeomParams& P = g->P;
+    const int nspan = (P.M + 31) / 32;
+    std::vector<int2> runs((size_t)P.K * nspan);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(runs.data(), g->d_runs, sizeof(int2) * runs.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    std::vector<int> order, cost;
+    window_order(runs, P.K, nspan, sub, &order, &cost);
+    return install_window(g, sub, order, cost);
+}
+
+cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
+                                  cudaStream_t st)
+{
+    return launch_sorted(g, g->fwd_sub, g->d_win_order, x, yf, yb, stride, st);
+}
+
 }  // namespace mbir
+
+extern "C" int mbir_set_forward_window(mbir_geometry* g, int spans)
+{
+    if (!g || (spans != 1 && spans != 2 && spans != 4)) return MBIR_ERR_INVALID_ARG;
+    if (!g->d_rec_key) return MBIR_ERR_UNSUPPORTED;
+    const cudaError_t e = mbir::set_forward_window(g, spans);
+    return e == cudaSuccess ? MBIR_OK : (e == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA);
+}

@@ -169,12 +169,12 @@ void free_geometry(mbir_geometry* g)
                     g->d_legs, g->d_hidx, g->d_direct, g->d_dinv, g->d_status, g->w_e, g->w_q,
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
                     g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
-                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_span_order, g->d_span_counter,
+                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_win_order, g->d_win_counter,
                     g->d_bwd_counter};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::prof_release(g);
     free(g->tab_host);
-    free(g->h_span_cost);
+    free(g->h_win_cost);
     free(g->h_tvert);
     free(g->h_bwd_cost);
     delete g;
@@ -526,6 +526,9 @@ int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info)
     info->mode = g->P.mode;
     info->precision = g->P.precision;
     info->device_bytes = (int64_t)g->bytes;
+    info->forward_window_spans = g->d_rec_key ? g->fwd_sub : 0;
+    for (int c = 0; c < 3; ++c) info->forward_window_ms[c] = g->fwd_tune_ms[c];
+    info->adjoint_groups = g->n_groups;
     return MBIR_OK;
 }
 

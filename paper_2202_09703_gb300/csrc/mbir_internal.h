@@ -351,10 +351,13 @@ struct mbir_geometry {
     int2* d_rec_key;
     float4* d_rec_w;
     int2* d_runs;
-    int* d_span_order;     // spans by decreasing record count
-    int* h_span_cost;      // host copy: records per span (K x nspan), for work partitioning
+    int fwd_sub;           // 32-sample spans per A x window (autotuned)
+    double fwd_tune_ms[3]; // measured A x times of windows of 1, 2, 4 spans
+    long long n_win;       // K x windows
+    int* d_win_order;      // windows by decreasing record count
+    int* h_win_cost;       // host copy: records per window (K x windows), for work partitioning
     float* h_tvert;        // host copy: vertical two-way time per image row (samples)
-    int* d_span_counter;   // work counter of the A x launch
+    int* d_win_counter;    // work counter of the A x launch
     long long n_records;
     // profiling of the apply kernels inside mbir_reconstruct
     int prof;

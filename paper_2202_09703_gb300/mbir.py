@@ -68,7 +68,8 @@ class Info(C.Structure):
     _fields_ = [("n_pixels", C.c_int64), ("n_ascans", C.c_int64), ("n_samples", C.c_int64),
                 ("pulse_support", C.c_int), ("gamma_bins", C.c_int), ("phases", C.c_int),
                 ("gamma_max_s", C.c_double), ("mode", C.c_int), ("precision", C.c_int),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("forward_window_spans", C.c_int),
+                ("forward_window_ms", C.c_double * 3), ("adjoint_groups", C.c_int)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def lib(path: str | None = None):
         "mbir_create_geometry": [D, _V, C.POINTER(_V)],
         "mbir_destroy_geometry": [_V],
         "mbir_geometry_get_info": [_V, I],
+        "mbir_set_forward_window": [_V, C.c_int],
         "mbir_forward": [_V, _V, _V, _V],
         "mbir_backproject": [_V, _V, _V, _V],
         "mbir_project": [_V, _V, _V, _V, _V],
@@ -266,6 +268,11 @@ class Geometry:
         _check(self._lib.mbir_get_kernel_times(self.h, C.byref(t), int(reset)), "mbir_get_kernel_times")
         return {"forward_launches": t.forward_launches, "backproject_launches": t.backproject_launches,
                 "forward_ms": t.forward_ms, "backproject_ms": t.backproject_ms}
+
+    def set_forward_window(self, spans: int):
+        """Override the autotuned A x window (1, 2 or 4 spans per warp)."""
+        _check(self._lib.mbir_set_forward_window(self.h, int(spans)), "mbir_set_forward_window")
+        _check(self._lib.mbir_geometry_get_info(self.h, C.byref(self.info)), "mbir_geometry_get_info")
 
     def count_taps(self):
         a, b = C.c_int64(), C.c_int64()

@@ -139,6 +139,29 @@ def test_outputs_are_bitwise_reproducible(mode):
     assert np.array_equal(gpu_forward(geo, x), gpu_forward(geo2, x))
 
 
+def test_forward_window_does_not_change_output_bits():
+    """A x windows of 1, 2 and 4 spans per warp give identical outputs, and the
+    creation-time autotuner reports the three timings it chose from."""
+    s = S.cfg0()
+    geo = make_geo(s, "tab")
+    info = geo.info
+    assert info.forward_window_spans in (1, 2, 4)
+    ms = list(info.forward_window_ms)
+    assert all(t > 0 for t in ms)
+    assert ms[(1, 2, 4).index(info.forward_window_spans)] == min(ms)
+    x = S.random_vector(s.N, 21).reshape(s.img_h, s.img_w)
+    outs = []
+    for spans in (1, 2, 4):
+        geo.set_forward_window(spans)
+        assert geo.info.forward_window_spans == spans
+        outs.append(gpu_forward(geo, x))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    plan = O.Plan(s)
+    assert rel_l2(outs[0], plan.forward(x)) <= 1e-5
+    with pytest.raises(M.MbirError):
+        geo.set_forward_window(3)
+
+
 def test_otf_and_tab_modes_agree():
     s = S.cfg0()
     x = S.phantom(s, 3)
