@@ -106,6 +106,17 @@ typedef struct {
  * record path of A x instead (less memory, slower). */
 #define MBIR_FLAG_NO_RECORDS 1
 
+/* BF16 precision with records normally applies A and A^T on the tensor
+ * cores.  A^T: per A-scan and 128-sample tile, the correlation of the stored
+ * residual with every stored table row is one BF16 matrix product with FP32
+ * accumulation (an exact rewriting of the adjoint of eq. 13, every tap of a
+ * pair sharing one table phase), and each pair then combines four of its
+ * values.  A x: per A-scan and tile of 128 first-tap samples, the pairs'
+ * weights times x are summed per (sample, table row) in FP32, rounded once to
+ * BF16, multiplied by the table on the tensor cores and added along the
+ * product's anti-diagonals.  This flag keeps the CUDA-core kernels instead. */
+#define MBIR_FLAG_NO_TENSOR_CORES 2
+
 /* QGGMRF prior (eq. 15-17) and the noise sigma of eq. 2.
  * Requires 1 < p < q = 2 (Section 2, "Prior model"), T > 0, sigma0 > 0,
  * m > 0, a >= 0 and sigma_noise > 0. */
@@ -136,6 +147,8 @@ typedef struct {
     int forward_window_spans;    /* TAB records: 32-sample spans per A x work unit (timed at creation), else 0 */
     double forward_window_ms[3]; /* the A x times measured for windows of 1, 2 and 4 spans (0 if not timed) */
     int adjoint_groups;          /* transmitter groups of the A^T r work items */
+    int adjoint_tensor_cores;    /* 1 if A^T runs on the tensor cores (BF16 form, see MBIR_FLAG_NO_TENSOR_CORES) */
+    int forward_tensor_cores;    /* 1 if A x runs on the tensor cores (BF16 form) */
 } mbir_geometry_info;
 
 typedef struct mbir_geometry mbir_geometry;

@@ -298,6 +298,30 @@ struct GeomDev;
 }  // namespace mbir
 
 // The geometry handle (opaque in the C ABI).
+// Shared-memory and tensor-memory layout of the tensor-core adjoint (BF16 form).
+struct TcLayout {
+    int kpad;              // taps rounded up to the MMA K step (16)
+    int ncols, npad;       // table rows G (Q + 1), rounded up to 16
+    int nchunk0, nchunk1;  // MMA N of the two column chunks
+    int cstride;           // row stride of the shared correlation tile (floats)
+    size_t off_h, off_b, off_e, off_c, smem;
+    bool ok;
+};
+
+// Shared-memory and tensor-memory layout of the tensor-core A x (BF16 form).
+struct TfLayout {
+    int ncols;             // table rows G (Q + 1)
+    int c0;                // columns of the first half
+    int k0, k1;            // MMA K of the two halves (multiples of 16)
+    int ka, kb;            // columns of the BF16 operand buffer / of the table operand image
+    int ntap;              // MMA N: taps rounded up to 16
+    int astride, astride1; // FP32 row strides of the two accumulator halves
+    int ustride;           // row stride of the product tile (floats)
+    int ylen;              // output window (floats)
+    size_t off_b, off_a, off_acc, off_acc1, off_y, smem;
+    bool ok;
+};
+
 struct mbir_geometry {
     int device;
     mbir::GeomParams P;
@@ -358,6 +382,20 @@ struct mbir_geometry {
     int* h_win_cost;       // host copy: records per window (K x windows), for work partitioning
     float* h_tvert;        // host copy: vertical two-way time per image row (samples)
     int* d_win_counter;    // work counter of the A x launch
+    // tensor-core adjoint of the BF16 form (see tc_adjoint.cu)
+    TcLayout tc;
+    uint4* d_tc_bop;       // table operand image (rows x taps, K-major)
+    int* d_tc_tile;        // first record of every 128-sample tile, K x (tiles + 1)
+    long long* d_tc_pixoff;// pixel-major record offsets, N + 1
+    uint32_t* d_tc_dest;   // record's place in pixel-major order (A-scan order within a pixel)
+    float* w_tc_contrib;   // one contribution per record, pixel-major
+    int* d_tc_counter;
+    // tensor-core A x of the BF16 form (see tc_forward.cu)
+    TfLayout tf;
+    uint4* d_tf_bop;       // table operand image (taps x table rows, K-major)
+    int* d_tf_n0off;       // first record of every sample n0, K x (M + 1)
+    int* d_tf_order;       // A-scans by decreasing record count
+    int* d_tf_counter;
     long long n_records;
     // profiling of the apply kernels inside mbir_reconstruct
     int prof;
@@ -394,4 +432,11 @@ cudaError_t backproject_tile_costs(const mbir_geometry* g, int ntr, int ntc, flo
 cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
                                         float* b, float* partial, cudaStream_t st);
 size_t forward_smem(const mbir_geometry* g, int* cb_out);
+TcLayout tc_layout(const GeomParams& P);
+cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st);
+cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e_bf, float* b, cudaStream_t st);
+TfLayout tf_layout(const GeomParams& P);
+cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st);
+cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
+                              cudaStream_t st);
 }  // namespace mbir

@@ -47,6 +47,7 @@ class GeometryDesc(C.Structure):
 
 
 FLAG_NO_RECORDS = 1
+FLAG_NO_TENSOR_CORES = 2
 
 
 class Prior(C.Structure):
@@ -69,7 +70,8 @@ class Info(C.Structure):
                 ("pulse_support", C.c_int), ("gamma_bins", C.c_int), ("phases", C.c_int),
                 ("gamma_max_s", C.c_double), ("mode", C.c_int), ("precision", C.c_int),
                 ("device_bytes", C.c_int64), ("forward_window_spans", C.c_int),
-                ("forward_window_ms", C.c_double * 3), ("adjoint_groups", C.c_int)]
+                ("forward_window_ms", C.c_double * 3), ("adjoint_groups", C.c_int),
+                ("adjoint_tensor_cores", C.c_int), ("forward_tensor_cores", C.c_int)]
 
 
 _lib = None
@@ -176,10 +178,11 @@ class Geometry:
     """A geometry handle: device tables of one scan (see include/mbir.h)."""
 
     def __init__(self, scene, mode: str = "auto", precision: str | None = None, stream=None,
-                 records: bool = True):
+                 records: bool = True, tensor_cores: bool = True):
         self.scene = scene
         self._lib = lib()
-        desc, self._keep = desc_from_scene(scene, mode, precision, 0 if records else FLAG_NO_RECORDS)
+        flags = (0 if records else FLAG_NO_RECORDS) | (0 if tensor_cores else FLAG_NO_TENSOR_CORES)
+        desc, self._keep = desc_from_scene(scene, mode, precision, flags)
         h = C.c_void_p()
         _check(self._lib.mbir_create_geometry(C.byref(desc), _stream_ptr(stream), C.byref(h)),
                "mbir_create_geometry")
