@@ -429,6 +429,12 @@ def run_batched(args):
     n = args.requests or 96
     scenes = S.cfg3_scenes(n, seed=0)
     out = {"workload": f"batched: {n} uneven scenes (cfg3 recipe), 50 iterations each"}
+    truth = [torch.as_tensor(S.phantom(sc, i).reshape(-1), dtype=torch.float32, device=dev)
+             for i, sc in enumerate(scenes)]
+
+    def image_err(xs_):
+        """mean over requests of |x - x_true| / |x_true| (the synthetic phantom)"""
+        return float(np.mean([float((a - t).norm() / max(float(t.norm()), 1e-30)) for a, t in zip(xs_, truth)]))
     for prec in ("fp32", "bf16"):
         reqs = [_synth_request(M, S, torch, sc, i, dev, precision=prec) for i, sc in enumerate(scenes)]
         xs = [torch.empty(sc.N, device=dev) for sc in scenes]
@@ -450,10 +456,12 @@ def run_batched(args):
         torch.cuda.synchronize()
         t_eng = time.perf_counter() - t0
         err = max(float((a - b).norm() / max(float(b.norm()), 1e-30)) for a, b in zip(xe, x_serial))
-        out[prec] = {"engine_recons_per_s": n / t_eng, "engine_s": t_eng, "max_rel_diff_vs_serial_fp32": err}
+        out[prec] = {"engine_recons_per_s": n / t_eng, "engine_s": t_eng, "max_rel_diff_vs_serial_fp32": err,
+                     "engine_image_rel_err_vs_truth": image_err(xe)}
         if prec == "fp32":
             out[prec]["serial_recons_per_s"] = n / t_serial
             out[prec]["serial_s"] = t_serial
+            out[prec]["serial_image_rel_err_vs_truth"] = image_err(x_serial)
         eng.close()
         del reqs
         torch.cuda.empty_cache()

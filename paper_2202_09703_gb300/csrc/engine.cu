@@ -35,6 +35,7 @@
 
 #include "apply_common.cuh"
 #include "map_common.cuh"
+#include "tc_apply.cuh"
 
 namespace mbir {
 PriorParams make_prior_params(const mbir_prior* pr);
@@ -87,6 +88,18 @@ struct ReqDesc {
     int nwin;              // K x windows of `sub` 32-sample spans
     int sub;
     int nblk;              // pixel blocks of kRedThreads
+    // tensor-core pools of the BF16 form (tc != 0)
+    int tc;
+    TcLayout tcl;
+    TfLayout tfl;
+    const uint4* tc_bop;
+    const int* tc_tile;
+    const uint32_t* tc_dest;
+    const long long* tc_pixoff;
+    float* tc_contrib;     // this request's contributions (pixel-major)
+    const uint4* tf_bop;
+    const int* tf_n0off;
+    const int* tf_order;
 };
 
 struct EngLists {
@@ -369,6 +382,81 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
     }
 }
 
+// A^T e of the BF16 form on the tensor cores over every active request: the
+// CTA walks the requests from its start, draining each one's (A-scan, tile)
+// pool with the single-request pool function.
+__global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc_kernel(EngLists L)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, kTcCols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
+    uint32_t phase = 0;
+    const int nreq = L.counts[0];
+    if (nreq > 0) {
+        const int r0 = L.start[blockIdx.x] % nreq;
+        for (int t = 0; t < nreq; ++t) {
+            const int rq = (r0 + t) % nreq;
+            const ReqDesc& R = L.desc[rq];
+            const int nitems = R.P.K * ((R.P.M + kTcTile - 1) / kTcTile);
+            if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
+            const TcAdjView V{R.P, R.tcl, R.tc_bop, R.tab_bf, R.ebf, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc_dest,
+                              R.tc_contrib, L.pool + 2 * rq + 1};
+            if (!tc_adjoint_pool(V, smem, tmem, phase, R.D.status)) break;
+            __syncthreads();
+        }
+    }
+    tc_header_release(smem, tmem, kTcCols);
+}
+
+// b = each pixel's contributions summed in A-scan order (the single-request
+// reduction's arithmetic: warp per pixel, lane-strided Neumaier, fixed tree)
+__global__ void eng_bwd_tc_reduce_kernel(EngLists L)
+{
+    const int nb = L.counts[1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int bb = blockIdx.x; bb < nb; bb += gridDim.x) {
+        const int2 rb = L.pixblk[bb];
+        const ReqDesc& R = L.desc[rb.x];
+        const int N = R.P.W * R.P.H;
+        for (int p = w; p < kRedThreads; p += nw) {
+            const int v = rb.y * kRedThreads + p;
+            if (v >= N) break;
+            const long long a = R.tc_pixoff[v], z = R.tc_pixoff[v + 1];
+            float s = 0.0f, c = 0.0f;
+            for (long long j = a + lane; j < z; j += 32) neumaier_add(s, c, R.tc_contrib[j]);
+            s += c;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) R.b[v] = s;
+        }
+    }
+}
+
+// q = A d of the BF16 form on the tensor cores over every active request
+__global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc_kernel(EngLists L)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, kTfCols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
+    uint32_t phase = 0;
+    const int nreq = L.counts[0];
+    if (nreq > 0) {
+        const int r0 = L.start[gridDim.x + blockIdx.x] % nreq;
+        for (int t = 0; t < nreq; ++t) {
+            const int rq = (r0 + t) % nreq;
+            const ReqDesc& R = L.desc[rq];
+            if (!eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
+            const TcFwdView V{R.P, R.tfl, R.tf_bop, R.tab_bf, R.rec_off, R.tf_n0off, R.rkey, R.rw, R.tf_order,
+                              dnew_of(R), R.q, nullptr, R.P.Mp, L.pool + 2 * rq};
+            if (!tc_forward_pool(V, smem, tmem, phase, R.D.status)) break;
+            __syncthreads();
+        }
+    }
+    tc_header_release(smem, tmem, kTfCols);
+}
+
 // in-place direct-arrival projection of q per (request, A-scan), FP64 |q|^2
 __global__ void eng_proj_kernel(EngLists L)
 {
@@ -464,7 +552,7 @@ struct Request {
     double cost = 0;        // estimated work of one iteration (A^T e estimate, twice)
     double waited = 0;      // work of the steps that ran while this request was passed over
     float *e = nullptr, *q = nullptr, *b = nullptr, *grad = nullptr, *gprev = nullptr, *d0 = nullptr,
-          *d1 = nullptr, *bpart = nullptr, *msq = nullptr;
+          *d1 = nullptr, *bpart = nullptr, *msq = nullptr, *contrib = nullptr;
     __nv_bfloat16* ebf = nullptr;
     double *sc = nullptr, *part = nullptr;
     std::vector<float> msq_host;
@@ -479,6 +567,7 @@ size_t request_bytes(const mbir_geometry* g, int ngroups)
     size_t b = 2 * KMp * 4 + 6 * N * 4 + (size_t)ngroups * N * 4 + (size_t)P.H * 4 + S_COUNT * 8 +
                (4 * nblk + P.K + 8) * 8;
     if (P.precision == MBIR_PREC_BF16) b += KMp * 2;
+    if (g->d_tc_bop && g->d_tf_bop) b += (size_t)g->n_records * 4;   // tensor-core contributions
     return b;
 }
 
@@ -499,7 +588,7 @@ struct mbir_engine {
     EngLists L{};
     size_t cap_desc = 0, cap_pool = 0, cap_pix = 0, cap_row = 0, cap_upd = 0;
     cudaGraphExec_t graph = nullptr;
-    int graph_bf16 = -1;
+    int graph_bf16 = -1, graph_tc = -1;
     size_t smem_bwd = 0, smem_fwd = 0;
     // host mirrors
     std::vector<ReqDesc> h_desc;
@@ -540,10 +629,11 @@ std::vector<int> balance(const std::vector<double>& cost, int parts)
 
 void free_request_state(Request* r, cudaStream_t st)
 {
-    void* ptrs[] = {r->e, r->q, r->b, r->grad, r->gprev, r->d0, r->d1, r->bpart, r->msq, r->ebf, r->sc, r->part};
+    void* ptrs[] = {r->e, r->q, r->b, r->grad, r->gprev, r->d0, r->d1, r->bpart, r->msq, r->ebf, r->sc, r->part,
+                    r->contrib};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, st);
-    r->e = r->q = r->b = r->grad = r->gprev = r->d0 = r->d1 = r->bpart = r->msq = nullptr;
+    r->e = r->q = r->b = r->grad = r->gprev = r->d0 = r->d1 = r->bpart = r->msq = r->contrib = nullptr;
     r->ebf = nullptr;
     r->sc = r->part = nullptr;
 }
@@ -569,6 +659,7 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     AL(r->sc, (size_t)S_COUNT);
     AL(r->part, (size_t)4 * r->nblk + P.K + 8);
     if (P.precision == MBIR_PREC_BF16) AL(r->ebf, KMp);
+    if (g->d_tc_bop && g->d_tf_bop) AL(r->contrib, (size_t)g->n_records);
 #undef AL
     if (e != cudaSuccess) { free_request_state(r, st); return e == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA; }
     r->msq_host.resize(P.H);
@@ -632,6 +723,17 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.nwin = (int)g->n_win;
     d.sub = g->fwd_sub;
     d.nblk = r->nblk;
+    d.tc = (g->d_tc_bop && g->d_tf_bop) ? 1 : 0;
+    d.tcl = g->tc;
+    d.tfl = g->tf;
+    d.tc_bop = g->d_tc_bop;
+    d.tc_tile = g->d_tc_tile;
+    d.tc_dest = g->d_tc_dest;
+    d.tc_pixoff = g->d_tc_pixoff;
+    d.tc_contrib = r->contrib;
+    d.tf_bop = g->d_tf_bop;
+    d.tf_n0off = g->d_tf_n0off;
+    d.tf_order = g->d_tf_order;
 }
 
 // First request of each CTA: the requests' costs laid end to end and cut into
@@ -742,18 +844,24 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 }
 
 // One MAP iteration of every active request, as launched inside the graph.
-cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, cudaStream_t st)
+cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, cudaStream_t st)
 {
     const int G = E->n_sm, SG = E->n_sm * 8;
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
     if (e != cudaSuccess) return e;
-    if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
-    else eng_bwd_kernel<false><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
-    eng_bwd_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
+    if (tc) {
+        eng_bwd_tc_kernel<<<G, kTcThreads, kEngSmem, st>>>(E->L);
+        eng_bwd_tc_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
+    } else {
+        if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
+        else eng_bwd_kernel<false><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
+        eng_bwd_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
+    }
     eng_grad_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     eng_findir_kernel<<<G, kRedThreads, 0, st>>>(E->L);
     eng_dir_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
-    if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
+    if (tc) eng_fwd_tc_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
+    else if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     else eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     eng_proj_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     eng_finstep_kernel<<<G, kRedThreads, 0, st>>>(E->L);
@@ -780,6 +888,8 @@ int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_bwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e != cudaSuccess) { delete E; return MBIR_ERR_CUDA; }
     *out = E;
     return MBIR_OK;
@@ -884,15 +994,18 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;
     const bool bf16 = E->sel[0]->g->P.precision == MBIR_PREC_BF16;
+    bool tc = bf16;                      // tensor-core pools when every request of the step has them
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
-    if (grew || !E->graph || E->graph_bf16 != (int)bf16) {
+    for (Request* r : E->sel)
+        if (!r->contrib) tc = false;
+    if (grew || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != (int)tc) {
         if (E->graph) { cudaGraphExecDestroy(E->graph); E->graph = nullptr; }
         cudaStream_t cs;
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         cudaGraph_t graph;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, cs);
+        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&E->graph, graph, 0);
@@ -900,6 +1013,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         cudaStreamDestroy(cs);
         if (e != cudaSuccess) return MBIR_ERR_CUDA;
         E->graph_bf16 = (int)bf16;
+        E->graph_tc = (int)tc;
     }
     e = cudaGraphLaunch(E->graph, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;

@@ -18,15 +18,9 @@
 #include <algorithm>
 #include <vector>
 
-#include "apply_common.cuh"
-#include "tc_common.cuh"
+#include "tc_apply.cuh"
 
 namespace mbir {
-
-constexpr int kTcTile = 128;         // samples per MMA tile (M)
-constexpr int kTcThreads = 512;      // 16 warps: four per tensor-memory lane quarter
-constexpr int kTcUnroll = 4;         // records in flight per thread
-constexpr uint32_t kTcCols = 512;    // tensor-memory columns allocated
 
 TcLayout tc_layout(const GeomParams& P)
 {
@@ -47,186 +41,14 @@ TcLayout tc_layout(const GeomParams& P)
     return L;
 }
 
-// A batch of records held in registers (kTcUnroll per thread).
-struct TcBatch {
-    int2 key[kTcUnroll];
-    float4 w[kTcUnroll];
-    uint32_t dst[kTcUnroll];
-};
-
-__device__ __forceinline__ void tc_load_batch(TcBatch& b, const int2* __restrict__ rkey, const float4* __restrict__ rw,
-                                              const uint32_t* __restrict__ dest, long long base, int rb, int r1,
-                                              int tid)
-{
-#pragma unroll
-    for (int u = 0; u < kTcUnroll; ++u) {
-        const int r = rb + u * kTcThreads + tid;
-        if (r < r1) {
-            b.key[u] = __ldg(rkey + base + r);
-            b.w[u] = __ldg(rw + base + r);
-            b.dst[u] = __ldg(dest + base + r);
-        }
-    }
-}
-
-// Contributions of a batch: four correlation values per record, less the
-// tau = t0 tap of the upper phase row for flagged records.
-__device__ __forceinline__ void tc_run_batch(const TcBatch& b, const GeomParams& P, const TcLayout& T,
-                                             const float* sC, const __nv_bfloat16* sE,
-                                             const __nv_bfloat162* __restrict__ tab, int ts, int rb, int r1, int tid,
-                                             float* __restrict__ contrib)
-{
-    const int R = P.Q + 1, S = table_stride(P.Tw4);
-#pragma unroll
-    for (int u = 0; u < kTcUnroll; ++u) {
-        const int r = rb + u * kTcThreads + tid;
-        if (r >= r1) continue;
-        const int n0 = b.key[u].y >> kRecShift, trow = (b.key[u].y >> 1) & 0xfff;
-        const int gi = trow / R, ph = trow - gi * R;
-        const int g1 = min(gi + 1, P.G - 1);
-        const float* cr = sC + (n0 - ts) * T.cstride;
-        float v = b.w[u].x * cr[ph * P.G + gi];
-        v = fmaf(b.w[u].y, cr[ph * P.G + g1], v);
-        v = fmaf(b.w[u].z, cr[(ph + 1) * P.G + gi], v);
-        v = fmaf(b.w[u].w, cr[(ph + 1) * P.G + g1], v);
-        if (b.key[u].y & 1) {
-            const float2 tl = __bfloat1622float2(__ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1));
-            const float ev = __bfloat162float(sE[n0 - ts + P.Tw - 1]);
-            v -= (b.w[u].z * tl.x + b.w[u].w * tl.y) * ev;
-        }
-        contrib[b.dst[u]] = v;
-    }
-}
-
-// Persistent: items = (A-scan, 128-sample tile) from a counter.  The next
-// item's residual window and first record batch are loaded into registers
-// while the current item's products and records are processed.
-__global__ void __launch_bounds__(kTcThreads, 1)
-    bwd_tc_kernel(GeomParams P, TcLayout T, const uint4* __restrict__ bop, const __nv_bfloat162* __restrict__ tab,
-                  const __nv_bfloat16* __restrict__ e, const long long* __restrict__ rec_off,
-                  const int2* __restrict__ rkey, const float4* __restrict__ rw, const int* __restrict__ tile_off,
-                  const uint32_t* __restrict__ dest, float* __restrict__ contrib, int* __restrict__ counter,
-                  int* __restrict__ status)
+__global__ void __launch_bounds__(kTcThreads, 1) bwd_tc_kernel(TcAdjView V, int* __restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 8);
-    volatile int* next = reinterpret_cast<volatile int*>(smem + 16);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
-    unsigned char* sH = smem + T.off_h;
-    unsigned char* sB = smem + T.off_b;
-    __nv_bfloat16* sE = reinterpret_cast<__nv_bfloat16*>(smem + T.off_e);
-    float* sC = reinterpret_cast<float*>(smem + T.off_c);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    // the table operand T^T (rows x taps, K-major), the same for every item
-    const int nb16 = (int)((size_t)T.npad * T.kpad * 2 / 16);
-    for (int i = tid; i < nb16; i += blockDim.x) reinterpret_cast<uint4*>(sB)[i] = __ldg(bop + i);
-    if (tid == 0) {
-        mbar_init(smem_u32(bar), 1);
-        *abort_flag = 0;
-        *next = atomicAdd(counter, 1);
-        fence_mbar_init();
-    }
-    if (warp == 0) tmem_alloc(smem_u32(tslot), kTcCols);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    const int ntile = (P.M + kTcTile - 1) / kTcTile;
-    const int nitems = P.K * ntile;
-    const int W = kTcTile + T.kpad;                  // residual window length (<= kTcThreads)
-    const uint32_t lbo = 128, sbo = (uint32_t)(T.kpad / 8) * 128;
-    const uint32_t id0 = umma_idesc_bf16(kTcTile, T.nchunk0), id1 = umma_idesc_bf16(kTcTile, T.nchunk1 ? T.nchunk1 : 16);
-    const int kc = T.kpad / 8;
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-
-    // prefetch of item `it`: window value, record range and first batch
-    int it = *next;
-    __nv_bfloat16 ew = zero;
-    long long pbase = 0;
-    int pr0 = 0, pr1 = 0;
-    TcBatch pb;
-    auto prefetch = [&](int item) {
-        const int k = item / ntile, t = item - k * ntile;
-        const int n = t * kTcTile + 1 + tid;
-        ew = (tid < W && n < P.Mp) ? e[(size_t)k * P.Mp + n] : zero;
-        pbase = __ldg(rec_off + k);
-        pr0 = __ldg(tile_off + (size_t)k * (ntile + 1) + t);
-        pr1 = __ldg(tile_off + (size_t)k * (ntile + 1) + t + 1);
-        tc_load_batch(pb, rkey, rw, dest, pbase, pr0, pr1, tid);
-    };
-    if (it < nitems) prefetch(it);
+    tc_header_init(smem, kTcCols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
     uint32_t phase = 0;
-    while (it < nitems) {
-        const int t = it % ntile, ts = t * kTcTile;
-        const long long base = pbase;
-        const int r0 = pr0, r1 = pr1;
-        if (tid < W) sE[tid] = ew;
-        __syncthreads();                             // window visible; every thread has read *next
-        if (tid == 0) *next = atomicAdd(counter, 1);
-        // Hankel tile H[n][m] = e[ts + n + 1 + m], 8 taps (16 bytes) per store
-        const unsigned short* sEu = reinterpret_cast<const unsigned short*>(sE);
-        for (int c = tid; c < kTcTile * kc; c += blockDim.x) {
-            const int n = c / kc, j = c - n * kc;
-            const unsigned short* src = sEu + n + 8 * j;
-            uint4 w;
-            w.x = (uint32_t)src[0] | ((uint32_t)src[1] << 16);
-            w.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
-            w.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
-            w.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
-            *reinterpret_cast<uint4*>(sH + kmajor_offset(n, 8 * j, T.kpad)) = w;
-        }
-        fence_async_smem();
-        __syncthreads();                             // H complete; *next holds the following item
-        const int it_next = *next;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB);
-            for (int s = 0; s < T.kpad / 16; ++s) {
-                const uint64_t da = umma_desc(a0 + 256 * s, lbo, sbo);
-                umma_bf16(tmem, da, umma_desc(b0 + 256 * s, lbo, sbo), id0, s > 0);
-                if (T.nchunk1)
-                    umma_bf16(tmem + T.nchunk0, da, umma_desc(b0 + (T.nchunk0 / 8) * sbo + 256 * s, lbo, sbo), id1,
-                              s > 0);
-            }
-            umma_commit(smem_u32(bar));
-        }
-        if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
-        phase ^= 1u;
-        __syncthreads();                             // the flag is read uniformly: tensor-memory loads are warp-collective
-        tc_fence_after();
-        if (!*abort_flag) {
-            // tensor memory -> shared C tile: warp = (lane quarter, column quarter)
-            const int q = warp & 3, part = warp >> 2;
-            const int row = q * 32 + lane;
-            const int cw = T.npad / 4;
-            for (int c = part * cw; c < part * cw + cw; c += 4) {
-                float v[4];
-                tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) sC[row * T.cstride + c + j] = v[j];
-            }
-        }
-        tc_fence_before();
-        __syncthreads();
-        if (*abort_flag) break;
-        // records: the prefetched first batch, then the next item's prefetch, then the rest
-        tc_run_batch(pb, P, T, sC, sE, tab, ts, r0, r1, tid, contrib);
-        if (it_next < nitems) prefetch(it_next);
-        for (int rb = r0 + kTcUnroll * kTcThreads; rb < r1; rb += kTcUnroll * kTcThreads) {
-            TcBatch b;
-            tc_load_batch(b, rkey, rw, dest, base, rb, r1, tid);
-            tc_run_batch(b, P, T, sC, sE, tab, ts, rb, r1, tid, contrib);
-        }
-        __syncthreads();                             // sC / sE are rewritten by the next item
-        it = it_next;
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, kTcCols);
+    tc_adjoint_pool(V, smem, tmem, phase, status);
+    tc_header_release(smem, tmem, kTcCols);
 }
 
 // b_v = sum of pixel v's contributions in A-scan order: one warp per pixel,
@@ -380,9 +202,9 @@ cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e
     if (ce != cudaSuccess) return ce;
     const int ntile = (P.M + kTcTile - 1) / kTcTile;
     const int grid = std::max(1, std::min(g->n_sm, P.K * ntile));
-    bwd_tc_kernel<<<grid, kTcThreads, L.smem, st>>>(P, L, g->d_tc_bop, g->d_tab_bf16, e_bf, g->d_rec_off,
-                                                    g->d_rec_key, g->d_rec_w, g->d_tc_tile, g->d_tc_dest,
-                                                    g->w_tc_contrib, g->d_tc_counter, g->d_status);
+    TcAdjView V{P, L, g->d_tc_bop, g->d_tab_bf16, e_bf, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_tile,
+                 g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
+    bwd_tc_kernel<<<grid, kTcThreads, L.smem, st>>>(V, g->d_status);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
     const int N = P.W * P.H;

@@ -1,0 +1,443 @@
+// Tensor-core apply pools of the BF16 form, shared by the single-request
+// kernels (tc_adjoint.cu, tc_forward.cu) and the batched engine (engine.cu).
+// A pool function drains one geometry's (or request's) work counter; every
+// thread of the CTA calls it, with the tensor memory already allocated and
+// the header of the dynamic shared memory (offset 0: mbarrier, tensor-memory
+// address, item slot, abort flag) initialised.  It returns false when a
+// bounded wait gave up (the status word is then set).
+#pragma once
+
+#include "apply_common.cuh"
+#include "tc_common.cuh"
+
+namespace mbir {
+
+constexpr int kTcTile = 128;         // A^T: samples per MMA tile (M)
+constexpr int kTcThreads = 512;      // 16 warps: four per tensor-memory lane quarter
+constexpr int kTcUnroll = 4;         // records in flight per thread
+constexpr uint32_t kTcCols = 512;    // tensor-memory columns of the A^T kernels
+constexpr int kTfTile = 128;         // A x: values of n0 per MMA tile (M)
+constexpr int kTfThreads = 512;      // scatter: 4 threads per n0 (phase classes mod 4)
+constexpr int kTfUnroll = 8;         // records in flight per scatter thread
+constexpr int kTfStage = 6;          // 8-column groups per thread held in registers while converting
+constexpr uint32_t kTfCols = 128;    // tensor-memory columns of the A x kernels
+static_assert(kTcThreads == kTfThreads, "the engine runs both pools with one block size");
+
+// A^T of one geometry / request.
+struct TcAdjView {
+    GeomParams P;
+    TcLayout T;
+    const uint4* bop;                // table operand image (rows x taps, K-major)
+    const __nv_bfloat162* tab;       // BF16 kernel table (for the tau = t0 tap)
+    const __nv_bfloat16* e;          // residual, K x Mp
+    const long long* rec_off;
+    const int2* rkey;
+    const float4* rw;
+    const int* tile_off;
+    const uint32_t* dest;            // record -> pixel-major place
+    float* contrib;                  // one contribution per record
+    int* counter;                    // item counter (zeroed before the launch)
+};
+
+// A x of one geometry / request.
+struct TcFwdView {
+    GeomParams P;
+    TfLayout T;
+    const uint4* bop;                // table operand image (taps x table rows, K-major)
+    const __nv_bfloat162* tab;
+    const long long* rec_off;
+    const int* n0_off;
+    const int2* rkey;
+    const float4* rw;
+    const int* order;                // A-scans by decreasing record count
+    const float* x;
+    float* y_f32;
+    __nv_bfloat16* y_bf16;
+    int out_stride;
+    int* counter;
+};
+
+// Shared-memory header of the tensor-core kernels.
+__device__ __forceinline__ void tc_header_init(unsigned char* smem, uint32_t ncols)
+{
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(bar), 1);
+        *reinterpret_cast<volatile int*>(smem + 20) = 0;
+        fence_mbar_init();
+    }
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(smem + 8), ncols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ void tc_header_release(unsigned char* smem, uint32_t tmem, uint32_t ncols)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, ncols);
+}
+
+// A batch of records held in registers (kTcUnroll per thread).
+struct TcBatch {
+    int2 key[kTcUnroll];
+    float4 w[kTcUnroll];
+    uint32_t dst[kTcUnroll];
+};
+
+__device__ __forceinline__ void tc_load_batch(TcBatch& b, const int2* __restrict__ rkey, const float4* __restrict__ rw,
+                                              const uint32_t* __restrict__ dest, long long base, int rb, int r1,
+                                              int tid)
+{
+#pragma unroll
+    for (int u = 0; u < kTcUnroll; ++u) {
+        const int r = rb + u * kTcThreads + tid;
+        if (r < r1) {
+            b.key[u] = __ldg(rkey + base + r);
+            b.w[u] = __ldg(rw + base + r);
+            b.dst[u] = __ldg(dest + base + r);
+        }
+    }
+}
+
+// Contributions of a batch: four correlation values per record, less the
+// tau = t0 tap of the upper phase row for flagged records.
+__device__ __forceinline__ void tc_run_batch(const TcBatch& b, const GeomParams& P, const TcLayout& T,
+                                             const float* sC, const __nv_bfloat16* sE,
+                                             const __nv_bfloat162* __restrict__ tab, int ts, int rb, int r1, int tid,
+                                             float* __restrict__ contrib)
+{
+    const int R = P.Q + 1, S = table_stride(P.Tw4);
+#pragma unroll
+    for (int u = 0; u < kTcUnroll; ++u) {
+        const int r = rb + u * kTcThreads + tid;
+        if (r >= r1) continue;
+        const int n0 = b.key[u].y >> kRecShift, trow = (b.key[u].y >> 1) & 0xfff;
+        const int gi = trow / R, ph = trow - gi * R;
+        const int g1 = min(gi + 1, P.G - 1);
+        const float* cr = sC + (n0 - ts) * T.cstride;
+        float v = b.w[u].x * cr[ph * P.G + gi];
+        v = fmaf(b.w[u].y, cr[ph * P.G + g1], v);
+        v = fmaf(b.w[u].z, cr[(ph + 1) * P.G + gi], v);
+        v = fmaf(b.w[u].w, cr[(ph + 1) * P.G + g1], v);
+        if (b.key[u].y & 1) {
+            const float2 tl = __bfloat1622float2(__ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1));
+            const float ev = __bfloat162float(sE[n0 - ts + P.Tw - 1]);
+            v -= (b.w[u].z * tl.x + b.w[u].w * tl.y) * ev;
+        }
+        contrib[b.dst[u]] = v;
+    }
+}
+
+
+// Drains the A^T items (A-scan, 128-sample tile) of V.  The next item's
+// residual window and first record batch are loaded into registers while the
+// current item's products and records are processed.
+__device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned char* smem, uint32_t tmem,
+                                                uint32_t& phase, int* status)
+{
+    const GeomParams& P = V.P;
+    const TcLayout& T = V.T;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    volatile int* next = reinterpret_cast<volatile int*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    unsigned char* sH = smem + T.off_h;
+    unsigned char* sB = smem + T.off_b;
+    __nv_bfloat16* sE = reinterpret_cast<__nv_bfloat16*>(smem + T.off_e);
+    float* sC = reinterpret_cast<float*>(smem + T.off_c);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const __nv_bfloat162* __restrict__ tab = V.tab;
+    const __nv_bfloat16* __restrict__ e = V.e;
+    const long long* __restrict__ rec_off = V.rec_off;
+    const int2* __restrict__ rkey = V.rkey;
+    const float4* __restrict__ rw = V.rw;
+    const int* __restrict__ tile_off = V.tile_off;
+    const uint32_t* __restrict__ dest = V.dest;
+    float* __restrict__ contrib = V.contrib;
+    int* counter = V.counter;
+
+    // the table operand T^T (rows x taps, K-major), the same for every item
+    const int nb16 = (int)((size_t)T.npad * T.kpad * 2 / 16);
+    for (int i = tid; i < nb16; i += blockDim.x) reinterpret_cast<uint4*>(sB)[i] = __ldg(V.bop + i);
+    if (tid == 0) *next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int ntile = (P.M + kTcTile - 1) / kTcTile;
+    const int nitems = P.K * ntile;
+    const int W = kTcTile + T.kpad;                  // residual window length (<= kTcThreads)
+    const uint32_t lbo = 128, sbo = (uint32_t)(T.kpad / 8) * 128;
+    const uint32_t id0 = umma_idesc_bf16(kTcTile, T.nchunk0), id1 = umma_idesc_bf16(kTcTile, T.nchunk1 ? T.nchunk1 : 16);
+    const int kc = T.kpad / 8;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+
+    // prefetch of item `it`: window value, record range and first batch
+    int it = *next;
+    __nv_bfloat16 ew = zero;
+    long long pbase = 0;
+    int pr0 = 0, pr1 = 0;
+    TcBatch pb;
+    auto prefetch = [&](int item) {
+        const int k = item / ntile, t = item - k * ntile;
+        const int n = t * kTcTile + 1 + tid;
+        ew = (tid < W && n < P.Mp) ? e[(size_t)k * P.Mp + n] : zero;
+        pbase = __ldg(rec_off + k);
+        pr0 = __ldg(tile_off + (size_t)k * (ntile + 1) + t);
+        pr1 = __ldg(tile_off + (size_t)k * (ntile + 1) + t + 1);
+        tc_load_batch(pb, rkey, rw, dest, pbase, pr0, pr1, tid);
+    };
+    if (it < nitems) prefetch(it);
+    while (it < nitems) {
+        const int t = it % ntile, ts = t * kTcTile;
+        const long long base = pbase;
+        const int r0 = pr0, r1 = pr1;
+        if (tid < W) sE[tid] = ew;
+        __syncthreads();                             // window visible; every thread has read *next
+        if (tid == 0) *next = atomicAdd(counter, 1);
+        // Hankel tile H[n][m] = e[ts + n + 1 + m], 8 taps (16 bytes) per store
+        const unsigned short* sEu = reinterpret_cast<const unsigned short*>(sE);
+        for (int c = tid; c < kTcTile * kc; c += blockDim.x) {
+            const int n = c / kc, j = c - n * kc;
+            const unsigned short* src = sEu + n + 8 * j;
+            uint4 w;
+            w.x = (uint32_t)src[0] | ((uint32_t)src[1] << 16);
+            w.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
+            w.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
+            w.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
+            *reinterpret_cast<uint4*>(sH + kmajor_offset(n, 8 * j, T.kpad)) = w;
+        }
+        fence_async_smem();
+        __syncthreads();                             // H complete; *next holds the following item
+        const int it_next = *next;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB);
+            for (int s = 0; s < T.kpad / 16; ++s) {
+                const uint64_t da = umma_desc(a0 + 256 * s, lbo, sbo);
+                umma_bf16(tmem, da, umma_desc(b0 + 256 * s, lbo, sbo), id0, s > 0);
+                if (T.nchunk1)
+                    umma_bf16(tmem + T.nchunk0, da, umma_desc(b0 + (T.nchunk0 / 8) * sbo + 256 * s, lbo, sbo), id1,
+                              s > 0);
+            }
+            umma_commit(smem_u32(bar));
+        }
+        if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
+        phase ^= 1u;
+        __syncthreads();                             // the flag is read uniformly: tensor-memory loads are warp-collective
+        tc_fence_after();
+        if (!*abort_flag) {
+            // tensor memory -> shared C tile: warp = (lane quarter, column quarter)
+            const int q = warp & 3, part = warp >> 2;
+            const int row = q * 32 + lane;
+            const int cw = T.npad / 4;
+            for (int c = part * cw; c < part * cw + cw; c += 4) {
+                float v[4];
+                tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sC[row * T.cstride + c + j] = v[j];
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (*abort_flag) break;
+        // records: the prefetched first batch, then the next item's prefetch, then the rest
+        tc_run_batch(pb, P, T, sC, sE, tab, ts, r0, r1, tid, contrib);
+        if (it_next < nitems) prefetch(it_next);
+        for (int rb = r0 + kTcUnroll * kTcThreads; rb < r1; rb += kTcUnroll * kTcThreads) {
+            TcBatch b;
+            tc_load_batch(b, rkey, rw, dest, base, rb, r1, tid);
+            tc_run_batch(b, P, T, sC, sE, tab, ts, rb, r1, tid, contrib);
+        }
+        __syncthreads();                             // sC / sE are rewritten by the next item
+        it = it_next;
+    }
+    return !*abort_flag;
+}
+
+// Drains the A x items (A-scans, largest first) of V.
+__device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned char* smem, uint32_t tmem,
+                                                uint32_t& phase, int* status)
+{
+    const GeomParams& P = V.P;
+    const TfLayout& T = V.T;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    volatile int* next = reinterpret_cast<volatile int*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    unsigned char* sB = smem + T.off_b;
+    unsigned char* sA = smem + T.off_a;
+    float* sAcc = reinterpret_cast<float*>(smem + T.off_acc);
+    float* sAcc1 = reinterpret_cast<float*>(smem + T.off_acc1);
+    float* sY = reinterpret_cast<float*>(smem + T.off_y);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = P.Q + 1, S = table_stride(P.Tw4);
+    const __nv_bfloat162* __restrict__ tab = V.tab;
+    const long long* __restrict__ rec_off = V.rec_off;
+    const int* __restrict__ n0_off = V.n0_off;
+    const int2* __restrict__ rkey = V.rkey;
+    const float4* __restrict__ rw = V.rw;
+    const int* __restrict__ order = V.order;
+    const float* __restrict__ x = V.x;
+    float* __restrict__ y_f32 = V.y_f32;
+    __nv_bfloat16* __restrict__ y_bf16 = V.y_bf16;
+    const int out_stride = V.out_stride;
+    int* counter = V.counter;
+
+    // table operand: rows = taps, columns = table rows (phase * G + plane), K-major
+    const int nb16 = (int)((size_t)T.ntap * T.kb * 2 / 16);
+    for (int i = tid; i < nb16; i += blockDim.x) reinterpret_cast<uint4*>(sB)[i] = __ldg(V.bop + i);
+    __syncthreads();
+    const int ntile = (P.M + kTfTile - 1) / kTfTile;
+    const uint32_t lbo = 128, sboA = (uint32_t)(T.ka / 8) * 128, sboB = (uint32_t)(T.kb / 8) * 128;
+    const uint32_t idesc = umma_idesc_bf16(kTfTile, T.ntap);
+    const int si = tid >> 2, pj = tid & 3;            // scatter role: n0 row and phase class
+    for (;;) {
+        if (tid == 0) *next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = *next;
+        if (idx >= P.K) break;
+        const int k = __ldg(order + idx);
+        const long long base = __ldg(rec_off + k);
+        const int* no = n0_off + (size_t)k * (P.M + 1);
+        for (int i = tid; i < T.ylen; i += blockDim.x) sY[i] = 0.0f;
+        for (int t = 0; t < ntile; ++t) {
+            const int ts = t * kTfTile;
+            const int n0 = ts + si;
+            const int ra = n0 < P.M ? __ldg(no + n0) : 0, rz = n0 < P.M ? __ldg(no + n0 + 1) : 0;
+            for (int i = tid; i < kTfTile * T.astride; i += blockDim.x) sAcc[i] = 0.0f;
+            for (int i = tid; i < kTfTile * T.astride1; i += blockDim.x) sAcc1[i] = 0.0f;
+            __syncthreads();
+            // scatter: thread (n0 row si, phase class pj) adds the corners that fall in its cells
+            float* arow0 = sAcc + si * T.astride;
+            float* arow1 = sAcc1 + si * T.astride1 - T.c0;
+            for (int rb = ra; rb < rz; rb += kTfUnroll) {
+                int2 key[kTfUnroll];
+                float4 w4[kTfUnroll];
+                float xv[kTfUnroll];
+#pragma unroll
+                for (int u = 0; u < kTfUnroll; ++u)
+                    if (rb + u < rz) {
+                        key[u] = __ldg(rkey + base + rb + u);
+                        w4[u] = __ldg(rw + base + rb + u);
+                    }
+#pragma unroll
+                for (int u = 0; u < kTfUnroll; ++u)
+                    if (rb + u < rz) xv[u] = __ldg(x + key[u].x);
+#pragma unroll
+                for (int u = 0; u < kTfUnroll; ++u) {
+                    if (rb + u >= rz) break;
+                    const int trow = (key[u].y >> 1) & 0xfff;
+                    const int gi = trow / R, ph = trow - gi * R;
+                    const int g1 = min(gi + 1, P.G - 1);
+                    if ((ph & 3) == pj) {
+                        const int c = ph * P.G;
+                        (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].x * xv[u];
+                        (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].y * xv[u];
+                    }
+                    if (((ph + 1) & 3) == pj) {
+                        const int c = (ph + 1) * P.G;
+                        (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].z * xv[u];
+                        (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].w * xv[u];
+                    }
+                    if (pj == 0 && (key[u].y & 1)) {
+                        // tau = t0 exactly: the last tap of the upper phase row lies outside
+                        const float2 tl = __bfloat1622float2(__ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1));
+                        sY[n0 + P.Tw] -= xv[u] * (w4[u].z * tl.x + w4[u].w * tl.y);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int h = 0; h < 2; ++h) {
+                const int cw = h ? P.G * R - T.c0 : T.c0, kh = h ? T.k1 : T.k0;
+                if (cw <= 0) break;
+                const float* src = h ? sAcc1 : sAcc;
+                const int astr = h ? T.astride1 : T.astride;
+                const int kc = kh / 8;
+                // FP32 sums -> registers -> BF16 operand (K-major, 8 columns per 16-byte store);
+                // the first half's operand is written over its own sums
+                uint4 pk[kTfStage];
+#pragma unroll
+                for (int q = 0; q < kTfStage; ++q) {
+                    const int c = tid + q * kTfThreads;
+                    if (c < kTfTile * kc) {
+                        const int i = c / kc, j = c - i * kc;
+                        const float* sp = src + i * astr + 8 * j;
+                        uint32_t w[4];
+#pragma unroll
+                        for (int e2 = 0; e2 < 4; ++e2) {
+                            const int cc = 8 * j + 2 * e2;
+                            const float a = cc < cw ? sp[2 * e2] : 0.0f, b = cc + 1 < cw ? sp[2 * e2 + 1] : 0.0f;
+                            const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+                            w[e2] = *reinterpret_cast<const uint32_t*>(&v);
+                        }
+                        pk[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+                if (h == 1) {
+                    // the first half's MMA reads the operand buffer: wait before rewriting it
+                    if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
+                    phase ^= 1u;
+                }
+                __syncthreads();
+                if (*abort_flag) break;
+#pragma unroll
+                for (int q = 0; q < kTfStage; ++q) {
+                    const int c = tid + q * kTfThreads;
+                    if (c < kTfTile * kc) {
+                        const int i = c / kc, j = c - i * kc;
+                        *reinterpret_cast<uint4*>(sA + kmajor_offset(i, 8 * j, T.ka)) = pk[q];
+                    }
+                }
+                fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB) + (uint32_t)((h ? T.c0 : 0) / 8) * 128;
+                    for (int s = 0; s < kh / 16; ++s)
+                        umma_bf16(tmem, umma_desc(a0 + 256 * s, lbo, sboA), umma_desc(b0 + 256 * s, lbo, sboB), idesc,
+                                  h > 0 || s > 0);
+                    umma_commit(smem_u32(bar));
+                }
+            }
+            if (*abort_flag) break;
+            if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
+            phase ^= 1u;
+            __syncthreads();
+            tc_fence_after();
+            if (*abort_flag) break;
+            // U (tensor memory) -> shared, rows = n0 - ts, columns = taps
+            {
+                const int q = warp & 3, part = warp >> 2;        // 16 warps: lane quarter x column quarter
+                const int row = q * 32 + lane;
+                const int cwid = T.ntap / 4;
+                for (int c = part * cwid; c < part * cwid + cwid; c += 4) {
+                    float v[4];
+                    tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sAcc1[row * T.ustride + c + j] = v[j];
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            // anti-diagonals: y[ts + 1 + j] += sum_i U[i][j - i]
+            for (int j = tid; j < kTfTile + T.ntap - 1; j += blockDim.x) {
+                float acc = 0.0f;
+                const int i0 = max(0, j - T.ntap + 1), i1 = min(kTfTile - 1, j);
+                for (int i = i0; i <= i1; ++i) acc += sAcc1[i * T.ustride + j - i];
+                sY[ts + 1 + j] += acc;
+            }
+            __syncthreads();
+        }
+        if (*abort_flag) break;
+        float* yo = y_f32 ? y_f32 + (size_t)k * out_stride : nullptr;
+        __nv_bfloat16* yb = y_f32 ? nullptr : y_bf16 + (size_t)k * out_stride;
+        for (int n = tid; n < out_stride; n += blockDim.x) {
+            const float v = n < P.M ? sY[n] : 0.0f;
+            if (yo) yo[n] = v;
+            else yb[n] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+    }
+    return !*abort_flag;
+}
+
+}  // namespace mbir

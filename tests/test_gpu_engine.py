@@ -142,6 +142,12 @@ def test_engine_bf16_storage(problems):
     torch.cuda.synchronize()
     xs, _ = single(problems[0][1], y, sig, s.n_iter)
     assert rel_l2(x.cpu().numpy(), xs) <= 3e-2
+    # the engine runs the BF16 form on the tensor cores with the single-request pools: same bits
+    assert geo_b.info.forward_tensor_cores == 1 and geo_b.info.adjoint_tensor_cores == 1
+    xb = torch.empty(s.N, device=DEV)
+    geo_b.reconstruct(yb, sig, s.n_iter, xb)
+    torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy(), xb.cpu().numpy())
 
 
 def test_engine_wait_times_out_and_the_request_keeps_running(problems):
