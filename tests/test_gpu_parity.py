@@ -369,3 +369,57 @@ def test_records_too_long_for_shared_memory_are_refused():
     with pytest.raises(M.MbirError) as ei:
         M.Geometry(s, mode="tab")
     assert ei.value.code == -7
+
+
+# --------------------------------------------------------------------------
+# image error against the oracle, per configuration and precision
+# --------------------------------------------------------------------------
+def _gpu_reconstruct(s, y, sig, n_iter):
+    geo = M.Geometry(s)
+    yt = to_dev(np.asarray(y, np.float32).reshape(-1))
+    if geo.precision == "bf16":
+        yt = yt.to(torch.bfloat16)
+    x = torch.empty(s.N, device=DEV)
+    geo.reconstruct(yt, sig, n_iter, x)
+    torch.cuda.synchronize()
+    geo.close()
+    return x.cpu().numpy()
+
+
+def test_cfg1_reconstruction_matches_oracle():
+    """The 4-layer 256x512 workload in FP32: three MAP iterations against the
+    FP64 oracle's (measured 9.5e-8 relative)."""
+    s = S.cfg1()
+    plan, x_true, g_true, y, sig = oracle_data(s, seed=1)
+    x_ref = np.asarray(plan.reconstruct(y, sig, 3)[0]).reshape(-1)
+    assert rel_l2(_gpu_reconstruct(s, y, sig, 3), x_ref) <= 1e-4
+
+
+def test_bf16_reconstruction_image_error_against_oracle():
+    """BF16 storage form of the 2-layer 64x64 workload, 20 iterations, against
+    the FP64 oracle (measured 1.4e-3 relative)."""
+    s = S.cfg0().copy(precision="bf16")
+    plan, x_true, g_true, y, sig = oracle_data(s, seed=1)
+    x_ref = np.asarray(plan.reconstruct(y, sig, s.n_iter)[0]).reshape(-1)
+    assert rel_l2(_gpu_reconstruct(s, y, sig, s.n_iter), x_ref) <= 1e-2
+
+
+def test_cfg2_bf16_image_against_fp32_form():
+    """The 512x1024 precision workload, 50 iterations: the BF16 storage form
+    (tensor cores) against the FP32 form on the same data (measured 1.8e-3),
+    both equally far from the phantom."""
+    s16 = S.cfg2()
+    s32 = s16.copy(precision="fp32")
+    g32 = M.Geometry(s32)
+    xt = np.asarray(S.phantom(s32, 0), np.float64).reshape(-1)
+    y = torch.empty(s32.K * s32.M, device=DEV)
+    g32.forward(to_dev(xt), y)      # data from the FP32 operator (pinned to the oracle elsewhere)
+    sig = float(np.sqrt(float((y.double() ** 2).sum()) / (100 * s32.K * s32.M)))
+    y += sig * to_dev(S.unit_noise(s32, 0).reshape(-1))
+    y_np = y.cpu().numpy()
+    g32.close()
+    x32 = _gpu_reconstruct(s32, y_np, sig, s32.n_iter)
+    x16 = _gpu_reconstruct(s16, y_np, sig, s16.n_iter)
+    assert rel_l2(x16, x32) <= 1e-2
+    e32, e16 = rel_l2(x32, xt), rel_l2(x16, xt)
+    assert abs(e16 - e32) <= 1e-2 * e32
