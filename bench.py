@@ -218,6 +218,19 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def combine_ranks(t_dev: float, wall: float, steps: int, world: int, dist=None):
+    """Whole-job figures from one rank's timings: every rank takes the slowest
+    rank's device time and wall time (the timed region is fenced by barriers
+    on both sides), and the throughput is steps x world over that time
+    (N independent replicas, weak scaling)."""
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t_dev, wall], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, wall = float(tt[0]), float(tt[1])
+    return t_dev, wall, steps * world / t_dev
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -287,11 +300,7 @@ def run_gpu(args):
     geo.set_profiling(False)
     lat = [a.elapsed_time(b) for a, b in ev]                 # ms per reconstruction
     t_dev = sum(lat) / 1e3
-    if dist:
-        tt = torch.tensor([t_dev, wall], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev, wall = float(tt[0]), float(tt[1])
-    value = args.steps * world / t_dev
+    t_dev, wall, value = combine_ranks(t_dev, wall, args.steps, world, dist)
 
     # end to end through the host-buffer call: H2D of y, D2H of x and g
     y_h = y.cpu().pin_memory()
