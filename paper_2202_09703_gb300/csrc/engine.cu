@@ -99,7 +99,9 @@ struct ReqDesc {
     float* tc_contrib;     // this request's contributions (pixel-major)
     const uint4* tf_bop;
     const int* tf_n0off;
+    const ushort4* tf_grpoff;
     const int* tf_order;
+    long long nrec;        // records of the geometry
 };
 
 struct EngLists {
@@ -433,6 +435,17 @@ __global__ void eng_bwd_tc_reduce_kernel(EngLists L)
     }
 }
 
+// the direction gathered per record of every active request (record order),
+// into the request's contribution buffer (free between the two applies)
+__global__ void eng_tc_gather_kernel(EngLists L)
+{
+    const int nreq = L.counts[0];
+    for (int rq = 0; rq < nreq; ++rq) {
+        const ReqDesc& R = L.desc[rq];
+        tc_gather_x(R.nrec, R.rkey, dnew_of(R), R.tc_contrib);
+    }
+}
+
 // q = A d of the BF16 form on the tensor cores over every active request
 __global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc_kernel(EngLists L)
 {
@@ -448,8 +461,8 @@ __global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc_kernel(EngLists L)
             const int rq = (r0 + t) % nreq;
             const ReqDesc& R = L.desc[rq];
             if (!eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
-            const TcFwdView V{R.P, R.tfl, R.tf_bop, R.tab_bf, R.rec_off, R.tf_n0off, R.rkey, R.rw, R.tf_order,
-                              dnew_of(R), R.q, nullptr, R.P.Mp, L.pool + 2 * rq};
+            const TcFwdView V{R.P, R.tfl, R.tf_bop, R.tab_bf, R.rec_off, R.tf_n0off, R.tf_grpoff, R.rkey, R.rw,
+                              R.tf_order, R.tc_contrib, R.q, nullptr, R.P.Mp, L.pool + 2 * rq};
             if (!tc_forward_pool(V, smem, tmem, phase, R.D.status)) break;
             __syncthreads();
         }
@@ -733,7 +746,9 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.tc_contrib = r->contrib;
     d.tf_bop = g->d_tf_bop;
     d.tf_n0off = g->d_tf_n0off;
+    d.tf_grpoff = g->d_tf_grpoff;
     d.tf_order = g->d_tf_order;
+    d.nrec = g->n_records;
 }
 
 // First request of each CTA: the requests' costs laid end to end and cut into
@@ -860,7 +875,10 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, cudaStream_t s
     eng_grad_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     eng_findir_kernel<<<G, kRedThreads, 0, st>>>(E->L);
     eng_dir_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
-    if (tc) eng_fwd_tc_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
+    if (tc) {
+        eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
+        eng_fwd_tc_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
+    }
     else if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     else eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     eng_proj_kernel<<<SG, kRedThreads, 0, st>>>(E->L);

@@ -3,8 +3,8 @@
 // The geometry is fixed, so once per geometry (the paper's "compute the
 // system matrix once", Section 3) every A-scan's active pairs are written as
 // records {pixel, first tap sample n0 | table row | tau = t0 flag, bilinear
-// weights times w} sorted by n0 (ties by pixel index, so the order is
-// deterministic).  For each 32-sample span of an A-scan the records whose tap
+// weights times w} sorted by n0 (ties by table phase mod 4, then pixel index,
+// so the order is deterministic).  For each 32-sample span of an A-scan the records whose tap
 // window reaches the span are then one contiguous range, stored as run bounds.
 //
 // The apply kernel is a persistent, barrier-free gather: every warp takes
@@ -71,7 +71,8 @@ __global__ void rec_count_kernel(GeomParams P, DevPtrs D, long long* __restrict_
 }
 
 // Counting sort of one A-scan's records by n0, then each bucket ordered by
-// pixel index; run bounds per 32-sample span from the bucket starts.
+// phase class and pixel index; run bounds per 32-sample span from the bucket
+// starts.
 __global__ void __launch_bounds__(kSortThreads)
     rec_fill_kernel(GeomParams P, DevPtrs D, const long long* __restrict__ off, int2* __restrict__ rkey,
                     float4* __restrict__ rw, int2* __restrict__ runs)
@@ -115,14 +116,20 @@ __global__ void __launch_bounds__(kSortThreads)
     }
     __syncthreads();
     __threadfence_block();
-    // order each bucket by pixel index (insertion sort; buckets hold a few dozen records)
+    // order each bucket by (phase class = table phase mod 4, pixel index) (insertion sort; buckets hold a
+    // few dozen records): the tensor-core A x then finds each phase class's records as one range
+    const int R = P.Q + 1;
+    auto order_key = [R](int2 k) {
+        return ((long long)((((k.y >> 1) & 0xfff) % R) & 3) << 32) | (long long)(unsigned)k.x;
+    };
     for (int t = threadIdx.x; t < P.M; t += blockDim.x) {
         const long long a = base + start[t], b = base + start[t + 1];
         for (long long q = a + 1; q < b; ++q) {
             const int2 kq = rkey[q];
             const float4 wq = rw[q];
+            const long long oq = order_key(kq);
             long long p = q - 1;
-            while (p >= a && rkey[p].x > kq.x) {
+            while (p >= a && order_key(rkey[p]) > oq) {
                 rkey[p + 1] = rkey[p];
                 rw[p + 1] = rw[p];
                 --p;

@@ -394,6 +394,7 @@ struct mbir_geometry {
     TfLayout tf;
     uint4* d_tf_bop;       // table operand image (taps x table rows, K-major)
     int* d_tf_n0off;       // first record of every sample n0, K x (M + 1)
+    ushort4* d_tf_grpoff;  // phase-class starts inside every (A-scan, n0) bucket, K x M
     int* d_tf_order;       // A-scans by decreasing record count
     int* d_tf_counter;
     long long n_records;

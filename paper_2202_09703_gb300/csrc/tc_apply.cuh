@@ -47,10 +47,11 @@ struct TcFwdView {
     const __nv_bfloat162* tab;
     const long long* rec_off;
     const int* n0_off;
+    const ushort4* grp_off;          // per (A-scan, n0): starts of phase classes 1..3 in the bucket
     const int2* rkey;
     const float4* rw;
     const int* order;                // A-scans by decreasing record count
-    const float* x;
+    const float* xr;                 // x gathered per record (record order), see tc_gather_x
     float* y_f32;
     __nv_bfloat16* y_bf16;
     int out_stride;
@@ -254,6 +255,52 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
     return !*abort_flag;
 }
 
+// FP32 sums of one column half (cw valid columns, kh padded) -> BF16 pairs in registers.
+__device__ __forceinline__ void tf_stage_half(uint4 (&pk)[kTfStage], const float* src, int astr, int cw, int kh, int tid)
+{
+    const int kc = kh / 8;
+#pragma unroll
+    for (int q = 0; q < kTfStage; ++q) {
+        const int c = tid + q * kTfThreads;
+        if (c < kTfTile * kc) {
+            const int i = c / kc, j = c - i * kc;
+            const float* sp = src + i * astr + 8 * j;
+            uint32_t w[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+                const int cc = 8 * j + 2 * e2;
+                const float a = cc < cw ? sp[2 * e2] : 0.0f, b = cc + 1 < cw ? sp[2 * e2 + 1] : 0.0f;
+                const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+                w[e2] = *reinterpret_cast<const uint32_t*>(&v);
+            }
+            pk[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// The staged BF16 pairs -> an operand buffer (K-major core matrices, ka columns).
+__device__ __forceinline__ void tf_write_half(const uint4 (&pk)[kTfStage], unsigned char* dst, int kh, int ka, int tid)
+{
+    const int kc = kh / 8;
+#pragma unroll
+    for (int q = 0; q < kTfStage; ++q) {
+        const int c = tid + q * kTfThreads;
+        if (c < kTfTile * kc) {
+            const int i = c / kc, j = c - i * kc;
+            *reinterpret_cast<uint4*>(dst + kmajor_offset(i, 8 * j, ka)) = pk[q];
+        }
+    }
+}
+
+// xr[r] = x[pixel of record r] for records [0, nrec) (grid-stride, all blocks).
+__device__ __forceinline__ void tc_gather_x(long long nrec, const int2* __restrict__ rkey, const float* __restrict__ x,
+                                            float* __restrict__ xr)
+{
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrec;
+         r += (long long)gridDim.x * blockDim.x)
+        xr[r] = __ldg(x + __ldg(&rkey[r].x));
+}
+
 // Drains the A x items (A-scans, largest first) of V.
 __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned char* smem, uint32_t tmem,
                                                 uint32_t& phase, int* status)
@@ -273,10 +320,11 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
     const __nv_bfloat162* __restrict__ tab = V.tab;
     const long long* __restrict__ rec_off = V.rec_off;
     const int* __restrict__ n0_off = V.n0_off;
+    const ushort4* __restrict__ grp_off = V.grp_off;
     const int2* __restrict__ rkey = V.rkey;
     const float4* __restrict__ rw = V.rw;
     const int* __restrict__ order = V.order;
-    const float* __restrict__ x = V.x;
+    const float* __restrict__ xr = V.xr;
     float* __restrict__ y_f32 = V.y_f32;
     __nv_bfloat16* __restrict__ y_bf16 = V.y_bf16;
     const int out_stride = V.out_stride;
@@ -306,95 +354,88 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
             for (int i = tid; i < kTfTile * T.astride; i += blockDim.x) sAcc[i] = 0.0f;
             for (int i = tid; i < kTfTile * T.astride1; i += blockDim.x) sAcc1[i] = 0.0f;
             __syncthreads();
-            // scatter: thread (n0 row si, phase class pj) adds the corners that fall in its cells
+            // scatter: thread (n0 row si, phase class pj) owns the cells of the phases = pj (mod 4).  The
+            // bucket is ordered by phase class: records of class pj - 1 bring their upper-row corners
+            // (z, w), then records of class pj their lower-row corners (x, y), each in record order.
             float* arow0 = sAcc + si * T.astride;
             float* arow1 = sAcc1 + si * T.astride1 - T.c0;
-            for (int rb = ra; rb < rz; rb += kTfUnroll) {
-                int2 key[kTfUnroll];
-                float4 w4[kTfUnroll];
-                float xv[kTfUnroll];
+            float flag_corr = 0.0f;
+            if (ra < rz) {
+                const ushort4 go = __ldg(grp_off + (size_t)k * P.M + n0);
+                const int gs[5] = {0, go.x, go.y, go.z, rz - ra};
+                for (int pass = 0; pass < 2; ++pass) {
+                    const int grp = pass == 0 ? ((pj + 3) & 3) : pj;
+                    const int qa = ra + gs[grp], qz = ra + gs[grp + 1];
+                    for (int rb = qa; rb < qz; rb += kTfUnroll) {
+                        int2 key[kTfUnroll];
+                        float4 w4[kTfUnroll];
+                        float xv[kTfUnroll];
 #pragma unroll
-                for (int u = 0; u < kTfUnroll; ++u)
-                    if (rb + u < rz) {
-                        key[u] = __ldg(rkey + base + rb + u);
-                        w4[u] = __ldg(rw + base + rb + u);
-                    }
+                        for (int u = 0; u < kTfUnroll; ++u)
+                            if (rb + u < qz) {
+                                key[u] = __ldg(rkey + base + rb + u);
+                                w4[u] = __ldg(rw + base + rb + u);
+                                xv[u] = __ldg(xr + base + rb + u);
+                            }
 #pragma unroll
-                for (int u = 0; u < kTfUnroll; ++u)
-                    if (rb + u < rz) xv[u] = __ldg(x + key[u].x);
-#pragma unroll
-                for (int u = 0; u < kTfUnroll; ++u) {
-                    if (rb + u >= rz) break;
-                    const int trow = (key[u].y >> 1) & 0xfff;
-                    const int gi = trow / R, ph = trow - gi * R;
-                    const int g1 = min(gi + 1, P.G - 1);
-                    if ((ph & 3) == pj) {
-                        const int c = ph * P.G;
-                        (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].x * xv[u];
-                        (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].y * xv[u];
-                    }
-                    if (((ph + 1) & 3) == pj) {
-                        const int c = (ph + 1) * P.G;
-                        (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].z * xv[u];
-                        (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].w * xv[u];
-                    }
-                    if (pj == 0 && (key[u].y & 1)) {
-                        // tau = t0 exactly: the last tap of the upper phase row lies outside
-                        const float2 tl = __bfloat1622float2(__ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1));
-                        sY[n0 + P.Tw] -= xv[u] * (w4[u].z * tl.x + w4[u].w * tl.y);
+                        for (int u = 0; u < kTfUnroll; ++u) {
+                            if (rb + u >= qz) break;
+                            const int trow = (key[u].y >> 1) & 0xfff;
+                            const int gi = trow / R, ph = trow - gi * R;
+                            const int g1 = min(gi + 1, P.G - 1);
+                            if (pass == 0) {
+                                const int c = (ph + 1) * P.G;
+                                (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].z * xv[u];
+                                (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].w * xv[u];
+                                if (key[u].y & 1) {
+                                    // tau = t0 exactly: the last tap of the upper phase row lies outside
+                                    const float2 tl =
+                                        __bfloat1622float2(__ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1));
+                                    flag_corr += xv[u] * (w4[u].z * tl.x + w4[u].w * tl.y);
+                                }
+                            } else {
+                                const int c = ph * P.G;
+                                (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].x * xv[u];
+                                (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].y * xv[u];
+                            }
+                        }
                     }
                 }
             }
+            // the four class threads of a sample are adjacent lanes: their flag corrections in class order
+            {
+                const float f1 = __shfl_down_sync(0xffffffffu, flag_corr, 1);
+                const float f2 = __shfl_down_sync(0xffffffffu, flag_corr, 2);
+                const float f3 = __shfl_down_sync(0xffffffffu, flag_corr, 3);
+                if (pj == 0 && n0 < P.M) sY[n0 + P.Tw] -= ((flag_corr + f1) + f2) + f3;
+            }
             __syncthreads();
-            for (int h = 0; h < 2; ++h) {
-                const int cw = h ? P.G * R - T.c0 : T.c0, kh = h ? T.k1 : T.k0;
-                if (cw <= 0) break;
-                const float* src = h ? sAcc1 : sAcc;
-                const int astr = h ? T.astride1 : T.astride;
-                const int kc = kh / 8;
-                // FP32 sums -> registers -> BF16 operand (K-major, 8 columns per 16-byte store);
-                // the first half's operand is written over its own sums
+            // FP32 sums -> registers -> BF16 operands (K-major, 8 columns per 16-byte store): the first
+            // half's operand goes over the start of its own sums, the second half's right after it
+            {
+                const int cw1 = P.G * R - T.c0;
+                unsigned char* sA1 = sA + (size_t)kTfTile * T.ka * 2;
                 uint4 pk[kTfStage];
-#pragma unroll
-                for (int q = 0; q < kTfStage; ++q) {
-                    const int c = tid + q * kTfThreads;
-                    if (c < kTfTile * kc) {
-                        const int i = c / kc, j = c - i * kc;
-                        const float* sp = src + i * astr + 8 * j;
-                        uint32_t w[4];
-#pragma unroll
-                        for (int e2 = 0; e2 < 4; ++e2) {
-                            const int cc = 8 * j + 2 * e2;
-                            const float a = cc < cw ? sp[2 * e2] : 0.0f, b = cc + 1 < cw ? sp[2 * e2 + 1] : 0.0f;
-                            const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-                            w[e2] = *reinterpret_cast<const uint32_t*>(&v);
-                        }
-                        pk[q] = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
-                }
-                if (h == 1) {
-                    // the first half's MMA reads the operand buffer: wait before rewriting it
-                    if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
-                    phase ^= 1u;
-                }
-                __syncthreads();
-                if (*abort_flag) break;
-#pragma unroll
-                for (int q = 0; q < kTfStage; ++q) {
-                    const int c = tid + q * kTfThreads;
-                    if (c < kTfTile * kc) {
-                        const int i = c / kc, j = c - i * kc;
-                        *reinterpret_cast<uint4*>(sA + kmajor_offset(i, 8 * j, T.ka)) = pk[q];
-                    }
+                tf_stage_half(pk, sAcc, T.astride, T.c0, T.k0, tid);
+                __syncthreads();                     // every first-half sum is in registers
+                tf_write_half(pk, sA, T.k0, T.ka, tid);
+                if (cw1 > 0) {
+                    tf_stage_half(pk, sAcc1, T.astride1, cw1, T.k1, tid);
+                    tf_write_half(pk, sA1, T.k1, T.ka, tid);
                 }
                 fence_async_smem();
                 __syncthreads();
                 if (tid == 0) {
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB) + (uint32_t)((h ? T.c0 : 0) / 8) * 128;
-                    for (int s = 0; s < kh / 16; ++s)
+                    const uint32_t b0 = smem_u32(sB);
+                    const uint32_t a0 = smem_u32(sA), a1 = smem_u32(sA1), b1 = b0 + (uint32_t)(T.c0 / 8) * 128;
+                    for (int s = 0; s < T.k0 / 16; ++s)
                         umma_bf16(tmem, umma_desc(a0 + 256 * s, lbo, sboA), umma_desc(b0 + 256 * s, lbo, sboB), idesc,
-                                  h > 0 || s > 0);
+                                  s > 0);
+                    if (cw1 > 0)
+                        for (int s = 0; s < T.k1 / 16; ++s)
+                            umma_bf16(tmem, umma_desc(a1 + 256 * s, lbo, sboA), umma_desc(b1 + 256 * s, lbo, sboB),
+                                      idesc, true);
                     umma_commit(smem_u32(bar));
                 }
             }

@@ -36,7 +36,8 @@ TfLayout tf_layout(const GeomParams& P)
     L.off_b = 1024;
     // first-half accumulator; the BF16 operand buffer is written over it once its sums are in registers
     L.off_acc = (L.off_b + (size_t)L.ntap * L.kb * 2 + 1023) & ~(size_t)1023;
-    const size_t acc0 = std::max((size_t)kTfTile * L.astride * 4, (size_t)kTfTile * L.ka * 2);
+    // the two halves' BF16 operands follow each other over the first half's sums
+    const size_t acc0 = std::max((size_t)kTfTile * L.astride * 4, (size_t)2 * kTfTile * L.ka * 2);
     L.off_a = L.off_acc;
     L.off_acc1 = (L.off_acc + acc0 + 127) & ~(size_t)127;
     L.off_y = (L.off_acc1 + (size_t)kTfTile * L.astride1 * 4 + 127) & ~(size_t)127;
@@ -45,6 +46,12 @@ TfLayout tf_layout(const GeomParams& P)
     const int per_thread = (kTfTile * (L.k0 / 8) + kTfThreads - 1) / kTfThreads;
     L.ok = L.ntap <= 256 && L.k0 > 0 && L.smem <= 227 * 1024 && L.ncols <= 4096 && per_thread <= kTfStage;
     return L;
+}
+
+__global__ void tc_gather_x_kernel(long long nrec, const int2* __restrict__ rkey, const float* __restrict__ x,
+                                   float* __restrict__ xr)
+{
+    tc_gather_x(nrec, rkey, x, xr);
 }
 
 __global__ void __launch_bounds__(kTfThreads, 1) fwd_tc_kernel(TcFwdView V, int* __restrict__ status)
@@ -74,12 +81,38 @@ __global__ void tf_n0_off_kernel(GeomParams P, const long long* __restrict__ rec
     n0_off[i] = lo;
 }
 
+// start of every phase class (table phase mod 4) inside every (A-scan, n0)
+// bucket; buckets are ordered by class.  *too_long is set for a bucket of
+// more than 65535 records (the offsets are 16-bit).
+__global__ void tf_grp_off_kernel(GeomParams P, const long long* __restrict__ rec_off, const int2* __restrict__ rkey,
+                                  const int* __restrict__ n0_off, ushort4* __restrict__ grp_off,
+                                  int* __restrict__ too_long)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)P.K * P.M) return;
+    const int k = (int)(i / P.M), n = (int)(i - (long long)k * P.M);
+    const long long base = rec_off[k];
+    const int a = n0_off[(size_t)k * (P.M + 1) + n], z = n0_off[(size_t)k * (P.M + 1) + n + 1];
+    const int R = P.Q + 1;
+    if (z - a > 65535) atomicExch(too_long, 1);
+    int st[4] = {0, 0, 0, 0};
+    int c = 0;
+    for (int r = a; r < z; ++r) {
+        const int cls = ((((rkey[base + r].y >> 1) & 0xfff) % R) & 3);
+        while (c < cls) st[++c] = r - a;
+    }
+    while (c < 3) st[++c] = z - a;
+    grp_off[i] = make_ushort4((unsigned short)st[1], (unsigned short)st[2], (unsigned short)st[3], 0);
+}
+
 // Tables of the tensor-core A x for a BF16 geometry with records;
 // cudaErrorNotSupported keeps the CUDA-core A x.
 cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
 {
     const GeomParams& P = g->P;
-    if (P.precision != MBIR_PREC_BF16 || !g->d_rec_key || g->n_records <= 0) return cudaErrorNotSupported;
+    // the record-ordered x of each apply lives in the adjoint's contribution buffer
+    if (P.precision != MBIR_PREC_BF16 || !g->d_rec_key || g->n_records <= 0 || !g->w_tc_contrib)
+        return cudaErrorNotSupported;
     const TfLayout L = tf_layout(P);
     if (!L.ok || (long long)P.K * (P.M + 1) >= (1LL << 31)) return cudaErrorNotSupported;
     const int nq = P.Q * P.Tw + 1;
@@ -101,10 +134,12 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
                      [&](int a, int b) { return roff[a + 1] - roff[a] > roff[b + 1] - roff[b]; });
     uint4* d_b = nullptr;
     int *d_n0 = nullptr, *d_ord = nullptr, *d_ctr = nullptr;
+    ushort4* d_grp = nullptr;
     e = cudaMalloc((void**)&d_b, bimg.size() * 2);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_n0, sizeof(int) * (size_t)P.K * (P.M + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ord, sizeof(int) * (size_t)P.K);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_grp, sizeof(ushort4) * (size_t)P.K * P.M);
     if (e == cudaSuccess) e = cudaMemcpy(d_b, bimg.data(), bimg.size() * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_ord, order.data(), sizeof(int) * (size_t)P.K, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -112,12 +147,22 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
         tf_n0_off_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(P, g->d_rec_off, g->d_rec_key, d_n0);
         e = cudaGetLastError();
     }
+    int too_long = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        const long long n = (long long)P.K * P.M;
+        tf_grp_off_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(P, g->d_rec_off, g->d_rec_key, d_n0, d_grp, d_ctr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&too_long, d_ctr, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && too_long) e = cudaErrorNotSupported;   // buckets beyond 16-bit offsets
     if (e != cudaSuccess) {
         cudaFree(d_b);
         cudaFree(d_n0);
         cudaFree(d_ord);
         cudaFree(d_ctr);
+        cudaFree(d_grp);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
@@ -126,7 +171,9 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
     g->d_tf_n0off = d_n0;
     g->d_tf_order = d_ord;
     g->d_tf_counter = d_ctr;
-    g->bytes += bimg.size() * 2 + sizeof(int) * ((size_t)P.K * (P.M + 1) + P.K + 1);
+    g->d_tf_grpoff = d_grp;
+    g->bytes += bimg.size() * 2 + sizeof(int) * ((size_t)P.K * (P.M + 1) + P.K + 1) +
+                sizeof(ushort4) * (size_t)P.K * P.M;
     return cudaSuccess;
 }
 
@@ -139,8 +186,12 @@ cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf,
     if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tf_counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return ce;
     const int grid = std::max(1, std::min(g->n_sm, P.K));
-    TcFwdView V{P, L, g->d_tf_bop, g->d_tab_bf16, g->d_rec_off, g->d_tf_n0off, g->d_rec_key, g->d_rec_w,
-                 g->d_tf_order, x, yf, yb, stride, g->d_tf_counter};
+    // x per record, in record order (the adjoint's contribution buffer is free between applies)
+    tc_gather_x_kernel<<<g->n_sm * 8, 256, 0, st>>>(g->n_records, g->d_rec_key, x, g->w_tc_contrib);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return ce;
+    TcFwdView V{P, L, g->d_tf_bop, g->d_tab_bf16, g->d_rec_off, g->d_tf_n0off, g->d_tf_grpoff, g->d_rec_key,
+                 g->d_rec_w, g->d_tf_order, g->w_tc_contrib, yf, yb, stride, g->d_tf_counter};
     fwd_tc_kernel<<<grid, kTfThreads, L.smem, st>>>(V, g->d_status);
     return cudaGetLastError();
 }
