@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--apply-only", type=int, default=0,
                     help="run only A x and A^T r this many times (for profiler captures) and exit")
-    ap.add_argument("--workload", default="cfg1", choices=["cfg1", "batched", "served"],
+    ap.add_argument("--workload", default="cfg1", choices=["cfg1", "batched", "served", "saft"],
                     help="cfg1: the headline workload; batched: uneven scenes through the engine vs serial "
                          "solves; served: Poisson arrivals of mixed sizes through the engine vs a serial queue")
     ap.add_argument("--requests", type=int, default=0, help="requests for the batched / served workloads")
@@ -555,6 +555,57 @@ def run_served(args):
                       "data": "synthetic", "config": cfg}), flush=True)
 
 
+def run_saft(args):
+    """The paper's comparison axis on the 4-layer 256x512 workload: SAFT
+    (delay-and-sum, A^T y with the beam profile phi = 1, one pass) against the
+    50-iteration MAP reconstruction, both from the same synthetic scan; image
+    error against the phantom after the least-squares scale for SAFT (whose
+    values are not reflectivities)."""
+    import numpy as np
+    import torch
+    from paper_2202_09703_gb300 import build as B
+    B.build()
+    from paper_2202_09703_gb300 import mbir as M
+    from paper_2202_09703_gb300 import synth as S
+    dev = torch.device("cuda:0")
+    scene = S.cfg1()
+    geo, y, sig = _synth_request(M, S, torch, scene, 0, dev)
+    saft = M.Geometry(scene.copy(beta=0.0), mode="tab")
+    xt = torch.as_tensor(S.phantom(scene, 0).reshape(-1), dtype=torch.float32, device=dev)
+    img = torch.empty(scene.N, device=dev)
+    for _ in range(3):
+        saft.backproject(y, img)
+    steps = max(args.steps, 5) * 10
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(steps):
+        saft.backproject(y, img)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_saft = ev[0].elapsed_time(ev[1]) / 1e3 / steps
+    x = torch.empty(scene.N, device=dev)
+    ev[0].record()
+    geo.reconstruct(y, sig, scene.n_iter, x)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_mbir = ev[0].elapsed_time(ev[1]) / 1e3
+
+    def err(a):
+        a = a.double()
+        t = xt.double()
+        scale = float((a @ t) / max(float(a @ a), 1e-300))
+        return float((scale * a - t).norm() / t.norm())
+
+    cfg = {"workload": "SAFT vs MAP on the 4-layer 256x512 scan (64 Tx x 16 Rx, 2048 samples), synthetic phantom",
+           "saft_ms_per_image": 1e3 * t_saft, "mbir_ms_per_image": 1e3 * t_mbir,
+           "saft_image_rel_err_vs_truth_ls_scaled": err(img), "mbir_image_rel_err_vs_truth": float(
+               (x.double() - xt.double()).norm() / xt.double().norm()),
+           "mbir_image_rel_err_vs_truth_ls_scaled": err(x)}
+    print(json.dumps({"metric": "SAFT images/s", "value": 1.0 / t_saft, "unit": "images/s", "higher_is_better": True,
+                      "data": "synthetic", "config": cfg}), flush=True)
+
+
 def main():
     args = parse()
     if args.source_hash:
@@ -565,6 +616,9 @@ def main():
         return
     if args.workload == "served":
         run_served(args)
+        return
+    if args.workload == "saft":
+        run_saft(args)
         return
     if args.apply_only:
         run_apply_only(args)

@@ -215,3 +215,27 @@ def test_small_requests_are_not_paced_by_a_large_one(problems):
         assert np.array_equal(x.cpu().numpy(), xa.cpu().numpy())
         e2.close()
     eng.close()
+
+
+def test_bf16_mix_on_the_tensor_cores_matches_each_request_alone(problems):
+    """Three uneven BF16 problems advance together through the engine's
+    tensor-core pools (one kernel walking requests with different tables and
+    sizes); each result is bitwise that of mbir_reconstruct on its own."""
+    eng = M.Engine(1 << 32)
+    runs = []
+    for (s, _, y, sig, _, y_np), n in zip(problems, (6, 9, 4)):
+        sb = s.copy(precision="bf16")
+        gb = M.Geometry(sb, mode="tab")
+        assert gb.info.forward_tensor_cores == 1 and gb.info.adjoint_tensor_cores == 1
+        yb = torch.as_tensor(np.asarray(y_np, np.float32).reshape(-1), dtype=torch.bfloat16, device=DEV)
+        x = torch.empty(s.N, device=DEV)
+        runs.append((eng.submit(gb, yb, sig, n, x), x, gb, yb, sig, n, s))
+    eng.run_until_idle()
+    torch.cuda.synchronize()
+    for t, x, gb, yb, sig, n, s in runs:
+        assert eng.poll(t) == M.Engine.DONE
+        xs = torch.empty(s.N, device=DEV)
+        gb.reconstruct(yb, sig, n, xs)
+        torch.cuda.synchronize()
+        assert np.array_equal(x.cpu().numpy(), xs.cpu().numpy())
+    eng.close()

@@ -423,3 +423,15 @@ def test_cfg2_bf16_image_against_fp32_form():
     assert rel_l2(x16, x32) <= 1e-2
     e32, e16 = rel_l2(x32, xt), rel_l2(x16, xt)
     assert abs(e16 - e32) <= 1e-2 * e32
+
+
+@pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene])
+def test_saft_image_matches_oracle(scene_fn):
+    """SAFT (delay-and-sum) is A^T y with the beam profile phi = 1: the GPU
+    adjoint of a beta = 0 geometry against the oracle's, on data made with
+    the beam model."""
+    s = scene_fn()
+    plan, x_true, g_true, y, sig = oracle_data(s, seed=3)
+    s0 = s.copy(beta=0.0)
+    geo = make_geo(s0, "tab")
+    assert rel_l2(gpu_backproject(geo, y), O.Plan(s0).backproject(y)) <= 1e-5

@@ -270,6 +270,40 @@ def test_pair_weight_is_transmission_times_apodization():
     assert w == pytest.approx(ref_w, rel=1e-14)
 
 
+def test_saft_weights_are_the_transmission_alone():
+    """SAFT (delay-and-sum, Section 1) is A^T with the beam profile phi = 1:
+    with beta = 0 every pair inside the 90-degree limit weighs the
+    interface transmission only, wherever the pixel lies."""
+    s = _tiny(layers=2)
+    s.beta = 0.0
+    p = O.Plan(s, nthreads=1)
+    g = O.Geometry(s)
+    for v in (3, 7 * s.img_w + 3, s.N - 1):
+        zr = (v // s.img_w + 0.5) * s.pitch
+        for k in range(s.K):
+            assert p.pair(v, k)[2] == g.transmission(zr)
+
+
+def test_saft_image_of_a_point_reflector_peaks_at_the_reflector():
+    """Delay-and-sum focuses: the SAFT image (A^T y, beta = 0) of the data of
+    one point reflector (y = A e_v with the beam model) is largest at v among
+    the pixels of v's layer (the transmission factor differs between layers:
+    about 0.12 from water into steel, so water pixels are not comparable)."""
+    for n_layers, pixels in ((1, (9 * 24 + 11, 15 * 24 + 6)), (2, (9 * 24 + 11, 15 * 24 + 6))):
+        s = S.small_scene(n_layers=n_layers, w=24, h=20, n_tx=6, n_rx=4, M=400, atten=False)
+        p = O.Plan(s, nthreads=2)
+        p0 = O.Plan(s.copy(beta=0.0), nthreads=2)
+        top = s.layers[0].thickness if n_layers == 2 else 0.0
+        z = (np.arange(s.img_h) + 0.5) * s.pitch
+        same_layer = np.repeat(z >= top, s.img_w)
+        for v in pixels:
+            x = np.zeros(s.N)
+            x[v] = 1.0
+            img = p0.backproject(p.forward(x).reshape(-1))
+            assert same_layer[v]
+            assert int(np.argmax(np.where(same_layer, img, -np.inf))) == v
+
+
 def test_projection_removes_direct_arrivals():
     s = _tiny(direct=True)
     p = O.Plan(s, nthreads=1)
