@@ -60,6 +60,14 @@ typedef enum {
     MBIR_MODE_TAB = 2            /* legs solved once per geometry, kept in device memory */
 } mbir_mode;
 
+/* Angle of eq. 12's beam profile cos^beta(angle).  ANGLE_SUM follows eq. 12
+ * (the sum of the layer angles); FIRST_ANGLE is a variant that uses the
+ * first-layer angle only. */
+typedef enum {
+    MBIR_APOD_ANGLE_SUM = 0,
+    MBIR_APOD_FIRST_ANGLE = 1
+} mbir_apodization;
+
 /*
  * Geometry of one scan (Section 2 "Multi-layered structures", eq. 3-6, and the
  * acquisition of Section 3).  Arrays are host memory and are copied.
@@ -75,6 +83,12 @@ typedef enum {
  *   gamma_bins (G), phases (Q): pulse table of G attenuation bins and Q
  *       phases per sample, read by bilinear interpolation (0 selects 16, 16).
  *   flags: MBIR_FLAG_* below (0 for the defaults).
+ *   firing_angle_rad: the transmitter's beam axis is turned by this angle
+ *       toward +x (the Section 3 source is tilted by 5 degrees), so its
+ *       factor of eq. 12 is cos^beta(signed ray angle - firing angle); the
+ *       receivers are not tilted.  |angle| < pi/2; a nonzero angle needs TAB
+ *       mode (MBIR_ERR_UNSUPPORTED with MBIR_MODE_OTF).
+ *   apodization: mbir_apodization (0 selects eq. 12 as written).
  */
 typedef struct {
     int n_layers;
@@ -98,6 +112,8 @@ typedef struct {
     int precision;               /* mbir_precision */
     int mode;                    /* mbir_mode */
     int flags;                   /* MBIR_FLAG_* */
+    double firing_angle_rad;     /* transmitter beam axis turned toward +x (Section 3: 5 degrees); TAB mode */
+    int apodization;             /* mbir_apodization */
 } mbir_geometry_desc;
 
 /* TAB mode normally also stores every A-scan's active pairs as records

@@ -254,7 +254,8 @@ struct orc_plan {
     long npix;
     long* pix;            /* pixel index of each slot */
     int npos;
-    double* pos;          /* distinct transducer lateral positions */
+    double* pos;          /* distinct transducer lateral positions (then the tilted Tx, if any) */
+    int* pos_tx;          /* 1 for an entry of a tilted transmitter */
     int* tx_pos;          /* n_tx */
     int* rx_pos;          /* n_tx * n_rx */
     double* tau_row;      /* transmission per image row */
@@ -302,17 +303,27 @@ orc_plan* orc_plan_create(const orc_geom* g, const long* pix, long npix, int nth
     for (int i = 0; i < g->n_tx; ++i)
         for (int j = 0; j < g->n_rx; ++j) all[n++] = g->tx_x[i] + g->rx_offset[j];
     qsort(all, nall, sizeof(double), cmp_double);
-    p->pos = (double*)malloc(sizeof(double) * nall);
+    p->pos = (double*)malloc(sizeof(double) * (nall + g->n_tx));
+    p->pos_tx = (int*)calloc(nall + g->n_tx, sizeof(int));
     p->npos = 0;
     for (int a = 0; a < nall; ++a)
         if (p->npos == 0 || all[a] != p->pos[p->npos - 1]) p->pos[p->npos++] = all[a];
     free(all);
+    const int nshared = p->npos;
     p->tx_pos = (int*)malloc(sizeof(int) * g->n_tx);
     p->rx_pos = (int*)malloc(sizeof(int) * g->n_tx * g->n_rx);
     for (int i = 0; i < g->n_tx; ++i) {
-        p->tx_pos[i] = find_pos(p->pos, p->npos, g->tx_x[i]);
+        p->tx_pos[i] = find_pos(p->pos, nshared, g->tx_x[i]);
         for (int j = 0; j < g->n_rx; ++j)
-            p->rx_pos[i * g->n_rx + j] = find_pos(p->pos, p->npos, g->tx_x[i] + g->rx_offset[j]);
+            p->rx_pos[i * g->n_rx + j] = find_pos(p->pos, nshared, g->tx_x[i] + g->rx_offset[j]);
+    }
+    if (g->tilt != 0.0) {
+        /* a tilted transmitter's legs weigh differently from a receiver's at the same place */
+        for (int i = 0; i < g->n_tx; ++i) {
+            p->pos[p->npos] = g->tx_x[i];
+            p->pos_tx[p->npos] = 1;
+            p->tx_pos[i] = p->npos++;
+        }
     }
     p->tau_row = (double*)malloc(sizeof(double) * g->img_h);
     for (int r = 0; r < g->img_h; ++r)
@@ -336,6 +347,7 @@ void orc_plan_destroy(orc_plan* p)
     free(p->tab);
     free(p->pix);
     free(p->pos);
+    free(p->pos_tx);
     free(p->tx_pos);
     free(p->rx_pos);
     free(p->tau_row);
@@ -359,9 +371,14 @@ static void ensure_pos(orc_plan* p, int a, int nthreads)
         int r = (int)(v / g->img_w), c = (int)(v % g->img_w);
         double xc = g->x0 + (c + 0.5) * g->pitch;
         double zr = g->z0 + (r + 0.5) * g->pitch;
-        double T, gm, Th;
-        orc_leg(g, xc - u, zr, &T, &gm, &Th, NULL);
-        double cth = cos(Th);
+        double T, gm, Th, th1;
+        orc_leg(g, xc - u, zr, &T, &gm, &Th, &th1);
+        /* eq. 12: the beam-profile angle is the sum of the layer angles (or the
+         * first-layer angle); a tilted transmitter's beam axis is turned by
+         * the firing angle toward +x, so the signed angle of the ray counts */
+        double ang = g->apod_first ? th1 : Th;
+        if (p->pos_tx[a]) ang = (xc - u >= 0.0 ? ang : -ang) - g->tilt;
+        double cth = cos(ang);
         L[3 * s + 0] = T;
         L[3 * s + 1] = gm;
         L[3 * s + 2] = cth > 0.0 ? pow(cth, g->beta) : 0.0;   /* eq. 12 factor */

@@ -41,6 +41,8 @@ typedef struct {
     int direct_arrival;                /* 1: model D g of eq. 1 */
     double gamma_max;                  /* s; <= 0 selects the default rule */
     int G, Q;                          /* pulse-table gamma bins and phases per sample */
+    double tilt;                       /* transmitter firing angle (rad) toward +x (Section 3: 5 degrees) */
+    int apod_first;                    /* 1: eq. 12 with the first-layer angle instead of the angle sum */
 } orc_geom;
 
 typedef struct {

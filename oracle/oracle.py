@@ -53,6 +53,7 @@ class _Geom(C.Structure):
         ("fc", C.c_double), ("n_cycles", C.c_double),
         ("beta", C.c_double), ("direct_arrival", C.c_int),
         ("gamma_max", C.c_double), ("G", C.c_int), ("Q", C.c_int),
+        ("tilt", C.c_double), ("apod_first", C.c_int),
     ]
 
 
@@ -136,6 +137,7 @@ class Geometry:
         g.fc, g.n_cycles = scene.fc, scene.n_cycles
         g.beta, g.direct_arrival = scene.beta, int(bool(scene.direct_arrival))
         g.gamma_max, g.G, g.Q = scene.gamma_max, scene.G, scene.Q
+        g.tilt, g.apod_first = scene.firing_angle, int(bool(scene.apod_first_angle))
         self.g = g
 
     @property

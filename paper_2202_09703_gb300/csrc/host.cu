@@ -88,6 +88,9 @@ int validate(const mbir_geometry_desc* d)
         return MBIR_ERR_INVALID_ARG;
     if (d->precision != MBIR_PREC_FP32 && d->precision != MBIR_PREC_BF16) return MBIR_ERR_INVALID_ARG;
     if (d->mode < MBIR_MODE_AUTO || d->mode > MBIR_MODE_TAB) return MBIR_ERR_INVALID_ARG;
+    if (!std::isfinite(d->firing_angle_rad) || !(std::fabs(d->firing_angle_rad) < 0.5 * M_PI) ||
+        (d->apodization != MBIR_APOD_ANGLE_SUM && d->apodization != MBIR_APOD_FIRST_ANGLE))
+        return MBIR_ERR_INVALID_ARG;
     for (int i = 0; i < d->n_tx; ++i) if (!std::isfinite(d->tx_x_m[i])) return MBIR_ERR_INVALID_ARG;
     for (int j = 0; j < d->n_rx; ++j) if (!std::isfinite(d->rx_offset_m[j])) return MBIR_ERR_INVALID_ARG;
     long long N = (long long)d->img_w * d->img_h;
@@ -233,6 +236,9 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
     double bi = std::round(d->beta);
     P.beta_int = (std::fabs(d->beta - bi) == 0.0 && bi <= 64) ? (int)bi : -1;
     P.beta = (float)d->beta;
+    P.apod_first = d->apodization == MBIR_APOD_FIRST_ANGLE ? 1 : 0;
+    P.tilt_c = split_df(std::cos(d->firing_angle_rad));
+    P.tilt_s = split_df(std::sin(d->firing_angle_rad));
     g->gamma_max = D.gmax;
     g->fs = d->fs_hz;
     g->z0 = d->img_z0_m;
@@ -316,6 +322,16 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
         txpos[i] = pos_index(d->tx_x_m[i]);
         for (int j = 0; j < P.n_rx; ++j) rxpos[i * P.n_rx + j] = pos_index(d->tx_x_m[i] + d->rx_offset_m[j]);
     }
+    // a tilted transmitter's legs weigh differently from a receiver's at the same place:
+    // its positions get entries of their own, whose legs depend on the sign of x_c - u
+    const bool tilted = d->firing_angle_rad != 0.0;
+    const int nshared = P.npos;
+    if (tilted) {
+        for (int i = 0; i < P.n_tx; ++i) {
+            pos.push_back(d->tx_x_m[i]);
+            txpos[i] = P.npos++;
+        }
+    }
     std::vector<float2> posdf(P.npos);
     for (int a = 0; a < P.npos; ++a) posdf[a] = split_df(pos[a]);
 
@@ -368,33 +384,52 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
     }
 
     // TAB: distinct |x_c - u| values per (position, column)
+    // legs are keyed by |x_c - u| for receivers and untilted transmitters, and by the
+    // signed x_c - u for tilted transmitters (listed after the others); hsign: 0, +1, -1
     std::vector<int> hidx;
     std::vector<float2> hvals;
+    std::vector<int> hsign;
     int mode = d->mode;
+    if (tilted && mode == MBIR_MODE_OTF) { free_geometry(g); return MBIR_ERR_UNSUPPORTED; }
     {
         std::vector<double> hv;
         hv.reserve((size_t)P.npos * P.W);
         for (int a = 0; a < P.npos; ++a)
-            for (int c = 0; c < P.W; ++c)
-                hv.push_back(std::fabs(d->img_x0_m + (c + 0.5) * d->pitch_m - pos[a]));
-        std::vector<double> sorted(hv);
-        std::sort(sorted.begin(), sorted.end());
-        double tol = 1e-9 * d->pitch_m;
-        std::vector<double> uniq;
-        for (double v : sorted)
-            if (uniq.empty() || v - uniq.back() > tol) uniq.push_back(v);
-        size_t tab_bytes = (size_t)P.H * uniq.size() * sizeof(float4);
-        if (mode == MBIR_MODE_AUTO) mode = (tab_bytes <= ((size_t)4 << 30)) ? MBIR_MODE_TAB : MBIR_MODE_OTF;
-        if (mode == MBIR_MODE_TAB) {
-            hidx.resize(hv.size());
-            for (size_t t = 0; t < hv.size(); ++t) {
-                size_t u = std::lower_bound(uniq.begin(), uniq.end(), hv[t] - tol) - uniq.begin();
-                if (u + 1 < uniq.size() && std::fabs(uniq[u + 1] - hv[t]) < std::fabs(uniq[u] - hv[t])) ++u;
-                hidx[t] = (int)u;
+            for (int c = 0; c < P.W; ++c) {
+                const double x = d->img_x0_m + (c + 0.5) * d->pitch_m - pos[a];
+                hv.push_back(a < nshared ? std::fabs(x) : x);
             }
-            hvals.resize(uniq.size());
-            for (size_t u = 0; u < uniq.size(); ++u) hvals[u] = split_df(uniq[u]);
-            P.nh = (int)uniq.size();
+        const double tol = 1e-9 * d->pitch_m;
+        auto uniq_of = [tol](std::vector<double> v) {
+            std::sort(v.begin(), v.end());
+            std::vector<double> u;
+            for (double x : v)
+                if (u.empty() || x - u.back() > tol) u.push_back(x);
+            return u;
+        };
+        std::vector<double> u0 = uniq_of(std::vector<double>(hv.begin(), hv.begin() + (size_t)nshared * P.W));
+        std::vector<double> u1 = uniq_of(std::vector<double>(hv.begin() + (size_t)nshared * P.W, hv.end()));
+        size_t tab_bytes = (size_t)P.H * (u0.size() + u1.size()) * sizeof(float4);
+        if (mode == MBIR_MODE_AUTO) mode = (tab_bytes <= ((size_t)4 << 30)) ? MBIR_MODE_TAB : MBIR_MODE_OTF;
+        if (tilted && mode != MBIR_MODE_TAB) { free_geometry(g); return MBIR_ERR_UNSUPPORTED; }
+        if (mode == MBIR_MODE_TAB) {
+            auto nearest = [tol](const std::vector<double>& u, double x) {
+                size_t i = std::lower_bound(u.begin(), u.end(), x - tol) - u.begin();
+                if (i + 1 < u.size() && std::fabs(u[i + 1] - x) < std::fabs(u[i] - x)) ++i;
+                return i;
+            };
+            hidx.resize(hv.size());
+            for (size_t t = 0; t < hv.size(); ++t)
+                hidx[t] = t < (size_t)nshared * P.W ? (int)nearest(u0, hv[t]) : (int)(u0.size() + nearest(u1, hv[t]));
+            for (double x : u0) {
+                hvals.push_back(split_df(x));
+                hsign.push_back(0);
+            }
+            for (double x : u1) {
+                hvals.push_back(split_df(std::fabs(x)));
+                hsign.push_back(x >= 0.0 ? 1 : -1);
+            }
+            P.nh = (int)hvals.size();
         }
     }
     P.mode = mode;
@@ -420,15 +455,18 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
     if (mode == MBIR_MODE_TAB) {
         UP(g->d_hidx, hidx);
         float2* d_hv = nullptr;
+        int* d_hs = nullptr;
         size_t tmpb = 0;
         ce = upload(&d_hv, hvals.data(), hvals.size(), &tmpb);
-        if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
-        ce = cudaMalloc((void**)&g->d_legs, sizeof(float4) * (size_t)P.H * P.nh);
+        if (ce == cudaSuccess) ce = upload(&d_hs, hsign.data(), hsign.size(), &tmpb);
         if (ce != cudaSuccess) { cudaFree(d_hv); free_geometry(g); return cuda_err(ce); }
+        ce = cudaMalloc((void**)&g->d_legs, sizeof(float4) * (size_t)P.H * P.nh);
+        if (ce != cudaSuccess) { cudaFree(d_hv); cudaFree(d_hs); free_geometry(g); return cuda_err(ce); }
         bytes += sizeof(float4) * (size_t)P.H * P.nh;
-        ce = mbir::launch_build_legs(g, nullptr, d_hv, st);
+        ce = mbir::launch_build_legs(g, d_hs, d_hv, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
         cudaFree(d_hv);
+        cudaFree(d_hs);
         if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
     }
     if (!mbir::backproject_config(P, &g->bwd_halves, &g->bwd_stages)) {

@@ -33,6 +33,8 @@ struct GeomParams {
     float alpha_c[kMaxLayers];        // alpha_l (s/m) * gscale: gamma-bin units per metre
     int n_seg;                        // layer segments among image rows
     int seg_row[kMaxLayers + 1];      // first row of each segment, seg_row[n_seg] = H
+    int apod_first;                   // eq. 12 with the first-layer angle instead of the angle sum
+    float2 tilt_c, tilt_s;            // cos / sin of the transmitter firing angle (double-float)
 };
 
 // Per image row.
@@ -176,7 +178,7 @@ __device__ __forceinline__ df abs_diff(float2 xc, float2 u)
 // relative error of the cosine by eight.
 // ---------------------------------------------------------------------------
 template <int NL>
-__device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri, df h)
+__device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri, df h, int tsign = 0)
 {
     float eta[NL], kk[NL];
 #pragma unroll
@@ -230,6 +232,7 @@ __device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri,
     df p2 = df_mul(p, p);
     float g = 0.0f;
     df C = {1.0f, 0.0f}, Sn = {0.0f, 0.0f};
+    df C1 = {1.0f, 0.0f}, S1 = {0.0f, 0.0f};                      // cos, sin of theta_1
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         if (l < ri.nl) {
@@ -244,7 +247,14 @@ __device__ __forceinline__ Leg solve_leg(const GeomParams& P, const RowInfo& ri,
             df Cn = df_sub(df_mul(C, c), df_mul(Sn, t));          // cos, sin of the angle sum
             Sn = df_add(df_mul(Sn, c), df_mul(C, t));
             C = Cn;
+            if (l == 0) { C1 = c; S1 = t; }
         }
+    }
+    if (P.apod_first) { C = C1; Sn = S1; }
+    if (tsign != 0) {
+        // a transmitter tilted by psi toward +x: cos(s * angle - psi) = cos a cos psi + s sin a sin psi
+        df a = df_mul(C, {P.tilt_c.x, P.tilt_c.y}), b = df_mul(Sn, {P.tilt_s.x, P.tilt_s.y});
+        C = tsign > 0 ? df_add(a, b) : df_sub(a, b);
     }
     Leg out;
     out.Th = T.hi;
@@ -407,8 +417,7 @@ struct mbir_geometry {
 
 namespace mbir {
 // launchers implemented in apply.cu
-cudaError_t launch_build_legs(const mbir_geometry* g, const double* hvals_dev_unused, const float2* d_hvals,
-                              cudaStream_t st);
+cudaError_t launch_build_legs(const mbir_geometry* g, const int* d_hsign, const float2* d_hvals, cudaStream_t st);
 cudaError_t launch_backproject(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
                                float* b, cudaStream_t st);
 cudaError_t launch_forward(const mbir_geometry* g, const float* x, float* y_f32, __nv_bfloat16* y_bf16,

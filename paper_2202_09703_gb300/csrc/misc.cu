@@ -7,9 +7,11 @@
 
 namespace mbir {
 
+// one TAB leg per (row, distinct offset); hsign != 0 marks a tilted transmitter's
+// signed offset (its eq. 12 factor depends on the side of the ray)
 template <int NL>
 __global__ void build_legs_kernel(GeomParams P, const RowInfo* __restrict__ rows, const float2* __restrict__ hv,
-                                  float4* __restrict__ legs)
+                                  const int* __restrict__ hsign, float4* __restrict__ legs)
 {
     const long long total = (long long)P.H * P.nh;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -17,22 +19,22 @@ __global__ void build_legs_kernel(GeomParams P, const RowInfo* __restrict__ rows
         const int row = (int)(t / P.nh), hix = (int)(t - (long long)row * P.nh);
         RowInfo ri = load_row(rows, row);
         float2 h = hv[hix];
-        Leg L = solve_leg<NL>(P, ri, df{h.x, h.y});
+        Leg L = solve_leg<NL>(P, ri, df{h.x, h.y}, hsign[hix]);
         legs[t] = make_float4(L.Th, L.Tl, L.g, L.phi);
     }
 }
 
-cudaError_t launch_build_legs(const mbir_geometry* g, const double*, const float2* d_hvals, cudaStream_t st)
+cudaError_t launch_build_legs(const mbir_geometry* g, const int* d_hsign, const float2* d_hvals, cudaStream_t st)
 {
     const GeomParams& P = g->P;
     long long total = (long long)P.H * P.nh;
     int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
     if (P.L <= 2)
-        build_legs_kernel<2><<<blocks, 256, 0, st>>>(P, g->d_rows, d_hvals, g->d_legs);
+        build_legs_kernel<2><<<blocks, 256, 0, st>>>(P, g->d_rows, d_hvals, d_hsign, g->d_legs);
     else if (P.L <= 4)
-        build_legs_kernel<4><<<blocks, 256, 0, st>>>(P, g->d_rows, d_hvals, g->d_legs);
+        build_legs_kernel<4><<<blocks, 256, 0, st>>>(P, g->d_rows, d_hvals, d_hsign, g->d_legs);
     else
-        build_legs_kernel<8><<<blocks, 256, 0, st>>>(P, g->d_rows, d_hvals, g->d_legs);
+        build_legs_kernel<8><<<blocks, 256, 0, st>>>(P, g->d_rows, d_hvals, d_hsign, g->d_legs);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,7 @@ class GeometryDesc(C.Structure):
         ("beta", C.c_double), ("direct_arrival", C.c_int),
         ("gamma_max_s", C.c_double), ("gamma_bins", C.c_int), ("phases", C.c_int),
         ("precision", C.c_int), ("mode", C.c_int), ("flags", C.c_int),
+        ("firing_angle_rad", C.c_double), ("apodization", C.c_int),
     ]
 
 
@@ -166,6 +167,8 @@ def desc_from_scene(scene, mode: str = "auto", precision: str | None = None, fla
     d.precision = PRECISIONS[precision or scene.precision]
     d.mode = MODES[mode]
     d.flags = flags
+    d.firing_angle_rad = getattr(scene, "firing_angle", 0.0)
+    d.apodization = 1 if getattr(scene, "apod_first_angle", False) else 0
     return d, (tx, rx)
 
 

@@ -115,6 +115,8 @@ class Scene:
     prior: Prior = field(default_factory=Prior)
     n_iter: int = 20
     precision: str = "fp32"
+    firing_angle: float = 0.0       # rad: transmitter beam axis turned toward +x (Section 3 uses 5 degrees)
+    apod_first_angle: bool = False  # eq. 12 with the first-layer angle instead of the sum of the angles
 
     @property
     def n_tx(self) -> int:

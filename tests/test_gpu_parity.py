@@ -435,3 +435,39 @@ def test_saft_image_matches_oracle(scene_fn):
     s0 = s.copy(beta=0.0)
     geo = make_geo(s0, "tab")
     assert rel_l2(gpu_backproject(geo, y), O.Plan(s0).backproject(y)) <= 1e-5
+
+
+# --------------------------------------------------------------------------
+# beam-model variants: transmitter firing angle, first-layer apodization angle
+# --------------------------------------------------------------------------
+BEAM_VARIANTS = [
+    ("tilt+5deg", lambda: S.cfg0().copy(firing_angle=math.radians(5.0)), "tab"),
+    ("tilt-3deg ragged", lambda: ragged_scene().copy(firing_angle=math.radians(-3.0)), "tab"),
+    ("first angle", lambda: ragged_scene().copy(apod_first_angle=True), "tab"),
+    ("first angle otf", lambda: ragged_scene().copy(apod_first_angle=True), "otf"),
+    ("first angle + tilt", lambda: S.cfg0().copy(apod_first_angle=True, firing_angle=math.radians(5.0)), "tab"),
+]
+
+
+@pytest.mark.parametrize("name,scene_fn,mode", BEAM_VARIANTS, ids=[v[0] for v in BEAM_VARIANTS])
+def test_beam_variants_match_oracle(name, scene_fn, mode):
+    s = scene_fn()
+    geo = make_geo(s, mode)
+    plan = O.Plan(s)
+    pix = np.repeat(np.arange(s.N), s.K)
+    ks = np.tile(np.arange(s.K), s.N)
+    T, g, w = geo.pair_quantities(pix, ks)
+    ref = np.array([plan.pair(int(v), int(k)) for v, k in zip(pix, ks)])
+    assert np.max(np.abs(w - ref[:, 2])) <= 2e-6
+    assert np.max(np.abs(T - ref[:, 0] * s.fs)) <= 1e-3
+    x = S.random_vector(s.N, 41).reshape(s.img_h, s.img_w)
+    assert rel_l2(gpu_forward(geo, x), plan.forward(x)) <= 1e-5
+    r = S.random_vector(s.K * s.M, 42)
+    assert rel_l2(gpu_backproject(geo, r), plan.backproject(r)) <= 1e-5
+
+
+def test_tilted_transmitter_needs_tab_mode():
+    s = S.cfg0().copy(firing_angle=math.radians(5.0))
+    with pytest.raises(M.MbirError) as ei:
+        make_geo(s, "otf")
+    assert ei.value.code == -7

@@ -304,6 +304,52 @@ def test_saft_image_of_a_point_reflector_peaks_at_the_reflector():
             assert int(np.argmax(np.where(same_layer, img, -np.inf))) == v
 
 
+def _pair_factors(s, v, k):
+    p = O.Plan(s, nthreads=1)
+    g = O.Geometry(s)
+    r, c = divmod(v, s.img_w)
+    xc, zr = (c + 0.5) * s.pitch, (r + 0.5) * s.pitch
+    i, j = divmod(k, s.n_rx)
+    return p.pair(v, k)[2], g, xc, zr, s.tx_x[i], s.tx_x[i] + s.rx_offset[j]
+
+
+def test_first_angle_apodization():
+    """Beam-profile variant (eq. 12 with theta_1 instead of the angle sum):
+    identical to eq. 12 in one layer, and cos^beta(theta_1) of each leg with
+    the transmission in two layers."""
+    s1 = _tiny(layers=1)
+    for v, k in ((7 * s1.img_w + 3, 3), (2, 0)):
+        assert _pair_factors(s1.copy(apod_first_angle=True), v, k)[0] == pytest.approx(
+            _pair_factors(s1, v, k)[0], rel=1e-14)
+    s2 = _tiny(layers=2).copy(apod_first_angle=True)
+    v, k = 7 * s2.img_w + 3, 3
+    w, g, xc, zr, ut, ur = _pair_factors(s2, v, k)
+    a_t, a_r = g.leg(xc - ut, zr)[3], g.leg(xc - ur, zr)[3]
+    assert g.leg(xc - ut, zr)[2] > a_t                       # the sum differs from theta_1 here
+    ref = g.transmission(zr) * math.cos(a_t) ** s2.beta * math.cos(a_r) ** s2.beta
+    assert w == pytest.approx(ref, rel=1e-14)
+
+
+def test_firing_angle_closed_form_in_one_layer():
+    """A transmitter tilted by psi toward +x (Section 3's 5-degree firing
+    angle): in one layer its factor is max(cos(atan((x - u)/z) - psi), 0)^beta,
+    larger on the +x side than at the mirrored pixel; receivers are unchanged."""
+    psi = math.radians(5.0)
+    s = _tiny(layers=1).copy(firing_angle=psi)
+    for v, k in ((7 * s.img_w + 6, 2), (7 * s.img_w + 1, 2), (3, 0), (9 * s.img_w + 7, 1)):
+        w, g, xc, zr, ut, ur = _pair_factors(s, v, k)
+        phi_t = max(math.cos(math.atan((xc - ut) / zr) - psi), 0.0) ** s.beta
+        phi_r = max(math.cos(math.atan(abs(xc - ur) / zr)), 0.0) ** s.beta
+        assert w == pytest.approx(phi_t * phi_r, rel=1e-12)
+    # mirror: tilt -psi on the mirrored scan gives the same weight
+    sm = s.copy(firing_angle=-psi, tx_x=s.img_w * s.pitch - np.asarray(s.tx_x),
+                rx_offset=-np.asarray(s.rx_offset))
+    for v, k in ((7 * s.img_w + 6, 2), (4 * s.img_w + 1, 3)):
+        r, c = divmod(v, s.img_w)
+        vm = r * s.img_w + (s.img_w - 1 - c)
+        assert _pair_factors(sm, vm, k)[0] == pytest.approx(_pair_factors(s, v, k)[0], rel=1e-12)
+
+
 def test_projection_removes_direct_arrivals():
     s = _tiny(direct=True)
     p = O.Plan(s, nthreads=1)
