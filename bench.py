@@ -353,7 +353,11 @@ def run_gpu(args):
                         "achieved_gbs": algo_bytes / (dom_ms * 1e-3) / 1e9,
                         "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),
                         "frac": algo_bytes / (dom_ms * 1e-3) / 1e9 / float(pk.get("hbm_gbs", 6800.0))}}
-    launches = args.steps * (2 + 8 * scene.n_iter)
+    # per timed reconstruction: the projection of y, then 9 kernels per iteration (A^T r and its group
+    # reduction, prior gradient, PR+ scalars, direction, A x, projection, step, update); the ncu launch
+    # list of this command agrees (451 for 50 iterations; the host-buffer call adds A x and the
+    # projection of the final direct-arrival gains)
+    launches = args.steps * (9 * scene.n_iter + 1)
 
     out = {"metric": "recons/s", "value": value, "unit": "recons/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
