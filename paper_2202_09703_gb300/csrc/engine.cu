@@ -90,6 +90,9 @@ struct ReqDesc {
     int nblk;              // pixel blocks of kRedThreads
     // tensor-core pools of the BF16 form (tc != 0)
     int tc;
+    int tc32;              // FP32 tensor-core adjoint pool available
+    Tc3Layout tc3l;
+    const uint4* tc3_bop;
     TcLayout tcl;
     TfLayout tfl;
     const uint4* tc_bop;
@@ -411,6 +414,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc_kernel(EngLists L)
     tc_header_release(smem, tmem, kTcCols);
 }
 
+// A^T e of the FP32 form on the tensor cores (three-part BF16 split) over every
+// active request, with the single-request pool function
+__global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc32_kernel(EngLists L)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, 256);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
+    uint32_t phase = 0, bphase = 0;
+    const int nreq = L.counts[0];
+    if (nreq > 0) {
+        const int r0 = L.start[blockIdx.x] % nreq;
+        for (int t = 0; t < nreq; ++t) {
+            const int rq = (r0 + t) % nreq;
+            const ReqDesc& R = L.desc[rq];
+            const int nitems = R.P.K * ((R.P.M + kTcTile - 1) / kTcTile);
+            if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
+            const Tc3View V{R.P, R.tc3l, R.tc3_bop, R.tab, R.e, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc_dest,
+                            R.tc_contrib, L.pool + 2 * rq + 1};
+            if (!tc_adjoint32_pool(V, smem, tmem, phase, bphase, R.D.status)) break;
+            __syncthreads();
+        }
+    }
+    tc_header_release(smem, tmem, 256);
+}
+
 // b = each pixel's contributions summed in A-scan order (the single-request
 // reduction's arithmetic: warp per pixel, lane-strided Neumaier, fixed tree)
 __global__ void eng_bwd_tc_reduce_kernel(EngLists L)
@@ -580,7 +609,7 @@ size_t request_bytes(const mbir_geometry* g, int ngroups)
     size_t b = 2 * KMp * 4 + 6 * N * 4 + (size_t)ngroups * N * 4 + (size_t)P.H * 4 + S_COUNT * 8 +
                (4 * nblk + P.K + 8) * 8;
     if (P.precision == MBIR_PREC_BF16) b += KMp * 2;
-    if (g->d_tc_bop && g->d_tf_bop) b += (size_t)g->n_records * 4;   // tensor-core contributions
+    if ((g->d_tc_bop && g->d_tf_bop) || g->d_tc3_bop) b += (size_t)g->n_records * 4;   // tensor-core contributions
     return b;
 }
 
@@ -672,7 +701,7 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     AL(r->sc, (size_t)S_COUNT);
     AL(r->part, (size_t)4 * r->nblk + P.K + 8);
     if (P.precision == MBIR_PREC_BF16) AL(r->ebf, KMp);
-    if (g->d_tc_bop && g->d_tf_bop) AL(r->contrib, (size_t)g->n_records);
+    if ((g->d_tc_bop && g->d_tf_bop) || g->d_tc3_bop) AL(r->contrib, (size_t)g->n_records);
 #undef AL
     if (e != cudaSuccess) { free_request_state(r, st); return e == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA; }
     r->msq_host.resize(P.H);
@@ -737,6 +766,9 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.sub = g->fwd_sub;
     d.nblk = r->nblk;
     d.tc = (g->d_tc_bop && g->d_tf_bop) ? 1 : 0;
+    d.tc32 = g->d_tc3_bop ? 1 : 0;
+    d.tc3l = g->tc3;
+    d.tc3_bop = g->d_tc3_bop;
     d.tcl = g->tc;
     d.tfl = g->tf;
     d.tc_bop = g->d_tc_bop;
@@ -864,8 +896,11 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, cudaStream_t s
     const int G = E->n_sm, SG = E->n_sm * 8;
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
     if (e != cudaSuccess) return e;
-    if (tc) {
+    if (tc && bf16) {
         eng_bwd_tc_kernel<<<G, kTcThreads, kEngSmem, st>>>(E->L);
+        eng_bwd_tc_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
+    } else if (tc) {
+        eng_bwd_tc32_kernel<<<G, kTcThreads, kEngSmem, st>>>(E->L);
         eng_bwd_tc_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     } else {
         if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
@@ -875,7 +910,7 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, cudaStream_t s
     eng_grad_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     eng_findir_kernel<<<G, kRedThreads, 0, st>>>(E->L);
     eng_dir_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
-    if (tc) {
+    if (tc && bf16) {
         eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
         eng_fwd_tc_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
     }
@@ -907,6 +942,7 @@ int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e != cudaSuccess) { delete E; return MBIR_ERR_CUDA; }
     *out = E;
@@ -1012,7 +1048,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;
     const bool bf16 = E->sel[0]->g->P.precision == MBIR_PREC_BF16;
-    bool tc = bf16;                      // tensor-core pools when every request of the step has them
+    bool tc = true;                      // tensor-core pools when every request of the step has them
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
     for (Request* r : E->sel)

@@ -318,6 +318,21 @@ struct TcLayout {
     bool ok;
 };
 
+// Layout of the FP32 tensor-core adjoint: the residual and the table are each
+// split into three BF16 parts; table rows are taken in two phase-aligned
+// halves (phases [0, phsplit] and [phsplit, Q]) so one half's operands and
+// correlation tile fit shared memory at a time.
+struct Tc3Layout {
+    int kpad;              // taps rounded up to 16
+    int phsplit;           // phase where the halves meet (shared by both)
+    int nrows[2];          // table rows of each half (multiples of 16)
+    int nmax;              // larger of the two
+    int cstride;           // row stride of the shared correlation tile (floats)
+    size_t bhalf[2];       // bytes of each half's three-part operand image
+    size_t off_h, off_b, off_e, off_c, smem;
+    bool ok;
+};
+
 // Shared-memory and tensor-memory layout of the tensor-core A x (BF16 form).
 struct TfLayout {
     int ncols;             // table rows G (Q + 1)
@@ -400,6 +415,8 @@ struct mbir_geometry {
     uint32_t* d_tc_dest;   // record's place in pixel-major order (A-scan order within a pixel)
     float* w_tc_contrib;   // one contribution per record, pixel-major
     int* d_tc_counter;
+    Tc3Layout tc3;
+    uint4* d_tc3_bop;      // FP32 adjoint: both halves' three-part table operand images
     // tensor-core A x of the BF16 form (see tc_forward.cu)
     TfLayout tf;
     uint4* d_tf_bop;       // table operand image (taps x table rows, K-major)
@@ -443,8 +460,10 @@ cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_p
                                         float* b, float* partial, cudaStream_t st);
 size_t forward_smem(const mbir_geometry* g, int* cb_out);
 TcLayout tc_layout(const GeomParams& P);
+Tc3Layout tc3_layout(const GeomParams& P);
 cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e_bf, float* b, cudaStream_t st);
+cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, float* b, cudaStream_t st);
 TfLayout tf_layout(const GeomParams& P);
 cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,

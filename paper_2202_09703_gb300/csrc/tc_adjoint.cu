@@ -41,6 +41,37 @@ TcLayout tc_layout(const GeomParams& P)
     return L;
 }
 
+Tc3Layout tc3_layout(const GeomParams& P)
+{
+    Tc3Layout L{};
+    const int R = P.Q + 1;
+    L.kpad = (P.Tw + 15) & ~15;
+    L.phsplit = R / 2;
+    L.nrows[0] = (((L.phsplit + 1) * P.G) + 15) & ~15;
+    L.nrows[1] = (((R - L.phsplit) * P.G) + 15) & ~15;
+    L.nmax = std::max(L.nrows[0], L.nrows[1]);
+    L.cstride = L.nmax + 1;
+    L.bhalf[0] = (size_t)3 * L.nrows[0] * L.kpad * 2;
+    L.bhalf[1] = (size_t)3 * L.nrows[1] * L.kpad * 2;
+    L.off_h = 1024;
+    L.off_b = L.off_h + (size_t)3 * kTcTile * L.kpad * 2;
+    L.off_e = (L.off_b + std::max(L.bhalf[0], L.bhalf[1]) + 127) & ~(size_t)127;
+    L.off_c = (L.off_e + (size_t)(kTcTile + L.kpad + 16) * 4 + 127) & ~(size_t)127;
+    L.smem = L.off_c + (size_t)kTcTile * L.cstride * 4;
+    L.ok = R >= 2 && L.nmax <= 256 && L.smem <= 227 * 1024 && P.K <= 65535 && kTcTile + L.kpad <= kTcThreads;
+    return L;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) bwd_tc32_kernel(Tc3View V, int* __restrict__ status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, 256);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    uint32_t phase = 0, bphase = 0;
+    tc_adjoint32_pool(V, smem, tmem, phase, bphase, status);
+    tc_header_release(smem, tmem, 256);
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) bwd_tc_kernel(TcAdjView V, int* __restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -115,21 +146,48 @@ __global__ void tc_tile_off_kernel(GeomParams P, int ntile, const long long* __r
 cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
 {
     const GeomParams& P = g->P;
-    if (P.precision != MBIR_PREC_BF16 || !g->d_rec_key || g->n_records <= 0 || g->n_records >= (1LL << 32))
-        return cudaErrorNotSupported;
+    if (!g->d_rec_key || g->n_records <= 0 || g->n_records >= (1LL << 32)) return cudaErrorNotSupported;
+    const bool bf = P.precision == MBIR_PREC_BF16;
     const TcLayout L = tc_layout(P);
-    if (!L.ok) return cudaErrorNotSupported;
+    const Tc3Layout L3 = tc3_layout(P);
+    if (bf ? !L.ok : !L3.ok) return cudaErrorNotSupported;
     const int N = P.W * P.H;
     const int ntile = (P.M + kTcTile - 1) / kTcTile;
     const int R = P.Q + 1, nq = P.Q * P.Tw + 1;
-    // table operand: row c = phase * G + plane, column m = tap, BF16 as in the stored table
-    std::vector<__nv_bfloat16> bimg((size_t)L.npad * L.kpad, __float2bfloat16_rn(0.0f));
-    for (int c = 0; c < L.ncols; ++c) {
-        const int gpl = c % P.G, ph = c / P.G;
-        for (int m = 0; m < P.Tw; ++m)
-            bimg[kmajor_offset(c, m, L.kpad) / 2] = __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
+    std::vector<__nv_bfloat16> bimg;
+    if (bf) {
+        // table operand: row c = phase * G + plane, column m = tap, BF16 as in the stored table
+        bimg.assign((size_t)L.npad * L.kpad, __float2bfloat16_rn(0.0f));
+        for (int c = 0; c < L.ncols; ++c) {
+            const int gpl = c % P.G, ph = c / P.G;
+            for (int m = 0; m < P.Tw; ++m)
+                bimg[kmajor_offset(c, m, L.kpad) / 2] =
+                    __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
+        }
+    } else {
+        // FP32 form: per row half, the FP32 table (as the CUDA-core kernels read it) split into
+        // three BF16 parts t = t1 + t2 + t3; half h holds phases [h ? phsplit : 0, h ? Q : phsplit]
+        bimg.assign((L3.bhalf[0] + L3.bhalf[1]) / 2, __float2bfloat16_rn(0.0f));
+        size_t base = 0;
+        for (int h = 0; h < 2; ++h) {
+            const int phb = h ? L3.phsplit : 0, phe = h ? R - 1 : L3.phsplit;
+            const size_t part = (size_t)L3.nrows[h] * L3.kpad;
+            for (int ph = phb; ph <= phe; ++ph)
+                for (int gpl = 0; gpl < P.G; ++gpl)
+                    for (int m = 0; m < P.Tw; ++m) {
+                        const float t = (float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph];
+                        const __nv_bfloat16 p1 = __float2bfloat16_rn(t);
+                        const float r1 = t - __bfloat162float(p1);
+                        const __nv_bfloat16 p2 = __float2bfloat16_rn(r1);
+                        const __nv_bfloat16 p3 = __float2bfloat16_rn(r1 - __bfloat162float(p2));
+                        const size_t o = kmajor_offset((ph - phb) * P.G + gpl, m, L3.kpad) / 2;
+                        bimg[base + o] = p1;
+                        bimg[base + part + o] = p2;
+                        bimg[base + 2 * part + o] = p3;
+                    }
+            base += 3 * part;
+        }
     }
-    (void)R;
     int* d_cnt = nullptr;
     int* d_tile = nullptr;
     long long* d_poff = nullptr;
@@ -182,8 +240,13 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
-    g->tc = L;
-    g->d_tc_bop = d_b;
+    if (bf) {
+        g->tc = L;
+        g->d_tc_bop = d_b;
+    } else {
+        g->tc3 = L3;
+        g->d_tc3_bop = d_b;
+    }
     g->d_tc_tile = d_tile;
     g->d_tc_pixoff = d_poff;
     g->d_tc_dest = d_dest;
@@ -205,6 +268,26 @@ cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e
     TcAdjView V{P, L, g->d_tc_bop, g->d_tab_bf16, e_bf, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_tile,
                  g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
     bwd_tc_kernel<<<grid, kTcThreads, L.smem, st>>>(V, g->d_status);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return ce;
+    const int N = P.W * P.H;
+    bwd_tc_reduce_kernel<<<std::max(1, std::min((N + 7) / 8, 152 * 16)), 256, 0, st>>>(N, g->d_tc_pixoff,
+                                                                                     g->w_tc_contrib, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, float* b, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const Tc3Layout& L = g->tc3;
+    cudaError_t ce = cudaFuncSetAttribute(bwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tc_counter, 0, sizeof(int), st);
+    if (ce != cudaSuccess) return ce;
+    const int ntile = (P.M + kTcTile - 1) / kTcTile;
+    const int grid = std::max(1, std::min(g->n_sm, P.K * ntile));
+    Tc3View V{P, L, g->d_tc3_bop, g->d_tab, e_pad, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_tile,
+              g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
+    bwd_tc32_kernel<<<grid, kTcThreads, L.smem, st>>>(V, g->d_status);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
     const int N = P.W * P.H;

@@ -39,6 +39,22 @@ struct TcAdjView {
     int* counter;                    // item counter (zeroed before the launch)
 };
 
+// FP32 A^T of one geometry / request (three-part BF16 split, two row halves).
+struct Tc3View {
+    GeomParams P;
+    Tc3Layout T;
+    const uint4* bop;                // half 0 image then half 1 image (three parts each)
+    const float2* tab;               // FP32 kernel table (for the tau = t0 tap)
+    const float* e;                  // residual, K x Mp
+    const long long* rec_off;
+    const int2* rkey;
+    const float4* rw;
+    const int* tile_off;
+    const uint32_t* dest;
+    float* contrib;
+    int* counter;
+};
+
 // A x of one geometry / request.
 struct TcFwdView {
     GeomParams P;
@@ -64,6 +80,7 @@ __device__ __forceinline__ void tc_header_init(unsigned char* smem, uint32_t nco
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(bar), 1);
+        mbar_init(smem_u32(smem + 32), 1);          // operand copies of the FP32 adjoint
         *reinterpret_cast<volatile int*>(smem + 20) = 0;
         fence_mbar_init();
     }
@@ -252,6 +269,200 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
         __syncthreads();                             // sC / sE are rewritten by the next item
         it = it_next;
     }
+    return !*abort_flag;
+}
+
+// x = b1 + b2 + b3 with BF16 parts (exact for FP32 x away from underflow).
+__device__ __forceinline__ void split3(float x, unsigned short& a, unsigned short& b, unsigned short& c)
+{
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(p1);
+    const __nv_bfloat16 p2 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 p3 = __float2bfloat16_rn(r1 - __bfloat162float(p2));
+    a = __bfloat16_as_ushort(p1);
+    b = __bfloat16_as_ushort(p2);
+    c = __bfloat16_as_ushort(p3);
+}
+
+// Contributions of a batch's records whose phase falls in `half`, from that
+// half's correlation tile (columns (phase - first phase of the half) * G + plane).
+__device__ __forceinline__ void tc3_run_batch(const TcBatch& b, const GeomParams& P, const Tc3Layout& T, int half,
+                                              const float* sC, const float* sE, const float2* __restrict__ tab,
+                                              int ts, int rb, int r1, int tid, float* __restrict__ contrib)
+{
+    const int R = P.Q + 1, S = table_stride(P.Tw4);
+    const int phb = half ? T.phsplit : 0;
+#pragma unroll
+    for (int u = 0; u < kTcUnroll; ++u) {
+        const int r = rb + u * kTcThreads + tid;
+        if (r >= r1) continue;
+        const int n0 = b.key[u].y >> kRecShift, trow = (b.key[u].y >> 1) & 0xfff;
+        const int gi = trow / R, ph = trow - gi * R;
+        if ((ph >= T.phsplit) != (half == 1)) continue;
+        const int g1 = min(gi + 1, P.G - 1);
+        const float* cr = sC + (n0 - ts) * T.cstride + (ph - phb) * P.G;
+        float v = b.w[u].x * cr[gi];
+        v = fmaf(b.w[u].y, cr[g1], v);
+        v = fmaf(b.w[u].z, cr[P.G + gi], v);
+        v = fmaf(b.w[u].w, cr[P.G + g1], v);
+        if (b.key[u].y & 1) {
+            const float2 tl = __ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1);
+            v -= (b.w[u].z * tl.x + b.w[u].w * tl.y) * sE[n0 - ts + P.Tw - 1];
+        }
+        contrib[b.dst[u]] = v;
+    }
+}
+
+// Drains the FP32 A^T items (A-scan, 128-sample tile) of V.  Per item: the
+// residual window split into three BF16 Hankel tiles; for each row half, the
+// six products whose parts' orders sum to at most 4 (H_i T_j, i + j <= 4:
+// error below FP32 rounding) accumulate in tensor memory, the next half's
+// table operand is copied in (bulk copy) while this half's records are
+// processed.  smem + 32 holds the operand copy's mbarrier.
+__device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned char* smem, uint32_t tmem,
+                                                  uint32_t& phase, uint32_t& bphase, int* status)
+{
+    const GeomParams& P = V.P;
+    const Tc3Layout& T = V.T;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* bbar = reinterpret_cast<uint64_t*>(smem + 32);
+    volatile int* next = reinterpret_cast<volatile int*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    unsigned char* sH = smem + T.off_h;
+    unsigned char* sB = smem + T.off_b;
+    float* sE = reinterpret_cast<float*>(smem + T.off_e);
+    float* sC = reinterpret_cast<float*>(smem + T.off_c);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float* __restrict__ e = V.e;
+    const long long* __restrict__ rec_off = V.rec_off;
+    const int2* __restrict__ rkey = V.rkey;
+    const float4* __restrict__ rw = V.rw;
+    const int* __restrict__ tile_off = V.tile_off;
+    const uint32_t* __restrict__ dest = V.dest;
+    float* __restrict__ contrib = V.contrib;
+    int* counter = V.counter;
+    const unsigned char* bimg = reinterpret_cast<const unsigned char*>(V.bop);
+    const size_t hbytes = (size_t)kTcTile * T.kpad * 2;     // one part of the Hankel tile
+
+    auto copy_half = [&](int h) {               // tid 0: bulk copy of half h's operand image
+        mbar_arrive_expect_tx(smem_u32(bbar), (uint32_t)T.bhalf[h]);
+        bulk_g2s(smem_u32(sB), bimg + (h ? T.bhalf[0] : 0), (uint32_t)T.bhalf[h], smem_u32(bbar));
+    };
+    int copies = 1, waits = 0;                   // the same on every thread
+    if (tid == 0) {
+        copy_half(0);
+        *next = atomicAdd(counter, 1);
+    }
+    __syncthreads();
+    const int ntile = (P.M + kTcTile - 1) / kTcTile;
+    const int nitems = P.K * ntile;
+    const int W = kTcTile + T.kpad;
+    const uint32_t lbo = 128, sbo = (uint32_t)(T.kpad / 8) * 128;
+    const int kc = T.kpad / 8;
+    int it = *next;
+    float ew = 0.0f;
+    long long pbase = 0;
+    int pr0 = 0, pr1 = 0;
+    TcBatch pb;
+    auto prefetch = [&](int item) {
+        const int k = item / ntile, t = item - k * ntile;
+        const int n = t * kTcTile + 1 + tid;
+        ew = (tid < W && n < P.Mp) ? e[(size_t)k * P.Mp + n] : 0.0f;
+        pbase = __ldg(rec_off + k);
+        pr0 = __ldg(tile_off + (size_t)k * (ntile + 1) + t);
+        pr1 = __ldg(tile_off + (size_t)k * (ntile + 1) + t + 1);
+        tc_load_batch(pb, rkey, rw, dest, pbase, pr0, pr1, tid);
+    };
+    if (it < nitems) prefetch(it);
+    while (it < nitems) {
+        const int t = it % ntile, ts = t * kTcTile;
+        const long long base = pbase;
+        const int r0 = pr0, r1 = pr1;
+        if (tid < W) sE[tid] = ew;
+        __syncthreads();
+        if (tid == 0) *next = atomicAdd(counter, 1);
+        // three BF16 Hankel tiles H_i[n][m] = part i of e[ts + n + 1 + m]
+        for (int c = tid; c < kTcTile * kc; c += blockDim.x) {
+            const int n = c / kc, j = c - n * kc;
+            unsigned short a[8], b2[8], c3[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) split3(sE[n + 8 * j + q], a[q], b2[q], c3[q]);
+            const uint32_t off = kmajor_offset(n, 8 * j, T.kpad);
+            *reinterpret_cast<uint4*>(sH + off) =
+                make_uint4(a[0] | (uint32_t)a[1] << 16, a[2] | (uint32_t)a[3] << 16, a[4] | (uint32_t)a[5] << 16,
+                           a[6] | (uint32_t)a[7] << 16);
+            *reinterpret_cast<uint4*>(sH + hbytes + off) =
+                make_uint4(b2[0] | (uint32_t)b2[1] << 16, b2[2] | (uint32_t)b2[3] << 16,
+                           b2[4] | (uint32_t)b2[5] << 16, b2[6] | (uint32_t)b2[7] << 16);
+            *reinterpret_cast<uint4*>(sH + 2 * hbytes + off) =
+                make_uint4(c3[0] | (uint32_t)c3[1] << 16, c3[2] | (uint32_t)c3[3] << 16,
+                           c3[4] | (uint32_t)c3[5] << 16, c3[6] | (uint32_t)c3[7] << 16);
+        }
+        fence_async_smem();
+        __syncthreads();
+        const int it_next = *next;
+        for (int h = 0; h < 2; ++h) {
+            // this half's operand image has landed
+            if (!mbar_wait_bounded(smem_u32(bbar), bphase, status)) *abort_flag = 1;
+            bphase ^= 1u;
+            ++waits;
+            if (tid == 0 && !*abort_flag) {
+                tc_fence_after();
+                const int nr = T.nrows[h];
+                const uint32_t idesc = umma_idesc_bf16(kTcTile, nr);
+                const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB);
+                const uint32_t bpart = (uint32_t)((size_t)nr * T.kpad * 2);
+                const int terms[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+                for (int s = 0; s < T.kpad / 16; ++s)
+                    for (int q = 0; q < 6; ++q)
+                        umma_bf16(tmem, umma_desc(a0 + (uint32_t)(terms[q][0] * hbytes) + 256 * s, lbo, sbo),
+                                  umma_desc(b0 + terms[q][1] * bpart + 256 * s, lbo, sbo), idesc, s > 0 || q > 0);
+                umma_commit(smem_u32(bar));
+            }
+            __syncthreads();
+            if (*abort_flag) break;
+            if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
+            phase ^= 1u;
+            __syncthreads();                         // uniform flag; the operand buffer is free again
+            tc_fence_after();
+            if (*abort_flag) break;
+            // the other half next (or half 0 of the next item), copied during this half's records
+            if (h == 0 || it_next < nitems) {
+                if (tid == 0) copy_half(1 - h);
+                ++copies;
+            }
+            {
+                const int q = warp & 3, part = warp >> 2;
+                const int row = q * 32 + lane;
+                const int cw = T.nrows[h] / 4;
+                for (int c = part * cw; c < part * cw + cw; c += 4) {
+                    float v[4];
+                    tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sC[row * T.cstride + c + j] = v[j];
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            tc3_run_batch(pb, P, T, h, sC, sE, V.tab, ts, r0, r1, tid, contrib);
+            for (int rb = r0 + kTcUnroll * kTcThreads; rb < r1; rb += kTcUnroll * kTcThreads) {
+                TcBatch b;
+                tc_load_batch(b, rkey, rw, dest, base, rb, r1, tid);
+                tc3_run_batch(b, P, T, h, sC, sE, V.tab, ts, rb, r1, tid, contrib);
+            }
+            __syncthreads();                         // sC is rewritten by the next half
+        }
+        if (*abort_flag) break;
+        if (it_next < nitems) prefetch(it_next);
+        it = it_next;
+    }
+    // no operand copy may outlive the pool (bounded)
+    while (waits < copies) {
+        mbar_wait_bounded(smem_u32(bbar), bphase, status);
+        bphase ^= 1u;
+        ++waits;
+    }
+    __syncthreads();
     return !*abort_flag;
 }
 

@@ -181,6 +181,25 @@ def test_bf16_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn)
     assert np.array_equal(gpu_backproject(tc, r), b_tc)
 
 
+@pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene,
+                                      lambda: S.small_scene(n_layers=1, w=32, h=16, n_tx=2, n_rx=3, M=200)])
+def test_fp32_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn):
+    """FP32 form: A^T on the tensor cores with the residual and the table each
+    split into three BF16 parts (six products kept, error below FP32
+    rounding), against the CUDA-core adjoint and the FP64 oracle."""
+    s = scene_fn()
+    tc = make_geo(s, "tab")
+    cc = make_geo(s, "tab", tensor_cores=False)
+    assert tc.info.adjoint_tensor_cores == 1 and cc.info.adjoint_tensor_cores == 0
+    plan = O.Plan(s)
+    for seed in (51, 52):
+        r = S.random_vector(s.K * s.M, seed)
+        b_tc, b_cc = gpu_backproject(tc, r), gpu_backproject(cc, r)
+        assert rel_l2(b_tc, b_cc) <= 1e-6
+        assert rel_l2(b_tc, plan.backproject(r)) <= 1e-5
+    assert np.array_equal(gpu_backproject(tc, r), b_tc)
+
+
 @pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene])
 def test_bf16_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn):
     """BF16 form: A x on the tensor cores (per-(sample, table row) sums of
