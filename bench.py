@@ -341,7 +341,9 @@ def run_gpu(args):
     roofline = {"bound": "alu", "resource": "shared-memory load bandwidth (pulse-table corners per tap)",
                 "kernel": dom, "achieved": smem_bytes / (dom_ms * 1e-3) / 1e9, "peak": smem_peak,
                 "unit": "GB/s", "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak,
-                "traffic": measured_traffic("forward_sorted_kernel" if dom == "forward" else "backproject_kernel"),
+                "traffic": measured_traffic("forward_sorted_kernel" if dom == "forward" else
+                                            "bwd_tc32_kernel" if geo.info.adjoint_tensor_cores else
+                                            "backproject_kernel"),
                 "traffic_note": "DRAM read+write bytes per launch (ncu); the kernel streams from L2/shared memory",
                 "peak_source": f"{sm_count} SMs x {SMEM_BYTES_PER_CLK} B/clk x {clk_mhz:.0f} MHz "
                                f"(sm_max_mhz, {src})",
