@@ -11,7 +11,8 @@
  *   - direct arrivals (eq. 1) eliminated by projection;
  *   - the QGGMRF prior with spatially varying scale (eq. 14-17);
  *   - the MAP cost of eq. 18 minimised by a fixed majorize-minimize
- *     conjugate-gradient iteration.
+ *     conjugate-gradient iteration, or by coloured iterative coordinate
+ *     descent (the paper's ICD).
  * OpenMP pragmas only split independent loops across threads; they change no
  * arithmetic.
  */
@@ -725,5 +726,119 @@ int orc_reconstruct(orc_plan* p, const orc_prior* pr, const double* y, int n_ite
         orc_project(p, r, q, gk);
     }
     free(r); free(e); free(q); free(grad); free(gprev); free(gr); free(d);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Iterative coordinate descent                                        */
+/* ------------------------------------------------------------------ */
+void orc_column_norms(orc_plan* p, double* out, int nthreads)
+{
+    const orc_geom* g = &p->g;
+    int K = g->n_tx * g->n_rx;
+    ensure_all_positions(p, nthreads);
+    #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    for (long s = 0; s < p->npix; ++s) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double T, gm, w;
+            pair_from_legs(p, s, k, &T, &gm, &w);
+            if (w == 0.0) continue;
+            int n0, n1;
+            tap_range(p, T, &n0, &n1);
+            for (int n = n0; n <= n1; ++n) {
+                double a = w * orc_plan_H(p, gm, n / g->fs - T);   /* entry (k, n) of column s */
+                acc += a * a;
+            }
+        }
+        out[s] = acc;
+    }
+}
+
+int orc_icd(orc_plan* p, const orc_prior* pr, const double* y, int n_sweeps, int spacing,
+            double* x, int x_given, double* gk, double* cost, int nthreads)
+{
+    /* ICD on the cost of eq. 18 with g eliminated (e = P (y - A x)).  For pixel
+     * v the data term along x_v is the quadratic theta1 u + theta2 u^2 / 2 with
+     * theta1 = -(A^T e)_v / sigma^2 and theta2 = |A_v|^2 / sigma^2 (the column
+     * before the projection: an upper bound of the projected curvature), and
+     * each clique {v, r} is replaced by its symmetric quadratic bound with
+     * curvature b kappa(x_v - x_r).  The 1-D minimiser of that surrogate is
+     *     dx_v = -(theta1 + sum_r b rho'(x_v - x_r)) / (theta2 + sum_r b kappa).
+     * Pixels of one colour share no clique; the group moves along dx by the
+     * step alpha that minimises the exact data term plus the prior bound on
+     * that line (alpha = 1 for a group of one pixel). */
+    const orc_geom* g = &p->g;
+    int W = g->img_w, H = g->img_h;
+    long N = (long)W * H;
+    int K = g->n_tx * g->n_rx, M = g->n_samples;
+    long KM = (long)K * M;
+    if (p->npix != N) return -1;
+    if (spacing < 2) return -2;
+    double s2 = pr->sigma_noise * pr->sigma_noise;
+    double* cn = (double*)malloc(sizeof(double) * N);
+    double* b = (double*)malloc(sizeof(double) * N);
+    double* dx = (double*)calloc(N, sizeof(double));
+    double* r = (double*)malloc(sizeof(double) * KM);
+    double* e = (double*)malloc(sizeof(double) * KM);
+    double* q = (double*)malloc(sizeof(double) * KM);
+    orc_column_norms(p, cn, nthreads);
+    if (!x_given) for (long v = 0; v < N; ++v) x[v] = 0.0;
+    orc_forward(p, x, r, 0, K, nthreads);
+    for (long a = 0; a < KM; ++a) r[a] = y[a] - r[a];
+    orc_project(p, r, e, NULL);
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        for (int colour = 0; colour < spacing * spacing; ++colour) {
+            int cr = colour / spacing, cc = colour % spacing;
+            if (cr >= H || cc >= W) continue;
+            orc_backproject(p, e, b, nthreads);                  /* A^T e */
+            double gd = 0.0, curv = 0.0;
+            for (int rr = cr; rr < H; rr += spacing)
+                for (int c = cc; c < W; c += spacing) {
+                    long v = (long)rr * W + c;
+                    double gR = 0.0, D = 0.0;
+                    for (int dr = -1; dr <= 1; ++dr)
+                        for (int dc = -1; dc <= 1; ++dc) {
+                            if (dr == 0 && dc == 0) continue;
+                            int r2 = rr + dr, c2 = c + dc;
+                            if (r2 < 0 || r2 >= H || c2 < 0 || c2 >= W) continue;
+                            double sg = pr->sigma0 * sqrt(row_weight(g, pr, rr) * row_weight(g, pr, r2));
+                            double wgt = nb_weight(dr == 0 || dc == 0 ? 0 : 1);
+                            double delta = x[v] - x[(long)r2 * W + c2];
+                            gR += wgt * orc_drho(pr, delta, sg);
+                            D += wgt * orc_kappa(pr, delta, sg);
+                        }
+                    double grad = -b[v] / s2 + gR;
+                    double den = cn[v] / s2 + D;
+                    dx[v] = den > 0.0 ? -grad / den : 0.0;
+                    gd += grad * dx[v];
+                    curv += D * dx[v] * dx[v];
+                }
+            orc_forward(p, dx, r, 0, K, nthreads);               /* A dx */
+            orc_project(p, r, q, NULL);
+            double qq = 0.0;
+            for (long a = 0; a < KM; ++a) qq += q[a] * q[a];
+            double den = qq / s2 + curv;
+            double alpha = den > 0.0 ? -gd / den : 0.0;
+            for (int rr = cr; rr < H; rr += spacing)
+                for (int c = cc; c < W; c += spacing) {
+                    long v = (long)rr * W + c;
+                    x[v] += alpha * dx[v];
+                    dx[v] = 0.0;
+                }
+            for (long a = 0; a < KM; ++a) e[a] -= alpha * q[a];
+        }
+        if (cost) {
+            double ee = 0.0;
+            for (long a = 0; a < KM; ++a) ee += e[a] * e[a];
+            cost[sw] = ee / (2.0 * s2) + orc_prior_cost(g, pr, x);
+        }
+    }
+    if (gk) {
+        orc_forward(p, x, r, 0, K, nthreads);
+        for (long a = 0; a < KM; ++a) r[a] = y[a] - r[a];
+        orc_project(p, r, q, gk);
+    }
+    free(cn); free(b); free(dx); free(r); free(e); free(q);
     return 0;
 }

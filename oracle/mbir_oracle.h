@@ -91,6 +91,18 @@ int orc_reconstruct(orc_plan* p, const orc_prior* pr, const double* y, int n_ite
                     double* x, int x_given, double* gk, double* cost, double* gnorm,
                     int nthreads);
 
+/* ||A_v||^2 per plan pixel: the sum over A-scans and taps of (w H)^2 */
+void orc_column_norms(orc_plan* p, double* out, int nthreads);
+
+/* MAP estimate of eq. 18 by coloured iterative coordinate descent (the
+ * paper's optimiser, Section 2 "Optimization"): pixels (r, c) are grouped by
+ * (r mod spacing, c mod spacing); each group takes every member's 1-D ICD
+ * update at once, scaled by one majorize-minimize step.  A group of one pixel
+ * is the sequential ICD update exactly.  cost[sweep] after every sweep.
+ * Returns -1 unless the plan covers every pixel, -2 for spacing < 2. */
+int orc_icd(orc_plan* p, const orc_prior* pr, const double* y, int n_sweeps, int spacing,
+            double* x, int x_given, double* gk, double* cost, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,8 @@ def lib():
                 "orc_kappa": (C.c_double, [P, C.c_double, C.c_double]),
                 "orc_reconstruct": (C.c_int, [C.c_void_p, P, _D, C.c_int, _D, C.c_int,
                                               _D, _D, _D, C.c_int]),
+                "orc_column_norms": (None, [C.c_void_p, _D, C.c_int]),
+                "orc_icd": (C.c_int, [C.c_void_p, P, _D, C.c_int, C.c_int, _D, C.c_int, _D, _D, C.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -261,6 +263,27 @@ class Plan:
         if rc != 0:
             raise RuntimeError("oracle reconstruct needs a plan over every pixel")
         return x.reshape(s.img_h, s.img_w), gk, cost[:n_iter], gn[:n_iter]
+
+
+    def column_norms(self) -> np.ndarray:
+        """|A_v|^2 for every plan pixel."""
+        out = np.zeros(self.npix)
+        lib().orc_column_norms(self.h, _ptr(out), self.nthreads)
+        return out
+
+    def icd(self, y, sigma_noise: float, n_sweeps: int, spacing: int, x0=None):
+        """Coloured ICD (spacing >= image side: sequential ICD in raster order)."""
+        s = self.scene
+        pr = make_prior(s, sigma_noise)
+        y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1)
+        x = np.zeros(s.N) if x0 is None else np.array(x0, dtype=np.float64).reshape(-1)
+        gk = np.zeros(s.K)
+        cost = np.zeros(max(n_sweeps, 1))
+        rc = lib().orc_icd(self.h, C.byref(pr), _ptr(y), n_sweeps, spacing, _ptr(x),
+                           int(x0 is not None), _ptr(gk), _ptr(cost), self.nthreads)
+        if rc != 0:
+            raise RuntimeError("oracle ICD needs a plan over every pixel and spacing >= 2")
+        return x.reshape(s.img_h, s.img_w), gk, cost[:n_sweeps]
 
 
 # prior helpers ------------------------------------------------------------

@@ -482,3 +482,81 @@ def test_gradient_vanishes_at_convergence():
     p, _, y, sig = _noisy_data(s, seed=2)
     x, gk, cost, gn = p.reconstruct(y, sig, 4000)
     assert gn[-1] / gn[0] < 1e-9
+
+
+# --------------------------------------------------------------------------
+# iterative coordinate descent (Section 2 "Optimization": the paper's ICD)
+# --------------------------------------------------------------------------
+def test_icd_column_norms_match_dense_columns():
+    s = S.small_scene(n_layers=2, w=5, h=4, n_tx=3, n_rx=2, M=128, direct=False)
+    p = O.Plan(s, nthreads=2)
+    A = p.dense_A()                     # every sample of every column, no tap window
+    np.testing.assert_allclose(p.column_norms(), (A ** 2).sum(axis=0), rtol=1e-12, atol=0)
+
+
+def test_icd_single_pixel_lands_on_the_least_squares_gain():
+    # one pixel, no clique: one ICD update (with its step along the update) is the least-squares
+    # fit of the projected column to the projected data, whatever curvature scaled the update
+    s = S.small_scene(n_layers=2, w=1, h=1, n_tx=3, n_rx=2, M=128, direct=True).copy(z0=1.5e-3)
+    p = O.Plan(s, nthreads=2)
+    a = p.dense_A()[:, 0]
+    y = 0.7 * a + 0.05 * np.max(np.abs(a)) * S.unit_noise(s, 3).reshape(-1)
+    Pa = p.project(a)[0].reshape(-1)
+    Py = p.project(y)[0].reshape(-1)
+    x_ls = (Pa @ Py) / (Pa @ Pa)
+    x, _, cost = p.icd(y, 0.1, 1, 2)
+    assert x[0, 0] == pytest.approx(x_ls, rel=1e-12)
+    assert cost[0] == pytest.approx(np.sum((Py - x_ls * Pa) ** 2) / (2 * 0.01), rel=1e-12)
+
+
+def test_icd_update_minimises_the_surrogate_by_brute_force():
+    # sequential ICD (one pixel per colour) from a non-flat start: each update is the minimiser of
+    # the exact data term along that pixel plus, for every clique, the symmetric quadratic bound
+    # of the potential taken at the start of the update; found here by a bounded 1-D search
+    from scipy.optimize import minimize_scalar
+    s = S.small_scene(n_layers=2, w=2, h=1, n_tx=3, n_rx=2, M=128, direct=True).copy(
+        z0=1.5e-3, prior=S.Prior(m=0.5))
+    p, _, y, sig = _noisy_data(s, seed=5)
+    x0 = np.array([0.3, -0.2])
+    be = 1.0 / (4.0 + 4.0 / math.sqrt(2.0))           # edge clique weight (8-neighbourhood, sum 1)
+    zc = s.z0 + 0.5 * s.pitch
+    sg = s.prior.sigma0 * (1.0 + (s.prior.m - 1.0) * (zc / zc) ** s.prior.a)   # sigma0 sqrt(m_s m_r), one row
+    x = x0.copy()
+    for v in (0, 1):
+        r = 1 - v
+        d0 = x[v] - x[r]
+        kap = O.kappa(s, d0, sg)
+
+        def f(u):
+            xv = x.copy()
+            xv[v] += u
+            e, _ = p.project(y - p.forward(xv))
+            return np.sum(e ** 2) / (2 * sig ** 2) + be * kap / 2 * (d0 + u) ** 2
+
+        res = minimize_scalar(f, bounds=(-5.0, 5.0), method="bounded", options={"xatol": 1e-12})
+        x[v] += res.x
+    xi, _, _ = p.icd(y, sig, 1, 2, x0=x0)
+    np.testing.assert_allclose(xi.reshape(-1), x, rtol=1e-7, atol=1e-9)
+
+
+@pytest.mark.parametrize("spacing", [2, 3])
+def test_icd_reaches_the_map_minimiser(spacing):
+    # pixels 3 mm apart (longer than the pulse) have nearly orthogonal columns: ICD converges in a
+    # few dozen sweeps to the unique minimiser of eq. 18 that the conjugate-gradient iteration finds
+    s = S.small_scene(n_layers=2, w=3, h=3, n_tx=4, n_rx=3, M=256, direct=True)
+    s = s.copy(pitch=3e-3, tx_x=S.centred_positions(4, 2e-3, 4.5e-3))
+    p, _, y, sig = _noisy_data(s, seed=1)
+    xc, _, cc, gn = p.reconstruct(y, sig, 400)
+    assert gn[-1] < 1e-10 * gn[0]
+    xi, _, ci = p.icd(y, sig, 200, spacing)
+    assert np.linalg.norm(xi - xc) <= 1e-9 * np.linalg.norm(xc)
+    assert ci[-1] == pytest.approx(cc[-1], rel=1e-12)
+
+
+@pytest.mark.parametrize("spacing", [2, 4, 16])
+def test_icd_cost_is_non_increasing(spacing):
+    s = _tiny(direct=True, layers=3).copy(prior=S.Prior(m=0.2))
+    p, _, y, sig = _noisy_data(s)
+    x, gk, cost = p.icd(y, sig, 8, spacing)
+    assert np.all(np.diff(cost) <= 1e-12 * abs(cost[0]))
+    assert cost[-1] < cost[0]
