@@ -259,6 +259,33 @@ int mbir_reconstruct(const mbir_geometry* g, const void* y_dev, const mbir_prior
                      int n_iter, float* x_dev, int x_given, float* g_dev, mbir_stats* st,
                      void* stream);
 
+/* MAP estimate of eq. 18 by coloured iterative coordinate descent (Section 2
+ * "Optimization": the paper optimises with ICD).  Pixels (r, c) are grouped
+ * by colour (r mod spacing, c mod spacing); spacing >= 2 keeps the two ends
+ * of every 8-neighbour clique in different colours.  For a colour, every
+ * member v takes its 1-D ICD update
+ *     dx_v = -(theta1 + sum_r b rho'(x_v - x_r)) / (theta2 + sum_r b kappa),
+ * theta1 = -(A^T e)_v / sigma^2, theta2 = |A_v|^2 / sigma^2 (e the projected
+ * residual; kappa = rho'/delta, the symmetric quadratic bound of each clique),
+ * and the colour moves along dx by the step alpha that minimises the exact
+ * data term plus the bound on that line; for a colour of one pixel
+ * (spacing >= both image sides) alpha = 1 and this is sequential ICD in
+ * raster order.  A sweep visits the spacing^2 colours in order (empty ones
+ * skipped), each with one A^T, one A and the projection.
+ * Arguments as mbir_reconstruct, with n_sweeps in place of n_iter;
+ * st->cost receives the cost after each sweep and the gradient norms are 0.
+ * The column norms are computed on the first call and kept by g (N floats).
+ * Synchronises `stream`.  Errors: as mbir_reconstruct, and
+ * MBIR_ERR_INVALID_ARG for spacing outside 2..65536. */
+int mbir_reconstruct_icd(const mbir_geometry* g, const void* y_dev, const mbir_prior* pr,
+                         int n_sweeps, int spacing, float* x_dev, int x_given, float* g_dev,
+                         mbir_stats* st, void* stream);
+
+/* |A_v|^2 per pixel (the coordinate descent's data curvature times sigma^2):
+ * the sum over A-scans and taps inside the record of (w H)^2 with the FP32
+ * pulse table.  out_dev: N floats.  Asynchronous on `stream`. */
+int mbir_column_norms(const mbir_geometry* g, float* out_dev, void* stream);
+
 /* mbir_reconstruct on host buffers: copies y_host (K x M float) in, runs, and
  * copies x_host (N floats) and g_host (K floats, may be NULL) out, all on
  * `stream`.  Synchronises the stream. */

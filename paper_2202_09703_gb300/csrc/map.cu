@@ -237,6 +237,75 @@ __global__ void finalize_cost_kernel(const double* __restrict__ part, int nb, in
     }
 }
 
+// One colour of the coordinate descent (pixels r = cr, c = cc mod s; no two share a clique):
+//   grad_v = -b_v / sigma^2 + sum_r b rho'(x_v - x_r),  D_v = sum_r b kappa(x_v - x_r),
+//   dx_v = -grad_v / (|A_v|^2 / sigma^2 + D_v)   (the 1-D minimiser of the ICD surrogate),
+// dx = 0 off the colour; FP64 partials of <grad, dx> and of sum b kappa (dx_s - dx_r)^2, which is
+// sum_v D_v dx_v^2 since every clique touching the colour has its other end off it.
+__global__ void icd_dir_kernel(GeomParams P, PriorParams pr, const float* __restrict__ x,
+                               const float* __restrict__ b, const float* __restrict__ msq,
+                               const float* __restrict__ colnorm, int s, int cr, int cc, float* __restrict__ dx,
+                               double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    const int N = P.W * P.H;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double a0 = 0, a1 = 0;
+    if (v < N) {
+        const int r = v / P.W, c = v - r * P.W;
+        float d = 0.0f;
+        if (r % s == cr && c % s == cc) {
+            const float xs = x[v], ms = msq[r];
+            float gr = 0.0f, D = 0.0f;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int r2 = r + c_nb_dr[t], c2 = c + c_nb_dc[t];
+                if (r2 < 0 || r2 >= P.H || c2 < 0 || c2 >= P.W) continue;
+                float dr, kap;
+                qggmrf(pr, xs - x[r2 * P.W + c2], pr.sigma0 * ms * msq[r2], &dr, &kap, nullptr);
+                const float wgt = nb_weight(c_nb_dr[t], c_nb_dc[t]);
+                gr += wgt * dr;
+                D += wgt * kap;
+            }
+            const float g = -b[v] * pr.inv_s2 + gr;
+            const float den = colnorm[v] * pr.inv_s2 + D;
+            d = den > 0.0f ? -g / den : 0.0f;
+            a0 = (double)g * d;
+            a1 = (double)D * d * d;
+        }
+        dx[v] = d;
+    }
+    double s0 = block_sum(a0, sh);
+    double s1 = block_sum(a1, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x + 0] = s0;
+        part[2 * blockIdx.x + 1] = s1;
+    }
+}
+
+// step of one colour: alpha = -<grad, dx> / (|q|^2 / sigma^2 + sum b kappa (dx_s - dx_r)^2)
+__global__ void icd_step_kernel(const double* __restrict__ part, int nb, const double* __restrict__ qpart, int nq,
+                                float inv_s2, double* __restrict__ sc)
+{
+    __shared__ double sh[32];
+    double a = 0, c = 0, q = 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        a += part[2 * t];
+        c += part[2 * t + 1];
+    }
+    for (int t = threadIdx.x; t < nq; t += blockDim.x) q += qpart[t];
+    double gd = block_sum(a, sh), cv = block_sum(c, sh), qq = block_sum(q, sh);
+    if (threadIdx.x == 0) {
+        double den = qq * (double)inv_s2 + cv;
+        double alpha = den > 0.0 ? -gd / den : 0.0;
+        if (!isfinite(alpha)) { alpha = 0.0; sc[S_BAD] = 1.0; }
+        sc[S_GD] = gd;
+        sc[S_QQ] = qq;
+        sc[S_CURV] = cv;
+        sc[S_ALPHA] = alpha;
+    }
+}
+
 __global__ void add_direct_kernel(GeomParams P, const float* __restrict__ gk, const float* __restrict__ direct,
                                   float* __restrict__ y)
 {
@@ -495,6 +564,118 @@ int reconstruct_core(mbir_geometry* g, const void* y_dev, int y_bf16, const mbir
     return MBIR_OK;
 }
 
+// Coloured iterative coordinate descent on eq. 18 (the paper's optimiser).  Per colour
+// (spacing^2 colours per sweep, empty ones skipped): b = A^T e, the per-pixel ICD updates dx of the
+// colour, q = P A dx, the majorize-minimize step alpha along dx, x += alpha dx, e -= alpha q.
+int icd_core(mbir_geometry* g, const void* y_dev, int y_bf16, const mbir_prior* pr, int n_sweeps, int spacing,
+             float* x, int x_given, float* g_dev, mbir_stats* st_out, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const int N = P.W * P.H;
+    const long long KMp = (long long)P.K * P.Mp;
+    const int nbpix = (N + kRedThreads - 1) / kRedThreads;
+    const bool want_cost = st_out && st_out->cost && st_out->cost_len > 0;
+    int rc = ensure_workspace(g, std::max(n_sweeps, 1));
+    if (rc != MBIR_OK) return rc;
+    if (!g->w_colnorm) {
+        CK(cudaMalloc((void**)&g->w_colnorm, sizeof(float) * N));
+        g->bytes += sizeof(float) * N;
+        cudaError_t e = launch_column_norms(g, g->w_colnorm, st);
+        if (e != cudaSuccess) {
+            cudaFree(g->w_colnorm);
+            g->w_colnorm = nullptr;
+            g->bytes -= sizeof(float) * N;
+            return cerr_code(e);
+        }
+    }
+    PriorParams pp = prior_params(pr);
+    CK(upload_msq(g, pr, st));
+    double* sc = g->w_scal;
+    double* part = g->w_part;
+    double* part2 = g->w_part + g->part_len;
+    const int use_direct = 1;
+    CK(cudaMemsetAsync(sc, 0, sizeof(double) * S_COUNT, st));
+    CK(cudaMemsetAsync(g->w_hist, 0, sizeof(double) * 2 * g->hist_len, st));
+    if (!x_given) CK(cudaMemsetAsync(x, 0, sizeof(float) * N, st));
+    __nv_bfloat16* ebf = P.precision == MBIR_PREC_BF16 ? g->w_ebf : nullptr;
+
+    // e = P (y - A x)
+    if (x_given) {
+        CK(launch_forward(g, x, g->w_q, nullptr, P.Mp, st));
+        project_kernel<<<P.K, kRedThreads, 0, st>>>(P, y_dev, y_bf16, P.M, g->w_q, P.Mp, g->d_direct, g->d_dinv,
+                                                    use_direct, g->w_e, P.Mp, nullptr, part);
+    } else {
+        project_kernel<<<P.K, kRedThreads, 0, st>>>(P, y_dev, y_bf16, P.M, nullptr, 0, g->d_direct, g->d_dinv,
+                                                    use_direct, g->w_e, P.Mp, nullptr, part);
+    }
+    CK(cudaGetLastError());
+    residual_sum_kernel<<<1, kRedThreads, 0, st>>>(part, P.K, sc);
+    if (ebf) to_bf16_kernel<<<1024, 256, 0, st>>>(g->w_e, ebf, KMp);
+    CK(cudaGetLastError());
+    double bad = 0;
+    CK(cudaMemcpyAsync(&bad, sc + S_BAD, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (bad != 0.0) return MBIR_ERR_NONFINITE;
+
+    float* dx = g->w_d;
+    const int ublocks = (int)std::min<long long>((N + KMp + 255) / 256, 152LL * 32);
+    const int cblocks = 152 * 4;
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        for (int colour = 0; colour < spacing * spacing; ++colour) {
+            const int cr = colour / spacing, cc = colour % spacing;
+            if (cr >= P.H || cc >= P.W) continue;
+            prof_begin(g, 1, st);
+            CK(launch_backproject(g, g->w_e, ebf, g->w_b, st));
+            prof_end(g, st);
+            icd_dir_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, x, g->w_b, g->w_msq, g->w_colnorm, spacing, cr, cc,
+                                                          dx, part);
+            CK(cudaGetLastError());
+            prof_begin(g, 0, st);
+            CK(launch_forward(g, dx, g->w_q, nullptr, P.Mp, st));
+            prof_end(g, st);
+            project_kernel<<<P.K, kRedThreads, 0, st>>>(P, g->w_q, 0, P.Mp, nullptr, 0, g->d_direct, g->d_dinv,
+                                                        use_direct, g->w_q, P.Mp, nullptr, part2);
+            icd_step_kernel<<<1, kRedThreads, 0, st>>>(part, nbpix, part2, P.K, pp.inv_s2, sc);
+            update_kernel<<<ublocks, 256, 0, st>>>(N, KMp, sc, x, dx, g->w_e, g->w_q, ebf);
+            CK(cudaGetLastError());
+        }
+        if (want_cost) {
+            cost_part_kernel<<<cblocks, kRedThreads, 0, st>>>(P, pp, x, g->w_msq, g->w_e, KMp, part);
+            finalize_cost_kernel<<<1, kRedThreads, 0, st>>>(part, cblocks, sw, sc, g->w_hist);
+            CK(cudaGetLastError());
+        }
+    }
+    if (g_dev) {
+        CK(launch_forward(g, x, g->w_q, nullptr, P.Mp, st));
+        project_kernel<<<P.K, kRedThreads, 0, st>>>(P, y_dev, y_bf16, P.M, g->w_q, P.Mp, g->d_direct, g->d_dinv,
+                                                    use_direct, g->w_q, P.Mp, g_dev, nullptr);
+        CK(cudaGetLastError());
+    }
+    std::vector<double> scal(S_COUNT);
+    CK(cudaMemcpyAsync(scal.data(), sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+    std::vector<double> hist(2 * (size_t)g->hist_len);
+    if (st_out && n_sweeps > 0)
+        CK(cudaMemcpyAsync(hist.data(), g->w_hist, sizeof(double) * 2 * g->hist_len, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    prof_collect(g);
+    int status = 0;
+    CK(cudaMemcpy(&status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        int zero = 0;
+        cudaMemcpy(g->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return MBIR_ERR_TIMEOUT;
+    }
+    if (st_out) {
+        st_out->iterations = n_sweeps;
+        st_out->grad_norm_first = 0.0;
+        st_out->grad_norm_last = 0.0;
+        if (want_cost)
+            for (int t = 0; t < std::min(n_sweeps, st_out->cost_len); ++t) st_out->cost[t] = hist[t];
+    }
+    if (scal[S_BAD] != 0.0) return MBIR_ERR_NONFINITE;
+    return MBIR_OK;
+}
+
 }  // namespace
 
 void mbir::prof_release(mbir_geometry* g)
@@ -597,6 +778,23 @@ int mbir_reconstruct(const mbir_geometry* gc, const void* y_dev, const mbir_prio
     mbir_geometry* g = const_cast<mbir_geometry*>(gc);
     return reconstruct_core(g, y_dev, g->P.precision == MBIR_PREC_BF16 ? 1 : 0, pr, n_iter, x_dev, x_given, g_dev,
                             st, (cudaStream_t)stream);
+}
+
+int mbir_reconstruct_icd(const mbir_geometry* gc, const void* y_dev, const mbir_prior* pr, int n_sweeps,
+                         int spacing, float* x_dev, int x_given, float* g_dev, mbir_stats* st, void* stream)
+{
+    if (!gc || !y_dev || !x_dev || n_sweeps < 0 || spacing < 2 || spacing > 65536 || !prior_ok(pr))
+        return MBIR_ERR_INVALID_ARG;
+    mbir_geometry* g = const_cast<mbir_geometry*>(gc);
+    return icd_core(g, y_dev, g->P.precision == MBIR_PREC_BF16 ? 1 : 0, pr, n_sweeps, spacing, x_dev, x_given, g_dev,
+                    st, (cudaStream_t)stream);
+}
+
+int mbir_column_norms(const mbir_geometry* g, float* out_dev, void* stream)
+{
+    if (!g || !out_dev) return MBIR_ERR_INVALID_ARG;
+    cudaError_t e = launch_column_norms(g, out_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? MBIR_OK : cerr_code(e);
 }
 
 int mbir_reconstruct_host(const mbir_geometry* gc, const float* y_host, const mbir_prior* pr, int n_iter,

@@ -425,6 +425,8 @@ struct mbir_geometry {
     int* d_tf_order;       // A-scans by decreasing record count
     int* d_tf_counter;
     long long n_records;
+    // |A_v|^2 per pixel for the coordinate descent (computed on its first call)
+    float* w_colnorm;
     // profiling of the apply kernels inside mbir_reconstruct
     int prof;
     void* prof_state;      // host-side event lists (see map.cu)
@@ -468,4 +470,5 @@ TfLayout tf_layout(const GeomParams& P);
 cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
                               cudaStream_t st);
+cudaError_t launch_column_norms(const mbir_geometry* g, float* out, cudaStream_t st);
 }  // namespace mbir

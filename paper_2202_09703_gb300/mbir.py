@@ -101,6 +101,8 @@ def lib(path: str | None = None):
         "mbir_prior_gradient": [_V, Pp, _V, _V, _V],
         "mbir_add_direct": [_V, _V, _V, _V],
         "mbir_reconstruct": [_V, _V, Pp, C.c_int, _V, C.c_int, _V, S, _V],
+        "mbir_reconstruct_icd": [_V, _V, Pp, C.c_int, C.c_int, _V, C.c_int, _V, S, _V],
+        "mbir_column_norms": [_V, _V, _V],
         "mbir_reconstruct_host": [_V, _V, Pp, C.c_int, _V, _V, S, _V],
         "mbir_pair_quantities": [_V, _V, _V, C.c_int, _V, _V, _V],
         "mbir_pulse_table": [_V, _V, C.c_size_t],
@@ -245,6 +247,25 @@ class Geometry:
                                           C.byref(st), _stream_ptr(stream)), "mbir_reconstruct")
         return {"cost": cost[:n_iter] if want_cost else None, "iterations": st.iterations,
                 "grad_norm_first": st.grad_norm_first, "grad_norm_last": st.grad_norm_last}
+
+    def reconstruct_icd(self, y, sigma_noise: float, n_sweeps: int, spacing: int, x, x_given: bool = False,
+                        g=None, want_cost: bool = False, stream=None):
+        """Coloured ICD (``mbir_reconstruct_icd``); spacing >= the image sides is sequential ICD."""
+        pr = prior_struct(self.scene, sigma_noise)
+        st = Stats()
+        cost = np.zeros(max(n_sweeps, 1))
+        if want_cost:
+            st.cost = cost.ctypes.data_as(C.POINTER(C.c_double))
+            st.cost_len = n_sweeps
+        _check(self._lib.mbir_reconstruct_icd(self.h, _ptr(y), C.byref(pr), n_sweeps, spacing, _ptr(x),
+                                              int(x_given), _ptr(g), C.byref(st), _stream_ptr(stream)),
+               "mbir_reconstruct_icd")
+        return {"cost": cost[:n_sweeps] if want_cost else None, "iterations": st.iterations}
+
+    def column_norms(self, out, stream=None):
+        """|A_v|^2 per pixel into the N-float device tensor ``out``."""
+        _check(self._lib.mbir_column_norms(self.h, _ptr(out), _stream_ptr(stream)), "mbir_column_norms")
+        return out
 
     def reconstruct_host(self, y_host, sigma_noise: float, n_iter: int, x_host, g_host=None, stream=None):
         """y_host, x_host, g_host: host tensors (pinned for asynchronous copies)."""
