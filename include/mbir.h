@@ -271,12 +271,14 @@ int mbir_reconstruct(const mbir_geometry* g, const void* y_dev, const mbir_prior
  * data term plus the bound on that line; for a colour of one pixel
  * (spacing >= both image sides) alpha = 1 and this is sequential ICD in
  * raster order.  A sweep visits the spacing^2 colours in order (empty ones
- * skipped), each with one A^T, one A and the projection.
+ * skipped), each with A^T on the colour's pixels only, A of its update and
+ * the projection; with TAB records and spacing <= 64 the A reads only the
+ * colour's records (a per-colour copy of the record list, built on the first
+ * call with that spacing and kept by g, as are the column norms, N floats).
  * Arguments as mbir_reconstruct, with n_sweeps in place of n_iter;
  * st->cost receives the cost after each sweep and the gradient norms are 0.
- * The column norms are computed on the first call and kept by g (N floats).
  * Synchronises `stream`.  Errors: as mbir_reconstruct, and
- * MBIR_ERR_INVALID_ARG for spacing outside 2..65536. */
+ * MBIR_ERR_INVALID_ARG for spacing outside 2..256. */
 int mbir_reconstruct_icd(const mbir_geometry* g, const void* y_dev, const mbir_prior* pr,
                          int n_sweeps, int spacing, float* x_dev, int x_given, float* g_dev,
                          mbir_stats* st, void* stream);

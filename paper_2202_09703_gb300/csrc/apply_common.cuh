@@ -176,7 +176,7 @@ __device__ __forceinline__ bool backproject_item(const GeomParams& P, const DevP
                                                  const typename ET<BF16>::type* __restrict__ e_g, const int4 item,
                                                  float* __restrict__ partial, typename ET<BF16>::type* ering,
                                                  uint32_t bar0, int nst, size_t ebytes, volatile int* abort_flag,
-                                                 uint32_t& par, int h, int hw, int lane, int ht)
+                                                 uint32_t& par, int h, int hw, int lane, int ht, int3 lat)
 {
     using Tab = typename TabT<BF16>::type;
     using E = typename ET<BF16>::type;
@@ -184,7 +184,8 @@ __device__ __forceinline__ bool backproject_item(const GeomParams& P, const DevP
     const int R = P.Q + 1;
     const uint32_t rowbytes = (uint32_t)((size_t)P.Mp * sizeof(E));
     const size_t estride = ebytes / sizeof(E);
-    const int row = item.x * kBwdTileRows + hw, col = item.y * 32 + lane;
+    // lat = (spacing, first row, first column) of the pixel lattice the tiles cover ((1, 0, 0): the image)
+    const int row = (item.x * kBwdTileRows + hw) * lat.x + lat.y, col = (item.y * 32 + lane) * lat.x + lat.z;
     const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
     const bool pix_ok = col < P.W && row < P.H;
     const RowInfo ri = load_row(D.rows, min(row, P.H - 1));

@@ -26,7 +26,7 @@ template <int NL, int MODE, bool BF16>
 __global__ void __launch_bounds__(kBwdThreads, 1)
     backproject_kernel(GeomParams P, DevPtrs D, const typename TabT<BF16>::type* __restrict__ tab_g,
                        const typename ET<BF16>::type* __restrict__ e_g, const int4* __restrict__ items,
-                       int nitems, int* __restrict__ counter, float* __restrict__ partial, int nst)
+                       int nitems, int* __restrict__ counter, float* __restrict__ partial, int nst, int3 lat)
 {
     using Tab = typename TabT<BF16>::type;
     using E = typename ET<BF16>::type;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
         worker_barrier(h);               // every thread has read the slot before it is reused
         if (it >= nitems) break;
         if (!backproject_item<NL, MODE, BF16>(P, D, tab, e_g, __ldg(items + it), partial, ering, bar0, nst, ebytes,
-                                              abort_flag, par, h, hw, lane, ht))
+                                              abort_flag, par, h, hw, lane, ht, lat))
             break;
     }
 }
@@ -86,6 +86,34 @@ __global__ void backproject_reduce_kernel(GeomParams P, const RowInfo* __restric
         const float t = s + val;
         c += (fabsf(s) >= fabsf(val)) ? (s - t) + val : (val - t) + s;
         s = t;
+    }
+    b[v] = s + c;
+}
+
+// b on the pixels (r, c) = (i s + r0, j s + c0) of one lattice, lat = (s, r0, c0), Wc x Hc of them, from
+// the partial images of its items (same order and compensation as above); pixels of lattice tiles that
+// cannot reach the record (no items) are zero.  Other pixels of b are not written.
+__global__ void backproject_reduce_lattice_kernel(GeomParams P, const RowInfo* __restrict__ rows,
+                                                  const float* __restrict__ partial, int ngroups, int3 lat, int Wc,
+                                                  int Nc, float* __restrict__ b)
+{
+    const int N = P.W * P.H;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Nc) return;
+    const int ri = t / Wc, ci = t - ri * Wc;
+    const int row = ri * lat.x + lat.y, col = ci * lat.x + lat.z;
+    const int v = row * P.W + col;
+    const int row0 = (ri / kBwdRows) * kBwdRows * lat.x + lat.y;
+    if (__ldg(&rows[row0].tvert) >= (float)(P.M - 1)) {
+        b[v] = 0.0f;
+        return;
+    }
+    float s = 0.0f, c = 0.0f;
+    for (int g = 0; g < ngroups; ++g) {
+        const float val = partial[(size_t)g * N + v];
+        const float t2 = s + val;
+        c += (fabsf(s) >= fabsf(val)) ? (s - t2) + val : (val - t2) + s;
+        s = t2;
     }
     b[v] = s + c;
 }
@@ -204,7 +232,7 @@ static cudaError_t launch_bwd_t(const mbir_geometry* g, const DevPtrs& D, const 
         int grid = std::min(g->n_sm, (g->n_items + g->bwd_halves - 1) / g->bwd_halves);
         kern<<<grid, g->bwd_halves * kBwdHalfThreads, sm, st>>>(P, D, tab, (const typename ET<BF16>::type*)e,
                                                                 g->d_items, g->n_items, g->d_bwd_counter,
-                                                                g->w_bpart, g->bwd_stages);
+                                                                g->w_bpart, g->bwd_stages, make_int3(1, 0, 0));
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return ce;
     }
@@ -271,13 +299,63 @@ static cudaError_t launch_bwd_partials_t(const mbir_geometry* g, const void* e, 
         kern<<<grid, g->bwd_halves * kBwdHalfThreads, sm, st>>>(P, dev_ptrs(g), tab,
                                                                 (const typename ET<BF16>::type*)e, g->d_items,
                                                                 g->n_items, g->d_bwd_counter, partial,
-                                                                g->bwd_stages);
+                                                                g->bwd_stages, make_int3(1, 0, 0));
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return ce;
     }
     const int N = P.W * P.H;
     backproject_reduce_kernel<<<(N + 255) / 256, 256, 0, st>>>(P, g->d_rows, partial, g->n_groups, b);
     return cudaGetLastError();
+}
+
+// A^T r on the pixels of one lattice only (CUDA-core kernel): items = (lattice tile row, lattice tile
+// column, Tx range, group) of that lattice, partial = ngroups x N floats.
+template <int NL, int MODE, bool BF16>
+static cudaError_t launch_bwd_lattice_t(const mbir_geometry* g, const int4* items, int nitems, int ngroups, int3 lat,
+                                        float* partial, const void* e, float* b, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    size_t sm = backproject_smem(g);
+    auto kern = backproject_kernel<NL, MODE, BF16>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce != cudaSuccess) return ce;
+    using Tab = typename TabT<BF16>::type;
+    const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
+    if (nitems > 0) {
+        ce = cudaMemsetAsync(g->d_bwd_counter, 0, sizeof(int), st);
+        if (ce != cudaSuccess) return ce;
+        int grid = std::min(g->n_sm, (nitems + g->bwd_halves - 1) / g->bwd_halves);
+        kern<<<grid, g->bwd_halves * kBwdHalfThreads, sm, st>>>(P, dev_ptrs(g), tab,
+                                                                (const typename ET<BF16>::type*)e, items, nitems,
+                                                                g->d_bwd_counter, partial, g->bwd_stages, lat);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return ce;
+    }
+    const int Hc = (P.H - lat.y + lat.x - 1) / lat.x, Wc = (P.W - lat.z + lat.x - 1) / lat.x;
+    const int Nc = Hc * Wc;
+    if (Nc > 0)
+        backproject_reduce_lattice_kernel<<<(Nc + 255) / 256, 256, 0, st>>>(P, g->d_rows, partial, ngroups, lat, Wc,
+                                                                           Nc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_lattice(const mbir_geometry* g, const int4* items, int nitems, int ngroups, int3 lat,
+                                       float* partial, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
+                                       cudaStream_t st)
+{
+    const bool bf = g->P.precision == MBIR_PREC_BF16;
+    const void* e = bf ? (const void*)e_bf : (const void*)e_pad;
+    if (g->P.mode == MBIR_MODE_TAB)
+        return bf ? launch_bwd_lattice_t<1, kModeTAB, true>(g, items, nitems, ngroups, lat, partial, e, b, st)
+                  : launch_bwd_lattice_t<1, kModeTAB, false>(g, items, nitems, ngroups, lat, partial, e, b, st);
+    if (g->P.L <= 2)
+        return bf ? launch_bwd_lattice_t<2, kModeOTF, true>(g, items, nitems, ngroups, lat, partial, e, b, st)
+                  : launch_bwd_lattice_t<2, kModeOTF, false>(g, items, nitems, ngroups, lat, partial, e, b, st);
+    if (g->P.L <= 4)
+        return bf ? launch_bwd_lattice_t<4, kModeOTF, true>(g, items, nitems, ngroups, lat, partial, e, b, st)
+                  : launch_bwd_lattice_t<4, kModeOTF, false>(g, items, nitems, ngroups, lat, partial, e, b, st);
+    return bf ? launch_bwd_lattice_t<8, kModeOTF, true>(g, items, nitems, ngroups, lat, partial, e, b, st)
+              : launch_bwd_lattice_t<8, kModeOTF, false>(g, items, nitems, ngroups, lat, partial, e, b, st);
 }
 
 cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_bwd_kernel(EngLists L)
             worker_barrier(h);
             if (it >= R.n_items) break;
             if (!backproject_item<1, kModeTAB, BF16>(P, R.D, tab, e_g, __ldg(R.items + it), R.bpart, ering, bar0, nst,
-                                                     ebytes, flags + h, par, h, hw, lane, ht))
+                                                     ebytes, flags + h, par, h, hw, lane, ht, make_int3(1, 0, 0)))
                 break;
         }
         __syncthreads();                 // both workers are done before the table is replaced

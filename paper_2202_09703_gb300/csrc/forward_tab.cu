@@ -52,14 +52,37 @@ __device__ __forceinline__ RecPair tab_record(const GeomParams& P, const DevPtrs
     return o;
 }
 
-// active-pair count per A-scan (integer sums: order-independent)
-__global__ void rec_count_kernel(GeomParams P, DevPtrs D, long long* __restrict__ counts)
+// Pixels of the lattice lat = (spacing s, first row, first column): t -> pixel index, Wc x Hc of them
+// ((1, 0, 0): every pixel, t = pixel index).
+struct Lattice {
+    int s, r0, c0, Wc, Nc;
+};
+
+__host__ __device__ inline Lattice make_lattice(const GeomParams& P, int3 lat)
+{
+    Lattice L;
+    L.s = lat.x;
+    L.r0 = lat.y;
+    L.c0 = lat.z;
+    L.Wc = (P.W - lat.z + lat.x - 1) / lat.x;
+    L.Nc = ((P.H - lat.y + lat.x - 1) / lat.x) * L.Wc;
+    return L;
+}
+
+__device__ __forceinline__ int lattice_pixel(const GeomParams& P, const Lattice& L, int t)
+{
+    const int i = t / L.Wc;
+    return (i * L.s + L.r0) * P.W + (t - i * L.Wc) * L.s + L.c0;
+}
+
+// active-pair count per A-scan over the lattice's pixels (integer sums: order-independent)
+__global__ void rec_count_kernel(GeomParams P, DevPtrs D, int3 lat, long long* __restrict__ counts)
 {
     __shared__ int sh[32];
     const int k = blockIdx.x;
-    const int N = P.W * P.H;
+    const Lattice L = make_lattice(P, lat);
     int c = 0;
-    for (int v = threadIdx.x; v < N; v += blockDim.x) c += tab_record(P, D, k, v).act ? 1 : 0;
+    for (int t = threadIdx.x; t < L.Nc; t += blockDim.x) c += tab_record(P, D, k, lattice_pixel(P, L, t)).act ? 1 : 0;
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
     __syncthreads();
@@ -70,23 +93,23 @@ __global__ void rec_count_kernel(GeomParams P, DevPtrs D, long long* __restrict_
     }
 }
 
-// Counting sort of one A-scan's records by n0, then each bucket ordered by
-// phase class and pixel index; run bounds per 32-sample span from the bucket
-// starts.
+// Counting sort of one A-scan's records (pixels of the lattice) by n0, then
+// each bucket ordered by phase class and pixel index; run bounds per 32-sample
+// span from the bucket starts.
 __global__ void __launch_bounds__(kSortThreads)
-    rec_fill_kernel(GeomParams P, DevPtrs D, const long long* __restrict__ off, int2* __restrict__ rkey,
+    rec_fill_kernel(GeomParams P, DevPtrs D, int3 lat, const long long* __restrict__ off, int2* __restrict__ rkey,
                     float4* __restrict__ rw, int2* __restrict__ runs)
 {
     extern __shared__ int hs[];                    // hist[M], start[M + 1]
     int* hist = hs;
     int* start = hs + P.M;
     const int k = blockIdx.x;
-    const int N = P.W * P.H;
+    const Lattice L = make_lattice(P, lat);
     const long long base = off[k];
     for (int t = threadIdx.x; t < P.M; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    for (int v = threadIdx.x; v < N; v += blockDim.x) {
-        RecPair r = tab_record(P, D, k, v);
+    for (int t = threadIdx.x; t < L.Nc; t += blockDim.x) {
+        RecPair r = tab_record(P, D, k, lattice_pixel(P, L, t));
         if (r.act) atomicAdd(&hist[r.n0], 1);
     }
     __syncthreads();
@@ -107,7 +130,8 @@ __global__ void __launch_bounds__(kSortThreads)
         runs[(size_t)k * nspan + s] = make_int2(start[lo], start[hi]);
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+    for (int t = threadIdx.x; t < L.Nc; t += blockDim.x) {
+        const int v = lattice_pixel(P, L, t);
         RecPair r = tab_record(P, D, k, v);
         if (!r.act) continue;
         const long long p = base + start[r.n0] + atomicAdd(&hist[r.n0], 1);
@@ -145,8 +169,9 @@ __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     forward_sorted_kernel(GeomParams P, const typename TabT<BF16>::type* __restrict__ tab_g,
                           const long long* __restrict__ off, const int2* __restrict__ rkey,
                           const float4* __restrict__ rw, const int2* __restrict__ runs,
-                          const int* __restrict__ order, int* __restrict__ next_win, const float* __restrict__ x,
-                          float* __restrict__ y_f32, __nv_bfloat16* __restrict__ y_bf16, int out_stride)
+                          const int* __restrict__ order, int total, int* __restrict__ next_win,
+                          const float* __restrict__ x, float* __restrict__ y_f32, __nv_bfloat16* __restrict__ y_bf16,
+                          int out_stride)
 {
     using Tab = typename TabT<BF16>::type;
     constexpr int WARPS = kFwdSortedThreads / 32;
@@ -162,7 +187,6 @@ __global__ void __launch_bounds__(kFwdSortedThreads, 1)
     __syncthreads();
     const int nspan = (P.M + 31) >> 5;
     const int nwin = (nspan + SUB - 1) / SUB;
-    const int total = P.K * nwin;
     for (;;) {
         // windows are handed out largest-first through a counter, one per warp
         int idx = 0;
@@ -210,7 +234,7 @@ cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_b
     long long* d_cnt = nullptr;
     cudaError_t e = cudaMalloc(&d_cnt, sizeof(long long) * (P.K + 1));
     if (e != cudaSuccess) return e;
-    rec_count_kernel<<<P.K, 256, 0, st>>>(P, D, d_cnt);
+    rec_count_kernel<<<P.K, 256, 0, st>>>(P, D, make_int3(1, 0, 0), d_cnt);
     std::vector<long long> cnt(P.K), off(P.K + 1, 0);
     e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(long long) * P.K, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -231,7 +255,8 @@ cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_b
     const size_t sm = sizeof(int) * (2 * (size_t)P.M + 1);
     e = cudaFuncSetAttribute(rec_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    rec_fill_kernel<<<P.K, kSortThreads, sm, st>>>(P, D, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs);
+    rec_fill_kernel<<<P.K, kSortThreads, sm, st>>>(P, D, make_int3(1, 0, 0), g->d_rec_off, g->d_rec_key, g->d_rec_w,
+                                                   g->d_runs);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
@@ -266,7 +291,7 @@ static cudaError_t launch_sorted_t(const mbir_geometry* g, const int* order, con
     if (ce != cudaSuccess) return ce;
     const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
     kern<<<grid, kFwdSortedThreads, sm, st>>>(g->P, tab, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, order,
-                                              g->d_win_counter, x, yf, yb, stride);
+                                              (int)wins, g->d_win_counter, x, yf, yb, stride);
     return cudaGetLastError();
 }
 
@@ -383,6 +408,131 @@ cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float*
                                   cudaStream_t st)
 {
     return launch_sorted(g, g->fwd_sub, g->d_win_order, x, yf, yb, stride, st);
+}
+
+// Record lists of the coordinate descent's colours: for spacing s, colour c = (c / s, c mod s) holds the
+// records of the pixels (r, col) with r = c / s and col = c mod s (mod s), built like the full list
+// (same order within each bucket); per colour the non-empty windows of `sub` spans, largest first.
+// The lists of all colours follow each other; their offsets are absolute.
+cudaError_t build_colour_records(mbir_geometry* g, int s, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const int nc = s * s, nspan = (P.M + 31) / 32, sub = g->fwd_sub > 0 ? g->fwd_sub : 2;
+    const int nwin = (nspan + sub - 1) / sub;
+    const DevPtrs D = dev_ptrs(g);
+    const size_t noff = (size_t)nc * (P.K + 1);
+    long long* d_off = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_off, sizeof(long long) * noff);
+    if (e != cudaSuccess) return e;
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        rec_count_kernel<<<P.K, 256, 0, st>>>(P, D, make_int3(s, c / s, c % s), d_off + (size_t)c * (P.K + 1));
+        e = cudaGetLastError();
+    }
+    std::vector<long long> off(noff);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(off.data(), d_off, sizeof(long long) * noff, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cudaFree(d_off); return e; }
+    long long acc = 0;
+    for (int c = 0; c < nc; ++c)
+        for (int k = 0; k <= P.K; ++k) {
+            const long long n = k < P.K ? off[(size_t)c * (P.K + 1) + k] : 0;
+            off[(size_t)c * (P.K + 1) + k] = acc;
+            acc += n;
+        }
+    if (acc != g->n_records) { cudaFree(d_off); return cudaErrorInvalidValue; }   // the colours partition the pairs
+    int2* d_key = nullptr;
+    float4* d_w = nullptr;
+    int2* d_runs = nullptr;
+    e = cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * noff, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_key, sizeof(int2) * std::max<long long>(acc, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_w, sizeof(float4) * std::max<long long>(acc, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_runs, sizeof(int2) * (size_t)nc * P.K * nspan);
+    const size_t sm = sizeof(int) * (2 * (size_t)P.M + 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rec_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        rec_fill_kernel<<<P.K, kSortThreads, sm, st>>>(P, D, make_int3(s, c / s, c % s), d_off + (size_t)c * (P.K + 1),
+                                                       d_key, d_w, d_runs + (size_t)c * P.K * nspan);
+        e = cudaGetLastError();
+    }
+    std::vector<int2> runs((size_t)nc * P.K * nspan);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(runs.data(), d_runs, sizeof(int2) * runs.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    std::vector<int> wins;
+    std::vector<long long> woff(nc + 1, 0);
+    if (e == cudaSuccess) {
+        for (int c = 0; c < nc; ++c) {
+            const int2* rc = runs.data() + (size_t)c * P.K * nspan;
+            std::vector<std::pair<int, int>> cw;      // (records, window)
+            for (int k = 0; k < P.K; ++k)
+                for (int w = 0; w < nwin; ++w) {
+                    const int sp0 = w * sub, sp1 = std::min(sp0 + sub, nspan) - 1;
+                    const int n = rc[(size_t)k * nspan + sp1].y - rc[(size_t)k * nspan + sp0].x;
+                    if (n > 0) cw.push_back({n, k * nwin + w});
+                }
+            std::stable_sort(cw.begin(), cw.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+                return a.first > b.first;
+            });
+            for (auto& p : cw) wins.push_back(p.second);
+            woff[c + 1] = (long long)wins.size();
+        }
+    }
+    int* d_win = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_win, sizeof(int) * std::max<size_t>(wins.size(), 1));
+    if (e == cudaSuccess && !wins.empty())
+        e = cudaMemcpy(d_win, wins.data(), sizeof(int) * wins.size(), cudaMemcpyHostToDevice);
+    long long* h_woff = (long long*)malloc(sizeof(long long) * (nc + 1));
+    if (e == cudaSuccess && !h_woff) e = cudaErrorMemoryAllocation;
+    if (e != cudaSuccess) {
+        cudaFree(d_off); cudaFree(d_key); cudaFree(d_w); cudaFree(d_runs); cudaFree(d_win); free(h_woff);
+        return e;
+    }
+    std::copy(woff.begin(), woff.end(), h_woff);
+    g->d_icd_rec_off = d_off;
+    g->d_icd_rec_key = d_key;
+    g->d_icd_rec_w = d_w;
+    g->d_icd_runs = d_runs;
+    g->d_icd_win = d_win;
+    g->h_icd_win_off = h_woff;
+    g->icd_win_sub = sub;
+    g->icd_rec_bytes = sizeof(long long) * noff + (sizeof(int2) + sizeof(float4)) * (size_t)std::max<long long>(acc, 1) +
+                       sizeof(int2) * runs.size() + sizeof(int) * std::max<size_t>(wins.size(), 1);
+    return cudaSuccess;
+}
+
+template <bool BF16, int SUB>
+static cudaError_t launch_colour_t(const mbir_geometry* g, int c, const float* x, float* yf, int stride,
+                                   cudaStream_t st)
+{
+    using Tab = typename TabT<BF16>::type;
+    const GeomParams& P = g->P;
+    const int nspan = (P.M + 31) / 32;
+    const long long w0 = g->h_icd_win_off[c], total = g->h_icd_win_off[c + 1] - w0;
+    cudaError_t ce = cudaMemsetAsync(yf, 0, sizeof(float) * (size_t)P.K * stride, st);
+    if (ce != cudaSuccess || total == 0) return ce;
+    const size_t sm = forward_sorted_smem(g);
+    auto kern = forward_sorted_kernel<BF16, SUB>;
+    ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_win_counter, 0, sizeof(int), st);
+    if (ce != cudaSuccess) return ce;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(g->n_sm, (total + 31) / 32));
+    const Tab* tab = BF16 ? (const Tab*)(const void*)g->d_tab_bf16 : (const Tab*)(const void*)g->d_tab;
+    kern<<<grid, kFwdSortedThreads, sm, st>>>(P, tab, g->d_icd_rec_off + (size_t)c * (P.K + 1), g->d_icd_rec_key,
+                                              g->d_icd_rec_w, g->d_icd_runs + (size_t)c * P.K * nspan,
+                                              g->d_icd_win + w0, (int)total, g->d_win_counter, x, yf, nullptr, stride);
+    return cudaGetLastError();
+}
+
+// y = A x for an x that is zero off colour c (y zeroed first; only the colour's records are read).
+cudaError_t launch_forward_colour(const mbir_geometry* g, int c, const float* x, float* yf, int stride,
+                                  cudaStream_t st)
+{
+    const bool bf = g->P.precision == MBIR_PREC_BF16;
+    switch (g->icd_win_sub) {
+    case 1: return bf ? launch_colour_t<true, 1>(g, c, x, yf, stride, st) : launch_colour_t<false, 1>(g, c, x, yf, stride, st);
+    case 2: return bf ? launch_colour_t<true, 2>(g, c, x, yf, stride, st) : launch_colour_t<false, 2>(g, c, x, yf, stride, st);
+    default: return bf ? launch_colour_t<true, 4>(g, c, x, yf, stride, st) : launch_colour_t<false, 4>(g, c, x, yf, stride, st);
+    }
 }
 
 }  // namespace mbir

@@ -177,6 +177,7 @@ void free_geometry(mbir_geometry* g)
                     g->d_tc_counter, g->d_tf_bop, g->d_tf_n0off, g->d_tf_order, g->d_tf_counter,
                     g->d_tf_grpoff, g->d_tc3_bop, g->w_colnorm};
     for (void* p : ptrs) if (p) cudaFree(p);
+    mbir::free_icd_lists(g);
     mbir::prof_release(g);
     free(g->tab_host);
     free(g->h_win_cost);
@@ -543,7 +544,7 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
     }
     ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
-    g->bytes = bytes;
+    g->bytes += bytes;          // the record and tensor-core tables added theirs already
     *out = g;
     return MBIR_OK;
 }

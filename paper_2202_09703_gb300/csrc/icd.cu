@@ -6,6 +6,12 @@
 // adds w^2 sum_m H(m)^2 over the pair's taps inside the record, the tau = t0
 // tap of a flagged pair taking only its lower table row (eq. 10's open
 // window).  The sum per pixel runs in A-scan order: deterministic.
+//
+// It also builds the per-colour work lists of the descent: the A^T items of
+// each colour's pixel lattice and, with TAB records, each colour's records.
+#include <algorithm>
+#include <vector>
+
 #include "apply_common.cuh"
 
 namespace mbir {
@@ -62,6 +68,95 @@ cudaError_t launch_column_norms(const mbir_geometry* g, float* out, cudaStream_t
     if (g->P.L <= 2) return launch_colnorm_t<2, kModeOTF>(g, out, st);
     if (g->P.L <= 4) return launch_colnorm_t<4, kModeOTF>(g, out, st);
     return launch_colnorm_t<8, kModeOTF>(g, out, st);
+}
+
+void free_icd_lists(mbir_geometry* g)
+{
+    void* ptrs[] = {g->d_icd_items, g->w_icd_bpart, g->d_icd_rec_off, g->d_icd_rec_key, g->d_icd_rec_w,
+                    g->d_icd_runs, g->d_icd_win};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    free(g->h_icd_item_off);
+    free(g->h_icd_win_off);
+    g->bytes -= g->icd_bytes + g->icd_rec_bytes;
+    g->d_icd_items = nullptr;
+    g->w_icd_bpart = nullptr;
+    g->d_icd_rec_off = nullptr;
+    g->d_icd_rec_key = nullptr;
+    g->d_icd_rec_w = nullptr;
+    g->d_icd_runs = nullptr;
+    g->d_icd_win = nullptr;
+    g->h_icd_item_off = nullptr;
+    g->h_icd_win_off = nullptr;
+    g->icd_bytes = g->icd_rec_bytes = 0;
+    g->icd_s = 0;
+}
+
+// Work lists for colour spacing s.  A^T: per colour the 16 x 32 tiles of its pixel lattice (those whose
+// first row can reach the record) times groups of transmitter positions, the same group count for every
+// colour, enough items to occupy every tile worker.  A x: per-colour record lists when the geometry has
+// records (the colours partition the pairs) and s <= 64; otherwise (or if they do not fit) the full A x.
+cudaError_t build_icd_lists(mbir_geometry* g, int s, cudaStream_t st)
+{
+    free_icd_lists(g);
+    const GeomParams& P = g->P;
+    const int nc = s * s, TR = backproject_tile_rows();
+    int min_tiles = 0;
+    for (int c = 0; c < nc; ++c) {
+        const int r0 = c / s, c0 = c % s;
+        if (r0 >= P.H || c0 >= P.W) continue;
+        const int Hc = (P.H - r0 + s - 1) / s, Wc = (P.W - c0 + s - 1) / s;
+        int tiles = 0;
+        for (int tr = 0; tr * TR < Hc; ++tr)
+            if (g->h_tvert[tr * TR * s + r0] < (float)(P.M - 1)) tiles += (Wc + 31) / 32;
+        if (tiles > 0) min_tiles = min_tiles == 0 ? tiles : std::min(min_tiles, tiles);
+    }
+    int ng = 1;
+    if (min_tiles > 0) ng = std::max(1, std::min(P.n_tx, (4 * g->bwd_halves * g->n_sm + min_tiles - 1) / min_tiles));
+    const int txg = (P.n_tx + ng - 1) / ng;
+    ng = (P.n_tx + txg - 1) / txg;
+    std::vector<int4> items;
+    std::vector<int> ioff(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        const int r0 = c / s, c0 = c % s;
+        if (r0 < P.H && c0 < P.W) {
+            const int Hc = (P.H - r0 + s - 1) / s, Wc = (P.W - c0 + s - 1) / s;
+            for (int tr = 0; tr * TR < Hc; ++tr) {
+                if (!(g->h_tvert[tr * TR * s + r0] < (float)(P.M - 1))) continue;
+                for (int tc = 0; tc * 32 < Wc; ++tc)
+                    for (int gi = 0; gi < ng; ++gi) {
+                        const int t0 = gi * txg, t1 = std::min(P.n_tx, t0 + txg);
+                        items.push_back(make_int4(tr, tc, t0 | (t1 << 16), gi));
+                    }
+            }
+        }
+        ioff[c + 1] = (int)items.size();
+    }
+    const size_t N = (size_t)P.W * P.H;
+    cudaError_t e = cudaMalloc((void**)&g->d_icd_items, sizeof(int4) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(g->d_icd_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->w_icd_bpart, sizeof(float) * N * ng);
+    g->h_icd_item_off = (int*)malloc(sizeof(int) * (nc + 1));
+    if (e == cudaSuccess && !g->h_icd_item_off) e = cudaErrorMemoryAllocation;
+    if (e != cudaSuccess) {
+        free_icd_lists(g);
+        return e;
+    }
+    std::copy(ioff.begin(), ioff.end(), g->h_icd_item_off);
+    g->icd_groups = ng;
+    g->icd_bytes = sizeof(int4) * std::max<size_t>(items.size(), 1) + sizeof(float) * N * ng;
+    g->bytes += g->icd_bytes;
+    g->icd_s = s;
+    // per-colour record lists up to 64 x 64 colours (their span bounds grow with the colour count)
+    if (g->d_rec_key && nc <= 4096) {
+        e = build_colour_records(g, s, st);
+        if (e == cudaSuccess) g->bytes += g->icd_rec_bytes;
+        else if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();                  // no room for a second copy of the records: full A x
+            e = cudaSuccess;
+        }
+    }
+    return e;
 }
 
 }  // namespace mbir

@@ -617,6 +617,8 @@ int icd_core(mbir_geometry* g, const void* y_dev, int y_bf16, const mbir_prior* 
     CK(cudaStreamSynchronize(st));
     if (bad != 0.0) return MBIR_ERR_NONFINITE;
 
+    if (g->icd_s != spacing) CK(build_icd_lists(g, spacing, st));
+    const bool colour_fwd = g->d_icd_rec_key != nullptr;
     float* dx = g->w_d;
     const int ublocks = (int)std::min<long long>((N + KMp + 255) / 256, 152LL * 32);
     const int cblocks = 152 * 4;
@@ -624,14 +626,19 @@ int icd_core(mbir_geometry* g, const void* y_dev, int y_bf16, const mbir_prior* 
         for (int colour = 0; colour < spacing * spacing; ++colour) {
             const int cr = colour / spacing, cc = colour % spacing;
             if (cr >= P.H || cc >= P.W) continue;
+            // A^T e on the colour's pixels only
             prof_begin(g, 1, st);
-            CK(launch_backproject(g, g->w_e, ebf, g->w_b, st));
+            const int i0 = g->h_icd_item_off[colour], ni = g->h_icd_item_off[colour + 1] - i0;
+            CK(launch_backproject_lattice(g, g->d_icd_items + i0, ni, g->icd_groups, make_int3(spacing, cr, cc),
+                                          g->w_icd_bpart, g->w_e, ebf, g->w_b, st));
             prof_end(g, st);
             icd_dir_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, x, g->w_b, g->w_msq, g->w_colnorm, spacing, cr, cc,
                                                           dx, part);
             CK(cudaGetLastError());
+            // A dx from the colour's records (dx is zero elsewhere)
             prof_begin(g, 0, st);
-            CK(launch_forward(g, dx, g->w_q, nullptr, P.Mp, st));
+            if (colour_fwd) CK(launch_forward_colour(g, colour, dx, g->w_q, P.Mp, st));
+            else CK(launch_forward(g, dx, g->w_q, nullptr, P.Mp, st));
             prof_end(g, st);
             project_kernel<<<P.K, kRedThreads, 0, st>>>(P, g->w_q, 0, P.Mp, nullptr, 0, g->d_direct, g->d_dinv,
                                                         use_direct, g->w_q, P.Mp, nullptr, part2);
@@ -783,7 +790,7 @@ int mbir_reconstruct(const mbir_geometry* gc, const void* y_dev, const mbir_prio
 int mbir_reconstruct_icd(const mbir_geometry* gc, const void* y_dev, const mbir_prior* pr, int n_sweeps,
                          int spacing, float* x_dev, int x_given, float* g_dev, mbir_stats* st, void* stream)
 {
-    if (!gc || !y_dev || !x_dev || n_sweeps < 0 || spacing < 2 || spacing > 65536 || !prior_ok(pr))
+    if (!gc || !y_dev || !x_dev || n_sweeps < 0 || spacing < 2 || spacing > 256 || !prior_ok(pr))
         return MBIR_ERR_INVALID_ARG;
     mbir_geometry* g = const_cast<mbir_geometry*>(gc);
     return icd_core(g, y_dev, g->P.precision == MBIR_PREC_BF16 ? 1 : 0, pr, n_sweeps, spacing, x_dev, x_given, g_dev,

@@ -427,6 +427,22 @@ struct mbir_geometry {
     long long n_records;
     // |A_v|^2 per pixel for the coordinate descent (computed on its first call)
     float* w_colnorm;
+    // coordinate descent work lists for colour spacing icd_s (built on the first call with that spacing):
+    // A^T items per colour over lattice tiles, and (with records) per-colour record lists for A x
+    int icd_s;
+    int icd_groups;             // transmitter groups of the colour A^T items
+    int* h_icd_item_off;        // host: s^2 + 1 offsets into d_icd_items
+    int4* d_icd_items;
+    float* w_icd_bpart;         // icd_groups x N partial images
+    size_t icd_bytes;
+    long long* d_icd_rec_off;   // s^2 x (K + 1) absolute record offsets
+    int2* d_icd_rec_key;
+    float4* d_icd_rec_w;
+    int2* d_icd_runs;           // s^2 x K x spans
+    int* d_icd_win;             // non-empty windows of every colour, largest first
+    long long* h_icd_win_off;   // host: s^2 + 1 offsets into d_icd_win
+    int icd_win_sub;            // spans per window of those lists
+    size_t icd_rec_bytes;
     // profiling of the apply kernels inside mbir_reconstruct
     int prof;
     void* prof_state;      // host-side event lists (see map.cu)
@@ -471,4 +487,12 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
                               cudaStream_t st);
 cudaError_t launch_column_norms(const mbir_geometry* g, float* out, cudaStream_t st);
+cudaError_t build_colour_records(mbir_geometry* g, int s, cudaStream_t st);
+cudaError_t launch_forward_colour(const mbir_geometry* g, int c, const float* x, float* yf, int stride,
+                                  cudaStream_t st);
+cudaError_t launch_backproject_lattice(const mbir_geometry* g, const int4* items, int nitems, int ngroups, int3 lat,
+                                       float* partial, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
+                                       cudaStream_t st);
+cudaError_t build_icd_lists(mbir_geometry* g, int s, cudaStream_t st);
+void free_icd_lists(mbir_geometry* g);
 }  // namespace mbir

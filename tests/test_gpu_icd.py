@@ -60,6 +60,36 @@ def test_icd_matches_oracle(scene_fn, spacing):
         assert rel_l2(g.cpu().numpy(), g_ref) <= 1e-4
 
 
+@pytest.mark.parametrize("mode", ["otf", "tab-norec"])
+def test_icd_without_colour_records(mode):
+    """OTF mode and TAB mode without records: the colour's A^T on its pixel lattice, the full A x."""
+    s = ragged_scene()
+    plan, x_true, g_true, y, sig = oracle_data(s, seed=5)
+    x_ref, _, cost_ref = plan.icd(y, sig, 2, 3)
+    geo = M.Geometry(s, mode="tab", records=False) if mode == "tab-norec" else M.Geometry(s, mode=mode)
+    x = torch.empty(s.N, device=DEV)
+    out = geo.reconstruct_icd(to_dev(y), sig, 2, 3, x, want_cost=True)
+    torch.cuda.synchronize()
+    assert rel_l2(x.cpu().numpy(), x_ref) <= 1e-4
+    assert np.allclose(out["cost"], cost_ref, rtol=1e-4)
+
+
+def test_icd_work_lists_rebuilt_per_spacing():
+    """Switching the spacing rebuilds the colour lists; the same spacing gives the same bits again."""
+    s = S.cfg0()
+    plan, x_true, g_true, y, sig = oracle_data(s, seed=6)
+    geo = M.Geometry(s)
+    yd = to_dev(y)
+    xs = []
+    for sp in (4, 3, 4):
+        x = torch.empty(s.N, device=DEV)
+        geo.reconstruct_icd(yd, sig, 1, sp, x)
+        torch.cuda.synchronize()
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[2])
+    assert rel_l2(xs[1], plan.icd(y, sig, 1, 3)[0]) <= 1e-4
+
+
 def test_icd_from_a_start_image():
     s = ragged_scene()
     plan, x_true, g_true, y, sig = oracle_data(s, seed=4)
