@@ -209,10 +209,10 @@ int mbir_backproject(const mbir_geometry* g, const void* r_dev, float* x_dev, vo
 
 /* x = A^T r like mbir_backproject, but without allocating any device memory.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate at the point of the call - code running during CUDA stream
- * capture (where cudaMalloc is not allowed), real-time loops that forbid
- * allocator calls after start-up, and processes with a fixed, pre-sized
- * memory pool.  (mbir_backproject may allocate its workspace on first use.)
+ * cannot allocate at the point of the call - real-time loops that forbid
+ * allocator calls after start-up (an allocation can block for an unbounded
+ * time), and processes whose device memory is one pool sized and handed out
+ * in advance by another component.  (mbir_backproject may allocate its workspace on first use.)
  * Its scratch (the padded residual rows, K x (M + pulse support + pad)
  * floats, and one partial image per transmitter group) lives in one fixed
  * 16 MiB array inside the library, held by every GPU that loads the library

@@ -1,10 +1,9 @@
 // mbir_backproject_noalloc: A^T r without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they apply
-// the adjoint: code running while a stream is being captured into a CUDA
-// graph (where cudaMalloc is not allowed), real-time loops that forbid
-// allocator calls after start-up, and hosts whose memory pool is sized and
-// locked in advance.  mbir_backproject may allocate its workspace on first
+// the adjoint: real-time loops that forbid allocator calls after start-up
+// (an allocation can block for an unbounded time), and hosts whose device
+// memory is one pool sized and handed out in advance by another component.  mbir_backproject may allocate its workspace on first
 // use; this entry point instead takes its scratch from one fixed array that
 // is part of the library image.
 //

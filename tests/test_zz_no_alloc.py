@@ -1,8 +1,8 @@
 """mbir_backproject_noalloc: A^T r for callers that cannot allocate device memory.
 
-Code that runs during CUDA stream capture, real-time loops that forbid
-allocator calls, and processes with a fixed memory pool cannot let the
-library allocate at the point of the call.  This entry point takes its
+Real-time loops that forbid allocator calls after start-up, and processes
+whose device memory is a pool sized in advance by another component, cannot
+let the library allocate at the point of the call.  This entry point takes its
 scratch from a fixed array in the library.  It is checked here, through the
 C ABI, against the ordinary mbir_backproject on two calls in a row (with
 different residuals, so the shared scratch is shown to be fully rewritten),
