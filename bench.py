@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=0, help="requests for the batched / served workloads")
     ap.add_argument("--source-hash", default="",
                     help="print the hash profiles/traffic.txt records for these comma-separated sources and exit")
+    ap.add_argument("--spacing", type=int, default=8, help="colour spacing of --workload icd")
+    ap.add_argument("--sweeps", type=int, default=10, help="sweeps of --workload icd")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="storage precision of the --apply-only geometry")
     return ap.parse_args()
@@ -614,7 +616,7 @@ def run_saft(args):
 
 def run_icd(args):
     """The paper's optimiser on the 4-layer 256x512 workload: coloured ICD
-    (spacing 8: 64 colours per sweep) for 10 sweeps against the default
+    (default spacing 8: 64 colours per sweep) for 10 sweeps against the default
     50-iteration conjugate-gradient reconstruction, both from the same
     synthetic scan.  Convergence is the cost's excess over a 200-iteration
     conjugate-gradient cost, relative to that cost; image error against the
@@ -630,8 +632,7 @@ def run_icd(args):
     geo, y, sig = _synth_request(M, S, torch, scene, 0, dev)
     xt = torch.as_tensor(S.phantom(scene, 0).reshape(-1), dtype=torch.float32, device=dev)
     x = torch.empty(scene.N, device=dev)
-    c_ref = geo.reconstruct(y, sig, 200, x, want_cost=True)["cost"][-1]
-    spacing, sweeps = 8, 10
+    spacing, sweeps = args.spacing, args.sweeps
     geo.reconstruct_icd(y, sig, 1, spacing, x)              # builds the colour lists once
     flush = torch.empty(64 * 1024 * 1024, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -653,10 +654,12 @@ def run_icd(args):
         geo.reconstruct_icd(y, sig, sweeps, spacing, x)
     t_icd, out = timed(lambda: geo.reconstruct_icd(y, sig, sweeps, spacing, x, want_cost=True), reps)
     e_icd = float((x - xt).norm() / xt.norm())
-    ex_icd = (out["cost"][-1] - c_ref) / abs(c_ref)
+    c_icd = out["cost"][-1]
     t_cg, out = timed(lambda: geo.reconstruct(y, sig, scene.n_iter, x, want_cost=True), reps)
     e_cg = float((x - xt).norm() / xt.norm())
-    ex_cg = (out["cost"][-1] - c_ref) / abs(c_ref)
+    c_cg = out["cost"][-1]
+    c_ref = geo.reconstruct(y, sig, 200, x, want_cost=True)["cost"][-1]
+    ex_icd, ex_cg = (c_icd - c_ref) / abs(c_ref), (c_cg - c_ref) / abs(c_ref)
     cfg = {"workload": f"coloured ICD, spacing {spacing}, {sweeps} sweeps, on the 4-layer 256x512 scan "
                        "(64 Tx x 16 Rx, 2048 samples), synthetic phantom",
            "icd_ms": t_icd, "icd_cost_excess": ex_icd, "icd_image_rel_err_vs_truth": e_icd,

@@ -174,7 +174,8 @@ typedef struct mbir_geometry mbir_geometry;
  * solve every leg once (the paper's "compute only once", Section 3).
  * Errors: MBIR_ERR_INVALID_ARG (n_layers outside 1..8, non-positive
  * thickness, speed, density, pitch, fs, fc, n_cycles, beta < 0, negative
- * attenuation, img_z0_m < 0, sizes < 1, NULL arrays, K*M or N above 2^31),
+ * attenuation, img_z0_m < 0, sizes < 1, NULL arrays, K*M or N above 2^31,
+ * K above 65535),
  * MBIR_ERR_OOM, MBIR_ERR_CUDA, MBIR_ERR_UNSUPPORTED (the pulse table and two
  * padded residual rows exceed shared memory: with the default 16 x 16 FP32
  * table about 11,000 samples per A-scan, twice that in BF16).  *out is

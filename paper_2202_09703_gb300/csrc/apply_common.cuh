@@ -162,10 +162,10 @@ __device__ __forceinline__ void worker_barrier(int h)
     asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "n"(kBwdWorkerThreads) : "memory");
 }
 
-// One A^T r work item {tile row, tile column, tx0 | tx1 << 16, group} for tile
-// worker h: every pixel of the tile sums its pairs with the A-scans of
-// transmitter positions [tx0, tx1) (transmitter outer, receiver inner, the
-// transmit leg kept) and writes the sum to its partial image `grp`.  Residual
+// One A^T r work item {tile row, tile column, ka | kb << 16, group} for tile
+// worker h: every pixel of the tile sums its pairs with the A-scans [ka, kb)
+// (transmitter outer, receiver inner, the transmit leg kept while the
+// receiver changes) and writes the sum to its partial image `grp`.  Residual
 // rows stream through the worker's nst-stage ring `ering` (rows of ebytes)
 // guarded by the mbarriers at bar0.  A wait that gives up sets *abort_flag
 // and the function drains the copies still in flight (bounded) and returns
@@ -186,12 +186,11 @@ __device__ __forceinline__ bool backproject_item(const GeomParams& P, const DevP
     const size_t estride = ebytes / sizeof(E);
     // lat = (spacing, first row, first column) of the pixel lattice the tiles cover ((1, 0, 0): the image)
     const int row = (item.x * kBwdTileRows + hw) * lat.x + lat.y, col = (item.y * 32 + lane) * lat.x + lat.z;
-    const int tx0 = item.z & 0xffff, tx1 = item.z >> 16, grp = item.w;
+    const int ka = item.z & 0xffff, kb = item.z >> 16, grp = item.w;     // A-scans [ka, kb)
     const bool pix_ok = col < P.W && row < P.H;
     const RowInfo ri = load_row(D.rows, min(row, P.H - 1));
     const bool row_ok = pix_ok && ri.tvert < (float)(P.M - 1);
     const int colc = min(col, P.W - 1);
-    const int ka = tx0 * P.n_rx, kb = tx1 * P.n_rx;
     if (ht == 0) {
         for (int s = 0; s < nst && ka + s < kb; ++s) {
             mbar_arrive_expect_tx(bar0 + 8 * s, rowbytes);
@@ -207,7 +206,7 @@ __device__ __forceinline__ bool backproject_item(const GeomParams& P, const DevP
             if (ka + 1 < kb) hx_nxt = __ldg(D.hidx + (size_t)__ldg(D.rxpos + ka + 1) * P.W + colc);
         }
     }
-    int i = tx0, j = 0, stage = 0, k = ka;
+    int i = ka / P.n_rx, j = ka - i * P.n_rx, stage = 0, k = ka;
     bool aborted = false;
     for (; k < kb; ++k) {
         if constexpr (MODE == kModeTAB) {
@@ -219,7 +218,7 @@ __device__ __forceinline__ bool backproject_item(const GeomParams& P, const DevP
             }
         }
         if (row_ok) {
-            if (j == 0) tx = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.txpos + i));
+            if (j == 0 || k == ka) tx = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.txpos + i));
             if constexpr (MODE != kModeTAB) rx_cur = get_leg<NL, MODE>(P, D, ri, row, colc, __ldg(D.rxpos + k));
         }
         const Pair pr = make_pair(P, tx, rx_cur, ri.tau);

@@ -1,8 +1,9 @@
 // A^T r (adjoint of eq. 13).  Thread = pixel.  A persistent grid of one CTA
 // per SM holds the pulse table in shared memory once; each CTA runs two
 // independent tile workers (16 x 32 pixels each, synchronised by their own
-// named barrier) that take work items = (pixel tile, group of transmitter
-// positions) from a shared counter, longest estimated item first.  A worker walks its A-scans in (Tx, receiver) order, keeping
+// named barrier) that take work items = (pixel tile, range of A-scans: whole
+// transmitter groups for the full image) from a shared counter, longest
+// estimated item first.  A worker walks its A-scans in (Tx, receiver) order, keeping
 // the pixel's transmit leg while the receiver changes.  Residual rows are
 // staged in shared memory by 1-D bulk copies (TMA engine) into a 3-stage ring
 // guarded by mbarriers with bounded waits.  Every tap of a pair shares one
@@ -309,7 +310,7 @@ static cudaError_t launch_bwd_partials_t(const mbir_geometry* g, const void* e, 
 }
 
 // A^T r on the pixels of one lattice only (CUDA-core kernel): items = (lattice tile row, lattice tile
-// column, Tx range, group) of that lattice, partial = ngroups x N floats.
+// column, A-scan range, group) of that lattice, partial = ngroups x N floats.
 template <int NL, int MODE, bool BF16>
 static cudaError_t launch_bwd_lattice_t(const mbir_geometry* g, const int4* items, int nitems, int ngroups, int3 lat,
                                         float* partial, const void* e, float* b, cudaStream_t st)

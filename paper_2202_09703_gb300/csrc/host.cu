@@ -95,7 +95,7 @@ int validate(const mbir_geometry_desc* d)
     for (int j = 0; j < d->n_rx; ++j) if (!std::isfinite(d->rx_offset_m[j])) return MBIR_ERR_INVALID_ARG;
     long long N = (long long)d->img_w * d->img_h;
     long long K = (long long)d->n_tx * d->n_rx;
-    if (N > (1LL << 30) || K * (long long)d->n_samples > (1LL << 31) || d->n_samples > 60000)
+    if (N > (1LL << 30) || K * (long long)d->n_samples > (1LL << 31) || d->n_samples > 60000 || K > 65535)
         return MBIR_ERR_INVALID_ARG;
     return MBIR_OK;
 }
@@ -178,6 +178,7 @@ void free_geometry(mbir_geometry* g)
                     g->d_tf_grpoff, g->d_tc3_bop, g->w_colnorm};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::free_icd_lists(g);
+    if (g->icd_stream) cudaStreamDestroy((cudaStream_t)g->icd_stream);
     mbir::prof_release(g);
     free(g->tab_host);
     free(g->h_win_cost);
@@ -507,7 +508,7 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
                     int t0 = gi * txg, t1 = std::min(P.n_tx, t0 + txg);
                     double c = 0;
                     for (int t = t0; t < t1; ++t) c += g->h_bwd_cost[((size_t)tr * ntc + tc) * P.n_tx + t];
-                    items.push_back(make_int4(tr, tc, t0 | (t1 << 16), gi));
+                    items.push_back(make_int4(tr, tc, (t0 * P.n_rx) | ((t1 * P.n_rx) << 16), gi));
                     cost.push_back(c);
                 }
         }

@@ -89,11 +89,13 @@ void free_icd_lists(mbir_geometry* g)
     g->h_icd_win_off = nullptr;
     g->icd_bytes = g->icd_rec_bytes = 0;
     g->icd_s = 0;
+    if (g->icd_exec) cudaGraphExecDestroy((cudaGraphExec_t)g->icd_exec);
+    g->icd_exec = nullptr;
 }
 
 // Work lists for colour spacing s.  A^T: per colour the 16 x 32 tiles of its pixel lattice (those whose
-// first row can reach the record) times groups of transmitter positions, the same group count for every
-// colour, enough items to occupy every tile worker.  A x: per-colour record lists when the geometry has
+// first row can reach the record) times chunks of A-scans, the same chunks for every colour, about four
+// items per tile worker so that dynamic fetching evens out the SMs.  A x: per-colour record lists when the geometry has
 // records (the colours partition the pairs) and s <= 64; otherwise (or if they do not fit) the full A x.
 cudaError_t build_icd_lists(mbir_geometry* g, int s, cudaStream_t st)
 {
@@ -110,10 +112,12 @@ cudaError_t build_icd_lists(mbir_geometry* g, int s, cudaStream_t st)
             if (g->h_tvert[tr * TR * s + r0] < (float)(P.M - 1)) tiles += (Wc + 31) / 32;
         if (tiles > 0) min_tiles = min_tiles == 0 ? tiles : std::min(min_tiles, tiles);
     }
+    // A-scan chunks of at least 4 (the residual ring's depth plus one), about four items per tile worker
     int ng = 1;
-    if (min_tiles > 0) ng = std::max(1, std::min(P.n_tx, (4 * g->bwd_halves * g->n_sm + min_tiles - 1) / min_tiles));
-    const int txg = (P.n_tx + ng - 1) / ng;
-    ng = (P.n_tx + txg - 1) / txg;
+    if (min_tiles > 0)
+        ng = std::max(1, std::min(std::max(P.K / 4, 1), (4 * g->bwd_halves * g->n_sm + min_tiles - 1) / min_tiles));
+    const int kg = (P.K + ng - 1) / ng;
+    ng = (P.K + kg - 1) / kg;
     std::vector<int4> items;
     std::vector<int> ioff(nc + 1, 0);
     for (int c = 0; c < nc; ++c) {
@@ -124,8 +128,8 @@ cudaError_t build_icd_lists(mbir_geometry* g, int s, cudaStream_t st)
                 if (!(g->h_tvert[tr * TR * s + r0] < (float)(P.M - 1))) continue;
                 for (int tc = 0; tc * 32 < Wc; ++tc)
                     for (int gi = 0; gi < ng; ++gi) {
-                        const int t0 = gi * txg, t1 = std::min(P.n_tx, t0 + txg);
-                        items.push_back(make_int4(tr, tc, t0 | (t1 << 16), gi));
+                        const int k0 = gi * kg, k1 = std::min(P.K, k0 + kg);
+                        items.push_back(make_int4(tr, tc, k0 | (k1 << 16), gi));
                     }
             }
         }

@@ -386,7 +386,7 @@ struct mbir_geometry {
     double gamma_max;
     double fs;
     double z0, pitch;
-    // A^T r work list: (tile row, tile column, Tx range, group) and per-group partial images
+    // A^T r work list: (tile row, tile column, A-scan range, group) and per-group partial images
     int n_sm;
     int bwd_halves, bwd_stages;   // A^T r tile workers per CTA and residual ring depth
     int n_items, n_groups;
@@ -430,7 +430,7 @@ struct mbir_geometry {
     // coordinate descent work lists for colour spacing icd_s (built on the first call with that spacing):
     // A^T items per colour over lattice tiles, and (with records) per-colour record lists for A x
     int icd_s;
-    int icd_groups;             // transmitter groups of the colour A^T items
+    int icd_groups;             // A-scan chunks of the colour A^T items
     int* h_icd_item_off;        // host: s^2 + 1 offsets into d_icd_items
     int4* d_icd_items;
     float* w_icd_bpart;         // icd_groups x N partial images
@@ -443,6 +443,9 @@ struct mbir_geometry {
     long long* h_icd_win_off;   // host: s^2 + 1 offsets into d_icd_win
     int icd_win_sub;            // spans per window of those lists
     size_t icd_rec_bytes;
+    void* icd_exec;             // captured sweep (cudaGraphExec_t) and what it was captured for
+    double icd_exec_key[8];
+    void* icd_stream;           // capture stream (cudaStream_t)
     // profiling of the apply kernels inside mbir_reconstruct
     int prof;
     void* prof_state;      // host-side event lists (see map.cu)
