@@ -324,10 +324,12 @@ def run_gpu(args):
     e2e = {"value": args.steps * world / e_wall, "unit": "recons/s",
            "h2d_bytes_per_step": y_h.numel() * 4, "d2h_bytes_per_step": (x_h.numel() + g_h.numel()) * 4}
 
-    # roofline of the dominant apply kernel.  Each tap reads the four bilinear
-    # corners of the pulse table (4 x 4 B) from shared memory and does 4 FMA;
-    # shared-memory bandwidth (128 B/clk/SM) binds before the FP32 pipes
-    # (128 FMA/clk/SM) do, so it is the primary roofline.
+    # roofline of the dominant apply kernel.  CUDA-core kernels: each tap reads
+    # the four bilinear corners of the pulse table (4 x 4 B) from shared memory
+    # and does 4 FMA; shared-memory bandwidth (128 B/clk/SM) binds before the
+    # FP32 pipes (128 FMA/clk/SM) do, so it is their primary roofline.
+    # Tensor-core kernels (taps become MMAs): the record stream is the
+    # algorithmic traffic, the TAB-mode bound of the path (HBM).
     pk, src = peaks()
     pairs, taps = geo.count_taps()
     fwd_ms = kt["forward_ms"] / max(kt["forward_launches"], 1)
@@ -340,6 +342,7 @@ def run_gpu(args):
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12       # TFLOP/s
     flops = 8.0 * taps
     algo_bytes = 4.0 * (N + K * Mn)                      # x and one A-scan array in HBM
+    tc_dom = bool(geo.info.forward_tensor_cores if dom == "forward" else geo.info.adjoint_tensor_cores)
     roofline = {"bound": "alu", "resource": "shared-memory load bandwidth (pulse-table corners per tap)",
                 "kernel": dom, "achieved": smem_bytes / (dom_ms * 1e-3) / 1e9, "peak": smem_peak,
                 "unit": "GB/s", "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak,
@@ -357,6 +360,25 @@ def run_gpu(args):
                         "achieved_gbs": algo_bytes / (dom_ms * 1e-3) / 1e9,
                         "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),
                         "frac": algo_bytes / (dom_ms * 1e-3) / 1e9 / float(pk.get("hbm_gbs", 6800.0))}}
+    if tc_dom:
+        # 12 B per active pair is the smallest FP32 record (delay, weight, attenuation coordinate); the
+        # stored records hold 24 B (pixel, first tap | table row | flag, four bilinear weights x w) and
+        # the apply reads 4 B more of gathered x (A x) or writes 4 B of contribution (A^T r)
+        rec_bytes = 12.0 * pairs + algo_bytes
+        hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+        name = "fwd_tc32_kernel" if dom == "forward" else "bwd_tc32_kernel"
+        roofline = {"bound": "hbm", "resource": "HBM: the TAB record stream (latency-bound record scatter)",
+                    "kernel": dom + " (tensor cores)", "achieved": rec_bytes / (dom_ms * 1e-3) / 1e9,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": rec_bytes / (dom_ms * 1e-3) / 1e9 / hbm_peak,
+                    "traffic": measured_traffic(name),
+                    "traffic_note": "DRAM read+write bytes per launch (ncu)",
+                    "peak_source": f"hbm_gbs ({src})", "algorithmic_bytes_per_launch": rec_bytes,
+                    "bytes_per_pair_minimum": 12, "bytes_per_pair_used": 28, "active_pairs": pairs,
+                    "taps_per_launch": taps, "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
+                    "shared_memory_tap_model": {"achieved_gbs": smem_bytes / (dom_ms * 1e-3) / 1e9,
+                                                "peak_gbs": smem_peak,
+                                                "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak}}
+
     # per timed reconstruction: the projection of y, then 9 kernels per iteration (A^T r and its group
     # reduction, prior gradient, PR+ scalars, direction, A x, projection, step, update); the ncu launch
     # list of this command agrees (451 for 50 iterations; the host-buffer call adds A x and the

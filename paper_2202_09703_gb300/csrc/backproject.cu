@@ -92,31 +92,35 @@ __global__ void backproject_reduce_kernel(GeomParams P, const RowInfo* __restric
 }
 
 // b on the pixels (r, c) = (i s + r0, j s + c0) of one lattice, lat = (s, r0, c0), Wc x Hc of them, from
-// the partial images of its items (same order and compensation as above); pixels of lattice tiles that
-// cannot reach the record (no items) are zero.  Other pixels of b are not written.
+// the partial images of its items: one warp per pixel, lane l compensating groups l, l + 32, ..., then a
+// fixed shuffle tree (deterministic); pixels of lattice tiles that cannot reach the record (no items) are
+// zero.  Other pixels of b are not written.
 __global__ void backproject_reduce_lattice_kernel(GeomParams P, const RowInfo* __restrict__ rows,
                                                   const float* __restrict__ partial, int ngroups, int3 lat, int Wc,
                                                   int Nc, float* __restrict__ b)
 {
     const int N = P.W * P.H;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= Nc) return;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (t >= Nc) return;                         // whole warps
     const int ri = t / Wc, ci = t - ri * Wc;
     const int row = ri * lat.x + lat.y, col = ci * lat.x + lat.z;
     const int v = row * P.W + col;
     const int row0 = (ri / kBwdRows) * kBwdRows * lat.x + lat.y;
     if (__ldg(&rows[row0].tvert) >= (float)(P.M - 1)) {
-        b[v] = 0.0f;
+        if (lane == 0) b[v] = 0.0f;
         return;
     }
     float s = 0.0f, c = 0.0f;
-    for (int g = 0; g < ngroups; ++g) {
+    for (int g = lane; g < ngroups; g += 32) {
         const float val = partial[(size_t)g * N + v];
         const float t2 = s + val;
         c += (fabsf(s) >= fabsf(val)) ? (s - t2) + val : (val - t2) + s;
         s = t2;
     }
-    b[v] = s + c;
+    float tot = s + c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) b[v] = tot;
 }
 
 // Estimated A^T r cost per (16 x 32 pixel tile, transmitter position), in
@@ -335,8 +339,8 @@ static cudaError_t launch_bwd_lattice_t(const mbir_geometry* g, const int4* item
     const int Hc = (P.H - lat.y + lat.x - 1) / lat.x, Wc = (P.W - lat.z + lat.x - 1) / lat.x;
     const int Nc = Hc * Wc;
     if (Nc > 0)
-        backproject_reduce_lattice_kernel<<<(Nc + 255) / 256, 256, 0, st>>>(P, g->d_rows, partial, ngroups, lat, Wc,
-                                                                           Nc, b);
+        backproject_reduce_lattice_kernel<<<(Nc + 7) / 8, 256, 0, st>>>(P, g->d_rows, partial, ngroups, lat, Wc, Nc,
+                                                                       b);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,10 @@ struct ReqDesc {
     const int* tf_n0off;
     const ushort4* tf_grpoff;
     const int* tf_order;
+    int tf32;              // FP32 tensor-core A x pool available
+    Tf3Layout tf3l;
+    const uint4* tf3_bop;
+    const uint4* tf3_grpoff;
     long long nrec;        // records of the geometry
 };
 
@@ -499,6 +503,30 @@ __global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc_kernel(EngLists L)
     tc_header_release(smem, tmem, kTfCols);
 }
 
+// q = A d of the FP32 form on the tensor cores over every active request
+__global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc32_kernel(EngLists L)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, kTf3Cols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
+    uint32_t phase = 0, bphase = 0;
+    const int nreq = L.counts[0];
+    if (nreq > 0) {
+        const int r0 = L.start[gridDim.x + blockIdx.x] % nreq;
+        for (int t = 0; t < nreq; ++t) {
+            const int rq = (r0 + t) % nreq;
+            const ReqDesc& R = L.desc[rq];
+            if (!eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
+            const TcFwd32View V{R.P, R.tf3l, R.tf3_bop, R.tab, R.rec_off, R.tf_n0off, R.tf3_grpoff, R.rkey, R.rw,
+                                R.tf_order, R.tc_contrib, R.q, R.P.Mp, L.pool + 2 * rq};
+            if (!tc_forward32_pool(V, smem, tmem, phase, bphase, R.D.status)) break;
+            __syncthreads();
+        }
+    }
+    tc_header_release(smem, tmem, kTf3Cols);
+}
+
 // in-place direct-arrival projection of q per (request, A-scan), FP64 |q|^2
 __global__ void eng_proj_kernel(EngLists L)
 {
@@ -780,6 +808,10 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.tf_n0off = g->d_tf_n0off;
     d.tf_grpoff = g->d_tf_grpoff;
     d.tf_order = g->d_tf_order;
+    d.tf32 = g->d_tf3_bop ? 1 : 0;
+    d.tf3l = g->tf3;
+    d.tf3_bop = g->d_tf3_bop;
+    d.tf3_grpoff = g->d_tf3_grpoff;
     d.nrec = g->n_records;
 }
 
@@ -891,7 +923,7 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 }
 
 // One MAP iteration of every active request, as launched inside the graph.
-cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, cudaStream_t st)
+cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cudaStream_t st)
 {
     const int G = E->n_sm, SG = E->n_sm * 8;
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
@@ -913,6 +945,9 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, cudaStream_t s
     if (tc && bf16) {
         eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
         eng_fwd_tc_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
+    } else if (tc && tcf) {
+        eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
+        eng_fwd_tc32_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
     }
     else if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     else eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
@@ -944,6 +979,7 @@ int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e != cudaSuccess) { delete E; return MBIR_ERR_CUDA; }
     *out = E;
     return MBIR_OK;
@@ -1051,15 +1087,19 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
     bool tc = true;                      // tensor-core pools when every request of the step has them
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
-    for (Request* r : E->sel)
+    bool tcf = !bf16;                    // FP32: tensor-core A x too when every request has its tables
+    for (Request* r : E->sel) {
         if (!r->contrib) tc = false;
-    if (grew || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != (int)tc) {
+        if (!r->g->d_tf3_bop) tcf = false;
+    }
+    const int gtc = (int)tc + 2 * (int)(tc && tcf);
+    if (grew || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != gtc) {
         if (E->graph) { cudaGraphExecDestroy(E->graph); E->graph = nullptr; }
         cudaStream_t cs;
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         cudaGraph_t graph;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, cs);
+        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, tcf, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&E->graph, graph, 0);
@@ -1067,7 +1107,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         cudaStreamDestroy(cs);
         if (e != cudaSuccess) return MBIR_ERR_CUDA;
         E->graph_bf16 = (int)bf16;
-        E->graph_tc = (int)tc;
+        E->graph_tc = gtc;
     }
     e = cudaGraphLaunch(E->graph, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;

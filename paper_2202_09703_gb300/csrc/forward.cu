@@ -251,6 +251,7 @@ cudaError_t launch_forward(const mbir_geometry* g, const float* x, float* y_f32,
                            int out_stride, cudaStream_t st)
 {
     if (g->d_tf_bop) return launch_forward_tc(g, x, y_f32, y_bf16, out_stride, st);
+    if (g->d_tf3_bop && y_f32) return launch_forward_tc32(g, x, y_f32, out_stride, st);
     if (g->d_rec_key) return launch_forward_sorted(g, x, y_f32, y_bf16, out_stride, st);
     const bool bf = g->P.precision == MBIR_PREC_BF16;
     if (g->P.mode == MBIR_MODE_TAB)

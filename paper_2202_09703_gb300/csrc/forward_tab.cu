@@ -141,10 +141,14 @@ __global__ void __launch_bounds__(kSortThreads)
     __syncthreads();
     __threadfence_block();
     // order each bucket by (phase class = table phase mod 4, pixel index) (insertion sort; buckets hold a
-    // few dozen records): the tensor-core A x then finds each phase class's records as one range
+    // few dozen records): the tensor-core A x then finds each phase class's records as one range.  In the
+    // FP32 form the half of the table rows (phase >= (Q + 1) / 2) comes first, as that A x takes the
+    // halves in turn.
     const int R = P.Q + 1;
-    auto order_key = [R](int2 k) {
-        return ((long long)((((k.y >> 1) & 0xfff) % R) & 3) << 32) | (long long)(unsigned)k.x;
+    const int hsplit = P.precision == MBIR_PREC_BF16 ? (1 << 30) : R / 2;
+    auto order_key = [R, hsplit](int2 k) {
+        const int ph = ((k.y >> 1) & 0xfff) % R;
+        return ((long long)((ph >= hsplit ? 4 : 0) + (ph & 3)) << 32) | (long long)(unsigned)k.x;
     };
     for (int t = threadIdx.x; t < P.M; t += blockDim.x) {
         const long long a = base + start[t], b = base + start[t + 1];

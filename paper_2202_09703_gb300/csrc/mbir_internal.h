@@ -347,6 +347,24 @@ struct TfLayout {
     bool ok;
 };
 
+// Shared-memory layout of the tensor-core A x of the FP32 form: two phase-aligned halves of the table
+// rows, each half's two-part FP16 table operand resident while its records are scattered.
+struct Tf3Layout {
+    int phsplit;           // first phase of the second half (both halves hold it)
+    int ncol[2];           // table rows (sum columns) of each half: phases x G
+    int kb;                // MMA K of a half (columns, multiple of 16)
+    int kc;                // columns converted and multiplied per chunk
+    int nbuf;              // chunk buffers (2: a chunk is converted while the previous one is multiplied)
+    int ntap;              // MMA N: taps rounded up to 16
+    int astride;           // FP32 row stride of the sums (floats, multiple of 4)
+    int ustride;           // row stride of the product tile (floats)
+    int ylen;              // output window (floats)
+    size_t bhalf;          // bytes of one half's two-part table operand
+    int texp;              // table scale: operand = table x 2^texp (largest magnitude in [2^14, 2^15))
+    size_t off_b, off_s, off_a, off_y, smem;
+    bool ok;
+};
+
 struct mbir_geometry {
     int device;
     mbir::GeomParams P;
@@ -424,6 +442,10 @@ struct mbir_geometry {
     ushort4* d_tf_grpoff;  // phase-class starts inside every (A-scan, n0) bucket, K x M
     int* d_tf_order;       // A-scans by decreasing record count
     int* d_tf_counter;
+    // tensor-core A x of the FP32 form (see tc_forward.cu); shares the n0 offsets, order and counter above
+    Tf3Layout tf3;
+    uint4* d_tf3_bop;      // both halves' two-part FP16 table operand images (taps x table rows, K-major)
+    uint4* d_tf3_grpoff;   // starts of the (half, phase class) groups inside every (A-scan, n0) bucket, K x M
     long long n_records;
     // |A_v|^2 per pixel for the coordinate descent (computed on its first call)
     float* w_colnorm;
@@ -486,9 +508,11 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e_bf, float* b, cudaStream_t st);
 cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, float* b, cudaStream_t st);
 TfLayout tf_layout(const GeomParams& P);
+Tf3Layout tf3_layout(const GeomParams& P);
 cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
                               cudaStream_t st);
+cudaError_t launch_forward_tc32(const mbir_geometry* g, const float* x, float* yf, int stride, cudaStream_t st);
 cudaError_t launch_column_norms(const mbir_geometry* g, float* out, cudaStream_t st);
 cudaError_t build_colour_records(mbir_geometry* g, int s, cudaStream_t st);
 cudaError_t launch_forward_colour(const mbir_geometry* g, int c, const float* x, float* yf, int stride,

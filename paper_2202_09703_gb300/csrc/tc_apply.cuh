@@ -8,6 +8,8 @@
 #pragma once
 
 #include "apply_common.cuh"
+#include <cuda_fp16.h>
+
 #include "tc_common.cuh"
 
 namespace mbir {
@@ -21,6 +23,9 @@ constexpr int kTfThreads = 512;      // scatter: 4 threads per n0 (phase classes
 constexpr int kTfUnroll = 8;         // records in flight per scatter thread
 constexpr int kTfStage = 6;          // 8-column groups per thread held in registers while converting
 constexpr uint32_t kTfCols = 128;    // tensor-memory columns of the A x kernels
+constexpr uint32_t kTf3Cols = 256;   // FP32 A x: one 128-column tile per row half
+constexpr int kTf3HalfCols = 128;
+constexpr int kTf3Unroll = 4;        // FP32 A x: records of each of the two groups in flight per thread
 static_assert(kTcThreads == kTfThreads, "the engine runs both pools with one block size");
 
 // A^T of one geometry / request.
@@ -74,13 +79,32 @@ struct TcFwdView {
     int* counter;
 };
 
+// FP32 A x of one geometry / request (three-part BF16 split, two phase-aligned halves).
+struct TcFwd32View {
+    GeomParams P;
+    Tf3Layout T;
+    const uint4* bop;                // half 0 image then half 1 image (three parts each)
+    const float2* tab;               // FP32 kernel table (for the tau = t0 tap)
+    const long long* rec_off;
+    const int* n0_off;
+    const uint4* grp_off;            // per (A-scan, n0): starts of the (half, class) groups 1..7 (16 bits each)
+    const int2* rkey;
+    const float4* rw;
+    const int* order;
+    const float* xr;
+    float* y;
+    int out_stride;
+    int* counter;
+};
+
 // Shared-memory header of the tensor-core kernels.
 __device__ __forceinline__ void tc_header_init(unsigned char* smem, uint32_t ncols)
 {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(bar), 1);
-        mbar_init(smem_u32(smem + 32), 1);          // operand copies of the FP32 adjoint
+        mbar_init(smem_u32(smem + 32), 1);          // operand copies of the FP32 kernels
+        mbar_init(smem_u32(smem + 40), 1);          // second MMA buffer of the FP32 A x
         *reinterpret_cast<volatile int*>(smem + 20) = 0;
         fence_mbar_init();
     }
@@ -282,6 +306,16 @@ __device__ __forceinline__ void split3(float x, unsigned short& a, unsigned shor
     a = __bfloat16_as_ushort(p1);
     b = __bfloat16_as_ushort(p2);
     c = __bfloat16_as_ushort(p3);
+}
+
+// x = a + b with a the FP16 rounding of x and b that of the remainder (22 significant bits for
+// |x| in [2^-3, 2^15]; the caller scales x into that range by a power of two).
+__device__ __forceinline__ void split2h(float x, unsigned short& a, unsigned short& b)
+{
+    const __half p1 = __float2half_rn(x);
+    const __half p2 = __float2half_rn(x - __half2float(p1));
+    a = __half_as_ushort(p1);
+    b = __half_as_ushort(p2);
 }
 
 // Contributions of a batch's records whose phase falls in `half`, from that
@@ -689,6 +723,293 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
         }
         __syncthreads();
     }
+    return !*abort_flag;
+}
+
+// Drains the FP32 A x items (A-scans, largest first) of V.  Per tile of 128
+// first-tap samples and per row half (phases [0, phsplit] and [phsplit, Q]):
+// the sums S[n0][row] of the half's records are accumulated in FP32 (four
+// threads per n0, one per phase class, buckets ordered by (half, class)),
+// scaled by a power of two that brings their largest magnitude into
+// [2^14, 2^15), converted chunk by chunk into two FP16 parts (22 significant
+// bits) and multiplied by the half's two-part table operand (scaled the same
+// way on the host): the three products S_1 T_1 + S_1 T_2 + S_2 T_1 (the
+// dropped S_2 T_2 is below 2^-22 of the result) accumulate in the half's own
+// tensor-memory tile.  U = U_0 / (s_0 t) + U_1 / (s_1 t) then gives the
+// anti-diagonal sums added to y.  The other half's table operand is
+// bulk-copied while a half's records are scattered (mbarrier at smem + 32);
+// smem + 48 holds the halves' scale exponents, smem + 64 the warp maxima.
+__device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned char* smem, uint32_t tmem,
+                                                  uint32_t& phase, uint32_t& bphase, int* status)
+{
+    // phase bit 0: the MMA barrier of chunk buffer 0 (smem + 0), bit 1: of buffer 1 (smem + 40)
+    const GeomParams& P = V.P;
+    const Tf3Layout& T = V.T;
+    uint64_t* bbar = reinterpret_cast<uint64_t*>(smem + 32);
+    volatile int* next = reinterpret_cast<volatile int*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    unsigned char* sB = smem + T.off_b;
+    unsigned char* sA = smem + T.off_a;
+    float* sS = reinterpret_cast<float*>(smem + T.off_s);
+    float* sY = reinterpret_cast<float*>(smem + T.off_y);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = P.Q + 1, S = table_stride(P.Tw4);
+    const float2* __restrict__ tab = V.tab;
+    const long long* __restrict__ rec_off = V.rec_off;
+    const int* __restrict__ n0_off = V.n0_off;
+    const uint4* __restrict__ grp_off = V.grp_off;
+    const int2* __restrict__ rkey = V.rkey;
+    const float4* __restrict__ rw = V.rw;
+    const int* __restrict__ order = V.order;
+    const float* __restrict__ xr = V.xr;
+    const unsigned char* bimg = reinterpret_cast<const unsigned char*>(V.bop);
+
+    auto copy_half = [&](int h) {               // tid 0: bulk copy of half h's operand image
+        mbar_arrive_expect_tx(smem_u32(bbar), (uint32_t)T.bhalf);
+        bulk_g2s(smem_u32(sB), bimg + (h ? T.bhalf : 0), (uint32_t)T.bhalf, smem_u32(bbar));
+    };
+    int copies = 1, waits = 0;                   // the same on every thread
+    if (tid == 0) copy_half(0);
+    const int ntile = (P.M + kTfTile - 1) / kTfTile;
+    const uint32_t lbo = 128, sboA = (uint32_t)(T.kc / 8) * 128, sboB = (uint32_t)(T.kb / 8) * 128;
+    const uint32_t idesc = umma_idesc_f16(kTfTile, T.ntap);
+    const uint32_t apart = (uint32_t)(kTfTile * T.kc * 2), bpart = (uint32_t)(T.ntap * T.kb * 2);
+    const int si = tid >> 2, pj = tid & 3;            // scatter role: n0 row and phase class
+    volatile int* sexp = reinterpret_cast<volatile int*>(smem + 48);
+    float* wmax = reinterpret_cast<float*>(smem + 64);
+    // the sums start at zero; every later pass that reads them (conversion, anti-diagonals) clears them
+    for (int i = tid; i < kTfTile * max(T.astride, T.ustride); i += blockDim.x) sS[i] = 0.0f;
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) *next = atomicAdd(V.counter, 1);
+        __syncthreads();
+        const int idx = *next;
+        if (idx >= P.K) break;
+        const int k = __ldg(order + idx);
+        const long long base = __ldg(rec_off + k);
+        const int* no = n0_off + (size_t)k * (P.M + 1);
+        for (int i = tid; i < T.ylen; i += blockDim.x) sY[i] = 0.0f;
+        // bucket bounds and group starts of this thread's n0, one tile ahead of their use
+        int ra_n = 0, rz_n = 0;
+        uint4 go_n = make_uint4(0u, 0u, 0u, 0u);
+        if (si < P.M) {
+            ra_n = __ldg(no + si);
+            rz_n = __ldg(no + si + 1);
+            go_n = __ldg(grp_off + (size_t)k * P.M + si);
+        }
+        for (int t = 0; t < ntile; ++t) {
+            const int ts = t * kTfTile;
+            const int n0 = ts + si;
+            const int ra = ra_n, rz = rz_n;
+            int gs[9];
+            {
+                const uint4 go = go_n;
+                const int n1 = n0 + kTfTile;
+                ra_n = rz_n = 0;
+                go_n = make_uint4(0u, 0u, 0u, 0u);
+                if (t + 1 < ntile && n1 < P.M) {
+                    ra_n = __ldg(no + n1);
+                    rz_n = __ldg(no + n1 + 1);
+                    go_n = __ldg(grp_off + (size_t)k * P.M + n1);
+                }
+                gs[0] = 0;
+                gs[1] = (int)(go.x & 0xffffu); gs[2] = (int)(go.x >> 16);
+                gs[3] = (int)(go.y & 0xffffu); gs[4] = (int)(go.y >> 16);
+                gs[5] = (int)(go.z & 0xffffu); gs[6] = (int)(go.z >> 16);
+                gs[7] = (int)(go.w & 0xffffu); gs[8] = rz - ra;
+            }
+            float flag_corr = 0.0f;
+            for (int h = 0; h < 2; ++h) {
+                const int phb = h ? T.phsplit : 0;
+                float bound = 0.0f;                  // sum of |contributions| of this thread: >= its |S| cells
+                // scatter: thread (n0 row si, phase class pj) owns the cells of this half whose phase is pj
+                // (mod 4): upper-row corners of class pj - 1 records, then lower-row corners of class pj
+                float* arow = sS + si * T.astride;
+                // both groups' records are fetched together, kTf3Unroll of each per round (usually one round)
+                int qa0 = ra + gs[4 * h + ((pj + 3) & 3)], qz0 = ra + gs[4 * h + ((pj + 3) & 3) + 1];
+                int qa1 = ra + gs[4 * h + pj], qz1 = ra + gs[4 * h + pj + 1];
+                while (qa0 < qz0 || qa1 < qz1) {
+                    const int n0c = min(qz0 - qa0, kTf3Unroll), n1c = min(qz1 - qa1, kTf3Unroll);
+                    int2 k0[kTf3Unroll], k1[kTf3Unroll];
+                    float4 w0[kTf3Unroll], w1[kTf3Unroll];
+                    float x0[kTf3Unroll], x1[kTf3Unroll];
+#pragma unroll
+                    for (int u = 0; u < kTf3Unroll; ++u) {
+                        if (u < n0c) {
+                            k0[u] = __ldg(rkey + base + qa0 + u);
+                            w0[u] = __ldg(rw + base + qa0 + u);
+                            x0[u] = __ldg(xr + base + qa0 + u);
+                        }
+                        if (u < n1c) {
+                            k1[u] = __ldg(rkey + base + qa1 + u);
+                            w1[u] = __ldg(rw + base + qa1 + u);
+                            x1[u] = __ldg(xr + base + qa1 + u);
+                        }
+                    }
+                    // class pj - 1: upper-row corners (record order)
+#pragma unroll
+                    for (int u = 0; u < kTf3Unroll; ++u) {
+                        if (u >= n0c) break;
+                        const int trow = (k0[u].y >> 1) & 0xfff;
+                        const int gi = trow / R, ph = trow - gi * R;
+                        const int g1 = min(gi + 1, P.G - 1);
+                        const int c = (ph + 1 - phb) * P.G;
+                        arow[c + gi] += w0[u].z * x0[u];
+                        arow[c + g1] += w0[u].w * x0[u];
+                        bound += (fabsf(w0[u].z) + fabsf(w0[u].w)) * fabsf(x0[u]);
+                        if (k0[u].y & 1) {
+                            // tau = t0 exactly: the last tap of the upper phase row lies outside
+                            const float2 tl = __ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1);
+                            flag_corr += x0[u] * (w0[u].z * tl.x + w0[u].w * tl.y);
+                        }
+                    }
+                    // class pj: lower-row corners (record order)
+#pragma unroll
+                    for (int u = 0; u < kTf3Unroll; ++u) {
+                        if (u >= n1c) break;
+                        const int trow = (k1[u].y >> 1) & 0xfff;
+                        const int gi = trow / R, ph = trow - gi * R;
+                        const int g1 = min(gi + 1, P.G - 1);
+                        const int c = (ph - phb) * P.G;
+                        arow[c + gi] += w1[u].x * x1[u];
+                        arow[c + g1] += w1[u].y * x1[u];
+                        bound += (fabsf(w1[u].x) + fabsf(w1[u].y)) * fabsf(x1[u]);
+                    }
+                    qa0 += n0c;
+                    qa1 += n1c;
+                }
+                // the half's scale: a bound of the largest |S| into [2^14, 2^15) (a power of two: exact)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_xor_sync(0xffffffffu, bound, o));
+                if (lane == 0) wmax[warp] = bound;
+                __syncthreads();                     // every record of the half is in S
+                int se = 0;
+                {
+                    float m = 0.0f;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+                    int ex = 0;
+                    frexpf(m, &ex);
+                    se = m > 0.0f ? min(15 - ex, 126) : 0;
+                }
+                if (tid == 0) sexp[h] = se;
+                const float scl = __int_as_float((se + 127) << 23);
+                // this half's table operand has landed (copied during the scatter)
+                if (!mbar_wait_bounded(smem_u32(bbar), bphase, status)) *abort_flag = 1;
+                bphase ^= 1u;
+                ++waits;
+                __syncthreads();                     // uniform flag
+                // chunks of kc columns: three BF16 parts of the sums, then the six products; with two chunk
+                // buffers a chunk is converted while the previous chunk's products run
+                int pending = 0;                     // bit b: products reading buffer b not yet waited for
+                for (int c0 = 0, q = 0; c0 < T.kb; c0 += T.kc, ++q) {
+                    const int b = T.nbuf == 2 ? (q & 1) : 0;
+                    if (pending & (1 << b)) {
+                        if (!mbar_wait_bounded(smem_u32(smem + (b ? 40 : 0)), (phase >> b) & 1u, status))
+                            *abort_flag = 1;
+                        phase ^= 1u << b;
+                        pending &= ~(1 << b);
+                        __syncthreads();
+                        if (*abort_flag) break;
+                    }
+                    unsigned char* sAb = sA + (size_t)b * 2 * apart;
+                    const int cw = min(T.kc, T.kb - c0), kc8 = cw / 8;
+                    for (int c = tid; c < kTfTile * kc8; c += blockDim.x) {
+                        const int i = c / kc8, j = c - i * kc8;
+                        float4* sp = reinterpret_cast<float4*>(sS + i * T.astride + c0 + 8 * j);
+                        const float4 v0 = sp[0], v1 = sp[1];
+                        sp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        sp[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                        unsigned short a[8], b2[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) split2h(vv[q] * scl, a[q], b2[q]);
+                        const uint32_t off = kmajor_offset(i, 8 * j, T.kc);
+                        *reinterpret_cast<uint4*>(sAb + off) =
+                            make_uint4(a[0] | (uint32_t)a[1] << 16, a[2] | (uint32_t)a[3] << 16,
+                                       a[4] | (uint32_t)a[5] << 16, a[6] | (uint32_t)a[7] << 16);
+                        *reinterpret_cast<uint4*>(sAb + apart + off) =
+                            make_uint4(b2[0] | (uint32_t)b2[1] << 16, b2[2] | (uint32_t)b2[3] << 16,
+                                       b2[4] | (uint32_t)b2[5] << 16, b2[6] | (uint32_t)b2[7] << 16);
+                    }
+                    fence_async_smem();
+                    __syncthreads();
+                    if (tid == 0) {
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sAb), b0 = smem_u32(sB) + (uint32_t)(c0 / 8) * 128;
+                        const int terms[3][2] = {{0, 0}, {0, 1}, {1, 0}};
+                        for (int s = 0; s < cw / 16; ++s)
+                            for (int tq = 0; tq < 3; ++tq)
+                                umma_bf16(tmem + (uint32_t)(h * kTf3HalfCols),
+                                          umma_desc(a0 + terms[tq][0] * apart + 256 * s, lbo, sboA),
+                                          umma_desc(b0 + terms[tq][1] * bpart + 256 * s, lbo, sboB), idesc,
+                                          c0 > 0 || s > 0 || tq > 0);
+                        umma_commit(smem_u32(smem + (b ? 40 : 0)));
+                    }
+                    pending |= 1 << b;
+                }
+                // every product of this half done: the table buffer and the chunk buffers are free
+                for (int b = 0; b < 2; ++b)
+                    if (pending & (1 << b)) {
+                        if (!mbar_wait_bounded(smem_u32(smem + (b ? 40 : 0)), (phase >> b) & 1u, status))
+                            *abort_flag = 1;
+                        phase ^= 1u << b;
+                    }
+                __syncthreads();
+                tc_fence_after();
+                if (*abort_flag) break;
+                // the table buffer is free: the other half next (or half 0 of the next tile / item)
+                if (tid == 0) copy_half(1 - h);
+                ++copies;
+            }
+            if (*abort_flag) break;
+            // the four class threads of a sample are adjacent lanes: their flag corrections in class order
+            {
+                const float f1 = __shfl_down_sync(0xffffffffu, flag_corr, 1);
+                const float f2 = __shfl_down_sync(0xffffffffu, flag_corr, 2);
+                const float f3 = __shfl_down_sync(0xffffffffu, flag_corr, 3);
+                if (pj == 0 && n0 < P.M) sY[n0 + P.Tw] -= ((flag_corr + f1) + f2) + f3;
+            }
+            // U = U_0 / (s_0 t) + U_1 / (s_1 t) (tensor memory) -> shared (over the sums), rows = n0 - ts
+            {
+                const int q = warp & 3, part = warp >> 2;
+                const int row = q * 32 + lane;
+                const int cwid = T.ntap / 4;
+                const float i0 = __int_as_float((127 - sexp[0]) << 23), i1 = __int_as_float((127 - sexp[1]) << 23);
+                const float it = __int_as_float((127 - T.texp) << 23);
+                for (int c = part * cwid; c < part * cwid + cwid; c += 4) {
+                    float v0[4], v1[4];
+                    tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v0);
+                    tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(kTf3HalfCols + c), v1);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sS[row * T.ustride + c + j] = (v0[j] * i0) * it + (v1[j] * i1) * it;
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            // anti-diagonals: y[ts + 1 + j] += sum_i U[i][j - i]
+            for (int j = tid; j < kTfTile + T.ntap - 1; j += blockDim.x) {
+                float acc = 0.0f;
+                const int i0 = max(0, j - T.ntap + 1), i1 = min(kTfTile - 1, j);
+                for (int i = i0; i <= i1; ++i) {
+                    acc += sS[i * T.ustride + j - i];
+                    sS[i * T.ustride + j - i] = 0.0f;    // each product is read once: the sums are clear again
+                }
+                sY[ts + 1 + j] += acc;
+            }
+            __syncthreads();
+        }
+        if (*abort_flag) break;
+        float* yo = V.y + (size_t)k * V.out_stride;
+        for (int n = tid; n < V.out_stride; n += blockDim.x) yo[n] = n < P.M ? sY[n] : 0.0f;
+        __syncthreads();
+    }
+    // no operand copy may outlive the pool (bounded)
+    while (waits < copies) {
+        mbar_wait_bounded(smem_u32(bbar), bphase, status);
+        bphase ^= 1u;
+        ++waits;
+    }
+    __syncthreads();
     return !*abort_flag;
 }
 

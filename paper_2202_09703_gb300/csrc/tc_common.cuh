@@ -32,10 +32,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Instruction descriptor: D FP32, A and B BF16, both K-major, M x N.
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M x N.  (The same MMA instruction serves
+// FP16 operands with the format fields 0.)
 __device__ __forceinline__ uint32_t umma_idesc_bf16(int m, int n)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// Instruction descriptor: D FP32, A and B FP16, both K-major, M x N.
+__device__ __forceinline__ uint32_t umma_idesc_f16(int m, int n)
+{
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 // D[tmem] (+)= A * B^T, issued by one thread.

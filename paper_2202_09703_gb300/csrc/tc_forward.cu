@@ -14,6 +14,7 @@
 // that the FP32 accumulator stays small.  The tau = t0 tap of flagged pairs
 // (outside the open window of eq. 10) is subtracted from y directly.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "tc_apply.cuh"
@@ -48,6 +49,33 @@ TfLayout tf_layout(const GeomParams& P)
     return L;
 }
 
+Tf3Layout tf3_layout(const GeomParams& P)
+{
+    Tf3Layout L{};
+    const int R = P.Q + 1;
+    L.phsplit = R / 2;
+    L.ncol[0] = (L.phsplit + 1) * P.G;
+    L.ncol[1] = (R - L.phsplit) * P.G;
+    L.kb = (std::max(L.ncol[0], L.ncol[1]) + 15) & ~15;
+    L.kc = std::min(48, L.kb);
+    L.ntap = (P.Tw + 15) & ~15;
+    L.astride = (L.kb + 4 + 3) & ~3;                   // float4 rows, not a multiple of 32 banks
+    L.ustride = L.ntap + 1;
+    L.bhalf = (size_t)2 * L.ntap * L.kb * 2;
+    L.off_b = 1024;
+    L.off_s = (L.off_b + L.bhalf + 1023) & ~(size_t)1023;
+    L.off_a = (L.off_s + (size_t)kTfTile * std::max(L.astride, L.ustride) * 4 + 1023) & ~(size_t)1023;
+    L.ylen = ((P.M + kTfTile - 1) / kTfTile) * kTfTile + L.ntap + 2;
+    for (L.nbuf = 2; L.nbuf >= 1; --L.nbuf) {
+        L.off_y = (L.off_a + (size_t)L.nbuf * 2 * kTfTile * L.kc * 2 + 127) & ~(size_t)127;
+        L.smem = L.off_y + (size_t)L.ylen * 4;
+        if (L.smem <= 227 * 1024) break;
+    }
+    if (L.nbuf < 1) L.nbuf = 1;
+    L.ok = R >= 2 && L.ntap <= 128 && L.smem <= 227 * 1024 && (P.Q + 1) * P.G <= 4096 && L.kc % 16 == 0;
+    return L;
+}
+
 __global__ void tc_gather_x_kernel(long long nrec, const int2* __restrict__ rkey, const float* __restrict__ x,
                                    float* __restrict__ xr)
 {
@@ -62,6 +90,16 @@ __global__ void __launch_bounds__(kTfThreads, 1) fwd_tc_kernel(TcFwdView V, int*
     uint32_t phase = 0;
     tc_forward_pool(V, smem, tmem, phase, status);
     tc_header_release(smem, tmem, kTfCols);
+}
+
+__global__ void __launch_bounds__(kTfThreads, 1) fwd_tc32_kernel(TcFwd32View V, int* __restrict__ status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, kTf3Cols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    uint32_t phase = 0, bphase = 0;
+    tc_forward32_pool(V, smem, tmem, phase, bphase, status);
+    tc_header_release(smem, tmem, kTf3Cols);
 }
 
 // first record of every sample n0 of every A-scan (records sorted by n0)
@@ -105,24 +143,80 @@ __global__ void tf_grp_off_kernel(GeomParams P, const long long* __restrict__ re
     grp_off[i] = make_ushort4((unsigned short)st[1], (unsigned short)st[2], (unsigned short)st[3], 0);
 }
 
-// Tables of the tensor-core A x for a BF16 geometry with records;
-// cudaErrorNotSupported keeps the CUDA-core A x.
+// FP32 form: start of every (half, phase class) group inside every (A-scan, n0) bucket (buckets are
+// ordered by half, then class; half 1 = phases >= phsplit), groups 1..7 as 16-bit offsets.
+__global__ void tf3_grp_off_kernel(GeomParams P, int phsplit, const long long* __restrict__ rec_off,
+                                   const int2* __restrict__ rkey, const int* __restrict__ n0_off,
+                                   uint4* __restrict__ grp_off, int* __restrict__ too_long)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)P.K * P.M) return;
+    const int k = (int)(i / P.M), n = (int)(i - (long long)k * P.M);
+    const long long base = rec_off[k];
+    const int a = n0_off[(size_t)k * (P.M + 1) + n], z = n0_off[(size_t)k * (P.M + 1) + n + 1];
+    const int R = P.Q + 1;
+    if (z - a > 65535) atomicExch(too_long, 1);
+    int st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int c = 0;
+    for (int r = a; r < z; ++r) {
+        const int ph = (((rkey[base + r].y >> 1) & 0xfff) % R);
+        const int grp = (ph >= phsplit ? 4 : 0) + (ph & 3);
+        while (c < grp) st[++c] = r - a;
+    }
+    while (c < 7) st[++c] = z - a;
+    grp_off[i] = make_uint4((uint32_t)st[1] | (uint32_t)st[2] << 16, (uint32_t)st[3] | (uint32_t)st[4] << 16,
+                            (uint32_t)st[5] | (uint32_t)st[6] << 16, (uint32_t)st[7]);
+}
+
+// Tables of the tensor-core A x for a geometry with records (BF16 form: one BF16 table operand; FP32
+// form: both row halves' three-part operands); cudaErrorNotSupported keeps the CUDA-core A x.
 cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
 {
     const GeomParams& P = g->P;
+    const bool bf = P.precision == MBIR_PREC_BF16;
     // the record-ordered x of each apply lives in the adjoint's contribution buffer
-    if (P.precision != MBIR_PREC_BF16 || !g->d_rec_key || g->n_records <= 0 || !g->w_tc_contrib)
-        return cudaErrorNotSupported;
+    if (!g->d_rec_key || g->n_records <= 0 || !g->w_tc_contrib) return cudaErrorNotSupported;
     const TfLayout L = tf_layout(P);
-    if (!L.ok || (long long)P.K * (P.M + 1) >= (1LL << 31)) return cudaErrorNotSupported;
-    const int nq = P.Q * P.Tw + 1;
-    // table operand: row m (tap), column c = phase * G + plane; the second half starts at column k0
-    std::vector<__nv_bfloat16> bimg((size_t)L.ntap * L.kb, __float2bfloat16_rn(0.0f));
-    for (int c = 0; c < L.ncols; ++c) {
-        const int gpl = c % P.G, ph = c / P.G;
-        const int kcol = c < L.c0 ? c : L.k0 + (c - L.c0);
-        for (int m = 0; m < P.Tw; ++m)
-            bimg[kmajor_offset(m, kcol, L.kb) / 2] = __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
+    Tf3Layout L3 = tf3_layout(P);
+    if ((bf ? !L.ok : !L3.ok) || (long long)P.K * (P.M + 1) >= (1LL << 31)) return cudaErrorNotSupported;
+    const int nq = P.Q * P.Tw + 1, R = P.Q + 1;
+    std::vector<__nv_bfloat16> bimg;
+    if (bf) {
+        // table operand: row m (tap), column c = phase * G + plane; the second half starts at column k0
+        bimg.assign((size_t)L.ntap * L.kb, __float2bfloat16_rn(0.0f));
+        for (int c = 0; c < L.ncols; ++c) {
+            const int gpl = c % P.G, ph = c / P.G;
+            const int kcol = c < L.c0 ? c : L.k0 + (c - L.c0);
+            for (int m = 0; m < P.Tw; ++m)
+                bimg[kmajor_offset(m, kcol, L.kb) / 2] =
+                    __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
+        }
+    } else {
+        // per row half h (phases [0, phsplit] / [phsplit, Q]): the FP32 table as the CUDA-core kernels
+        // read it, times 2^texp (largest magnitude into [2^14, 2^15)), split into two FP16 parts
+        // t = t1 + t2; row m (tap), column (phase - first) * G + plane
+        float tmax = 0.0f;
+        for (size_t i = 0; i < (size_t)P.G * nq; ++i) tmax = std::max(tmax, std::fabs((float)g->tab_host[i]));
+        int ex = 0;
+        std::frexp(tmax, &ex);
+        L3.texp = tmax > 0.0f ? std::min(15 - ex, 126) : 0;
+        bimg.assign(L3.bhalf, __float2bfloat16_rn(0.0f));    // bhalf bytes = both halves' elements (16-bit)
+        __half* himg = reinterpret_cast<__half*>(bimg.data());
+        const size_t part = (size_t)L3.ntap * L3.kb;
+        for (int h = 0; h < 2; ++h) {
+            const int phb = h ? L3.phsplit : 0, phe = h ? R - 1 : L3.phsplit;
+            const size_t base = (size_t)h * 2 * part;
+            for (int ph = phb; ph <= phe; ++ph)
+                for (int gpl = 0; gpl < P.G; ++gpl)
+                    for (int m = 0; m < P.Tw; ++m) {
+                        const float t = std::ldexp((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph], L3.texp);
+                        const __half p1 = __float2half_rn(t);
+                        const __half p2 = __float2half_rn(t - __half2float(p1));
+                        const size_t o = kmajor_offset(m, (ph - phb) * P.G + gpl, L3.kb) / 2;
+                        himg[base + o] = p1;
+                        himg[base + part + o] = p2;
+                    }
+        }
     }
     // A-scans by decreasing record count
     std::vector<long long> roff((size_t)P.K + 1);
@@ -134,12 +228,13 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
                      [&](int a, int b) { return roff[a + 1] - roff[a] > roff[b + 1] - roff[b]; });
     uint4* d_b = nullptr;
     int *d_n0 = nullptr, *d_ord = nullptr, *d_ctr = nullptr;
-    ushort4* d_grp = nullptr;
+    void* d_grp = nullptr;
+    const size_t grp_bytes = (bf ? sizeof(ushort4) : sizeof(uint4)) * (size_t)P.K * P.M;
     e = cudaMalloc((void**)&d_b, bimg.size() * 2);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_n0, sizeof(int) * (size_t)P.K * (P.M + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ord, sizeof(int) * (size_t)P.K);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctr, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_grp, sizeof(ushort4) * (size_t)P.K * P.M);
+    if (e == cudaSuccess) e = cudaMalloc(&d_grp, grp_bytes);
     if (e == cudaSuccess) e = cudaMemcpy(d_b, bimg.data(), bimg.size() * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_ord, order.data(), sizeof(int) * (size_t)P.K, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -151,7 +246,12 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, sizeof(int), st);
     if (e == cudaSuccess) {
         const long long n = (long long)P.K * P.M;
-        tf_grp_off_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(P, g->d_rec_off, g->d_rec_key, d_n0, d_grp, d_ctr);
+        if (bf)
+            tf_grp_off_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(P, g->d_rec_off, g->d_rec_key, d_n0,
+                                                                      (ushort4*)d_grp, d_ctr);
+        else
+            tf3_grp_off_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(P, L3.phsplit, g->d_rec_off, g->d_rec_key,
+                                                                       d_n0, (uint4*)d_grp, d_ctr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&too_long, d_ctr, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -166,14 +266,19 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
-    g->tf = L;
-    g->d_tf_bop = d_b;
+    if (bf) {
+        g->tf = L;
+        g->d_tf_bop = d_b;
+        g->d_tf_grpoff = (ushort4*)d_grp;
+    } else {
+        g->tf3 = L3;
+        g->d_tf3_bop = d_b;
+        g->d_tf3_grpoff = (uint4*)d_grp;
+    }
     g->d_tf_n0off = d_n0;
     g->d_tf_order = d_ord;
     g->d_tf_counter = d_ctr;
-    g->d_tf_grpoff = d_grp;
-    g->bytes += bimg.size() * 2 + sizeof(int) * ((size_t)P.K * (P.M + 1) + P.K + 1) +
-                sizeof(ushort4) * (size_t)P.K * P.M;
+    g->bytes += bimg.size() * 2 + sizeof(int) * ((size_t)P.K * (P.M + 1) + P.K + 1) + grp_bytes;
     return cudaSuccess;
 }
 
@@ -193,6 +298,23 @@ cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf,
     TcFwdView V{P, L, g->d_tf_bop, g->d_tab_bf16, g->d_rec_off, g->d_tf_n0off, g->d_tf_grpoff, g->d_rec_key,
                  g->d_rec_w, g->d_tf_order, g->w_tc_contrib, yf, yb, stride, g->d_tf_counter};
     fwd_tc_kernel<<<grid, kTfThreads, L.smem, st>>>(V, g->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_tc32(const mbir_geometry* g, const float* x, float* yf, int stride, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const Tf3Layout& L = g->tf3;
+    cudaError_t ce = cudaFuncSetAttribute(fwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tf_counter, 0, sizeof(int), st);
+    if (ce != cudaSuccess) return ce;
+    const int grid = std::max(1, std::min(g->n_sm, P.K));
+    tc_gather_x_kernel<<<g->n_sm * 8, 256, 0, st>>>(g->n_records, g->d_rec_key, x, g->w_tc_contrib);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return ce;
+    TcFwd32View V{P, L, g->d_tf3_bop, g->d_tab, g->d_rec_off, g->d_tf_n0off, g->d_tf3_grpoff, g->d_rec_key,
+                  g->d_rec_w, g->d_tf_order, g->w_tc_contrib, yf, stride, g->d_tf_counter};
+    fwd_tc32_kernel<<<grid, kTfThreads, L.smem, st>>>(V, g->d_status);
     return cudaGetLastError();
 }
 

@@ -200,6 +200,27 @@ def test_fp32_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn)
     assert np.array_equal(gpu_backproject(tc, r), b_tc)
 
 
+@pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene,
+                                      lambda: S.small_scene(n_layers=1, w=32, h=16, n_tx=2, n_rx=3, M=200),
+                                      lambda: S.small_scene(n_layers=2, w=24, h=20, n_tx=3, n_rx=2, M=180,
+                                                            atten=False)])
+def test_fp32_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn):
+    """FP32 form: A x on the tensor cores (per-(sample, table row) sums of
+    weight x x in FP32 and the table, each split into three BF16 parts, six
+    products kept, two phase-aligned halves of the table rows) against the
+    CUDA-core A x and the FP64 oracle; the last scene has one gamma plane."""
+    s = scene_fn()
+    tc = make_geo(s, "tab")
+    cc = make_geo(s, "tab", tensor_cores=False)
+    assert tc.info.forward_tensor_cores == 1 and cc.info.forward_tensor_cores == 0
+    plan = O.Plan(s)
+    for x in (S.phantom(s, 2), S.random_vector(s.N, 34).reshape(s.img_h, s.img_w)):
+        y_tc, y_cc = gpu_forward(tc, x), gpu_forward(cc, x)
+        assert rel_l2(y_tc, y_cc) <= 1e-6
+        assert rel_l2(y_tc, plan.forward(x)) <= 1e-5
+    assert np.array_equal(gpu_forward(tc, x), y_tc)
+
+
 @pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene])
 def test_bf16_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn):
     """BF16 form: A x on the tensor cores (per-(sample, table row) sums of
