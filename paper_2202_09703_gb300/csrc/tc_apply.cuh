@@ -239,7 +239,7 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
         // Hankel tile H[n][m] = e[ts + n + 1 + m], 8 taps (16 bytes) per store
         const unsigned short* sEu = reinterpret_cast<const unsigned short*>(sE);
         for (int c = tid; c < kTcTile * kc; c += blockDim.x) {
-            const int n = c / kc, j = c - n * kc;
+            const int n8 = c >> 3, j = n8 % kc, n = (n8 / kc) * 8 + (c & 7);   // lanes along a core matrix's rows
             const unsigned short* src = sEu + n + 8 * j;
             uint4 w;
             w.x = (uint32_t)src[0] | ((uint32_t)src[1] << 16);
@@ -308,14 +308,18 @@ __device__ __forceinline__ void split3(float x, unsigned short& a, unsigned shor
     c = __bfloat16_as_ushort(p3);
 }
 
-// x = a + b with a the FP16 rounding of x and b that of the remainder (22 significant bits for
-// |x| in [2^-3, 2^15]; the caller scales x into that range by a power of two).
-__device__ __forceinline__ void split2h(float x, unsigned short& a, unsigned short& b)
+// Two values into packed FP16 high and low parts: hi = x rounded to 11 significant bits by Veltkamp's
+// splitting, (x (2^13 + 1)) - ((x (2^13 + 1)) - x) (exact in FP16 for |x| in [2^-14, 2^15]), and
+// lo = x - hi (exact in FP32) rounded to FP16; x = hi + lo to 2^-23 relative.  No packed conversion
+// is spent on the high part's remainder.
+__device__ __forceinline__ void split2h_pair(float x0, float x1, uint32_t& hi, uint32_t& lo)
 {
-    const __half p1 = __float2half_rn(x);
-    const __half p2 = __float2half_rn(x - __half2float(p1));
-    a = __half_as_ushort(p1);
-    b = __half_as_ushort(p2);
+    const float t0 = __fmul_rn(x0, 8193.0f), t1 = __fmul_rn(x1, 8193.0f);
+    const float h0 = __fsub_rn(t0, __fsub_rn(t0, x0)), h1 = __fsub_rn(t1, __fsub_rn(t1, x1));
+    const __half2 H = __floats2half2_rn(h0, h1);
+    const __half2 L = __floats2half2_rn(__fsub_rn(x0, h0), __fsub_rn(x1, h1));
+    hi = *reinterpret_cast<const uint32_t*>(&H);
+    lo = *reinterpret_cast<const uint32_t*>(&L);
 }
 
 // Contributions of a batch's records whose phase falls in `half`, from that
@@ -417,7 +421,7 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
         if (tid == 0) *next = atomicAdd(counter, 1);
         // three BF16 Hankel tiles H_i[n][m] = part i of e[ts + n + 1 + m]
         for (int c = tid; c < kTcTile * kc; c += blockDim.x) {
-            const int n = c / kc, j = c - n * kc;
+            const int n8 = c >> 3, j = n8 % kc, n = (n8 / kc) * 8 + (c & 7);   // lanes along a core matrix's rows
             unsigned short a[8], b2[8], c3[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) split3(sE[n + 8 * j + q], a[q], b2[q], c3[q]);
@@ -508,7 +512,7 @@ __device__ __forceinline__ void tf_stage_half(uint4 (&pk)[kTfStage], const float
     for (int q = 0; q < kTfStage; ++q) {
         const int c = tid + q * kTfThreads;
         if (c < kTfTile * kc) {
-            const int i = c / kc, j = c - i * kc;
+            const int i8 = c >> 3, j = i8 % kc, i = (i8 / kc) * 8 + (c & 7);   // lanes along a core matrix's rows
             const float* sp = src + i * astr + 8 * j;
             uint32_t w[4];
 #pragma unroll
@@ -531,7 +535,7 @@ __device__ __forceinline__ void tf_write_half(const uint4 (&pk)[kTfStage], unsig
     for (int q = 0; q < kTfStage; ++q) {
         const int c = tid + q * kTfThreads;
         if (c < kTfTile * kc) {
-            const int i = c / kc, j = c - i * kc;
+            const int i8 = c >> 3, j = i8 % kc, i = (i8 / kc) * 8 + (c & 7);   // lanes along a core matrix's rows
             *reinterpret_cast<uint4*>(dst + kmajor_offset(i, 8 * j, ka)) = pk[q];
         }
     }
@@ -913,23 +917,26 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
                     }
                     unsigned char* sAb = sA + (size_t)b * 2 * apart;
                     const int cw = min(T.kc, T.kb - c0), kc8 = cw / 8;
-                    for (int c = tid; c < kTfTile * kc8; c += blockDim.x) {
-                        const int i = c / kc8, j = c - i * kc8;
+                    // with two buffers warp 0 only issues the products, so they overlap the next conversion
+                    const int cthr = T.nbuf == 2 ? (int)blockDim.x - 32 : (int)blockDim.x;
+                    for (int c = T.nbuf == 2 ? tid - 32 : tid; c < kTfTile * kc8; c += cthr) {
+                        if (c < 0) break;
+                        // eight consecutive items = the eight rows of one core matrix: their 16-byte stores
+                        // are contiguous and their row reads (stride astride, not a multiple of 32) hit
+                        // distinct banks
+                        const int i8 = c >> 3, j = i8 % kc8, i = (i8 / kc8) * 8 + (c & 7);
                         float4* sp = reinterpret_cast<float4*>(sS + i * T.astride + c0 + 8 * j);
                         const float4 v0 = sp[0], v1 = sp[1];
                         sp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
                         sp[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                        unsigned short a[8], b2[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) split2h(vv[q] * scl, a[q], b2[q]);
+                        uint4 hv, lv;
+                        split2h_pair(v0.x * scl, v0.y * scl, hv.x, lv.x);
+                        split2h_pair(v0.z * scl, v0.w * scl, hv.y, lv.y);
+                        split2h_pair(v1.x * scl, v1.y * scl, hv.z, lv.z);
+                        split2h_pair(v1.z * scl, v1.w * scl, hv.w, lv.w);
                         const uint32_t off = kmajor_offset(i, 8 * j, T.kc);
-                        *reinterpret_cast<uint4*>(sAb + off) =
-                            make_uint4(a[0] | (uint32_t)a[1] << 16, a[2] | (uint32_t)a[3] << 16,
-                                       a[4] | (uint32_t)a[5] << 16, a[6] | (uint32_t)a[7] << 16);
-                        *reinterpret_cast<uint4*>(sAb + apart + off) =
-                            make_uint4(b2[0] | (uint32_t)b2[1] << 16, b2[2] | (uint32_t)b2[3] << 16,
-                                       b2[4] | (uint32_t)b2[5] << 16, b2[6] | (uint32_t)b2[7] << 16);
+                        *reinterpret_cast<uint4*>(sAb + off) = hv;
+                        *reinterpret_cast<uint4*>(sAb + apart + off) = lv;
                     }
                     fence_async_smem();
                     __syncthreads();
