@@ -379,11 +379,12 @@ def run_gpu(args):
                                                 "peak_gbs": smem_peak,
                                                 "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak}}
 
-    # per timed reconstruction: the projection of y, then 9 kernels per iteration (A^T r and its group
-    # reduction, prior gradient, PR+ scalars, direction, A x, projection, step, update); the ncu launch
-    # list of this command agrees (451 for 50 iterations; the host-buffer call adds A x and the
-    # projection of the final direct-arrival gains)
-    launches = args.steps * (9 * scene.n_iter + 1)
+    # per timed reconstruction: the projection of y, then per iteration A^T r and its group reduction,
+    # prior gradient, PR+ scalars, direction, A x (with the tensor cores: the record-order gather of the
+    # direction, then the product kernel), projection, step, update; the ncu launch list of this command
+    # agrees (501 for 50 iterations with the tensor-core A x)
+    per_it = 10 if geo.info.forward_tensor_cores else 9
+    launches = args.steps * (per_it * scene.n_iter + 1)
 
     out = {"metric": "recons/s", "value": value, "unit": "recons/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
