@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=0, help="requests for the batched / served workloads")
     ap.add_argument("--source-hash", default="",
                     help="print the hash profiles/traffic.txt records for these comma-separated sources and exit")
+    ap.add_argument("--scene", default="cfg1", choices=["cfg1", "cfg2"], help="workload of --apply-only")
     ap.add_argument("--spacing", type=int, default=8, help="colour spacing of --workload icd")
     ap.add_argument("--sweeps", type=int, default=10, help="sweeps of --workload icd")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
@@ -421,7 +422,7 @@ def run_apply_only(args):
     B.build()
     from paper_2202_09703_gb300 import mbir as M
     from paper_2202_09703_gb300 import synth as S
-    scene = S.cfg1().copy(precision=args.precision)
+    scene = (S.cfg2() if args.scene == "cfg2" else S.cfg1()).copy(precision=args.precision)
     dev = torch.device("cuda:0")
     geo = M.Geometry(scene, mode=args.mode)
     x = torch.as_tensor(S.phantom(scene, 0).reshape(-1), dtype=torch.float32, device=dev)
@@ -432,7 +433,24 @@ def run_apply_only(args):
         geo.forward(x, y)
         geo.backproject(y, b)
     torch.cuda.synchronize()
-    print(json.dumps({"apply_only": args.apply_only, "mode": geo.mode, "precision": geo.precision,
+    # then per-apply device times: CUDA events around single calls, median of 5
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    tf, tb = [], []
+    for _ in range(5):
+        ev[0].record()
+        geo.forward(x, y)
+        ev[1].record()
+        torch.cuda.synchronize()
+        tf.append(ev[0].elapsed_time(ev[1]))
+        ev[0].record()
+        geo.backproject(y, b)
+        ev[1].record()
+        torch.cuda.synchronize()
+        tb.append(ev[0].elapsed_time(ev[1]))
+    print(json.dumps({"apply_only": args.apply_only, "scene": scene.name, "mode": geo.mode, "precision": geo.precision,
+                      "forward_tensor_cores": geo.info.forward_tensor_cores,
+                      "adjoint_tensor_cores": geo.info.adjoint_tensor_cores,
+                      "forward_ms": sorted(tf)[2], "backproject_ms": sorted(tb)[2],
                       "y_norm": float(y.float().norm()),
                       "b_norm": float(b.norm())}))
 
@@ -466,7 +484,7 @@ def run_batched(args):
     from paper_2202_09703_gb300 import mbir as M
     from paper_2202_09703_gb300 import synth as S
     dev = torch.device("cuda:0")
-    n = args.requests or 96
+    n = args.requests or 48
     scenes = S.cfg3_scenes(n, seed=0)
     out = {"workload": f"batched: {n} uneven scenes (cfg3 recipe), 50 iterations each"}
     truth = [torch.as_tensor(S.phantom(sc, i).reshape(-1), dtype=torch.float32, device=dev)
@@ -503,6 +521,8 @@ def run_batched(args):
             out[prec]["serial_s"] = t_serial
             out[prec]["serial_image_rel_err_vs_truth"] = image_err(x_serial)
         eng.close()
+        for geo, _, _ in reqs:          # each pass's geometries (records, tables) go before the next pass
+            geo.close()
         del reqs
         torch.cuda.empty_cache()
     print(json.dumps({"metric": "recons/s", "value": out["bf16"]["engine_recons_per_s"], "unit": "recons/s",
