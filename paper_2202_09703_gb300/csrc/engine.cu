@@ -621,6 +621,7 @@ struct Request {
     size_t bytes = 0;
     double cost = 0;        // estimated work of one iteration (A^T e estimate, twice)
     double waited = 0;      // work of the steps that ran while this request was passed over
+    double bwd_est = -1, fwd_est = -1;   // the geometry's A^T e and A d cost estimates (summed once)
     float *e = nullptr, *q = nullptr, *b = nullptr, *grad = nullptr, *gprev = nullptr, *d0 = nullptr,
           *d1 = nullptr, *bpart = nullptr, *msq = nullptr, *contrib = nullptr;
     __nv_bfloat16* ebf = nullptr;
@@ -875,19 +876,24 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
         const Request* r = E->sel[ri];
         const mbir_geometry* g = r->g;
         const GeomParams& P = g->P;
-        // A^T e: the geometry's estimates of its items (tile x transmitter group)
-        const int TR = backproject_tile_rows(), ntr = (P.H + TR - 1) / TR;
-        double cb = 0;
-        for (int tr = 0; tr < ntr; ++tr) {
-            if (!(g->h_tvert[tr * TR] < (float)(P.M - 1))) continue;
-            for (size_t t = (size_t)tr * g->bwd_ntc * P.n_tx; t < (size_t)(tr + 1) * g->bwd_ntc * P.n_tx; ++t)
-                cb += g->h_bwd_cost[t];
+        // A^T e: the geometry's estimates of its items (tile x transmitter group); A d: records visited per
+        // window plus a fixed cost per window.  Summed on the request's first step only.
+        Request* rw = E->sel[ri];
+        if (rw->bwd_est < 0) {
+            const int TR = backproject_tile_rows(), ntr = (P.H + TR - 1) / TR;
+            double cb = 0;
+            for (int tr = 0; tr < ntr; ++tr) {
+                if (!(g->h_tvert[tr * TR] < (float)(P.M - 1))) continue;
+                for (size_t t = (size_t)tr * g->bwd_ntc * P.n_tx; t < (size_t)(tr + 1) * g->bwd_ntc * P.n_tx; ++t)
+                    cb += g->h_bwd_cost[t];
+            }
+            double cf = 0;
+            for (long long w = 0; w < g->n_win; ++w) cf += g->h_win_cost[w] + 8;
+            rw->bwd_est = cb;
+            rw->fwd_est = cf;
         }
-        bwd_cost.push_back(cb);
-        // A d: records visited per window plus a fixed cost per window
-        double cf = 0;
-        for (long long w = 0; w < g->n_win; ++w) cf += g->h_win_cost[w] + 8;
-        fwd_cost.push_back(cf);
+        bwd_cost.push_back(rw->bwd_est);
+        fwd_cost.push_back(rw->fwd_est);
         for (int b = 0; b < r->nblk; ++b) pix.push_back(make_int2((int)ri, b));
         for (int k = 0; k < P.K; ++k) rows.push_back(make_int2((int)ri, k));
         const long long N = (long long)P.W * P.H, KMp = (long long)P.K * P.Mp;
