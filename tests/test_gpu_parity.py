@@ -221,6 +221,32 @@ def test_fp32_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn)
     assert np.array_equal(gpu_forward(tc, x), y_tc)
 
 
+@pytest.mark.parametrize("case", ["zero", "one_pixel", "tiny", "huge"])
+def test_fp32_tensor_core_forward_scaling_edge_cases(case):
+    """The FP32 tensor-core A x scales each (tile, row half) of per-sample sums by a power of two before
+    the FP16 split: an all-zero image gives exact zeros, and a single pixel or images at 1e-30 / 1e30
+    (far outside FP16's range) match the CUDA-core A x to FP32 accuracy."""
+    s = ragged_scene()
+    tc = make_geo(s, "tab")
+    cc = make_geo(s, "tab", tensor_cores=False)
+    x = S.phantom(s, 3).astype(np.float64)
+    if case == "zero":
+        x = np.zeros_like(x)
+    elif case == "one_pixel":
+        x = np.zeros_like(x)
+        x[s.img_h // 2, s.img_w // 3] = 0.7
+    elif case == "tiny":
+        x = x * 1e-30
+    else:
+        x = x * 1e30
+    y_tc, y_cc = gpu_forward(tc, x), gpu_forward(cc, x)
+    assert np.all(np.isfinite(y_tc))
+    if case == "zero":
+        assert not np.any(y_tc)
+    else:
+        assert rel_l2(y_tc, y_cc) <= 1e-6
+
+
 @pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene])
 def test_bf16_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn):
     """BF16 form: A x on the tensor cores (per-(sample, table row) sums of
