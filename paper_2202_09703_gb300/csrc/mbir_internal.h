@@ -328,7 +328,8 @@ struct Tc3Layout {
     int nrows[2];          // table rows of each half (multiples of 16)
     int nmax;              // larger of the two
     int cstride;           // row stride of the shared correlation tile (floats)
-    size_t bhalf[2];       // bytes of each half's three-part operand image
+    size_t bhalf[2];       // bytes of each half's two-part FP16 operand image (both resident)
+    int texp;              // table scale: operand = table x 2^texp (largest magnitude in [2^14, 2^15))
     size_t off_h, off_b, off_e, off_c, smem;
     bool ok;
 };

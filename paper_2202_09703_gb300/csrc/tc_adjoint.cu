@@ -16,6 +16,7 @@
 // stored at the record's place in pixel-major order.  A second kernel sums
 // every pixel's contributions in A-scan order, so the result is reproducible.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "tc_apply.cuh"
@@ -51,11 +52,11 @@ Tc3Layout tc3_layout(const GeomParams& P)
     L.nrows[1] = (((R - L.phsplit) * P.G) + 15) & ~15;
     L.nmax = std::max(L.nrows[0], L.nrows[1]);
     L.cstride = L.nmax + 1;
-    L.bhalf[0] = (size_t)3 * L.nrows[0] * L.kpad * 2;
-    L.bhalf[1] = (size_t)3 * L.nrows[1] * L.kpad * 2;
+    L.bhalf[0] = (size_t)2 * L.nrows[0] * L.kpad * 2;
+    L.bhalf[1] = (size_t)2 * L.nrows[1] * L.kpad * 2;
     L.off_h = 1024;
-    L.off_b = L.off_h + (size_t)3 * kTcTile * L.kpad * 2;
-    L.off_e = (L.off_b + std::max(L.bhalf[0], L.bhalf[1]) + 127) & ~(size_t)127;
+    L.off_b = L.off_h + (size_t)2 * kTcTile * L.kpad * 2;
+    L.off_e = (L.off_b + L.bhalf[0] + L.bhalf[1] + 127) & ~(size_t)127;
     L.off_c = (L.off_e + (size_t)(kTcTile + L.kpad + 16) * 4 + 127) & ~(size_t)127;
     L.smem = L.off_c + (size_t)kTcTile * L.cstride * 4;
     L.ok = R >= 2 && L.nmax <= 256 && L.smem <= 227 * 1024 && P.K <= 65535 && kTcTile + L.kpad <= kTcThreads;
@@ -149,7 +150,7 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     if (!g->d_rec_key || g->n_records <= 0 || g->n_records >= (1LL << 32)) return cudaErrorNotSupported;
     const bool bf = P.precision == MBIR_PREC_BF16;
     const TcLayout L = tc_layout(P);
-    const Tc3Layout L3 = tc3_layout(P);
+    Tc3Layout L3 = tc3_layout(P);
     if (bf ? !L.ok : !L3.ok) return cudaErrorNotSupported;
     const int N = P.W * P.H;
     const int ntile = (P.M + kTcTile - 1) / kTcTile;
@@ -165,9 +166,16 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
                     __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
         }
     } else {
-        // FP32 form: per row half, the FP32 table (as the CUDA-core kernels read it) split into
-        // three BF16 parts t = t1 + t2 + t3; half h holds phases [h ? phsplit : 0, h ? Q : phsplit]
+        // FP32 form: per row half, the FP32 table (as the CUDA-core kernels read it) times 2^texp
+        // (largest magnitude into [2^14, 2^15)), split into two FP16 parts t = t1 + t2; half h holds
+        // phases [h ? phsplit : 0, h ? Q : phsplit]
+        float tmax = 0.0f;
+        for (size_t i = 0; i < (size_t)P.G * nq; ++i) tmax = std::max(tmax, std::fabs((float)g->tab_host[i]));
+        int ex = 0;
+        std::frexp(tmax, &ex);
+        L3.texp = tmax > 0.0f ? std::min(15 - ex, 126) : 0;
         bimg.assign((L3.bhalf[0] + L3.bhalf[1]) / 2, __float2bfloat16_rn(0.0f));
+        __half* himg = reinterpret_cast<__half*>(bimg.data());
         size_t base = 0;
         for (int h = 0; h < 2; ++h) {
             const int phb = h ? L3.phsplit : 0, phe = h ? R - 1 : L3.phsplit;
@@ -175,17 +183,14 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
             for (int ph = phb; ph <= phe; ++ph)
                 for (int gpl = 0; gpl < P.G; ++gpl)
                     for (int m = 0; m < P.Tw; ++m) {
-                        const float t = (float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph];
-                        const __nv_bfloat16 p1 = __float2bfloat16_rn(t);
-                        const float r1 = t - __bfloat162float(p1);
-                        const __nv_bfloat16 p2 = __float2bfloat16_rn(r1);
-                        const __nv_bfloat16 p3 = __float2bfloat16_rn(r1 - __bfloat162float(p2));
+                        const float t = std::ldexp((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph], L3.texp);
+                        const __half p1 = __float2half_rn(t);
+                        const __half p2 = __float2half_rn(t - __half2float(p1));
                         const size_t o = kmajor_offset((ph - phb) * P.G + gpl, m, L3.kpad) / 2;
-                        bimg[base + o] = p1;
-                        bimg[base + part + o] = p2;
-                        bimg[base + 2 * part + o] = p3;
+                        himg[base + o] = p1;
+                        himg[base + part + o] = p2;
                     }
-            base += 3 * part;
+            base += 2 * part;
         }
     }
     int* d_cnt = nullptr;

@@ -352,11 +352,13 @@ __device__ __forceinline__ void tc3_run_batch(const TcBatch& b, const GeomParams
 }
 
 // Drains the FP32 A^T items (A-scan, 128-sample tile) of V.  Per item: the
-// residual window split into three BF16 Hankel tiles; for each row half, the
-// six products whose parts' orders sum to at most 4 (H_i T_j, i + j <= 4:
-// error below FP32 rounding) accumulate in tensor memory, the next half's
-// table operand is copied in (bulk copy) while this half's records are
-// processed.  smem + 32 holds the operand copy's mbarrier.
+// residual window, scaled by a power of two that brings its largest magnitude
+// into [2^14, 2^15), split into two FP16 Hankel tiles; for each row half the
+// three products H_1 T_1 + H_1 T_2 + H_2 T_1 with the two-part table (scaled
+// on the host; the dropped H_2 T_2 is below 2^-22 of the result) accumulate in
+// tensor memory and are scaled back as they are read.  Both halves' table
+// operands stay resident (one bulk copy per pool, mbarrier at smem + 32);
+// smem + 64 holds the warps' window maxima.
 __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned char* smem, uint32_t tmem,
                                                   uint32_t& phase, uint32_t& bphase, int* status)
 {
@@ -381,17 +383,16 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
     int* counter = V.counter;
     const unsigned char* bimg = reinterpret_cast<const unsigned char*>(V.bop);
     const size_t hbytes = (size_t)kTcTile * T.kpad * 2;     // one part of the Hankel tile
-
-    auto copy_half = [&](int h) {               // tid 0: bulk copy of half h's operand image
-        mbar_arrive_expect_tx(smem_u32(bbar), (uint32_t)T.bhalf[h]);
-        bulk_g2s(smem_u32(sB), bimg + (h ? T.bhalf[0] : 0), (uint32_t)T.bhalf[h], smem_u32(bbar));
-    };
+    float* wmax = reinterpret_cast<float*>(smem + 64);
+    // both halves' table operands, once
     int copies = 1, waits = 0;                   // the same on every thread
     if (tid == 0) {
-        copy_half(0);
+        mbar_arrive_expect_tx(smem_u32(bbar), (uint32_t)(T.bhalf[0] + T.bhalf[1]));
+        bulk_g2s(smem_u32(sB), bimg, (uint32_t)(T.bhalf[0] + T.bhalf[1]), smem_u32(bbar));
         *next = atomicAdd(counter, 1);
     }
     __syncthreads();
+    const float it_scale = __int_as_float((127 - T.texp) << 23);
     const int ntile = (P.M + kTcTile - 1) / kTcTile;
     const int nitems = P.K * ntile;
     const int W = kTcTile + T.kpad;
@@ -417,42 +418,58 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
         const long long base = pbase;
         const int r0 = pr0, r1 = pr1;
         if (tid < W) sE[tid] = ew;
+        {
+            // the window's largest magnitude, one value per warp
+            float mx = fabsf(ew);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) wmax[warp] = mx;
+        }
         __syncthreads();
         if (tid == 0) *next = atomicAdd(counter, 1);
-        // three BF16 Hankel tiles H_i[n][m] = part i of e[ts + n + 1 + m]
+        int se = 0;
+        {
+            float m = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+            int ex = 0;
+            frexpf(m, &ex);
+            se = m > 0.0f ? min(15 - ex, 126) : 0;
+        }
+        const float scl = __int_as_float((se + 127) << 23);
+        const float unscale = __int_as_float((127 - se) << 23);       // then 2^-texp: two normal factors
+        // two FP16 Hankel tiles H_i[n][m] = part i of 2^se e[ts + n + 1 + m]
         for (int c = tid; c < kTcTile * kc; c += blockDim.x) {
             const int n8 = c >> 3, j = n8 % kc, n = (n8 / kc) * 8 + (c & 7);   // lanes along a core matrix's rows
-            unsigned short a[8], b2[8], c3[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) split3(sE[n + 8 * j + q], a[q], b2[q], c3[q]);
+            uint4 hv, lv;
+            const float* src = sE + n + 8 * j;
+            split2h_pair(src[0] * scl, src[1] * scl, hv.x, lv.x);
+            split2h_pair(src[2] * scl, src[3] * scl, hv.y, lv.y);
+            split2h_pair(src[4] * scl, src[5] * scl, hv.z, lv.z);
+            split2h_pair(src[6] * scl, src[7] * scl, hv.w, lv.w);
             const uint32_t off = kmajor_offset(n, 8 * j, T.kpad);
-            *reinterpret_cast<uint4*>(sH + off) =
-                make_uint4(a[0] | (uint32_t)a[1] << 16, a[2] | (uint32_t)a[3] << 16, a[4] | (uint32_t)a[5] << 16,
-                           a[6] | (uint32_t)a[7] << 16);
-            *reinterpret_cast<uint4*>(sH + hbytes + off) =
-                make_uint4(b2[0] | (uint32_t)b2[1] << 16, b2[2] | (uint32_t)b2[3] << 16,
-                           b2[4] | (uint32_t)b2[5] << 16, b2[6] | (uint32_t)b2[7] << 16);
-            *reinterpret_cast<uint4*>(sH + 2 * hbytes + off) =
-                make_uint4(c3[0] | (uint32_t)c3[1] << 16, c3[2] | (uint32_t)c3[3] << 16,
-                           c3[4] | (uint32_t)c3[5] << 16, c3[6] | (uint32_t)c3[7] << 16);
+            *reinterpret_cast<uint4*>(sH + off) = hv;
+            *reinterpret_cast<uint4*>(sH + hbytes + off) = lv;
         }
         fence_async_smem();
         __syncthreads();
         const int it_next = *next;
-        for (int h = 0; h < 2; ++h) {
-            // this half's operand image has landed
+        if (waits < copies) {
+            // the table operands have landed (once per pool)
             if (!mbar_wait_bounded(smem_u32(bbar), bphase, status)) *abort_flag = 1;
             bphase ^= 1u;
             ++waits;
+            __syncthreads();
+        }
+        for (int h = 0; h < 2; ++h) {
             if (tid == 0 && !*abort_flag) {
                 tc_fence_after();
                 const int nr = T.nrows[h];
-                const uint32_t idesc = umma_idesc_bf16(kTcTile, nr);
-                const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB);
+                const uint32_t idesc = umma_idesc_f16(kTcTile, nr);
+                const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB) + (uint32_t)(h ? T.bhalf[0] : 0);
                 const uint32_t bpart = (uint32_t)((size_t)nr * T.kpad * 2);
-                const int terms[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+                const int terms[3][2] = {{0, 0}, {0, 1}, {1, 0}};
                 for (int s = 0; s < T.kpad / 16; ++s)
-                    for (int q = 0; q < 6; ++q)
+                    for (int q = 0; q < 3; ++q)
                         umma_bf16(tmem, umma_desc(a0 + (uint32_t)(terms[q][0] * hbytes) + 256 * s, lbo, sbo),
                                   umma_desc(b0 + terms[q][1] * bpart + 256 * s, lbo, sbo), idesc, s > 0 || q > 0);
                 umma_commit(smem_u32(bar));
@@ -461,14 +478,9 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
             if (*abort_flag) break;
             if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
             phase ^= 1u;
-            __syncthreads();                         // uniform flag; the operand buffer is free again
+            __syncthreads();                         // uniform flag
             tc_fence_after();
             if (*abort_flag) break;
-            // the other half next (or half 0 of the next item), copied during this half's records
-            if (h == 0 || it_next < nitems) {
-                if (tid == 0) copy_half(1 - h);
-                ++copies;
-            }
             {
                 const int q = warp & 3, part = warp >> 2;
                 const int row = q * 32 + lane;
@@ -477,7 +489,7 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
                     float v[4];
                     tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) sC[row * T.cstride + c + j] = v[j];
+                    for (int j = 0; j < 4; ++j) sC[row * T.cstride + c + j] = (v[j] * unscale) * it_scale;
                 }
             }
             tc_fence_before();
