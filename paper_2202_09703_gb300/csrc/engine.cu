@@ -445,26 +445,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc32_kernel(EngLists L)
 }
 
 // b = each pixel's contributions summed in A-scan order (the single-request
-// reduction's arithmetic: warp per pixel, lane-strided Neumaier, fixed tree)
+// reduction's arithmetic: warp per pixel, lane-strided Neumaier, fixed tree).
+// Warps stride over every (pixel block, pixel) slot of the step, so a step of
+// small requests still spreads one pixel per warp over the whole grid.
 __global__ void eng_bwd_tc_reduce_kernel(EngLists L)
 {
-    const int nb = L.counts[1];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int bb = blockIdx.x; bb < nb; bb += gridDim.x) {
-        const int2 rb = L.pixblk[bb];
+    const long long nt = (long long)L.counts[1] * kRedThreads;
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += nw) {
+        const int2 rb = L.pixblk[t / kRedThreads];
         const ReqDesc& R = L.desc[rb.x];
-        const int N = R.P.W * R.P.H;
-        for (int p = w; p < kRedThreads; p += nw) {
-            const int v = rb.y * kRedThreads + p;
-            if (v >= N) break;
-            const long long a = R.tc_pixoff[v], z = R.tc_pixoff[v + 1];
-            float s = 0.0f, c = 0.0f;
-            for (long long j = a + lane; j < z; j += 32) neumaier_add(s, c, R.tc_contrib[j]);
-            s += c;
+        const int v = rb.y * kRedThreads + (int)(t % kRedThreads);
+        if (v >= R.P.W * R.P.H) continue;
+        const long long* pix_off = R.tc_pixoff;
+        const float* contrib = R.tc_contrib;
+        float* b = R.b;
+        const long long a = pix_off[v], z = pix_off[v + 1];
+        float s = 0.0f, c = 0.0f;
+        for (long long j = a + lane; j < z; j += 32) neumaier_add(s, c, contrib[j]);
+        s += c;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) R.b[v] = s;
-        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) b[v] = s;
     }
 }
 
@@ -661,6 +664,9 @@ struct mbir_engine {
     cudaGraphExec_t graph = nullptr;
     int graph_bf16 = -1, graph_tc = -1;
     size_t smem_bwd = 0, smem_fwd = 0;
+    // dynamic shared memory of the tensor-core kernels as captured: the largest layout among the
+    // admitted requests, not the 227 KB maximum, so that the rest of each SM's 256 KB stays L1
+    size_t smem_tc[4] = {0, 0, 0, 0};    // bwd BF16, bwd FP32, fwd BF16, fwd FP32
     // host mirrors
     std::vector<ReqDesc> h_desc;
 };
@@ -935,11 +941,11 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cuda
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
     if (e != cudaSuccess) return e;
     if (tc && bf16) {
-        eng_bwd_tc_kernel<<<G, kTcThreads, kEngSmem, st>>>(E->L);
-        eng_bwd_tc_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
+        eng_bwd_tc_kernel<<<G, kTcThreads, E->smem_tc[0], st>>>(E->L);
+        eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
     } else if (tc) {
-        eng_bwd_tc32_kernel<<<G, kTcThreads, kEngSmem, st>>>(E->L);
-        eng_bwd_tc_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
+        eng_bwd_tc32_kernel<<<G, kTcThreads, E->smem_tc[1], st>>>(E->L);
+        eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
     } else {
         if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
         else eng_bwd_kernel<false><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
@@ -950,10 +956,10 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cuda
     eng_dir_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     if (tc && bf16) {
         eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
-        eng_fwd_tc_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
+        eng_fwd_tc_kernel<<<G, kTfThreads, E->smem_tc[2], st>>>(E->L);
     } else if (tc && tcf) {
         eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
-        eng_fwd_tc32_kernel<<<G, kTfThreads, kEngSmem, st>>>(E->L);
+        eng_fwd_tc32_kernel<<<G, kTfThreads, E->smem_tc[3], st>>>(E->L);
     }
     else if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     else eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
@@ -1099,7 +1105,17 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         if (!r->g->d_tf3_bop) tcf = false;
     }
     const int gtc = (int)tc + 2 * (int)(tc && tcf);
-    if (grew || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != gtc) {
+    size_t smem_tc[4] = {1024, 1024, 1024, 1024};
+    for (Request* r : E->active) {
+        const mbir_geometry* g = r->g;
+        if (g->d_tc_bop) smem_tc[0] = std::max(smem_tc[0], g->tc.smem);
+        if (g->d_tc3_bop) smem_tc[1] = std::max(smem_tc[1], g->tc3.smem);
+        if (g->d_tf_bop) smem_tc[2] = std::max(smem_tc[2], g->tf.smem);
+        if (g->d_tf3_bop) smem_tc[3] = std::max(smem_tc[3], g->tf3.smem);
+    }
+    const bool smem_changed = !std::equal(smem_tc, smem_tc + 4, E->smem_tc);
+    if (grew || smem_changed || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != gtc) {
+        std::copy(smem_tc, smem_tc + 4, E->smem_tc);
         if (E->graph) { cudaGraphExecDestroy(E->graph); E->graph = nullptr; }
         cudaStream_t cs;
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
