@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc_kernel(EngLists L)
     tc_header_release(smem, tmem, kTcCols);
 }
 
-// A^T e of the FP32 form on the tensor cores (three-part BF16 split) over every
+// A^T e of the FP32 form on the tensor cores (two-part FP16 split) over every
 // active request, with the single-request pool function
 __global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc32_kernel(EngLists L)
 {

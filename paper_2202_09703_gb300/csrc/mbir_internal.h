@@ -318,10 +318,10 @@ struct TcLayout {
     bool ok;
 };
 
-// Layout of the FP32 tensor-core adjoint: the residual and the table are each
-// split into three BF16 parts; table rows are taken in two phase-aligned
-// halves (phases [0, phsplit] and [phsplit, Q]) so one half's operands and
-// correlation tile fit shared memory at a time.
+// Layout of the FP32 tensor-core adjoint: the residual window and the table
+// are each scaled by a power of two and split into two FP16 parts; table rows
+// are taken in two phase-aligned halves (phases [0, phsplit] and [phsplit, Q])
+// whose operands both stay resident, with one half's correlation tile at a time.
 struct Tc3Layout {
     int kpad;              // taps rounded up to 16
     int phsplit;           // phase where the halves meet (shared by both)
@@ -435,7 +435,7 @@ struct mbir_geometry {
     float* w_tc_contrib;   // one contribution per record, pixel-major
     int* d_tc_counter;
     Tc3Layout tc3;
-    uint4* d_tc3_bop;      // FP32 adjoint: both halves' three-part table operand images
+    uint4* d_tc3_bop;      // FP32 adjoint: both halves' two-part FP16 table operand images
     // tensor-core A x of the BF16 form (see tc_forward.cu)
     TfLayout tf;
     uint4* d_tf_bop;       // table operand image (taps x table rows, K-major)

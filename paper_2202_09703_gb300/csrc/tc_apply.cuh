@@ -44,7 +44,7 @@ struct TcAdjView {
     int* counter;                    // item counter (zeroed before the launch)
 };
 
-// FP32 A^T of one geometry / request (three-part BF16 split, two row halves).
+// FP32 A^T of one geometry / request (two-part FP16 split, two row halves).
 struct Tc3View {
     GeomParams P;
     Tc3Layout T;
@@ -79,7 +79,7 @@ struct TcFwdView {
     int* counter;
 };
 
-// FP32 A x of one geometry / request (three-part BF16 split, two phase-aligned halves).
+// FP32 A x of one geometry / request (two-part FP16 split, two phase-aligned halves).
 struct TcFwd32View {
     GeomParams P;
     Tf3Layout T;
@@ -914,7 +914,7 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
                 bphase ^= 1u;
                 ++waits;
                 __syncthreads();                     // uniform flag
-                // chunks of kc columns: three BF16 parts of the sums, then the six products; with two chunk
+                // chunks of kc columns: two FP16 parts of the scaled sums, then the three products; with two chunk
                 // buffers a chunk is converted while the previous chunk's products run
                 int pending = 0;                     // bit b: products reading buffer b not yet waited for
                 for (int c0 = 0, q = 0; c0 < T.kb; c0 += T.kc, ++q) {

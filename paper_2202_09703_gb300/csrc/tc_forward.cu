@@ -169,7 +169,7 @@ __global__ void tf3_grp_off_kernel(GeomParams P, int phsplit, const long long* _
 }
 
 // Tables of the tensor-core A x for a geometry with records (BF16 form: one BF16 table operand; FP32
-// form: both row halves' three-part operands); cudaErrorNotSupported keeps the CUDA-core A x.
+// form: both row halves' two-part FP16 operands); cudaErrorNotSupported keeps the CUDA-core A x.
 cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
 {
     const GeomParams& P = g->P;
