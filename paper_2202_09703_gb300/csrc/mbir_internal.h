@@ -353,6 +353,7 @@ struct TfLayout {
 struct Tf3Layout {
     int phsplit;           // first phase of the second half (both halves hold it)
     int ncol[2];           // table rows (sum columns) of each half: phases x G
+    int pstride;           // phases per plane in a half's columns: column = plane * pstride + phase offset
     int kb;                // MMA K of a half (columns, multiple of 16)
     int kc;                // columns converted and multiplied per chunk
     int nbuf;              // chunk buffers (2: a chunk is converted while the previous one is multiplied)

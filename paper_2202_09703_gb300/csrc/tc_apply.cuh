@@ -751,10 +751,14 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
 // bits) and multiplied by the half's two-part table operand (scaled the same
 // way on the host): the three products S_1 T_1 + S_1 T_2 + S_2 T_1 (the
 // dropped S_2 T_2 is below 2^-22 of the result) accumulate in the half's own
-// tensor-memory tile.  U = U_0 / (s_0 t) + U_1 / (s_1 t) then gives the
+// tensor-memory tile.  The columns are plane-major (plane * pstride + phase
+// offset), so the attenuation planes that a tile's records reach (a few of G)
+// are one column range: only that range is converted and multiplied, the
+// other sums being zero.  U = U_0 / (s_0 t) + U_1 / (s_1 t) then gives the
 // anti-diagonal sums added to y.  The other half's table operand is
 // bulk-copied while a half's records are scattered (mbarrier at smem + 32);
-// smem + 48 holds the halves' scale exponents, smem + 64 the warp maxima.
+// smem + 48 holds the halves' scale exponents, smem + 64 the warp maxima,
+// smem + 128 / 192 the warps' lowest / highest plane.
 __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned char* smem, uint32_t tmem,
                                                   uint32_t& phase, uint32_t& bphase, int* status)
 {
@@ -793,6 +797,8 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
     const int si = tid >> 2, pj = tid & 3;            // scatter role: n0 row and phase class
     volatile int* sexp = reinterpret_cast<volatile int*>(smem + 48);
     float* wmax = reinterpret_cast<float*>(smem + 64);
+    int* wlo = reinterpret_cast<int*>(smem + 128);
+    int* whi = reinterpret_cast<int*>(smem + 192);
     // the sums start at zero; every later pass that reads them (conversion, anti-diagonals) clears them
     for (int i = tid; i < kTfTile * max(T.astride, T.ustride); i += blockDim.x) sS[i] = 0.0f;
     __syncthreads();
@@ -838,6 +844,7 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
             for (int h = 0; h < 2; ++h) {
                 const int phb = h ? T.phsplit : 0;
                 float bound = 0.0f;                  // sum of |contributions| of this thread: >= its |S| cells
+                int glo = P.G, ghi = -1;              // planes this thread's records reach
                 // scatter: thread (n0 row si, phase class pj) owns the cells of this half whose phase is pj
                 // (mod 4): upper-row corners of class pj - 1 records, then lower-row corners of class pj
                 float* arow = sS + si * T.astride;
@@ -869,10 +876,12 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
                         const int trow = (k0[u].y >> 1) & 0xfff;
                         const int gi = trow / R, ph = trow - gi * R;
                         const int g1 = min(gi + 1, P.G - 1);
-                        const int c = (ph + 1 - phb) * P.G;
-                        arow[c + gi] += w0[u].z * x0[u];
-                        arow[c + g1] += w0[u].w * x0[u];
+                        const int pc = ph + 1 - phb;
+                        arow[gi * T.pstride + pc] += w0[u].z * x0[u];
+                        arow[g1 * T.pstride + pc] += w0[u].w * x0[u];
                         bound += (fabsf(w0[u].z) + fabsf(w0[u].w)) * fabsf(x0[u]);
+                        glo = min(glo, gi);
+                        ghi = max(ghi, g1);
                         if (k0[u].y & 1) {
                             // tau = t0 exactly: the last tap of the upper phase row lies outside
                             const float2 tl = __ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1);
@@ -886,26 +895,46 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
                         const int trow = (k1[u].y >> 1) & 0xfff;
                         const int gi = trow / R, ph = trow - gi * R;
                         const int g1 = min(gi + 1, P.G - 1);
-                        const int c = (ph - phb) * P.G;
-                        arow[c + gi] += w1[u].x * x1[u];
-                        arow[c + g1] += w1[u].y * x1[u];
+                        const int pc = ph - phb;
+                        arow[gi * T.pstride + pc] += w1[u].x * x1[u];
+                        arow[g1 * T.pstride + pc] += w1[u].y * x1[u];
                         bound += (fabsf(w1[u].x) + fabsf(w1[u].y)) * fabsf(x1[u]);
+                        glo = min(glo, gi);
+                        ghi = max(ghi, g1);
                     }
                     qa0 += n0c;
                     qa1 += n1c;
                 }
                 // the half's scale: a bound of the largest |S| into [2^14, 2^15) (a power of two: exact)
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_xor_sync(0xffffffffu, bound, o));
-                if (lane == 0) wmax[warp] = bound;
+                for (int o = 16; o > 0; o >>= 1) {
+                    bound = fmaxf(bound, __shfl_xor_sync(0xffffffffu, bound, o));
+                    glo = min(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+                    ghi = max(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+                }
+                if (lane == 0) {
+                    wmax[warp] = bound;
+                    wlo[warp] = glo;
+                    whi[warp] = ghi;
+                }
                 __syncthreads();                     // every record of the half is in S
-                int se = 0;
+                int se = 0, c_lo = 0, c_hi = 16;     // a half without records multiplies one chunk of zeros
                 {
                     float m = 0.0f;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                        m = fmaxf(m, wmax[w]);
+                        glo = min(glo, wlo[w]);
+                        ghi = max(ghi, whi[w]);
+                    }
                     int ex = 0;
                     frexpf(m, &ex);
                     se = m > 0.0f ? min(15 - ex, 126) : 0;
+                    // the columns of the planes reached (plane-major), widened to whole 16-column K steps:
+                    // every other sum is zero and stays so
+                    if (ghi >= glo) {
+                        c_lo = (glo * T.pstride) & ~15;
+                        c_hi = min(T.kb, ((ghi + 1) * T.pstride + 15) & ~15);
+                    }
                 }
                 if (tid == 0) sexp[h] = se;
                 const float scl = __int_as_float((se + 127) << 23);
@@ -917,7 +946,7 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
                 // chunks of kc columns: two FP16 parts of the scaled sums, then the three products; with two chunk
                 // buffers a chunk is converted while the previous chunk's products run
                 int pending = 0;                     // bit b: products reading buffer b not yet waited for
-                for (int c0 = 0, q = 0; c0 < T.kb; c0 += T.kc, ++q) {
+                for (int c0 = c_lo, q = 0; c0 < c_hi; c0 += T.kc, ++q) {
                     const int b = T.nbuf == 2 ? (q & 1) : 0;
                     if (pending & (1 << b)) {
                         if (!mbar_wait_bounded(smem_u32(smem + (b ? 40 : 0)), (phase >> b) & 1u, status))
@@ -928,7 +957,7 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
                         if (*abort_flag) break;
                     }
                     unsigned char* sAb = sA + (size_t)b * 2 * apart;
-                    const int cw = min(T.kc, T.kb - c0), kc8 = cw / 8;
+                    const int cw = min(T.kc, c_hi - c0), kc8 = cw / 8;
                     // with two buffers warp 0 only issues the products, so they overlap the next conversion
                     const int cthr = T.nbuf == 2 ? (int)blockDim.x - 32 : (int)blockDim.x;
                     for (int c = T.nbuf == 2 ? tid - 32 : tid; c < kTfTile * kc8; c += cthr) {
@@ -961,7 +990,7 @@ __device__ __forceinline__ bool tc_forward32_pool(const TcFwd32View& V, unsigned
                                 umma_bf16(tmem + (uint32_t)(h * kTf3HalfCols),
                                           umma_desc(a0 + terms[tq][0] * apart + 256 * s, lbo, sboA),
                                           umma_desc(b0 + terms[tq][1] * bpart + 256 * s, lbo, sboB), idesc,
-                                          c0 > 0 || s > 0 || tq > 0);
+                                          c0 > c_lo || s > 0 || tq > 0);
                         umma_commit(smem_u32(smem + (b ? 40 : 0)));
                     }
                     pending |= 1 << b;

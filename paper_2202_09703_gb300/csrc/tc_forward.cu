@@ -56,7 +56,8 @@ Tf3Layout tf3_layout(const GeomParams& P)
     L.phsplit = R / 2;
     L.ncol[0] = (L.phsplit + 1) * P.G;
     L.ncol[1] = (R - L.phsplit) * P.G;
-    L.kb = (std::max(L.ncol[0], L.ncol[1]) + 15) & ~15;
+    L.pstride = std::max(L.phsplit + 1, R - L.phsplit);
+    L.kb = (L.pstride * P.G + 15) & ~15;
     L.kc = std::min(48, L.kb);
     L.ntap = (P.Tw + 15) & ~15;
     L.astride = (L.kb + 4 + 3) & ~3;                   // float4 rows, not a multiple of 32 banks
@@ -194,7 +195,8 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
     } else {
         // per row half h (phases [0, phsplit] / [phsplit, Q]): the FP32 table as the CUDA-core kernels
         // read it, times 2^texp (largest magnitude into [2^14, 2^15)), split into two FP16 parts
-        // t = t1 + t2; row m (tap), column (phase - first) * G + plane
+        // t = t1 + t2; row m (tap), column plane * pstride + (phase - first): plane-major, so that the
+        // planes a tile's records reach are one column range
         float tmax = 0.0f;
         for (size_t i = 0; i < (size_t)P.G * nq; ++i) tmax = std::max(tmax, std::fabs((float)g->tab_host[i]));
         int ex = 0;
@@ -212,7 +214,7 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
                         const float t = std::ldexp((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph], L3.texp);
                         const __half p1 = __float2half_rn(t);
                         const __half p2 = __float2half_rn(t - __half2float(p1));
-                        const size_t o = kmajor_offset(m, (ph - phb) * P.G + gpl, L3.kb) / 2;
+                        const size_t o = kmajor_offset(m, gpl * L3.pstride + (ph - phb), L3.kb) / 2;
                         himg[base + o] = p1;
                         himg[base + part + o] = p2;
                     }
