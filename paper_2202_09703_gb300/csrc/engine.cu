@@ -93,6 +93,7 @@ struct ReqDesc {
     int tc32;              // FP32 tensor-core adjoint pool available
     Tc3Layout tc3l;
     const uint4* tc3_bop;
+    const uint2* tc3_prange;
     TcLayout tcl;
     TfLayout tfl;
     const uint4* tc_bop;
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc32_kernel(EngLists L)
             const ReqDesc& R = L.desc[rq];
             const int nitems = R.P.K * ((R.P.M + kTcTile - 1) / kTcTile);
             if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
-            const Tc3View V{R.P, R.tc3l, R.tc3_bop, R.tab, R.e, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc_dest,
+            const Tc3View V{R.P, R.tc3l, R.tc3_bop, R.tab, R.e, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc3_prange, R.tc_dest,
                             R.tc_contrib, L.pool + 2 * rq + 1};
             if (!tc_adjoint32_pool(V, smem, tmem, phase, bphase, R.D.status)) break;
             __syncthreads();
@@ -804,6 +805,7 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.tc32 = g->d_tc3_bop ? 1 : 0;
     d.tc3l = g->tc3;
     d.tc3_bop = g->d_tc3_bop;
+    d.tc3_prange = g->d_tc3_prange;
     d.tcl = g->tc;
     d.tfl = g->tf;
     d.tc_bop = g->d_tc_bop;

@@ -175,7 +175,8 @@ void free_geometry(mbir_geometry* g)
                     g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_win_order, g->d_win_counter,
                     g->d_bwd_counter, g->d_tc_bop, g->d_tc_tile, g->d_tc_pixoff, g->d_tc_dest, g->w_tc_contrib,
                     g->d_tc_counter, g->d_tf_bop, g->d_tf_n0off, g->d_tf_order, g->d_tf_counter,
-                    g->d_tf_grpoff, g->d_tc3_bop, g->w_colnorm, g->d_tf3_bop, g->d_tf3_grpoff};
+                    g->d_tf_grpoff, g->d_tc3_bop, g->w_colnorm, g->d_tf3_bop, g->d_tf3_grpoff,
+                    g->d_tc3_prange};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::free_icd_lists(g);
     if (g->icd_stream) cudaStreamDestroy((cudaStream_t)g->icd_stream);

@@ -325,6 +325,7 @@ struct TcLayout {
 struct Tc3Layout {
     int kpad;              // taps rounded up to 16
     int phsplit;           // phase where the halves meet (shared by both)
+    int pstride;           // phases per plane in a half's rows: row = plane * pstride + phase offset
     int nrows[2];          // table rows of each half (multiples of 16)
     int nmax;              // larger of the two
     int cstride;           // row stride of the shared correlation tile (floats)
@@ -437,6 +438,7 @@ struct mbir_geometry {
     int* d_tc_counter;
     Tc3Layout tc3;
     uint4* d_tc3_bop;      // FP32 adjoint: both halves' two-part FP16 table operand images
+    uint2* d_tc3_prange;   // FP32 adjoint: per (A-scan, tile) and half, lowest | highest plane << 16
     // tensor-core A x of the BF16 form (see tc_forward.cu)
     TfLayout tf;
     uint4* d_tf_bop;       // table operand image (taps x table rows, K-major)

@@ -48,8 +48,8 @@ Tc3Layout tc3_layout(const GeomParams& P)
     const int R = P.Q + 1;
     L.kpad = (P.Tw + 15) & ~15;
     L.phsplit = R / 2;
-    L.nrows[0] = (((L.phsplit + 1) * P.G) + 15) & ~15;
-    L.nrows[1] = (((R - L.phsplit) * P.G) + 15) & ~15;
+    L.pstride = std::max(L.phsplit + 1, R - L.phsplit);
+    L.nrows[0] = L.nrows[1] = (L.pstride * P.G + 15) & ~15;
     L.nmax = std::max(L.nrows[0], L.nrows[1]);
     L.cstride = L.nmax + 1;
     L.bhalf[0] = (size_t)2 * L.nrows[0] * L.kpad * 2;
@@ -141,6 +141,37 @@ __global__ void tc_tile_off_kernel(GeomParams P, int ntile, const long long* __r
     tile_off[i] = lo;
 }
 
+// per (A-scan, tile) and row half: the lowest and highest attenuation plane
+// that the tile's records reach (lo | hi << 16; lo > hi when the half has no
+// record).  One warp per item.
+__global__ void tc3_prange_kernel(GeomParams P, int ntile, int phsplit, const long long* __restrict__ rec_off,
+                                  const int2* __restrict__ rkey, const int* __restrict__ tile_off,
+                                  uint2* __restrict__ prange)
+{
+    const long long item = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (item >= (long long)P.K * ntile) return;
+    const int k = (int)(item / ntile), t = (int)(item - (long long)k * ntile);
+    const long long base = rec_off[k];
+    const int a = tile_off[(size_t)k * (ntile + 1) + t], z = tile_off[(size_t)k * (ntile + 1) + t + 1];
+    const int R = P.Q + 1;
+    int lo[2] = {0xffff, 0xffff}, hi[2] = {0, 0};
+    for (int r = a + lane; r < z; r += 32) {
+        const int trow = (rkey[base + r].y >> 1) & 0xfff;
+        const int gi = trow / R, ph = trow - gi * R, h = ph >= phsplit ? 1 : 0;
+        lo[h] = min(lo[h], gi);
+        hi[h] = max(hi[h], min(gi + 1, P.G - 1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            lo[h] = min(lo[h], __shfl_xor_sync(0xffffffffu, lo[h], o));
+            hi[h] = max(hi[h], __shfl_xor_sync(0xffffffffu, hi[h], o));
+        }
+    if (lane == 0) prange[item] = make_uint2((uint32_t)lo[0] | (uint32_t)hi[0] << 16, (uint32_t)lo[1] | (uint32_t)hi[1] << 16);
+}
+
 // Builds the tensor-core adjoint's tables for a BF16 geometry with records.
 // Returns cudaErrorNotSupported (the caller keeps the other adjoint) when the
 // layout does not fit or memory is short.
@@ -168,7 +199,7 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     } else {
         // FP32 form: per row half, the FP32 table (as the CUDA-core kernels read it) times 2^texp
         // (largest magnitude into [2^14, 2^15)), split into two FP16 parts t = t1 + t2; half h holds
-        // phases [h ? phsplit : 0, h ? Q : phsplit]
+        // phases [h ? phsplit : 0, h ? Q : phsplit] in plane-major rows plane * pstride + (phase - first)
         float tmax = 0.0f;
         for (size_t i = 0; i < (size_t)P.G * nq; ++i) tmax = std::max(tmax, std::fabs((float)g->tab_host[i]));
         int ex = 0;
@@ -186,7 +217,7 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
                         const float t = std::ldexp((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph], L3.texp);
                         const __half p1 = __float2half_rn(t);
                         const __half p2 = __float2half_rn(t - __half2float(p1));
-                        const size_t o = kmajor_offset((ph - phb) * P.G + gpl, m, L3.kpad) / 2;
+                        const size_t o = kmajor_offset(gpl * L3.pstride + (ph - phb), m, L3.kpad) / 2;
                         himg[base + o] = p1;
                         himg[base + part + o] = p2;
                     }
@@ -199,7 +230,9 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     uint32_t* d_dest = nullptr;
     float* d_contrib = nullptr;
     uint4* d_b = nullptr;
+    uint2* d_prange = nullptr;
     cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int) * (size_t)N);
+    if (e == cudaSuccess && !bf) e = cudaMalloc((void**)&d_prange, sizeof(uint2) * (size_t)P.K * ntile);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_tile, sizeof(int) * (size_t)P.K * (ntile + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_poff, sizeof(long long) * ((size_t)N + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_dest, sizeof(uint32_t) * (size_t)g->n_records);
@@ -213,6 +246,11 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
                                                                                                       d_cnt);
         const long long items = (long long)P.K * (ntile + 1);
         tc_tile_off_kernel<<<(int)((items + 255) / 256), 256, 0, st>>>(P, ntile, g->d_rec_off, g->d_rec_key, d_tile);
+        if (!bf) {
+            const long long warps = (long long)P.K * ntile;
+            tc3_prange_kernel<<<(int)((warps * 32 + 255) / 256), 256, 0, st>>>(P, ntile, L3.phsplit, g->d_rec_off,
+                                                                              g->d_rec_key, d_tile, d_prange);
+        }
         e = cudaGetLastError();
     }
     std::vector<int> cnt(N);
@@ -242,6 +280,7 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
         cudaFree(d_dest);
         cudaFree(d_contrib);
         cudaFree(d_b);
+        cudaFree(d_prange);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
@@ -251,12 +290,14 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     } else {
         g->tc3 = L3;
         g->d_tc3_bop = d_b;
+        g->d_tc3_prange = d_prange;
     }
     g->d_tc_tile = d_tile;
     g->d_tc_pixoff = d_poff;
     g->d_tc_dest = d_dest;
     g->w_tc_contrib = d_contrib;
     g->bytes += bimg.size() * 2 + sizeof(int) * (size_t)P.K * (ntile + 1) + sizeof(long long) * ((size_t)N + 1) +
+                (bf ? 0 : sizeof(uint2) * (size_t)P.K * ntile) +
                 (sizeof(uint32_t) + sizeof(float)) * (size_t)g->n_records;
     return cudaMalloc((void**)&g->d_tc_counter, sizeof(int));
 }
@@ -290,7 +331,7 @@ cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, 
     if (ce != cudaSuccess) return ce;
     const int ntile = (P.M + kTcTile - 1) / kTcTile;
     const int grid = std::max(1, std::min(g->n_sm, P.K * ntile));
-    Tc3View V{P, L, g->d_tc3_bop, g->d_tab, e_pad, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_tile,
+    Tc3View V{P, L, g->d_tc3_bop, g->d_tab, e_pad, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_tile, g->d_tc3_prange,
               g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
     bwd_tc32_kernel<<<grid, kTcThreads, L.smem, st>>>(V, g->d_status);
     ce = cudaGetLastError();

@@ -48,13 +48,14 @@ struct TcAdjView {
 struct Tc3View {
     GeomParams P;
     Tc3Layout T;
-    const uint4* bop;                // half 0 image then half 1 image (three parts each)
+    const uint4* bop;                // half 0 image then half 1 image (two parts each)
     const float2* tab;               // FP32 kernel table (for the tau = t0 tap)
     const float* e;                  // residual, K x Mp
     const long long* rec_off;
     const int2* rkey;
     const float4* rw;
     const int* tile_off;
+    const uint2* prange;             // per (A-scan, tile): each half's lowest | highest plane << 16
     const uint32_t* dest;
     float* contrib;
     int* counter;
@@ -338,11 +339,11 @@ __device__ __forceinline__ void tc3_run_batch(const TcBatch& b, const GeomParams
         const int gi = trow / R, ph = trow - gi * R;
         if ((ph >= T.phsplit) != (half == 1)) continue;
         const int g1 = min(gi + 1, P.G - 1);
-        const float* cr = sC + (n0 - ts) * T.cstride + (ph - phb) * P.G;
-        float v = b.w[u].x * cr[gi];
-        v = fmaf(b.w[u].y, cr[g1], v);
-        v = fmaf(b.w[u].z, cr[P.G + gi], v);
-        v = fmaf(b.w[u].w, cr[P.G + g1], v);
+        const float* cr = sC + (n0 - ts) * T.cstride + (ph - phb);     // plane-major rows
+        float v = b.w[u].x * cr[gi * T.pstride];
+        v = fmaf(b.w[u].y, cr[g1 * T.pstride], v);
+        v = fmaf(b.w[u].z, cr[gi * T.pstride + 1], v);
+        v = fmaf(b.w[u].w, cr[g1 * T.pstride + 1], v);
         if (b.key[u].y & 1) {
             const float2 tl = __ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1);
             v -= (b.w[u].z * tl.x + b.w[u].w * tl.y) * sE[n0 - ts + P.Tw - 1];
@@ -356,9 +357,12 @@ __device__ __forceinline__ void tc3_run_batch(const TcBatch& b, const GeomParams
 // into [2^14, 2^15), split into two FP16 Hankel tiles; for each row half the
 // three products H_1 T_1 + H_1 T_2 + H_2 T_1 with the two-part table (scaled
 // on the host; the dropped H_2 T_2 is below 2^-22 of the result) accumulate in
-// tensor memory and are scaled back as they are read.  Both halves' table
-// operands stay resident (one bulk copy per pool, mbarrier at smem + 32);
-// smem + 64 holds the warps' window maxima.
+// tensor memory and are scaled back as they are read.  The table rows are
+// plane-major (plane * pstride + phase offset): per half only the rows of the
+// attenuation planes that the tile's records reach (precomputed per tile) are
+// multiplied and read back, and a half without records is skipped.  Both
+// halves' table operands stay resident (one bulk copy per pool, mbarrier at
+// smem + 32); smem + 64 holds the warps' window maxima.
 __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned char* smem, uint32_t tmem,
                                                   uint32_t& phase, uint32_t& bphase, int* status)
 {
@@ -402,6 +406,7 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
     float ew = 0.0f;
     long long pbase = 0;
     int pr0 = 0, pr1 = 0;
+    uint2 ppl = make_uint2(0u, 0u);
     TcBatch pb;
     auto prefetch = [&](int item) {
         const int k = item / ntile, t = item - k * ntile;
@@ -410,6 +415,7 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
         pbase = __ldg(rec_off + k);
         pr0 = __ldg(tile_off + (size_t)k * (ntile + 1) + t);
         pr1 = __ldg(tile_off + (size_t)k * (ntile + 1) + t + 1);
+        ppl = __ldg(V.prange + item);
         tc_load_batch(pb, rkey, rw, dest, pbase, pr0, pr1, tid);
     };
     if (it < nitems) prefetch(it);
@@ -417,6 +423,7 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
         const int t = it % ntile, ts = t * kTcTile;
         const long long base = pbase;
         const int r0 = pr0, r1 = pr1;
+        const uint2 planes = ppl;
         if (tid < W) sE[tid] = ew;
         {
             // the window's largest magnitude, one value per warp
@@ -461,12 +468,18 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
             __syncthreads();
         }
         for (int h = 0; h < 2; ++h) {
+            // the rows of the planes this half's records reach, in whole 16-row steps (uniform)
+            const uint32_t pw = h ? planes.y : planes.x;
+            const int glo = (int)(pw & 0xffffu), ghi = (int)(pw >> 16);
+            if (glo > ghi) continue;                 // no record of the tile in this half
+            const int n_lo = (glo * T.pstride) & ~15;
+            const int nr = min(T.nrows[h], ((ghi + 1) * T.pstride + 15) & ~15) - n_lo;
             if (tid == 0 && !*abort_flag) {
                 tc_fence_after();
-                const int nr = T.nrows[h];
                 const uint32_t idesc = umma_idesc_f16(kTcTile, nr);
-                const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB) + (uint32_t)(h ? T.bhalf[0] : 0);
-                const uint32_t bpart = (uint32_t)((size_t)nr * T.kpad * 2);
+                const uint32_t a0 = smem_u32(sH);
+                const uint32_t b0 = smem_u32(sB) + (uint32_t)(h ? T.bhalf[0] : 0) + (uint32_t)(n_lo / 8) * sbo;
+                const uint32_t bpart = (uint32_t)((size_t)T.nrows[h] * T.kpad * 2);
                 const int terms[3][2] = {{0, 0}, {0, 1}, {1, 0}};
                 for (int s = 0; s < T.kpad / 16; ++s)
                     for (int q = 0; q < 3; ++q)
@@ -484,12 +497,12 @@ __device__ __forceinline__ bool tc_adjoint32_pool(const Tc3View& V, unsigned cha
             {
                 const int q = warp & 3, part = warp >> 2;
                 const int row = q * 32 + lane;
-                const int cw = T.nrows[h] / 4;
+                const int cw = nr / 4;
                 for (int c = part * cw; c < part * cw + cw; c += 4) {
                     float v[4];
                     tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) sC[row * T.cstride + c + j] = (v[j] * unscale) * it_scale;
+                    for (int j = 0; j < 4; ++j) sC[row * T.cstride + n_lo + c + j] = (v[j] * unscale) * it_scale;
                 }
             }
             tc_fence_before();
