@@ -410,7 +410,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc_kernel(EngLists L)
             const ReqDesc& R = L.desc[rq];
             const int nitems = R.P.K * ((R.P.M + kTcTile - 1) / kTcTile);
             if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
-            const TcAdjView V{R.P, R.tcl, R.tc_bop, R.tab_bf, R.ebf, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc_dest,
+            const TcAdjView V{R.P, R.tcl, R.tc_bop, R.tab_bf, R.ebf, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc3_prange,
+                              R.tc_dest,
                               R.tc_contrib, L.pool + 2 * rq + 1};
             if (!tc_adjoint_pool(V, smem, tmem, phase, R.D.status)) break;
             __syncthreads();

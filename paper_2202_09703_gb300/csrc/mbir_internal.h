@@ -438,7 +438,8 @@ struct mbir_geometry {
     int* d_tc_counter;
     Tc3Layout tc3;
     uint4* d_tc3_bop;      // FP32 adjoint: both halves' two-part FP16 table operand images
-    uint2* d_tc3_prange;   // FP32 adjoint: per (A-scan, tile) and half, lowest | highest plane << 16
+    uint2* d_tc3_prange;   // tensor-core adjoints: per (A-scan, tile) and row half (FP32 form; the BF16 form
+                           // uses .x for the whole tile), lowest | highest plane << 16
     // tensor-core A x of the BF16 form (see tc_forward.cu)
     TfLayout tf;
     uint4* d_tf_bop;       // table operand image (taps x table rows, K-major)

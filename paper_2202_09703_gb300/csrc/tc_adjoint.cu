@@ -188,14 +188,14 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     const int R = P.Q + 1, nq = P.Q * P.Tw + 1;
     std::vector<__nv_bfloat16> bimg;
     if (bf) {
-        // table operand: row c = phase * G + plane, column m = tap, BF16 as in the stored table
+        // table operand: row plane * (Q + 1) + phase (plane-major, so that the planes a tile's records reach
+        // are one row range), column m = tap, BF16 as in the stored table
         bimg.assign((size_t)L.npad * L.kpad, __float2bfloat16_rn(0.0f));
-        for (int c = 0; c < L.ncols; ++c) {
-            const int gpl = c % P.G, ph = c / P.G;
-            for (int m = 0; m < P.Tw; ++m)
-                bimg[kmajor_offset(c, m, L.kpad) / 2] =
-                    __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
-        }
+        for (int gpl = 0; gpl < P.G; ++gpl)
+            for (int ph = 0; ph < R; ++ph)
+                for (int m = 0; m < P.Tw; ++m)
+                    bimg[kmajor_offset(gpl * R + ph, m, L.kpad) / 2] =
+                        __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
     } else {
         // FP32 form: per row half, the FP32 table (as the CUDA-core kernels read it) times 2^texp
         // (largest magnitude into [2^14, 2^15)), split into two FP16 parts t = t1 + t2; half h holds
@@ -232,7 +232,7 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     uint4* d_b = nullptr;
     uint2* d_prange = nullptr;
     cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int) * (size_t)N);
-    if (e == cudaSuccess && !bf) e = cudaMalloc((void**)&d_prange, sizeof(uint2) * (size_t)P.K * ntile);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_prange, sizeof(uint2) * (size_t)P.K * ntile);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_tile, sizeof(int) * (size_t)P.K * (ntile + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_poff, sizeof(long long) * ((size_t)N + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_dest, sizeof(uint32_t) * (size_t)g->n_records);
@@ -246,10 +246,13 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
                                                                                                       d_cnt);
         const long long items = (long long)P.K * (ntile + 1);
         tc_tile_off_kernel<<<(int)((items + 255) / 256), 256, 0, st>>>(P, ntile, g->d_rec_off, g->d_rec_key, d_tile);
-        if (!bf) {
+        {
+            // plane ranges per tile: per row half (FP32 form) or of the whole tile (BF16 form: no phase
+            // reaches the split R, every record counts as half 0)
             const long long warps = (long long)P.K * ntile;
-            tc3_prange_kernel<<<(int)((warps * 32 + 255) / 256), 256, 0, st>>>(P, ntile, L3.phsplit, g->d_rec_off,
-                                                                              g->d_rec_key, d_tile, d_prange);
+            tc3_prange_kernel<<<(int)((warps * 32 + 255) / 256), 256, 0, st>>>(P, ntile, bf ? R : L3.phsplit,
+                                                                              g->d_rec_off, g->d_rec_key, d_tile,
+                                                                              d_prange);
         }
         e = cudaGetLastError();
     }
@@ -290,14 +293,14 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     } else {
         g->tc3 = L3;
         g->d_tc3_bop = d_b;
-        g->d_tc3_prange = d_prange;
     }
+    g->d_tc3_prange = d_prange;
     g->d_tc_tile = d_tile;
     g->d_tc_pixoff = d_poff;
     g->d_tc_dest = d_dest;
     g->w_tc_contrib = d_contrib;
     g->bytes += bimg.size() * 2 + sizeof(int) * (size_t)P.K * (ntile + 1) + sizeof(long long) * ((size_t)N + 1) +
-                (bf ? 0 : sizeof(uint2) * (size_t)P.K * ntile) +
+                sizeof(uint2) * (size_t)P.K * ntile +
                 (sizeof(uint32_t) + sizeof(float)) * (size_t)g->n_records;
     return cudaMalloc((void**)&g->d_tc_counter, sizeof(int));
 }
@@ -312,7 +315,7 @@ cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e
     const int ntile = (P.M + kTcTile - 1) / kTcTile;
     const int grid = std::max(1, std::min(g->n_sm, P.K * ntile));
     TcAdjView V{P, L, g->d_tc_bop, g->d_tab_bf16, e_bf, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_tile,
-                 g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
+                 g->d_tc3_prange, g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
     bwd_tc_kernel<<<grid, kTcThreads, L.smem, st>>>(V, g->d_status);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;

@@ -39,6 +39,7 @@ struct TcAdjView {
     const int2* rkey;
     const float4* rw;
     const int* tile_off;
+    const uint2* prange;             // per (A-scan, tile): lowest | highest plane << 16 (.x)
     const uint32_t* dest;            // record -> pixel-major place
     float* contrib;                  // one contribution per record
     int* counter;                    // item counter (zeroed before the launch)
@@ -160,11 +161,11 @@ __device__ __forceinline__ void tc_run_batch(const TcBatch& b, const GeomParams&
         const int n0 = b.key[u].y >> kRecShift, trow = (b.key[u].y >> 1) & 0xfff;
         const int gi = trow / R, ph = trow - gi * R;
         const int g1 = min(gi + 1, P.G - 1);
-        const float* cr = sC + (n0 - ts) * T.cstride;
-        float v = b.w[u].x * cr[ph * P.G + gi];
-        v = fmaf(b.w[u].y, cr[ph * P.G + g1], v);
-        v = fmaf(b.w[u].z, cr[(ph + 1) * P.G + gi], v);
-        v = fmaf(b.w[u].w, cr[(ph + 1) * P.G + g1], v);
+        const float* cr = sC + (n0 - ts) * T.cstride + ph;      // plane-major rows: plane * (Q + 1) + phase
+        float v = b.w[u].x * cr[gi * R];
+        v = fmaf(b.w[u].y, cr[g1 * R], v);
+        v = fmaf(b.w[u].z, cr[gi * R + 1], v);
+        v = fmaf(b.w[u].w, cr[g1 * R + 1], v);
         if (b.key[u].y & 1) {
             const float2 tl = __bfloat1622float2(__ldg(tab + ((size_t)gi * R + ph + 1) * S + P.Tw - 1));
             const float ev = __bfloat162float(sE[n0 - ts + P.Tw - 1]);
@@ -177,7 +178,10 @@ __device__ __forceinline__ void tc_run_batch(const TcBatch& b, const GeomParams&
 
 // Drains the A^T items (A-scan, 128-sample tile) of V.  The next item's
 // residual window and first record batch are loaded into registers while the
-// current item's products and records are processed.
+// current item's products and records are processed.  Table rows are
+// plane-major (plane * (Q + 1) + phase): only the rows of the attenuation
+// planes that the tile's records reach (precomputed per tile) are multiplied
+// and read back, and a tile without records is skipped.
 __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned char* smem, uint32_t tmem,
                                                 uint32_t& phase, int* status)
 {
@@ -210,7 +214,6 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
     const int nitems = P.K * ntile;
     const int W = kTcTile + T.kpad;                  // residual window length (<= kTcThreads)
     const uint32_t lbo = 128, sbo = (uint32_t)(T.kpad / 8) * 128;
-    const uint32_t id0 = umma_idesc_bf16(kTcTile, T.nchunk0), id1 = umma_idesc_bf16(kTcTile, T.nchunk1 ? T.nchunk1 : 16);
     const int kc = T.kpad / 8;
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
 
@@ -219,6 +222,7 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
     __nv_bfloat16 ew = zero;
     long long pbase = 0;
     int pr0 = 0, pr1 = 0;
+    uint32_t ppl = 0;
     TcBatch pb;
     auto prefetch = [&](int item) {
         const int k = item / ntile, t = item - k * ntile;
@@ -227,6 +231,7 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
         pbase = __ldg(rec_off + k);
         pr0 = __ldg(tile_off + (size_t)k * (ntile + 1) + t);
         pr1 = __ldg(tile_off + (size_t)k * (ntile + 1) + t + 1);
+        ppl = __ldg(&V.prange[item].x);
         tc_load_batch(pb, rkey, rw, dest, pbase, pr0, pr1, tid);
     };
     if (it < nitems) prefetch(it);
@@ -234,6 +239,11 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
         const int t = it % ntile, ts = t * kTcTile;
         const long long base = pbase;
         const int r0 = pr0, r1 = pr1;
+        // the table rows (plane-major) of the planes the tile's records reach, in whole 16-row steps
+        const int glo = (int)(ppl & 0xffffu), ghi = (int)(ppl >> 16);
+        const int n_lo = glo <= ghi ? (glo * (P.Q + 1)) & ~15 : 0;
+        const int nr = glo <= ghi ? min(T.npad, ((ghi + 1) * (P.Q + 1) + 15) & ~15) - n_lo : 0;
+        const int nr0 = nr > 256 ? ((nr / 2) + 15) & ~15 : nr, nr1 = nr - nr0;
         if (tid < W) sE[tid] = ew;
         __syncthreads();                             // window visible; every thread has read *next
         if (tid == 0) *next = atomicAdd(counter, 1);
@@ -252,37 +262,39 @@ __device__ __forceinline__ bool tc_adjoint_pool(const TcAdjView& V, unsigned cha
         fence_async_smem();
         __syncthreads();                             // H complete; *next holds the following item
         const int it_next = *next;
-        if (tid == 0) {
+        if (nr > 0) {                                // a tile without records has nothing to correlate
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB) + (uint32_t)(n_lo / 8) * sbo;
+                const uint32_t id0 = umma_idesc_bf16(kTcTile, nr0), id1 = umma_idesc_bf16(kTcTile, nr1 ? nr1 : 16);
+                for (int s = 0; s < T.kpad / 16; ++s) {
+                    const uint64_t da = umma_desc(a0 + 256 * s, lbo, sbo);
+                    umma_bf16(tmem, da, umma_desc(b0 + 256 * s, lbo, sbo), id0, s > 0);
+                    if (nr1)
+                        umma_bf16(tmem + nr0, da, umma_desc(b0 + (nr0 / 8) * sbo + 256 * s, lbo, sbo), id1, s > 0);
+                }
+                umma_commit(smem_u32(bar));
+            }
+            if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
+            phase ^= 1u;
+            __syncthreads();                         // the flag is read uniformly: tensor-memory loads are warp-collective
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sH), b0 = smem_u32(sB);
-            for (int s = 0; s < T.kpad / 16; ++s) {
-                const uint64_t da = umma_desc(a0 + 256 * s, lbo, sbo);
-                umma_bf16(tmem, da, umma_desc(b0 + 256 * s, lbo, sbo), id0, s > 0);
-                if (T.nchunk1)
-                    umma_bf16(tmem + T.nchunk0, da, umma_desc(b0 + (T.nchunk0 / 8) * sbo + 256 * s, lbo, sbo), id1,
-                              s > 0);
-            }
-            umma_commit(smem_u32(bar));
-        }
-        if (!mbar_wait_bounded(smem_u32(bar), phase, status)) *abort_flag = 1;
-        phase ^= 1u;
-        __syncthreads();                             // the flag is read uniformly: tensor-memory loads are warp-collective
-        tc_fence_after();
-        if (!*abort_flag) {
-            // tensor memory -> shared C tile: warp = (lane quarter, column quarter)
-            const int q = warp & 3, part = warp >> 2;
-            const int row = q * 32 + lane;
-            const int cw = T.npad / 4;
-            for (int c = part * cw; c < part * cw + cw; c += 4) {
-                float v[4];
-                tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+            if (!*abort_flag) {
+                // tensor memory -> shared C tile (the range's rows only): warp = (lane quarter, column quarter)
+                const int q = warp & 3, part = warp >> 2;
+                const int row = q * 32 + lane;
+                const int cw = nr / 4;
+                for (int c = part * cw; c < part * cw + cw; c += 4) {
+                    float v[4];
+                    tmem_ld4(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) sC[row * T.cstride + c + j] = v[j];
+                    for (int j = 0; j < 4; ++j) sC[row * T.cstride + n_lo + c + j] = v[j];
+                }
             }
+            tc_fence_before();
+            __syncthreads();
+            if (*abort_flag) break;
         }
-        tc_fence_before();
-        __syncthreads();
-        if (*abort_flag) break;
         // records: the prefetched first batch, then the next item's prefetch, then the rest
         tc_run_batch(pb, P, T, sC, sE, tab, ts, r0, r1, tid, contrib);
         if (it_next < nitems) prefetch(it_next);
@@ -324,7 +336,7 @@ __device__ __forceinline__ void split2h_pair(float x0, float x1, uint32_t& hi, u
 }
 
 // Contributions of a batch's records whose phase falls in `half`, from that
-// half's correlation tile (columns (phase - first phase of the half) * G + plane).
+// half's correlation tile (columns plane * pstride + phase - first phase of the half).
 __device__ __forceinline__ void tc3_run_batch(const TcBatch& b, const GeomParams& P, const Tc3Layout& T, int half,
                                               const float* sC, const float* sE, const float2* __restrict__ tab,
                                               int ts, int rb, int r1, int tid, float* __restrict__ contrib)
