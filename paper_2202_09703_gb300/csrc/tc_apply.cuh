@@ -616,7 +616,7 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
     const int out_stride = V.out_stride;
     int* counter = V.counter;
 
-    // table operand: rows = taps, columns = table rows (phase * G + plane), K-major
+    // table operand: rows = taps, columns = table rows (plane * (Q + 1) + phase, plane-major), K-major
     const int nb16 = (int)((size_t)T.ntap * T.kb * 2 / 16);
     for (int i = tid; i < nb16; i += blockDim.x) reinterpret_cast<uint4*>(sB)[i] = __ldg(V.bop + i);
     __syncthreads();
@@ -624,6 +624,8 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
     const uint32_t lbo = 128, sboA = (uint32_t)(T.ka / 8) * 128, sboB = (uint32_t)(T.kb / 8) * 128;
     const uint32_t idesc = umma_idesc_bf16(kTfTile, T.ntap);
     const int si = tid >> 2, pj = tid & 3;            // scatter role: n0 row and phase class
+    int* wlo = reinterpret_cast<int*>(smem + 128);
+    int* whi = reinterpret_cast<int*>(smem + 192);
     for (;;) {
         if (tid == 0) *next = atomicAdd(counter, 1);
         __syncthreads();
@@ -646,6 +648,7 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
             float* arow0 = sAcc + si * T.astride;
             float* arow1 = sAcc1 + si * T.astride1 - T.c0;
             float flag_corr = 0.0f;
+            int glo = P.G, ghi = -1;                 // planes this thread's records reach
             if (ra < rz) {
                 const ushort4 go = __ldg(grp_off + (size_t)k * P.M + n0);
                 const int gs[5] = {0, go.x, go.y, go.z, rz - ra};
@@ -669,10 +672,12 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
                             const int trow = (key[u].y >> 1) & 0xfff;
                             const int gi = trow / R, ph = trow - gi * R;
                             const int g1 = min(gi + 1, P.G - 1);
+                            glo = min(glo, gi);
+                            ghi = max(ghi, g1);
                             if (pass == 0) {
-                                const int c = (ph + 1) * P.G;
-                                (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].z * xv[u];
-                                (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].w * xv[u];
+                                const int c0 = gi * R + ph + 1, c1 = g1 * R + ph + 1;
+                                (c0 < T.c0 ? arow0 : arow1)[c0] += w4[u].z * xv[u];
+                                (c1 < T.c0 ? arow0 : arow1)[c1] += w4[u].w * xv[u];
                                 if (key[u].y & 1) {
                                     // tau = t0 exactly: the last tap of the upper phase row lies outside
                                     const float2 tl =
@@ -680,9 +685,9 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
                                     flag_corr += xv[u] * (w4[u].z * tl.x + w4[u].w * tl.y);
                                 }
                             } else {
-                                const int c = ph * P.G;
-                                (c + gi < T.c0 ? arow0 : arow1)[c + gi] += w4[u].x * xv[u];
-                                (c + g1 < T.c0 ? arow0 : arow1)[c + g1] += w4[u].y * xv[u];
+                                const int c0 = gi * R + ph, c1 = g1 * R + ph;
+                                (c0 < T.c0 ? arow0 : arow1)[c0] += w4[u].x * xv[u];
+                                (c1 < T.c0 ? arow0 : arow1)[c1] += w4[u].y * xv[u];
                             }
                         }
                     }
@@ -695,33 +700,55 @@ __device__ __forceinline__ bool tc_forward_pool(const TcFwdView& V, unsigned cha
                 const float f3 = __shfl_down_sync(0xffffffffu, flag_corr, 3);
                 if (pj == 0 && n0 < P.M) sY[n0 + P.Tw] -= ((flag_corr + f1) + f2) + f3;
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                glo = min(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+                ghi = max(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+            }
+            if (lane == 0) {
+                wlo[warp] = glo;
+                whi[warp] = ghi;
+            }
             __syncthreads();
+            // the columns of the planes reached (plane-major), in whole 16-column K steps, split at the
+            // halves' boundary c0; every other sum is zero (a tile without records multiplies one zero step)
+            int c_lo = 0, c_hi = 16;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                glo = min(glo, wlo[w]);
+                ghi = max(ghi, whi[w]);
+            }
+            if (ghi >= glo) {
+                c_lo = (glo * R) & ~15;
+                c_hi = min(T.c0 + T.k1, ((ghi + 1) * R + 15) & ~15);
+            }
+            const int a0c = c_lo, z0c = min(c_hi, T.c0);                 // first half: [a0c, z0c)
+            const int a1c = max(c_lo, T.c0), z1c = c_hi;                 // second half: [a1c, z1c)
             // FP32 sums -> registers -> BF16 operands (K-major, 8 columns per 16-byte store): the first
             // half's operand goes over the start of its own sums, the second half's right after it
             {
-                const int cw1 = P.G * R - T.c0;
+                const int ncols = P.G * R;
                 unsigned char* sA1 = sA + (size_t)kTfTile * T.ka * 2;
                 uint4 pk[kTfStage];
-                tf_stage_half(pk, sAcc, T.astride, T.c0, T.k0, tid);
+                if (z0c > a0c) tf_stage_half(pk, sAcc + a0c, T.astride, z0c - a0c, z0c - a0c, tid);
                 __syncthreads();                     // every first-half sum is in registers
-                tf_write_half(pk, sA, T.k0, T.ka, tid);
-                if (cw1 > 0) {
-                    tf_stage_half(pk, sAcc1, T.astride1, cw1, T.k1, tid);
-                    tf_write_half(pk, sA1, T.k1, T.ka, tid);
+                if (z0c > a0c) tf_write_half(pk, sA, z0c - a0c, T.ka, tid);
+                if (z1c > a1c) {
+                    tf_stage_half(pk, sAcc1 + (a1c - T.c0), T.astride1, min(z1c, ncols) - a1c, z1c - a1c, tid);
+                    tf_write_half(pk, sA1, z1c - a1c, T.ka, tid);
                 }
                 fence_async_smem();
                 __syncthreads();
                 if (tid == 0) {
                     tc_fence_after();
-                    const uint32_t b0 = smem_u32(sB);
-                    const uint32_t a0 = smem_u32(sA), a1 = smem_u32(sA1), b1 = b0 + (uint32_t)(T.c0 / 8) * 128;
-                    for (int s = 0; s < T.k0 / 16; ++s)
+                    const uint32_t b0 = smem_u32(sB) + (uint32_t)(a0c / 8) * 128;
+                    const uint32_t b1 = smem_u32(sB) + (uint32_t)(a1c / 8) * 128;
+                    const uint32_t a0 = smem_u32(sA), a1 = smem_u32(sA1);
+                    for (int s = 0; s < (z0c - a0c) / 16; ++s)
                         umma_bf16(tmem, umma_desc(a0 + 256 * s, lbo, sboA), umma_desc(b0 + 256 * s, lbo, sboB), idesc,
                                   s > 0);
-                    if (cw1 > 0)
-                        for (int s = 0; s < T.k1 / 16; ++s)
-                            umma_bf16(tmem, umma_desc(a1 + 256 * s, lbo, sboA), umma_desc(b1 + 256 * s, lbo, sboB),
-                                      idesc, true);
+                    for (int s = 0; s < (z1c - a1c) / 16; ++s)
+                        umma_bf16(tmem, umma_desc(a1 + 256 * s, lbo, sboA), umma_desc(b1 + 256 * s, lbo, sboB),
+                                  idesc, z0c > a0c || s > 0);
                     umma_commit(smem_u32(bar));
                 }
             }

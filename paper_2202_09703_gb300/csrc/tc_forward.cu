@@ -45,7 +45,8 @@ TfLayout tf_layout(const GeomParams& P)
     L.ylen = ((P.M + kTfTile - 1) / kTfTile) * kTfTile + L.ntap + 2;   // every anti-diagonal target
     L.smem = L.off_y + (size_t)L.ylen * 4;
     const int per_thread = (kTfTile * (L.k0 / 8) + kTfThreads - 1) / kTfThreads;
-    L.ok = L.ntap <= 256 && L.k0 > 0 && L.smem <= 227 * 1024 && L.ncols <= 4096 && per_thread <= kTfStage;
+    L.ok = L.ntap <= 256 && L.k0 > 0 && L.k0 % 16 == 0 && L.smem <= 227 * 1024 && L.ncols <= 4096 &&
+           per_thread <= kTfStage;
     return L;
 }
 
@@ -183,10 +184,11 @@ cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st)
     const int nq = P.Q * P.Tw + 1, R = P.Q + 1;
     std::vector<__nv_bfloat16> bimg;
     if (bf) {
-        // table operand: row m (tap), column c = phase * G + plane; the second half starts at column k0
+        // table operand: row m (tap), column c = plane * (Q + 1) + phase (plane-major, so that the planes a
+        // tile's records reach are one column range); the second half starts at column k0
         bimg.assign((size_t)L.ntap * L.kb, __float2bfloat16_rn(0.0f));
         for (int c = 0; c < L.ncols; ++c) {
-            const int gpl = c % P.G, ph = c / P.G;
+            const int gpl = c / R, ph = c % R;
             const int kcol = c < L.c0 ? c : L.k0 + (c - L.c0);
             for (int m = 0; m < P.Tw; ++m)
                 bimg[kmajor_offset(m, kcol, L.kb) / 2] =
