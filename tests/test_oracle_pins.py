@@ -55,13 +55,14 @@ def test_leg_zero_offset_is_vertical():
     assert t1 == 0.0 and Th == 0.0
 
 
-def _fermat_time(speeds, eta, h):
-    """Minimum of sum sqrt((x_l - x_{l-1})^2 + eta_l^2) / c_l over crossings."""
-    L = len(eta)
-    if L == 1:
-        return math.hypot(h, eta[0]) / speeds[0]
+def _fermat_path(speeds, eta, h):
+    """Crossing points 0 = x_0 < x_1 < ... < x_L = h of the path that minimises
+    sum sqrt((x_l - x_{l-1})^2 + eta_l^2) / c_l (Fermat's principle, Newton
+    with backtracking on the convex total time), and that minimum."""
     c = np.asarray(speeds, float)
     e = np.asarray(eta, float)
+    if len(e) == 1:
+        return np.array([0.0, h]), math.hypot(h, e[0]) / c[0]
     x = h * np.cumsum(e)[:-1] / e.sum()              # straight-line start
 
     def total(xi):
@@ -84,7 +85,24 @@ def _fermat_time(speeds, eta, h):
         x = x - lam * step
         if np.max(np.abs(lam * step)) < 1e-18:
             break
-    return total(x)
+    return np.concatenate([[0.0], x, [h]]), total(x)
+
+
+def _fermat_time(speeds, eta, h):
+    """Minimum of sum sqrt((x_l - x_{l-1})^2 + eta_l^2) / c_l over crossings."""
+    return _fermat_path(speeds, eta, h)[1]
+
+
+def _crossed(thick, z):
+    """Layer thicknesses above depth z (the voxel's own layer cut at z)."""
+    eta, top = [], 0.0
+    for t in thick:
+        if z <= top + t or len(eta) == len(thick) - 1:
+            eta.append(z - top)
+            break
+        eta.append(t)
+        top += t
+    return eta
 
 
 @pytest.mark.parametrize("speeds,thick", [
@@ -96,15 +114,35 @@ def _fermat_time(speeds, eta, h):
 def test_leg_matches_fermat_minimum(speeds, thick, h, z):
     s = _scene_layers(speeds, thick)
     T = O.Geometry(s).leg(h, z)[0]
-    eta, top = [], 0.0
-    for t in thick:
-        if z <= top + t or len(eta) == len(thick) - 1:
-            eta.append(z - top)
-            break
-        eta.append(t)
-        top += t
+    eta = _crossed(thick, z)
     used = speeds[:len(eta)]
     assert T == pytest.approx(_fermat_time(used, eta, h), rel=1e-12)
+
+
+@pytest.mark.parametrize("speeds,thick,atten", [
+    ([1480.0, 5900.0], [2e-3, 10e-3], [0.7, 2.5]),
+    ([1480.0, 5900.0, 3000.0], [2e-3, 1.5e-3, 20e-3], [0.4, 1.3, 6.0]),
+    ([3000.0, 1500.0, 4500.0], [1e-3, 2e-3, 20e-3], [5.0, 0.3, 2.0]),
+])
+@pytest.mark.parametrize("h,z", [(1e-3, 4.5e-3), (6e-3, 8e-3), (2.5e-2, 12e-3)])
+def test_leg_gamma_and_angles_follow_the_fermat_path(speeds, thick, atten, h, z):
+    """Eq. 3, 6 and 12 along the ray in two and three layers: the attenuation
+    gamma is the sum over crossed layers of alpha_l times the length of the
+    path's segment in that layer, the first angle is atan(dx_1 / eta_1) and the
+    beam-profile angle Theta is the sum of atan(dx_l / eta_l), all taken from
+    the crossing points of the independent Fermat minimisation."""
+    s = _scene_layers(speeds, thick, atten=atten)
+    T, gm, Th, t1 = O.Geometry(s).leg(h, z)
+    eta = np.asarray(_crossed(thick, z))
+    assert len(eta) >= 2
+    pts, Tf = _fermat_path(speeds[:len(eta)], eta, h)
+    dx = np.diff(pts)
+    seg = np.sqrt(dx * dx + eta * eta)
+    alpha = np.asarray(atten[:len(eta)]) * 1e-6       # Np/(MHz m) -> s/m
+    assert T == pytest.approx(Tf, rel=1e-12)
+    assert gm == pytest.approx(float(np.sum(alpha * seg)), rel=1e-9)
+    assert t1 == pytest.approx(math.atan2(dx[0], eta[0]), rel=1e-9)
+    assert Th == pytest.approx(float(np.sum(np.arctan2(dx, eta))), rel=1e-9)
 
 
 def test_leg_binary_search_bracket_brute_force():
@@ -211,6 +249,78 @@ def test_pulse_table_quadrature_converged_and_energy_decreases():
     assert np.max(np.abs(t1 - t2)) < 1e-12
     energy = np.sum(t1 * t1, axis=1)
     assert np.all(np.diff(energy) < 0)
+
+
+def _cell_curvature_bound(s, gam_lo, dgam, tau_lo, dtau):
+    """Largest |d2h/dtau2| and |d2h/dgamma2| of the closed form over one table
+    cell, sampled on a 9 x 9 grid with central differences of step 1/40 cell."""
+    ht, hg = dtau / 40, dgam / 40 if dgam > 0 else 0.0
+    mt = mg = 0.0
+    for a in np.linspace(0.0, 1.0, 9):
+        for b in np.linspace(0.0, 1.0, 9):
+            g0, t0 = gam_lo + a * dgam, tau_lo + b * dtau
+            c = _h_closed_form(s, g0, t0)
+            mt = max(mt, abs(_h_closed_form(s, g0, t0 + ht) - 2 * c + _h_closed_form(s, g0, t0 - ht)) / ht ** 2)
+            if hg > 0:
+                gp, gm_ = g0 + hg, max(g0 - hg, 0.0)
+                mg = max(mg, abs(_h_closed_form(s, gp, t0) - 2 * c + _h_closed_form(s, gm_, t0))
+                         / (hg * (gp - gm_) / 2))
+    return mt, mg
+
+
+def test_table_read_between_nodes_matches_the_closed_form():
+    """The operator's h~(gamma, tau) between table nodes (eq. 9-10 read by the
+    bilinear rule of the discrete operator): at off-node phases and between
+    attenuation planes it equals the Faddeeva closed form within the
+    interpolation bound dtau^2/8 max|h_tautau| + dgamma^2/8 max|h_gammagamma|.
+    An interpolation weight taken on the wrong node (phi for 1 - phi, psi for
+    1 - psi) or a neighbouring cell is off by a first-order term, tens of times
+    that bound."""
+    s = S.cfg1()
+    p = O.Plan(s, pix=np.array([0]), nthreads=1)
+    g = O.Geometry(s)
+    G, gmax = g.effective_G(), g.gamma_max()
+    Tw = g.pulse_support()
+    dtau, dgam = 1.0 / (s.fs * s.Q), gmax / (G - 1)
+    checked = 0
+    for gi in (0, 4, G - 2):
+        for q in (5 * s.Q + 3, 30 * s.Q + 11, 41 * s.Q + 7, (Tw - 3) * s.Q + 14):
+            mt, mg = _cell_curvature_bound(s, gi * dgam, dgam, q * dtau, dtau)
+            bound = 1.05 * (dtau ** 2 / 8 * mt + dgam ** 2 / 8 * mg) + 5e-11
+            for phi in (0.27, 0.81):
+                for psi in (0.0, 0.33, 0.9):
+                    gam, tau = (gi + psi) * dgam, (q + phi) * dtau
+                    ref = _h_closed_form(s, gam, tau)
+                    assert abs(p.H(gam, tau) - ref) <= bound, (gi, q, phi, psi)
+                    checked += 1
+            # the read is affine along each axis inside the cell
+            h1, h2, h3 = (p.H((gi + 0.4) * dgam, (q + f) * dtau) for f in (0.1, 0.45, 0.8))
+            assert abs((h2 - h1) - (h3 - h2)) <= 1e-11 * (abs(h1) + abs(h3) + 1e-300)
+            h1, h2, h3 = (p.H((gi + f) * dgam, (q + 0.6) * dtau) for f in (0.1, 0.45, 0.8))
+            assert abs((h2 - h1) - (h3 - h2)) <= 1e-11 * (abs(h1) + abs(h3) + 1e-300)
+    assert checked == 72
+
+
+def test_table_read_clamps_gamma_and_honours_the_open_window():
+    """Attenuation beyond the table's top reads the last plane and negative
+    attenuation the first (both on a node: the closed form there); the open
+    window of eq. 10 gives 0 at tau <= 0 and tau >= t0."""
+    s = S.cfg1()
+    p = O.Plan(s, pix=np.array([0]), nthreads=1)
+    g = O.Geometry(s)
+    gmax, Tw = g.gamma_max(), g.pulse_support()
+    dtau = 1.0 / (s.fs * s.Q)
+    for q in (3 * s.Q, 20 * s.Q + 5, 47 * s.Q + 9):
+        tau = q * dtau
+        assert p.H(3.0 * gmax, tau) == p.H(gmax, tau)
+        assert abs(p.H(gmax, tau) - _h_closed_form(s, gmax, tau)) < 5e-11
+        assert p.H(-1e-6, tau) == p.H(0.0, tau)
+        assert abs(p.H(0.0, tau) - g.pulse(tau)) < 5e-11
+    t0 = Tw / s.fs
+    for gam in (0.0, 0.5 * gmax):
+        assert p.H(gam, 0.0) == 0.0 and p.H(gam, -dtau) == 0.0
+        assert p.H(gam, t0) == 0.0 and p.H(gam, t0 + 1e-12) == 0.0
+        assert p.H(gam, 0.5 * dtau) != 0.0 and p.H(gam, t0 - 0.5 * dtau) != 0.0
 
 
 # --------------------------------------------------------------------------
@@ -348,6 +458,37 @@ def test_firing_angle_closed_form_in_one_layer():
         r, c = divmod(v, s.img_w)
         vm = r * s.img_w + (s.img_w - 1 - c)
         assert _pair_factors(sm, vm, k)[0] == pytest.approx(_pair_factors(s, v, k)[0], rel=1e-12)
+
+
+def test_direct_columns_are_the_pulse_delayed_along_the_array():
+    """Eq. 1's direct-arrival basis (reading: one column per receiver, the
+    unattenuated pulse after the path |o_j| / c_1 through the first layer):
+    with offsets whose delays fall on whole samples the columns equal
+    s(n dt - |o_j| / c_1) inside the open window and 0 outside; an offset that
+    falls between table nodes agrees within the bilinear bound."""
+    fs, c1 = 10e6, 1500.0
+    offs = np.array([-1.5e-3, 0.75e-3, 3e-3, 1.0e-3])       # 10, 5, 20 and 6.67 samples
+    for atten in (False, True):
+        s = S.small_scene(n_layers=2, w=4, h=4, n_tx=1, n_rx=1, M=140, direct=True, atten=atten)
+        s.layers[0].speed = c1                        # the second layer (steel) is much faster
+        s.rx_offset = offs
+        p = O.Plan(s, pix=np.array([0]), nthreads=1)
+        g = O.Geometry(s)
+        Tw = g.pulse_support()
+        d = p.direct_columns()
+        assert d.shape == (len(offs), s.M)
+        n = np.arange(s.M)
+        for j, o in enumerate(offs[:3]):
+            D = round(abs(o) / c1 * fs)
+            ref = np.array([g.pulse((m - D) / fs) if 0 < m - D < Tw else 0.0 for m in n])
+            assert np.max(np.abs(d[j] - ref)) < (1e-12 if not atten else 5e-11), (atten, j)
+        Dt = abs(offs[3]) / c1
+        dtau = 1.0 / (fs * s.Q)
+        ts = np.linspace(0.0, Tw / fs, 4001)
+        s2 = np.array([g.pulse(t) for t in ts])
+        curv = np.max(np.abs(np.diff(s2, 2))) / (ts[1] - ts[0]) ** 2
+        ref = np.array([g.pulse(m / fs - Dt) if 0 < m / fs - Dt < Tw / fs else 0.0 for m in n])
+        assert np.max(np.abs(d[3] - ref)) <= 1.05 * dtau ** 2 / 8 * curv + 5e-11
 
 
 def test_projection_removes_direct_arrivals():
