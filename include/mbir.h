@@ -221,13 +221,19 @@ int mbir_backproject(const mbir_geometry* g, const void* r_dev, float* x_dev, vo
  *   - Geometries whose scratch would exceed 16 MiB (for a 256 x 512 image,
  *     more than about 3 M residual samples) and BF16-precision geometries
  *     return MBIR_ERR_UNSUPPORTED.
- *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture begins.  The geometry's device must be current.
+ *   - Set-up is part of mbir_create_geometry: creating a geometry that this
+ *     entry point takes looks up the array's device address on that device
+ *     (once per device; where modules load lazily this is when the array's
+ *     16 MiB are reserved) and loads the kernels of the call, so the call
+ *     itself loads and allocates nothing.  The geometry's device must be
+ *     current.
  *   - Every call rewrites the scratch before reading it, so no clearing is
  *     needed, but all calls share the one array: calls whose work overlaps on
  *     the GPU (other streams, other host threads) race and must be
- *     serialised by the caller.
+ *     serialised by the caller.  The call also uses the geometry's adjoint
+ *     work counter, so it must not overlap any other call that applies A^T
+ *     with the same geometry (mbir_backproject, the reconstructions, an
+ *     engine running a request of that geometry).
  * r_dev: K x M floats; x_dev: N floats, overwritten.  Asynchronous on
  * `stream`; no device memory is allocated or freed. */
 int mbir_backproject_noalloc(const mbir_geometry* g, const float* r_dev, float* x_dev, void* stream);

@@ -363,6 +363,19 @@ cudaError_t launch_backproject_lattice(const mbir_geometry* g, const int4* items
               : launch_bwd_lattice_t<8, kModeOTF, false>(g, items, nitems, ngroups, lat, partial, e, b, st);
 }
 
+// Loads the FP32 CUDA-core adjoint kernels that launch_backproject_partials runs for g (a query of their
+// attributes loads a lazily loaded module), so that a later launch does not load them.
+cudaError_t load_backproject_partials(const mbir_geometry* g)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, backproject_reduce_kernel);
+    if (e != cudaSuccess) return e;
+    if (g->P.mode == MBIR_MODE_TAB) return cudaFuncGetAttributes(&a, backproject_kernel<1, kModeTAB, false>);
+    if (g->P.L <= 2) return cudaFuncGetAttributes(&a, backproject_kernel<2, kModeOTF, false>);
+    if (g->P.L <= 4) return cudaFuncGetAttributes(&a, backproject_kernel<4, kModeOTF, false>);
+    return cudaFuncGetAttributes(&a, backproject_kernel<8, kModeOTF, false>);
+}
+
 cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
                                         float* b, float* partial, cudaStream_t st)
 {

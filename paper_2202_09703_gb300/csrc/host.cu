@@ -542,8 +542,12 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
             ce = mbir::build_tc_forward(g, st);
             if (ce == cudaErrorNotSupported) ce = cudaSuccess;  // keep the CUDA-core A x
             if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
+
         }
     }
+    // set-up of the allocation-free adjoint for this device (a no-op for geometries it does not take)
+    ce = mbir::noalloc_prepare(g);
+    if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
     ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
     g->bytes += bytes;          // the record and tensor-core tables added theirs already

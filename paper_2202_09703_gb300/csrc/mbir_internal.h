@@ -506,6 +506,9 @@ int backproject_tile_rows();
 cudaError_t backproject_tile_costs(const mbir_geometry* g, int ntr, int ntc, float* h_cost, cudaStream_t st);
 cudaError_t launch_backproject_partials(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
                                         float* b, float* partial, cudaStream_t st);
+cudaError_t load_backproject_partials(const mbir_geometry* g);
+cudaError_t load_pad_rows();
+cudaError_t noalloc_prepare(const mbir_geometry* g);
 size_t forward_smem(const mbir_geometry* g, int* cb_out);
 TcLayout tc_layout(const GeomParams& P);
 Tc3Layout tc3_layout(const GeomParams& P);

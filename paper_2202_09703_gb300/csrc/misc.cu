@@ -140,6 +140,13 @@ __global__ void pad_rows_kernel(GeomParams P, const void* __restrict__ src, int 
     }
 }
 
+// Loads pad_rows_kernel (see load_backproject_partials).
+cudaError_t load_pad_rows()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, pad_rows_kernel);
+}
+
 cudaError_t launch_pad_rows(const mbir_geometry* g, const void* src, int src_bf16, float* dst, cudaStream_t st)
 {
     pad_rows_kernel<<<g->P.K, 256, 0, st>>>(g->P, src, src_bf16, dst);

@@ -32,3 +32,18 @@ def ragged_scene():
     s = S.small_scene(n_layers=3, w=40, h=23, n_tx=3, n_rx=5, M=300, direct=True, name="tiny_ragged")
     s.layers[2].thickness = 50e-3
     return s
+
+
+def many_layer_scene(n_layers: int):
+    """A 5-8 layer medium (the kernels' 8-layer instantiation serves any scene
+    with more than 4 layers): 2 mm layers of alternating slow and fast
+    materials under a semi-infinite last layer, every layer holding pixels."""
+    assert 5 <= n_layers <= 8
+    s = S.small_scene(n_layers=1, w=36, h=30, n_tx=3, n_rx=4, M=420, direct=True,
+                      name=f"tiny_layers{n_layers}")
+    speeds = [1480.0, 5900.0, 3000.0, 4500.0, 2200.0, 3800.0, 2600.0, 5200.0]
+    atten = [2.0, 5.0, 30.0, 20.0, 12.0, 8.0, 15.0, 4.0]
+    dens = [1000.0, 7850.0, 1900.0, 2650.0, 1500.0, 2400.0, 1800.0, 7000.0]
+    s.layers = [S.Layer(1.5e-3 if i < n_layers - 1 else 20e-3, speeds[i],
+                        atten[i] * 0.058, dens[i]) for i in range(n_layers)]
+    return s

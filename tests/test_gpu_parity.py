@@ -12,7 +12,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2202_09703_gb300 import synth as S
-from tests.helpers import oracle_data, ragged_scene, rel_l2
+from tests.helpers import many_layer_scene, oracle_data, ragged_scene, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -115,6 +115,33 @@ def test_backproject_parity(mode, scene_fn):
 
 
 @pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n_layers", [5, 6])
+def test_many_layer_scenes_match_oracle(mode, n_layers):
+    """Five and six layers (eq. 4-6 with L > 4, served by the kernels' 8-layer
+    instantiation): delays, weights and attenuation of every pair, A x and
+    A^T r against the oracle."""
+    s = many_layer_scene(n_layers)
+    geo = make_geo(s, mode)
+    plan = O.Plan(s)
+    pix = np.repeat(np.arange(s.N), s.K)
+    ks = np.tile(np.arange(s.K), s.N)
+    T, g, w = geo.pair_quantities(pix, ks)
+    ref = np.array([plan.pair(int(v), int(k)) for v, k in zip(pix, ks)])
+    dT = T - ref[:, 0] * s.fs
+    assert np.max(np.abs(dT)) <= 1e-3
+    assert math.sqrt(np.mean(dT ** 2)) <= 2e-5
+    assert np.max(np.abs(w - ref[:, 2])) <= 2e-6
+    assert np.max(s.fc * np.abs(g - ref[:, 1]) * ref[:, 2]) <= 1e-6
+    rows = np.arange(s.img_h)
+    z = (rows + 0.5) * s.pitch
+    assert z[-1] > sum(L.thickness for L in s.layers[:-1])      # pixels in the last layer too
+    for x in (S.phantom(s, 4), S.random_vector(s.N, 43).reshape(s.img_h, s.img_w)):
+        assert rel_l2(gpu_forward(geo, x), plan.forward(x)) <= 1e-5
+    r = S.random_vector(s.K * s.M, 44)
+    assert rel_l2(gpu_backproject(geo, r), plan.backproject(r)) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_adjoint_identity_on_gpu(mode):
     s = S.cfg0()
     geo = make_geo(s, mode)
@@ -184,9 +211,10 @@ def test_bf16_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn)
 @pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene,
                                       lambda: S.small_scene(n_layers=1, w=32, h=16, n_tx=2, n_rx=3, M=200)])
 def test_fp32_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn):
-    """FP32 form: A^T on the tensor cores with the residual and the table each
-    split into three BF16 parts (six products kept, error below FP32
-    rounding), against the CUDA-core adjoint and the FP64 oracle."""
+    """FP32 form: A^T on the tensor cores with the residual window and the
+    table each scaled by a power of two and split into two FP16 parts (three
+    products kept, error below FP32 rounding), against the CUDA-core adjoint
+    and the FP64 oracle."""
     s = scene_fn()
     tc = make_geo(s, "tab")
     cc = make_geo(s, "tab", tensor_cores=False)
@@ -206,9 +234,10 @@ def test_fp32_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn)
                                                             atten=False)])
 def test_fp32_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn):
     """FP32 form: A x on the tensor cores (per-(sample, table row) sums of
-    weight x x in FP32 and the table, each split into three BF16 parts, six
-    products kept, two phase-aligned halves of the table rows) against the
-    CUDA-core A x and the FP64 oracle; the last scene has one gamma plane."""
+    weight x x in FP32 and the table, each scaled by a power of two and split
+    into two FP16 parts, three products kept, two phase-aligned halves of the
+    table rows) against the CUDA-core A x and the FP64 oracle; the last scene
+    has one gamma plane."""
     s = scene_fn()
     tc = make_geo(s, "tab")
     cc = make_geo(s, "tab", tensor_cores=False)
@@ -245,6 +274,40 @@ def test_fp32_tensor_core_forward_scaling_edge_cases(case):
         assert not np.any(y_tc)
     else:
         assert rel_l2(y_tc, y_cc) <= 1e-6
+
+
+@pytest.mark.parametrize("precision,bound", [("fp32", 1e-6), ("bf16", 4e-3)])
+@pytest.mark.parametrize("case", ["first_layer", "deepest_layer", "zero"])
+def test_tensor_core_forward_single_pixels_per_ascan(precision, bound, case):
+    """One pixel in the first layer, one in the deepest, and an all-zero image:
+    every A-scan of the tensor-core A x against the CUDA-core A x of the same
+    form on its own (an A-scan whose only record falls in a dropped plane or
+    column range would be far off), and against the oracle.  The BF16 form
+    rounds each per-(sample, table row) sum once to BF16 (2^-9 relative)."""
+    s = ragged_scene().copy(precision=precision)
+    tc = make_geo(s, "tab")
+    cc = make_geo(s, "tab", tensor_cores=False)
+    assert tc.info.forward_tensor_cores == 1 and cc.info.forward_tensor_cores == 0
+    x = np.zeros((s.img_h, s.img_w))
+    if case == "first_layer":
+        x[1, s.img_w // 2 + 3] = 0.8
+    elif case == "deepest_layer":
+        x[s.img_h - 1, s.img_w // 3] = -0.6
+    y_tc, y_cc = gpu_forward(tc, x), gpu_forward(cc, x)
+    if case == "zero":
+        assert not np.any(y_tc) and not np.any(y_cc)
+        return
+    y_ref = O.Plan(s).forward(x)
+    live = 0
+    for k in range(s.K):
+        nc = np.linalg.norm(y_cc[k])
+        if nc == 0.0:
+            assert not np.any(y_tc[k])
+            continue
+        live += 1
+        assert np.linalg.norm(y_tc[k] - y_cc[k]) <= bound * nc, k
+        assert rel_l2(y_tc[k], y_ref[k]) <= (1e-5 if precision == "fp32" else 1e-2), k
+    assert live >= s.K // 2
 
 
 @pytest.mark.parametrize("scene_fn", [S.cfg0, ragged_scene])
@@ -285,7 +348,7 @@ def test_bf16_storage_within_stated_error():
 
 
 # --------------------------------------------------------------------------
-# full-size cfg1 (the benchmark's launch configuration) on sampled outputs
+# full-size 256x512 workload on sampled outputs
 # --------------------------------------------------------------------------
 @pytest.fixture(scope="module")
 def cfg1_plan():
@@ -315,6 +378,54 @@ def test_cfg1_backproject_sampled_pixels(mode):
     plan = O.Plan(s, pix=pix)
     b_ref = plan.backproject(r)
     assert rel_l2(b[pix], b_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("cfg", ["cfg1", "cfg2"])
+def test_full_size_delays_on_sampled_pairs(cfg):
+    """Delays at the full workloads' magnitudes (up to ~4000 samples in the
+    256x512 scan and ~8000 in the 512x1024 one, where eq. 4's rounding bites
+    hardest): 4096 random (pixel, A-scan) pairs with a non-zero weight against
+    the oracle, max 1e-3 sample and RMS 2e-5 sample; weights and attenuation
+    as for the small scenes."""
+    s = S.CONFIGS[cfg]().copy(precision="fp32")
+    geo = make_geo(s, "tab")
+    rng = S.SplitMix64(31 if cfg == "cfg1" else 32)
+    pix = rng.integers(0, s.N - 1, 4096)
+    ks = rng.integers(0, s.K - 1, 4096)
+    upix, slot = np.unique(pix, return_inverse=True)
+    plan = O.Plan(s, pix=upix)
+    T, g, w = geo.pair_quantities(pix, ks)
+    ref = np.array([plan.pair(int(sl), int(k)) for sl, k in zip(slot, ks)])
+    act = ref[:, 2] > 0
+    assert act.sum() > 1000
+    dT = (T - ref[:, 0] * s.fs)[act]
+    assert np.max(ref[act, 0] * s.fs) > 0.8 * s.M          # delays near the end of the record are included
+    assert np.max(np.abs(dT)) <= 1e-3
+    assert math.sqrt(np.mean(dT ** 2)) <= 2e-5
+    assert np.max(np.abs(w - ref[:, 2])) <= 2e-6
+    assert np.max(s.fc * np.abs(g - ref[:, 1]) * ref[:, 2]) <= 1e-6
+
+
+def test_cfg2_fp32_sampled_ascans_and_pixels():
+    """The 512x1024 workload (128 Tx x 32 Rx, 4096 samples) in the FP32 form,
+    the benchmark's configuration: A x on the first, middle and last A-scans
+    and A^T r on 64 pixels (corners, centre and random) against the oracle at
+    relative L2 1e-5."""
+    s = S.cfg2().copy(precision="fp32")
+    geo = make_geo(s, "tab")
+    assert geo.info.forward_tensor_cores == 1 and geo.info.adjoint_tensor_cores == 1
+    plan = O.Plan(s)
+    x = S.phantom(s, 0)
+    y = gpu_forward(geo, x)
+    for k in (0, s.K // 2, s.K - 1):
+        assert rel_l2(y[k], plan.forward(x, k, k + 1)[0]) <= 1e-5, k
+    r = S.random_vector(s.K * s.M, 18)
+    b = gpu_backproject(geo, r)
+    rng = S.SplitMix64(6)
+    pix = np.unique(np.concatenate([[0, s.img_w - 1, s.N // 2 + s.img_w // 2, s.N - s.img_w, s.N - 1],
+                                    rng.integers(0, s.N - 1, 59)]))
+    bp = O.Plan(s, pix=pix)
+    assert rel_l2(b[pix], bp.backproject(r)) <= 1e-5
 
 
 # --------------------------------------------------------------------------
@@ -459,6 +570,22 @@ def test_cfg1_reconstruction_matches_oracle():
     plan, x_true, g_true, y, sig = oracle_data(s, seed=1)
     x_ref = np.asarray(plan.reconstruct(y, sig, 3)[0]).reshape(-1)
     assert rel_l2(_gpu_reconstruct(s, y, sig, 3), x_ref) <= 1e-4
+
+
+@pytest.mark.slow
+def test_cfg1_full_reconstruction_matches_oracle():
+    """The 4-layer 256x512 workload in FP32 with its full 50 MAP iterations
+    against the FP64 oracle's image (relative L2 1e-4), and the costs per
+    iteration."""
+    s = S.cfg1()
+    plan, x_true, g_true, y, sig = oracle_data(s, seed=1)
+    x_ref, g_ref, cost_ref, _ = plan.reconstruct(y, sig, s.n_iter)
+    geo = M.Geometry(s)
+    x = torch.empty(s.N, device=DEV)
+    out = geo.reconstruct(to_dev(np.asarray(y, np.float32).reshape(-1)), sig, s.n_iter, x, want_cost=True)
+    torch.cuda.synchronize()
+    assert rel_l2(x.cpu().numpy(), np.asarray(x_ref).reshape(-1)) <= 1e-4
+    assert np.allclose(out["cost"], cost_ref, rtol=1e-4)
 
 
 def test_bf16_reconstruction_image_error_against_oracle():
