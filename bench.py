@@ -2,17 +2,22 @@
 """Benchmark: MAP reconstructions per second of the layered collimated-beam
 model on one GB300 (and N independent replicas under torchrun).
 
-Workload (one step = one full reconstruction): the 4-layer scan of 256 x 512
-pixels at 0.5 mm (water 20 mm / steel 12 mm / cement 40 mm / rock), 64 Tx x
-16 receivers, 2048 samples at 20 MHz, 2 MHz 2-cycle pulse, direct arrivals on,
-depth-varying QGGMRF prior, 50 iterations in FP32.  Synthetic data
-y = A x + D g + w (SNR 20 dB) is made on the device by the library itself.
+Workload (one step = one full reconstruction): the 4-layer scan of 512 x 1024
+pixels at 0.25 mm (water 20 mm / steel 12 mm / cement 40 mm / rock), 128 Tx x
+32 receivers, 4096 samples at 20 MHz, 2 MHz 2-cycle pulse, direct arrivals on,
+depth-varying QGGMRF prior, 50 iterations in FP32 - the largest of the
+workloads that fits one GPU.  Synthetic data y = A x + D g + w (SNR 20 dB) is
+made on the device by the library itself.
 
 Reported: recons/s (device time of the timed steps, L2 flushed between steps),
 p50/p99 latency, an end-to-end figure through the host-buffer C ABI call, the
 roofline of the dominant kernel, GPU clocks sampled during the timed region,
-and (rank 0, one GPU) the FP64 oracle timed on a bounded sample on the host
-cores.  ``--impl reference`` times only the oracle.
+the geometry set-up time, and (rank 0, one GPU) the FP64 oracle timed on a
+bounded sample on the host cores.  Beside the headline (one GPU): the same
+workload in the BF16 storage form with its image error against the FP32 form,
+the 256 x 512 workload, the on-the-fly (OTF) applies, and a served stream of
+Poisson arrivals through the engine against serial FP32 solves.
+``--impl reference`` times only the oracle.
 """
 from __future__ import annotations
 
@@ -31,8 +36,12 @@ sys.path.insert(0, ROOT)
 
 FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
 SMEM_BYTES_PER_CLK = 128           # shared-memory load bandwidth per SM per clock
-WORKLOAD = ("4-layer water/steel/cement/rock, 256x512 image @0.5 mm, 64 Tx x 16 Rx, 2048 samples "
-            "@20 MHz, 2 MHz pulse, direct arrivals, depth-varying QGGMRF prior, 50 MAP iterations")
+WORKLOADS = {
+    "cfg2": ("4-layer water/steel/cement/rock, 512x1024 image @0.25 mm, 128 Tx x 32 Rx, 4096 samples "
+             "@20 MHz, 2 MHz pulse, direct arrivals, depth-varying QGGMRF prior, 50 MAP iterations, FP32"),
+    "cfg1": ("4-layer water/steel/cement/rock, 256x512 image @0.5 mm, 64 Tx x 16 Rx, 2048 samples "
+             "@20 MHz, 2 MHz pulse, direct arrivals, depth-varying QGGMRF prior, 50 MAP iterations, FP32"),
+}
 
 
 def parse():
@@ -46,9 +55,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--apply-only", type=int, default=0,
                     help="run only A x and A^T r this many times (for profiler captures) and exit")
-    ap.add_argument("--workload", default="cfg1", choices=["cfg1", "batched", "served", "saft", "icd"],
-                    help="cfg1: the headline workload; batched: uneven scenes through the engine vs serial "
-                         "solves; served: Poisson arrivals of mixed sizes through the engine vs a serial queue")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg1", "batched", "served", "saft", "icd"],
+                    help="cfg2: the headline workload (512x1024); cfg1: the 256x512 workload; batched: uneven "
+                         "scenes through the engine vs serial solves; served: Poisson arrivals of mixed sizes "
+                         "through the engine vs a serial queue")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the BF16 form, the 256x512 and OTF figures and the served stream")
+    ap.add_argument("--served-requests", type=int, default=100, help="requests per rate of the served figure")
     ap.add_argument("--requests", type=int, default=0, help="requests for the batched / served workloads")
     ap.add_argument("--source-hash", default="",
                     help="print the hash profiles/traffic.txt records for these comma-separated sources and exit")
@@ -138,63 +151,48 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # FP64 oracle on the host (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(scene, budget_s: float, x_img, gpu_rows=None):
+def oracle_sample(scene, budget_s: float, x_img):
     """Times the oracle on a bounded sample and extrapolates one reconstruction.
 
-    Sample: the forward operator on a few A-scans (legs cached separately) and
-    the adjoint on a block of pixels.  Returns (seconds per reconstruction,
-    description, threads, rel. L2 of the GPU's sampled A-scans vs the oracle)."""
+    Sample: a uniformly random set P of pixels, grown until the sample takes
+    about half the budget: the oracle's legs from every transducer position to
+    P, its A over every A-scan with the image restricted to P, and its A^T on
+    P.  Each cost is proportional to the pixels (pairs) it covers, so one
+    reconstruction (legs once, n_iter + 1 A, n_iter A^T) is the sample scaled
+    by N / |P|.  Returns (seconds per reconstruction, description, threads,
+    P, the oracle's A of the image restricted to P)."""
     import numpy as np
     from oracle import oracle as O
     from paper_2202_09703_gb300 import synth as S
 
     nthreads = os.cpu_count() or 1
-    plan = O.Plan(scene, nthreads=nthreads)
     K, N = scene.K, scene.N
-    ks = [0, K // 2, K - 1]
-    t0 = time.perf_counter()
-    yk = [plan.forward(x_img, k, k + 1)[0] for k in ks]       # legs for these positions + taps
-    t_first = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for k in ks:
-        plan.forward(x_img, k, k + 1)
-    t_fwd = (time.perf_counter() - t0) / len(ks)              # one A-scan, legs cached
-    legs_first = max(t_first - t_fwd * len(ks), 0.0)
-    n_pos_first = len({i for k in ks for i in (k // scene.n_rx,)}) + len(ks)
-    t_leg_per_pos = legs_first / max(n_pos_first, 1)          # all pixels, one position
-    # adjoint on a block of pixels inside the record, sized to the budget
-    rng = S.SplitMix64(7)
-    npix = 256
+    r = S.random_vector(K * scene.M, 3)
+    xf = np.asarray(x_img, np.float64).reshape(-1)
+    npix = 64
     while True:
-        pix = np.unique(rng.integers(0, min(N, 300 * scene.img_w) - 1, npix))
-        bp = O.Plan(scene, pix=pix, nthreads=nthreads)
-        r = S.random_vector(K * scene.M, 3)
+        pix = np.unique(S.SplitMix64(7).integers(0, N - 1, npix))
+        plan = O.Plan(scene, pix=pix, nthreads=nthreads)
         t0 = time.perf_counter()
-        bp.backproject(r)                                      # legs for these pixels + taps
+        plan.backproject(r)                                    # legs of every position to P, then the taps
         t_b1 = time.perf_counter() - t0
         t0 = time.perf_counter()
-        bp.backproject(r)
+        plan.backproject(r)
         t_b2 = time.perf_counter() - t0
-        bp.close()
-        if t_b1 + t_b2 > 0.3 * budget_s or npix >= N:
+        t0 = time.perf_counter()
+        y_p = plan.forward(xf)                                 # every A-scan, the image on P only
+        t_f = time.perf_counter() - t0
+        plan.close()
+        if t_b1 + t_b2 + t_f > 0.5 * budget_s or npix >= N:
             break
         npix = min(N, npix * 4)
-    active = min(N, 344 * scene.img_w)                        # rows whose vertical time is inside the record
-    t_bwd = t_b2 * active / len(pix)
-    legs_all = (t_b1 - t_b2) * active / len(pix)               # every position, every active pixel
-    t_fwd_full = t_fwd * K
+    scale = N / len(pix)
     n_iter = scene.n_iter
-    recon = legs_all + (n_iter + 1) * t_fwd_full + n_iter * t_bwd
-    desc = (f"oracle A on {len(ks)} A-scans and A^T on {len(pix)} pixels of the workload, "
-            f"extrapolated to one {n_iter}-iteration reconstruction (legs once, {n_iter + 1} A, {n_iter} A^T); "
-            f"{nthreads} OpenMP threads")
-    err = None
-    if gpu_rows is not None:
-        num = sum(float(np.sum((gpu_rows[i] - yk[i]) ** 2)) for i in range(len(ks)))
-        den = sum(float(np.sum(yk[i] ** 2)) for i in range(len(ks)))
-        err = math.sqrt(num / den)
-    plan.close()
-    return recon, desc, nthreads, err, ks
+    recon = scale * ((t_b1 - t_b2) + (n_iter + 1) * t_f + n_iter * t_b2)
+    desc = (f"oracle legs (every transducer position), A (all {K} A-scans) and A^T on {len(pix)} random pixels "
+            f"of the workload, scaled by N/|P| = {scale:.1f} to one {n_iter}-iteration reconstruction (legs once, "
+            f"{n_iter + 1} A, {n_iter} A^T); {nthreads} OpenMP threads")
+    return recon, desc, nthreads, pix, y_p
 
 
 def run_reference(args):
@@ -202,20 +200,20 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2202_09703_gb300 import synth as S
-    scene = S.cfg1()
+    scene = S.cfg1() if args.workload == "cfg1" else S.cfg2().copy(precision="fp32")
     x_img = S.phantom(scene, 0)
     times = []
     desc, nth = "", 1
     for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
         recon, desc, nth, _, _ = oracle_sample(scene, args.cpu_seconds / 3, x_img)
         if step >= args.warmup:
             times.append(recon)
     val = len(times) / sum(times)
+    wl = "cfg1" if args.workload == "cfg1" else "cfg2"
     out = {"impl": "reference", "metric": "recons/s", "value": val, "unit": "recons/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "data": "synthetic", "config": {"workload": WORKLOADS[wl]},
            "cpu_baseline": {"value": val, "unit": "recons/s", "cores": nth, "kind": "oracle", "sample": desc},
            "e2e": {"value": val, "unit": "recons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -237,6 +235,65 @@ def combine_ranks(t_dev: float, wall: float, steps: int, world: int, dist=None):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def headline_scene(S, workload: str):
+    return S.cfg1() if workload == "cfg1" else S.cfg2().copy(precision="fp32")
+
+
+def synth_scan(M, S, torch, geo, scene, seed, dev):
+    """y = A x_true + D g + w at 20 dB SNR, made by the library (FP32 storage)."""
+    K, Mn = scene.K, scene.M
+    x_true = torch.as_tensor(S.phantom(scene, seed).reshape(-1), dtype=torch.float32, device=dev)
+    y = torch.empty(K * Mn, dtype=torch.float32, device=dev)
+    geo.forward(x_true, y)
+    if scene.direct_arrival:
+        g_true = torch.as_tensor(S.direct_gains(scene, seed), dtype=torch.float32, device=dev) * y.abs().max()
+        geo.add_direct(g_true, y)
+    noise = torch.as_tensor(S.unit_noise(scene, seed).reshape(-1), dtype=torch.float32, device=dev)
+    sigma = math.sqrt(float((y.double() ** 2).sum()) / (100.0 * K * Mn))
+    y += sigma * noise
+    return x_true, y, sigma
+
+
+def timed_reconstructions(torch, geo, y, sigma, n_iter, x, steps, warmup, flush, stream):
+    """Device time per reconstruction (CUDA events on the launching stream), L2 flushed before each."""
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        geo.reconstruct(y, sigma, n_iter, x)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        geo.reconstruct(y, sigma, n_iter, x)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def apply_times(torch, geo, scene, dev, reps=5):
+    """Median device time of single A x and A^T r calls (CUDA events, after warm-up)."""
+    bf = geo.precision == "bf16"
+    x = torch.ones(scene.N, dtype=torch.float32, device=dev)
+    y = torch.empty(scene.K * scene.M, dtype=torch.bfloat16 if bf else torch.float32, device=dev)
+    b = torch.empty(scene.N, dtype=torch.float32, device=dev)
+    geo.forward(x, y)
+    geo.backproject(y, b)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    tf, tb = [], []
+    for _ in range(reps):
+        ev[0].record()
+        geo.forward(x, y)
+        ev[1].record()
+        torch.cuda.synchronize()
+        tf.append(ev[0].elapsed_time(ev[1]))
+        ev[0].record()
+        geo.backproject(y, b)
+        ev[1].record()
+        torch.cuda.synchronize()
+        tb.append(ev[0].elapsed_time(ev[1]))
+    return float(sorted(tf)[reps // 2]), float(sorted(tb)[reps // 2])
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -256,29 +313,23 @@ def run_gpu(args):
     from paper_2202_09703_gb300 import mbir as M
     from paper_2202_09703_gb300 import synth as S
 
-    scene = S.cfg1()
+    wl = "cfg1" if args.workload == "cfg1" else "cfg2"
+    scene = headline_scene(S, wl)
     stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     geo = M.Geometry(scene, mode=args.mode)
+    torch.cuda.synchronize()
+    geometry_ms = 1e3 * (time.perf_counter() - t0)
     K, Mn, N = scene.K, scene.M, scene.N
 
-    # synthetic scan: y = A x_true + D g + w at 20 dB SNR, made by the library
-    x_true = torch.as_tensor(S.phantom(scene, rank).reshape(-1), dtype=torch.float32, device=dev)
-    y = torch.empty(K * Mn, dtype=torch.float32, device=dev)
-    geo.forward(x_true, y)
-    g_true = torch.as_tensor(S.direct_gains(scene, rank), dtype=torch.float32, device=dev) * y.abs().max()
-    geo.add_direct(g_true, y)
-    noise = torch.as_tensor(S.unit_noise(scene, rank).reshape(-1), dtype=torch.float32, device=dev)
-    sigma = math.sqrt(float((y.double() ** 2).sum()) / (100.0 * K * Mn))
-    y += sigma * noise
+    x_true, y, sigma = synth_scan(M, S, torch, geo, scene, rank, dev)
     x = torch.empty(N, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
-    def step():
-        geo.reconstruct(y, sigma, scene.n_iter, x)
-
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        step()
+        geo.reconstruct(y, sigma, scene.n_iter, x)
     torch.cuda.synchronize()
     geo.set_profiling(True)
     geo.kernel_times(reset=True)
@@ -292,7 +343,7 @@ def run_gpu(args):
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
-        step()
+        geo.reconstruct(y, sigma, scene.n_iter, x)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
@@ -304,6 +355,8 @@ def run_gpu(args):
     lat = [a.elapsed_time(b) for a, b in ev]                 # ms per reconstruction
     t_dev = sum(lat) / 1e3
     t_dev, wall, value = combine_ranks(t_dev, wall, args.steps, world, dist)
+    x_fp32 = x.clone()
+    img_err_fp32 = float((x_fp32 - x_true).norm() / x_true.norm())
 
     # end to end through the host-buffer call: H2D of y, D2H of x and g
     y_h = y.cpu().pin_memory()
@@ -325,12 +378,11 @@ def run_gpu(args):
     e2e = {"value": args.steps * world / e_wall, "unit": "recons/s",
            "h2d_bytes_per_step": y_h.numel() * 4, "d2h_bytes_per_step": (x_h.numel() + g_h.numel()) * 4}
 
-    # roofline of the dominant apply kernel.  CUDA-core kernels: each tap reads
-    # the four bilinear corners of the pulse table (4 x 4 B) from shared memory
-    # and does 4 FMA; shared-memory bandwidth (128 B/clk/SM) binds before the
-    # FP32 pipes (128 FMA/clk/SM) do, so it is their primary roofline.
-    # Tensor-core kernels (taps become MMAs): the record stream is the
-    # algorithmic traffic, the TAB-mode bound of the path (HBM).
+    # roofline of the dominant apply kernel.  Tensor-core kernels (TAB mode): the record stream is the
+    # algorithmic traffic - 12 B per active pair is the smallest FP32 record (delay, weight, attenuation
+    # coordinate) - plus x and one A-scan array, against the measured HBM copy bandwidth.  CUDA-core kernels:
+    # each tap reads the four bilinear corners of the pulse table (4 x 4 B) from shared memory and does 4 FMA;
+    # shared-memory bandwidth (128 B/clk/SM) binds before the FP32 pipes (128 FMA/clk/SM) do.
     pk, src = peaks()
     pairs, taps = geo.count_taps()
     fwd_ms = kt["forward_ms"] / max(kt["forward_launches"], 1)
@@ -340,80 +392,127 @@ def run_gpu(args):
     clk_mhz = float(pk.get("sm_max_mhz", 2070.0))
     smem_peak = sm_count * SMEM_BYTES_PER_CLK * clk_mhz * 1e6 / 1e9            # GB/s
     smem_bytes = 16.0 * taps
-    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12       # TFLOP/s
-    flops = 8.0 * taps
     algo_bytes = 4.0 * (N + K * Mn)                      # x and one A-scan array in HBM
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     tc_dom = bool(geo.info.forward_tensor_cores if dom == "forward" else geo.info.adjoint_tensor_cores)
-    roofline = {"bound": "alu", "resource": "shared-memory load bandwidth (pulse-table corners per tap)",
-                "kernel": dom, "achieved": smem_bytes / (dom_ms * 1e-3) / 1e9, "peak": smem_peak,
-                "unit": "GB/s", "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak,
-                "traffic": measured_traffic("forward_sorted_kernel" if dom == "forward" else
-                                            "bwd_tc32_kernel" if geo.info.adjoint_tensor_cores else
-                                            "backproject_kernel"),
-                "traffic_note": "DRAM read+write bytes per launch (ncu); the kernel streams from L2/shared memory",
-                "peak_source": f"{sm_count} SMs x {SMEM_BYTES_PER_CLK} B/clk x {clk_mhz:.0f} MHz "
-                               f"(sm_max_mhz, {src})",
-                "algorithmic_bytes_per_launch": smem_bytes, "taps_per_launch": taps, "active_pairs": pairs,
-                "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
-                "fp32": {"algorithmic_flops_per_launch": flops, "achieved_tflops": flops / (dom_ms * 1e-3) / 1e12,
-                         "peak_tflops": fp32_peak, "frac": flops / (dom_ms * 1e-3) / 1e12 / fp32_peak},
-                "hbm": {"algorithmic_bytes_per_launch": algo_bytes,
-                        "achieved_gbs": algo_bytes / (dom_ms * 1e-3) / 1e9,
-                        "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),
-                        "frac": algo_bytes / (dom_ms * 1e-3) / 1e9 / float(pk.get("hbm_gbs", 6800.0))}}
     if tc_dom:
-        # 12 B per active pair is the smallest FP32 record (delay, weight, attenuation coordinate); the
-        # stored records hold 24 B (pixel, first tap | table row | flag, four bilinear weights x w) and
-        # the apply reads 4 B more of gathered x (A x) or writes 4 B of contribution (A^T r)
         rec_bytes = 12.0 * pairs + algo_bytes
-        hbm_peak = float(pk.get("hbm_gbs", 6800.0))
         name = "fwd_tc32_kernel" if dom == "forward" else "bwd_tc32_kernel"
-        roofline = {"bound": "hbm", "resource": "HBM: the TAB record stream (latency-bound record scatter)",
-                    "kernel": dom + " (tensor cores)", "achieved": rec_bytes / (dom_ms * 1e-3) / 1e9,
+        roofline = {"bound": "hbm", "resource": "HBM: the TAB record stream",
+                    "kernel": name, "achieved": rec_bytes / (dom_ms * 1e-3) / 1e9,
                     "peak": hbm_peak, "unit": "GB/s", "frac": rec_bytes / (dom_ms * 1e-3) / 1e9 / hbm_peak,
                     "traffic": measured_traffic(name),
-                    "traffic_note": "DRAM read+write bytes per launch (ncu)",
+                    "traffic_note": "DRAM read+write bytes per launch (ncu), null if the kernel changed since",
                     "peak_source": f"hbm_gbs ({src})", "algorithmic_bytes_per_launch": rec_bytes,
-                    "bytes_per_pair_minimum": 12, "bytes_per_pair_used": 28, "active_pairs": pairs,
-                    "taps_per_launch": taps, "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
-                    "shared_memory_tap_model": {"achieved_gbs": smem_bytes / (dom_ms * 1e-3) / 1e9,
-                                                "peak_gbs": smem_peak,
-                                                "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak}}
+                    "bytes_per_pair_minimum": 12, "active_pairs": pairs, "taps_per_launch": taps,
+                    "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
+                    "forward_frac": (12.0 * pairs + algo_bytes) / (fwd_ms * 1e-3) / 1e9 / hbm_peak,
+                    "backproject_frac": (12.0 * pairs + algo_bytes) / (bwd_ms * 1e-3) / 1e9 / hbm_peak}
+    else:
+        roofline = {"bound": "alu", "resource": "shared-memory load bandwidth (pulse-table corners per tap)",
+                    "kernel": dom, "achieved": smem_bytes / (dom_ms * 1e-3) / 1e9, "peak": smem_peak,
+                    "unit": "GB/s", "frac": smem_bytes / (dom_ms * 1e-3) / 1e9 / smem_peak,
+                    "traffic": None, "peak_source": f"{sm_count} SMs x {SMEM_BYTES_PER_CLK} B/clk x "
+                                                     f"{clk_mhz:.0f} MHz (sm_max_mhz, {src})",
+                    "algorithmic_bytes_per_launch": smem_bytes, "taps_per_launch": taps, "active_pairs": pairs,
+                    "forward_ms": fwd_ms, "backproject_ms": bwd_ms}
 
-    # per timed reconstruction: the projection of y, then per iteration A^T r and its group reduction,
-    # prior gradient, PR+ scalars, direction, A x (with the tensor cores: the record-order gather of the
-    # direction, then the product kernel), projection, step, update; the ncu launch list of this command
-    # agrees (501 for 50 iterations with the tensor-core A x)
-    per_it = 10 if geo.info.forward_tensor_cores else 9
-    launches = args.steps * (per_it * scene.n_iter + 1)
+    # per iteration: A^T r and its reduction, prior gradient, PR+ scalars, direction, A x, projection, step,
+    # update; per reconstruction one projection of y first
+    launches = args.steps * (9 * scene.n_iter + 1)
 
     out = {"metric": "recons/s", "value": value, "unit": "recons/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "mode": geo.mode, "iterations": scene.n_iter,
-                      "forward_window_spans": geo.info.forward_window_spans,
-                      "forward_window_ms": [round(t, 4) for t in geo.info.forward_window_ms],
+           "config": {"workload": WORKLOADS[wl], "mode": geo.mode, "iterations": scene.n_iter,
+                      "image": [scene.img_w, scene.img_h], "ascans": K, "samples": Mn,
                       "adjoint_groups": geo.info.adjoint_groups,
                       "l2": "flushed between steps (256 MB write); device time from CUDA events per step",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)),
                           "wall_s": wall},
+           "geometry_create_ms": geometry_ms,
+           "image_rel_err_vs_phantom": img_err_fp32,
            "e2e": e2e, "roofline": roofline, "clocks": clk, "gpu_launches": launches}
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    extras = world == 1 and rank == 0 and not args.no_extras
+    cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if cpu:
         xr = S.phantom(scene, 0)
-        yg = torch.empty(K * Mn, dtype=torch.float32, device=dev)
-        geo.forward(torch.as_tensor(xr.reshape(-1), dtype=torch.float32, device=dev), yg)
-        ygn = yg.cpu().numpy().reshape(K, Mn)
-        ks = [0, K // 2, K - 1]
-        recon, desc, nth, err, _ = oracle_sample(scene, args.cpu_seconds, xr, gpu_rows=[ygn[k] for k in ks])
+        recon, desc, nth, pix, y_p = oracle_sample(scene, args.cpu_seconds, xr)
         out["cpu_baseline"] = {"value": 1.0 / recon, "unit": "recons/s", "cores": nth, "kind": "oracle",
                                "sample": desc}
-        out["oracle_rel_l2_sampled_A"] = err
+        # full-size parity on the same sample: every A-scan of A x for the image restricted to P
+        xm = np.zeros(N)
+        xm[pix] = np.asarray(xr, np.float64).reshape(-1)[pix]
+        yg = torch.empty(K * Mn, dtype=torch.float32, device=dev)
+        geo.forward(torch.as_tensor(xm, dtype=torch.float32, device=dev), yg)
+        d = yg.cpu().numpy().astype(np.float64).reshape(K, Mn) - y_p
+        out["oracle_rel_l2_A_sampled_pixels_all_ascans"] = float(np.linalg.norm(d) / np.linalg.norm(y_p))
+        del yg
+
+    if extras:
+        out["extras"] = run_extras(args, M, S, torch, np, scene, geo, y, sigma, x_true, x_fp32, flush, stream, dev)
+    geo.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_extras(args, M, S, torch, np, scene, geo, y, sigma, x_true, x_fp32, flush, stream, dev):
+    """Figures beside the headline (one GPU): the BF16 storage form of the same scan, per-apply times, the
+    256 x 512 workload, the on-the-fly applies of that workload, and the served stream."""
+    ex = {}
+    steps = max(2, min(args.steps, 5))
+    fwd, bwd = apply_times(torch, geo, scene, dev)
+    ex["fp32_apply_ms"] = {"forward": fwd, "backproject": bwd}
+    ex["fp32_geometry_bytes"] = geo.nbytes
+    geo.close()                                  # the headline's tables go before the next geometries
+    torch.cuda.empty_cache()
+    # BF16 storage form: same data rounded to BF16, same sigma
+    t0 = time.perf_counter()
+    g16 = M.Geometry(scene.copy(precision="bf16"), mode="tab")
+    torch.cuda.synchronize()
+    g16_ms = 1e3 * (time.perf_counter() - t0)
+    ex["bf16_geometry_bytes"] = g16.nbytes
+    x16 = torch.empty(scene.N, dtype=torch.float32, device=dev)
+    lat16 = timed_reconstructions(torch, g16, y.to(torch.bfloat16), sigma, scene.n_iter, x16, steps, 1, flush,
+                                  stream)
+    f16, b16 = apply_times(torch, g16, scene, dev)
+    ex["bf16_storage"] = {"recons_per_s": 1e3 * len(lat16) / sum(lat16), "ms_per_step": sum(lat16) / len(lat16),
+                          "steps": len(lat16), "geometry_create_ms": g16_ms,
+                          "apply_ms": {"forward": f16, "backproject": b16},
+                          "image_rel_diff_vs_fp32": float((x16 - x_fp32).norm() / x_fp32.norm()),
+                          "image_rel_err_vs_phantom": float((x16 - x_true).norm() / x_true.norm())}
+    g16.close()
+    del x16
+    torch.cuda.empty_cache()
+    # the 256 x 512 workload, TAB (tensor cores) and OTF
+    s1 = S.cfg1()
+    t0 = time.perf_counter()
+    g1 = M.Geometry(s1, mode="tab")
+    torch.cuda.synchronize()
+    g1_ms = 1e3 * (time.perf_counter() - t0)
+    xt1, y1, sig1 = synth_scan(M, S, torch, g1, s1, 0, dev)
+    x1 = torch.empty(s1.N, dtype=torch.float32, device=dev)
+    lat1 = timed_reconstructions(torch, g1, y1, sig1, s1.n_iter, x1, max(args.steps, 5), args.warmup, flush, stream)
+    f1, b1 = apply_times(torch, g1, s1, dev)
+    pairs1, taps1 = g1.count_taps()
+    ex["cfg1"] = {"workload": WORKLOADS["cfg1"], "recons_per_s": 1e3 * len(lat1) / sum(lat1),
+                  "ms_per_step": sum(lat1) / len(lat1), "geometry_create_ms": g1_ms,
+                  "apply_ms": {"forward": f1, "backproject": b1}, "active_pairs": pairs1, "taps": taps1,
+                  "image_rel_err_vs_phantom": float((x1 - xt1).norm() / xt1.norm())}
+    g1.close()
+    go = M.Geometry(s1, mode="otf")
+    fo, bo = apply_times(torch, go, s1, dev)
+    ex["cfg1_otf"] = {"apply_ms": {"forward": fo, "backproject": bo},
+                      "note": "travel times solved in registers on every apply (eq. 4-6); no records"}
+    go.close()
+    torch.cuda.empty_cache()
+    if args.served_requests > 0:
+        ex["served"] = served_measure(M, S, torch, np, dev, args.served_requests, (20.0, 200.0))
+    return ex
 
 
 def run_apply_only(args):
@@ -529,20 +628,11 @@ def run_batched(args):
                       "higher_is_better": True, "data": "synthetic", "config": out}), flush=True)
 
 
-def run_served(args):
-    """Poisson arrivals mixing the three workload sizes (60/30/10 %), each a
-    50-iteration reconstruction, served by the engine (admission capped at
-    120 GB) in FP32 and in the BF16 storage form, against a serial FIFO of
-    FP32 mbir_reconstruct calls on the same GPU; image error against the
-    phantom reported for each."""
-    import numpy as np
-    import torch
-    from paper_2202_09703_gb300 import build as B
-    B.build()
-    from paper_2202_09703_gb300 import mbir as M
-    from paper_2202_09703_gb300 import synth as S
-    dev = torch.device("cuda:0")
-    n = args.requests or 24
+def served_measure(M, S, torch, np, dev, n, rates):
+    """Poisson arrivals mixing the three workload sizes (64x64 / 256x512 / 512x1024 at 60/30/10 %), each a
+    50-iteration reconstruction, served by the engine (admission capped at 120 GB) in FP32 and in the BF16
+    storage form, against a serial FIFO of FP32 mbir_reconstruct calls on the same GPU.  Latency runs from a
+    request's arrival to its completion seen by the host; image error against the phantom."""
     classes = [S.cfg0(), S.cfg1(), S.cfg2().copy(precision="fp32")]
     for c in classes:
         c.n_iter = 50
@@ -553,12 +643,12 @@ def run_served(args):
              for ci, c in enumerate(classes)}
     rng = S.SplitMix64(4242)
     results = {}
-    for rate in (20.0, 200.0):
+    for rate in rates:
         u = rng.uniform(n)
         kinds = np.where(u < 0.6, 0, np.where(u < 0.9, 1, 2))
         gaps = -np.log(1.0 - rng.uniform(n)) / rate
         arrive = np.cumsum(gaps)
-        res = {}
+        res = {"mix": [int(np.sum(kinds == c)) for c in range(3)]}
         for mode in ("engine", "engine_bf16", "serial"):
             src = pool_bf if mode == "engine_bf16" else pool
             xs = [torch.empty(classes[k].N, device=dev) for k in kinds]
@@ -599,9 +689,25 @@ def run_served(args):
                          "p99_ms": 1e3 * float(np.percentile(lat, 99)), "makespan_s": float(max(done)),
                          "image_rel_err_vs_truth": img}
         results[f"{rate:g}_req_per_s"] = res
-    cfg = {"workload": f"served: {n} Poisson requests per rate, sizes 64x64 / 256x512 / 512x1024 at 60/30/10 %",
-           "rates": results}
-    best = results["200_req_per_s"]["engine_bf16"]["recons_per_s"]
+    for p_ in (pool, pool_bf):
+        for geo, _, _ in p_.values():
+            geo.close()
+    torch.cuda.empty_cache()
+    return {"workload": f"served: {n} Poisson requests per rate, sizes 64x64 / 256x512 / 512x1024 at 60/30/10 %, "
+                        "50 iterations each", "rates": results}
+
+
+def run_served(args):
+    """The served stream alone (see served_measure)."""
+    import numpy as np
+    import torch
+    from paper_2202_09703_gb300 import build as B
+    B.build()
+    from paper_2202_09703_gb300 import mbir as M
+    from paper_2202_09703_gb300 import synth as S
+    dev = torch.device("cuda:0")
+    cfg = served_measure(M, S, torch, np, dev, args.requests or 100, (20.0, 200.0))
+    best = cfg["rates"]["200_req_per_s"]["engine_bf16"]["recons_per_s"]
     print(json.dumps({"metric": "recons/s", "value": best, "unit": "recons/s", "higher_is_better": True,
                       "data": "synthetic", "config": cfg}), flush=True)
 

@@ -36,6 +36,7 @@
 #include "apply_common.cuh"
 #include "map_common.cuh"
 #include "tc_apply.cuh"
+#include "tc_stream.cuh"
 
 namespace mbir {
 PriorParams make_prior_params(const mbir_prior* pr);
@@ -95,20 +96,18 @@ struct ReqDesc {
     const uint4* tc3_bop;
     const uint2* tc3_prange;
     TcLayout tcl;
-    TfLayout tfl;
     const uint4* tc_bop;
     const int* tc_tile;
     const uint32_t* tc_dest;
     const long long* tc_pixoff;
     float* tc_contrib;     // this request's contributions (pixel-major)
-    const uint4* tf_bop;
-    const int* tf_n0off;
-    const ushort4* tf_grpoff;
+    // tensor-core A x (tcs != 0)
+    int tcs;
+    Tf4Layout tf4l;
+    const uint4* tf4_bop;
+    const uint32_t* tf4_crange;
+    const int* tf4_split;
     const int* tf_order;
-    int tf32;              // FP32 tensor-core A x pool available
-    Tf3Layout tf3l;
-    const uint4* tf3_bop;
-    const uint4* tf3_grpoff;
     long long nrec;        // records of the geometry
 };
 
@@ -473,25 +472,15 @@ __global__ void eng_bwd_tc_reduce_kernel(EngLists L)
     }
 }
 
-// the direction gathered per record of every active request (record order),
-// into the request's contribution buffer (free between the two applies)
-__global__ void eng_tc_gather_kernel(EngLists L)
-{
-    const int nreq = L.counts[0];
-    for (int rq = 0; rq < nreq; ++rq) {
-        const ReqDesc& R = L.desc[rq];
-        tc_gather_x(R.nrec, R.rkey, dnew_of(R), R.tc_contrib);
-    }
-}
-
-// q = A d of the BF16 form on the tensor cores over every active request
-__global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc_kernel(EngLists L)
+// q = A d on the tensor cores over every active request (FP32 or BF16 form)
+template <bool BF16>
+__global__ void __launch_bounds__(kTsThreads, 1) eng_fwd_tcs_kernel(EngLists L)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    tc_header_init(smem, kTfCols);
+    tc_header_init(smem, kTsCols);
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
     volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
-    uint32_t phase = 0;
+    uint32_t mphase = 0, bphase = 0;
     const int nreq = L.counts[0];
     if (nreq > 0) {
         const int r0 = L.start[gridDim.x + blockIdx.x] % nreq;
@@ -499,37 +488,14 @@ __global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc_kernel(EngLists L)
             const int rq = (r0 + t) % nreq;
             const ReqDesc& R = L.desc[rq];
             if (!eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
-            const TcFwdView V{R.P, R.tfl, R.tf_bop, R.tab_bf, R.rec_off, R.tf_n0off, R.tf_grpoff, R.rkey, R.rw,
-                              R.tf_order, R.tc_contrib, R.q, nullptr, R.P.Mp, L.pool + 2 * rq};
-            if (!tc_forward_pool(V, smem, tmem, phase, R.D.status)) break;
+            const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
+            const TsView V{R.P, R.tf4l, R.tf4_bop, tab, R.rec_off, R.tf4_crange, R.tf4_split, R.rkey, R.rw,
+                           R.tf_order, dnew_of(R), R.q, 0, R.P.Mp, L.pool + 2 * rq};
+            if (!tcs_forward_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
             __syncthreads();
         }
     }
-    tc_header_release(smem, tmem, kTfCols);
-}
-
-// q = A d of the FP32 form on the tensor cores over every active request
-__global__ void __launch_bounds__(kTfThreads, 1) eng_fwd_tc32_kernel(EngLists L)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    tc_header_init(smem, kTf3Cols);
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
-    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
-    uint32_t phase = 0, bphase = 0;
-    const int nreq = L.counts[0];
-    if (nreq > 0) {
-        const int r0 = L.start[gridDim.x + blockIdx.x] % nreq;
-        for (int t = 0; t < nreq; ++t) {
-            const int rq = (r0 + t) % nreq;
-            const ReqDesc& R = L.desc[rq];
-            if (!eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
-            const TcFwd32View V{R.P, R.tf3l, R.tf3_bop, R.tab, R.rec_off, R.tf_n0off, R.tf3_grpoff, R.rkey, R.rw,
-                                R.tf_order, R.tc_contrib, R.q, R.P.Mp, L.pool + 2 * rq};
-            if (!tc_forward32_pool(V, smem, tmem, phase, bphase, R.D.status)) break;
-            __syncthreads();
-        }
-    }
-    tc_header_release(smem, tmem, kTf3Cols);
+    tc_header_release(smem, tmem, kTsCols);
 }
 
 // in-place direct-arrival projection of q per (request, A-scan), FP64 |q|^2
@@ -643,7 +609,7 @@ size_t request_bytes(const mbir_geometry* g, int ngroups)
     size_t b = 2 * KMp * 4 + 6 * N * 4 + (size_t)ngroups * N * 4 + (size_t)P.H * 4 + S_COUNT * 8 +
                (4 * nblk + P.K + 8) * 8;
     if (P.precision == MBIR_PREC_BF16) b += KMp * 2;
-    if ((g->d_tc_bop && g->d_tf_bop) || g->d_tc3_bop) b += (size_t)g->n_records * 4;   // tensor-core contributions
+    if (g->d_tc_bop || g->d_tc3_bop) b += (size_t)g->n_records * 4;   // tensor-core adjoint contributions
     return b;
 }
 
@@ -738,7 +704,7 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     AL(r->sc, (size_t)S_COUNT);
     AL(r->part, (size_t)4 * r->nblk + P.K + 8);
     if (P.precision == MBIR_PREC_BF16) AL(r->ebf, KMp);
-    if ((g->d_tc_bop && g->d_tf_bop) || g->d_tc3_bop) AL(r->contrib, (size_t)g->n_records);
+    if (g->d_tc_bop || g->d_tc3_bop) AL(r->contrib, (size_t)g->n_records);
 #undef AL
     if (e != cudaSuccess) { free_request_state(r, st); return e == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA; }
     r->msq_host.resize(P.H);
@@ -802,26 +768,23 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.nwin = (int)g->n_win;
     d.sub = g->fwd_sub;
     d.nblk = r->nblk;
-    d.tc = (g->d_tc_bop && g->d_tf_bop) ? 1 : 0;
+    d.tc = g->d_tc_bop ? 1 : 0;
     d.tc32 = g->d_tc3_bop ? 1 : 0;
     d.tc3l = g->tc3;
     d.tc3_bop = g->d_tc3_bop;
     d.tc3_prange = g->d_tc3_prange;
     d.tcl = g->tc;
-    d.tfl = g->tf;
     d.tc_bop = g->d_tc_bop;
     d.tc_tile = g->d_tc_tile;
     d.tc_dest = g->d_tc_dest;
     d.tc_pixoff = g->d_tc_pixoff;
     d.tc_contrib = r->contrib;
-    d.tf_bop = g->d_tf_bop;
-    d.tf_n0off = g->d_tf_n0off;
-    d.tf_grpoff = g->d_tf_grpoff;
+    d.tcs = g->d_tf4_bop ? 1 : 0;
+    d.tf4l = g->tf4;
+    d.tf4_bop = g->d_tf4_bop;
+    d.tf4_crange = g->d_tf4_crange;
+    d.tf4_split = g->d_tf4_split;
     d.tf_order = g->d_tf_order;
-    d.tf32 = g->d_tf3_bop ? 1 : 0;
-    d.tf3l = g->tf3;
-    d.tf3_bop = g->d_tf3_bop;
-    d.tf3_grpoff = g->d_tf3_grpoff;
     d.nrec = g->n_records;
 }
 
@@ -957,13 +920,8 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cuda
     eng_grad_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     eng_findir_kernel<<<G, kRedThreads, 0, st>>>(E->L);
     eng_dir_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
-    if (tc && bf16) {
-        eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
-        eng_fwd_tc_kernel<<<G, kTfThreads, E->smem_tc[2], st>>>(E->L);
-    } else if (tc && tcf) {
-        eng_tc_gather_kernel<<<SG, 256, 0, st>>>(E->L);
-        eng_fwd_tc32_kernel<<<G, kTfThreads, E->smem_tc[3], st>>>(E->L);
-    }
+    if (tcf && bf16) eng_fwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[2], st>>>(E->L);
+    else if (tcf) eng_fwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[2], st>>>(E->L);
     else if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     else eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     eng_proj_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
@@ -993,8 +951,8 @@ int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e != cudaSuccess) { delete E; return MBIR_ERR_CUDA; }
     *out = E;
     return MBIR_OK;
@@ -1102,19 +1060,18 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
     bool tc = true;                      // tensor-core pools when every request of the step has them
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
-    bool tcf = !bf16;                    // FP32: tensor-core A x too when every request has its tables
+    bool tcf = true;                     // tensor-core A x when every request has its tables
     for (Request* r : E->sel) {
         if (!r->contrib) tc = false;
-        if (!r->g->d_tf3_bop) tcf = false;
+        if (!r->g->d_tf4_bop) tcf = false;
     }
-    const int gtc = (int)tc + 2 * (int)(tc && tcf);
+    const int gtc = (int)tc + 2 * (int)tcf;
     size_t smem_tc[4] = {1024, 1024, 1024, 1024};
     for (Request* r : E->active) {
         const mbir_geometry* g = r->g;
         if (g->d_tc_bop) smem_tc[0] = std::max(smem_tc[0], g->tc.smem);
         if (g->d_tc3_bop) smem_tc[1] = std::max(smem_tc[1], g->tc3.smem);
-        if (g->d_tf_bop) smem_tc[2] = std::max(smem_tc[2], g->tf.smem);
-        if (g->d_tf3_bop) smem_tc[3] = std::max(smem_tc[3], g->tf3.smem);
+        if (g->d_tf4_bop) smem_tc[2] = std::max(smem_tc[2], g->tf4.smem);
     }
     const bool smem_changed = !std::equal(smem_tc, smem_tc + 4, E->smem_tc);
     if (grew || smem_changed || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != gtc) {

@@ -250,8 +250,7 @@ static cudaError_t launch_fwd_nl(const mbir_geometry* g, const float* x, float* 
 cudaError_t launch_forward(const mbir_geometry* g, const float* x, float* y_f32, __nv_bfloat16* y_bf16,
                            int out_stride, cudaStream_t st)
 {
-    if (g->d_tf_bop) return launch_forward_tc(g, x, y_f32, y_bf16, out_stride, st);
-    if (g->d_tf3_bop && y_f32) return launch_forward_tc32(g, x, y_f32, out_stride, st);
+    if (g->d_tf4_bop) return launch_forward_tcs(g, x, y_f32, y_bf16, out_stride, st);
     if (g->d_rec_key) return launch_forward_sorted(g, x, y_f32, y_bf16, out_stride, st);
     const bool bf = g->P.precision == MBIR_PREC_BF16;
     if (g->P.mode == MBIR_MODE_TAB)

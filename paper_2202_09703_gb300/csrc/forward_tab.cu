@@ -3,8 +3,8 @@
 // The geometry is fixed, so once per geometry (the paper's "compute the
 // system matrix once", Section 3) every A-scan's active pairs are written as
 // records {pixel, first tap sample n0 | table row | tau = t0 flag, bilinear
-// weights times w} sorted by n0 (ties by table phase mod 4, then pixel index,
-// so the order is deterministic).  For each 32-sample span of an A-scan the records whose tap
+// weights times w} sorted by n0 (ties by table row, then pixel index, so the
+// order is deterministic).  For each 32-sample span of an A-scan the records whose tap
 // window reaches the span are then one contiguous range, stored as run bounds.
 //
 // The apply kernel is a persistent, barrier-free gather: every warp takes
@@ -94,7 +94,7 @@ __global__ void rec_count_kernel(GeomParams P, DevPtrs D, int3 lat, long long* _
 }
 
 // Counting sort of one A-scan's records (pixels of the lattice) by n0, then
-// each bucket ordered by phase class and pixel index; run bounds per 32-sample
+// each bucket ordered by table row and pixel index; run bounds per 32-sample
 // span from the bucket starts.
 __global__ void __launch_bounds__(kSortThreads)
     rec_fill_kernel(GeomParams P, DevPtrs D, int3 lat, const long long* __restrict__ off, int2* __restrict__ rkey,
@@ -140,15 +140,10 @@ __global__ void __launch_bounds__(kSortThreads)
     }
     __syncthreads();
     __threadfence_block();
-    // order each bucket by (phase class = table phase mod 4, pixel index) (insertion sort; buckets hold a
-    // few dozen records): the tensor-core A x then finds each phase class's records as one range.  In the
-    // FP32 form the half of the table rows (phase >= (Q + 1) / 2) comes first, as that A x takes the
-    // halves in turn.
-    const int R = P.Q + 1;
-    const int hsplit = P.precision == MBIR_PREC_BF16 ? (1 << 30) : R / 2;
-    auto order_key = [R, hsplit](int2 k) {
-        const int ph = ((k.y >> 1) & 0xfff) % R;
-        return ((long long)((ph >= hsplit ? 4 : 0) + (ph & 3)) << 32) | (long long)(unsigned)k.x;
+    // order each bucket by (table row = plane * (Q + 1) + lower phase, pixel index) (insertion sort; buckets
+    // hold a few dozen records): the tensor-core A x then finds the records of one sum cell adjacent
+    auto order_key = [](int2 k) {
+        return ((long long)((k.y >> 1) & 0xfff) << 32) | (long long)(unsigned)k.x;
     };
     for (int t = threadIdx.x; t < P.M; t += blockDim.x) {
         const long long a = base + start[t], b = base + start[t + 1];

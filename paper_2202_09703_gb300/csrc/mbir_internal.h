@@ -335,36 +335,19 @@ struct Tc3Layout {
     bool ok;
 };
 
-// Shared-memory and tensor-memory layout of the tensor-core A x (BF16 form).
-struct TfLayout {
-    int ncols;             // table rows G (Q + 1)
-    int c0;                // columns of the first half
-    int k0, k1;            // MMA K of the two halves (multiples of 16)
-    int ka, kb;            // columns of the BF16 operand buffer / of the table operand image
+// Layout of the tensor-core A x (tc_stream.cuh): the table operand resident in shared memory, an FP32 sum
+// tile of kwmax columns, the output row; the sums go to tensor memory as the MMA's A operand.
+struct Tf4Layout {
+    int parts;             // 2: FP32 form (two FP16 parts of the table and of the sums), 1: BF16 form
+    int R;                 // phases per plane (Q + 1): column = plane * R + phase
+    int kb;                // table operand columns: G * R rounded up to 16
     int ntap;              // MMA N: taps rounded up to 16
-    int astride, astride1; // FP32 row strides of the two accumulator halves
-    int ustride;           // row stride of the product tile (floats)
+    int kwmax;             // widest column range of a tile that the sum tile holds (multiple of 16)
+    int astride;           // FP32 row stride of the sums (floats, 4 mod 32)
+    int texp;              // FP32 form: table operand = table x 2^texp (largest magnitude in [2^14, 2^15))
     int ylen;              // output window (floats)
-    size_t off_b, off_a, off_acc, off_acc1, off_y, smem;
-    bool ok;
-};
-
-// Shared-memory layout of the tensor-core A x of the FP32 form: two phase-aligned halves of the table
-// rows, each half's two-part FP16 table operand resident while its records are scattered.
-struct Tf3Layout {
-    int phsplit;           // first phase of the second half (both halves hold it)
-    int ncol[2];           // table rows (sum columns) of each half: phases x G
-    int pstride;           // phases per plane in a half's columns: column = plane * pstride + phase offset
-    int kb;                // MMA K of a half (columns, multiple of 16)
-    int kc;                // columns converted and multiplied per chunk
-    int nbuf;              // chunk buffers (2: a chunk is converted while the previous one is multiplied)
-    int ntap;              // MMA N: taps rounded up to 16
-    int astride;           // FP32 row stride of the sums (floats, multiple of 4)
-    int ustride;           // row stride of the product tile (floats)
-    int ylen;              // output window (floats)
-    size_t bhalf;          // bytes of one half's two-part table operand
-    int texp;              // table scale: operand = table x 2^texp (largest magnitude in [2^14, 2^15))
-    size_t off_b, off_s, off_a, off_y, smem;
+    size_t bbytes;         // bytes of the table operand
+    size_t off_part, off_rs, off_b, off_s, off_y, smem;
     bool ok;
 };
 
@@ -440,17 +423,14 @@ struct mbir_geometry {
     uint4* d_tc3_bop;      // FP32 adjoint: both halves' two-part FP16 table operand images
     uint2* d_tc3_prange;   // tensor-core adjoints: per (A-scan, tile) and row half (FP32 form; the BF16 form
                            // uses .x for the whole tile), lowest | highest plane << 16
-    // tensor-core A x of the BF16 form (see tc_forward.cu)
-    TfLayout tf;
-    uint4* d_tf_bop;       // table operand image (taps x table rows, K-major)
+    // tensor-core A x (see tc_stream.cuh, tc_fwd_stream.cu)
     int* d_tf_n0off;       // first record of every sample n0, K x (M + 1)
-    ushort4* d_tf_grpoff;  // phase-class starts inside every (A-scan, n0) bucket, K x M
     int* d_tf_order;       // A-scans by decreasing record count
     int* d_tf_counter;
-    // tensor-core A x of the FP32 form (see tc_forward.cu); shares the n0 offsets, order and counter above
-    Tf3Layout tf3;
-    uint4* d_tf3_bop;      // both halves' two-part FP16 table operand images (taps x table rows, K-major)
-    uint4* d_tf3_grpoff;   // starts of the (half, phase class) groups inside every (A-scan, n0) bucket, K x M
+    Tf4Layout tf4;
+    uint4* d_tf4_bop;      // table operand (taps x columns plane * (Q + 1) + phase, K-major; FP32: two parts)
+    uint32_t* d_tf4_crange;// per (A-scan, tile of 128 n0): first | end column << 16 of the planes its records reach
+    int* d_tf4_split;      // per (A-scan, tile): the 17 boundaries of the warps' parts (record offsets)
     long long n_records;
     // |A_v|^2 per pixel for the coordinate descent (computed on its first call)
     float* w_colnorm;
@@ -515,12 +495,10 @@ Tc3Layout tc3_layout(const GeomParams& P);
 cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e_bf, float* b, cudaStream_t st);
 cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, float* b, cudaStream_t st);
-TfLayout tf_layout(const GeomParams& P);
-Tf3Layout tf3_layout(const GeomParams& P);
-cudaError_t build_tc_forward(mbir_geometry* g, cudaStream_t st);
-cudaError_t launch_forward_tc(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
-                              cudaStream_t st);
-cudaError_t launch_forward_tc32(const mbir_geometry* g, const float* x, float* yf, int stride, cudaStream_t st);
+Tf4Layout tf4_layout(const GeomParams& P, int kwmax);
+cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st);
+cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
+                               cudaStream_t st);
 cudaError_t launch_column_norms(const mbir_geometry* g, float* out, cudaStream_t st);
 cudaError_t build_colour_records(mbir_geometry* g, int s, cudaStream_t st);
 cudaError_t launch_forward_colour(const mbir_geometry* g, int c, const float* x, float* yf, int stride,

@@ -54,6 +54,28 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t
         "l"(da), "l"(db), "r"(idesc), "r"(accumulate ? 1u : 0u));
 }
 
+// D[tmem] (+)= A[tmem] * B^T with A read from tensor memory (row i of A in lane i, two 16-bit
+// elements per 32-bit column, the lower K index in the low half), issued by one thread.
+__device__ __forceinline__ void umma_f16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc,
+                                            bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate ? 1u : 0u));
+}
+
+// 4 consecutive 32-bit columns of this thread's tensor-memory lane (the warp writes its own 32-lane
+// quarter); tmem_wait_st() before the values are read by an MMA.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint4& v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // The mbarrier completes once the MMAs this thread issued before have finished.
 __device__ __forceinline__ void umma_commit(uint32_t bar)
 {

@@ -1,0 +1,240 @@
+// A x on the tensor cores (FP32 and BF16 storage forms): set-up tables and the
+// single-request kernel.  The work itself is tcs_forward_pool (tc_stream.cuh).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tc_stream.cuh"
+
+namespace mbir {
+
+Tf4Layout tf4_layout(const GeomParams& P, int kwmax)
+{
+    Tf4Layout L{};
+    const bool bf = P.precision == MBIR_PREC_BF16;
+    L.parts = bf ? 1 : 2;
+    L.R = P.Q + 1;
+    L.kb = (P.G * L.R + 15) & ~15;
+    L.ntap = (P.Tw + 15) & ~15;
+    L.kwmax = std::min(kwmax, L.kb);
+    L.astride = ((L.kwmax + 31) & ~31) + 4;            // 4 mod 32: a warp's row reads hit distinct banks
+    L.bbytes = (size_t)L.parts * L.ntap * L.kb * 2;
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    L.off_part = 1024;                                 // anti-diagonal sums, 16 warps x 64 floats
+    L.off_rs = L.off_part + (size_t)kTsWarps * kTsPart * 4;   // per A-scan: part boundaries, column ranges
+    L.off_b = (L.off_rs + (size_t)ntile * (kTsSplit + 1) * 4 + 1023) & ~(size_t)1023;
+    L.off_s = (L.off_b + L.bbytes + 1023) & ~(size_t)1023;
+    L.ylen = ntile * kTsTile + L.ntap + 2;
+    L.off_y = L.off_s + (size_t)kTsTile * L.astride * 4;
+    L.smem = L.off_y + (size_t)L.ylen * 4;
+    L.ok = L.R >= 2 && L.ntap <= 128 && L.ntap / 4 <= 32 && L.kwmax >= 16 && L.kwmax % 16 == 0 &&
+           L.parts * L.kwmax / 2 <= (int)kTsDCol && L.smem <= 227 * 1024 && L.bbytes < (1u << 20) &&
+           P.G * L.R <= 4096 && (long long)P.K * (P.M + 1) < (1LL << 31);
+    return L;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kTsThreads, 1) fwd_tcs_kernel(TsView V, int* __restrict__ status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, kTsCols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    uint32_t mphase = 0, bphase = 0;
+    tcs_forward_pool<BF16>(V, smem, tmem, mphase, bphase, status);
+    tc_header_release(smem, tmem, kTsCols);
+}
+
+// first record of every sample n0 of every A-scan (records sorted by n0)
+__global__ void ts_n0_off_kernel(GeomParams P, const long long* __restrict__ rec_off, const int2* __restrict__ rkey,
+                                 int* __restrict__ n0_off)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)P.K * (P.M + 1)) return;
+    const int k = (int)(i / (P.M + 1)), n = (int)(i - (long long)k * (P.M + 1));
+    const long long base = rec_off[k];
+    int lo = 0, hi = (int)(rec_off[k + 1] - base);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((rkey[base + mid].y >> kRecShift) < n) lo = mid + 1;
+        else hi = mid;
+    }
+    n0_off[i] = lo;
+}
+
+// Per (A-scan, tile of 128 n0): the column range of the planes its records reach (warp per tile; the widest
+// range goes to *wmax) and the boundaries of the warps' parts: the tile's records cut at n0 boundaries into
+// kTsWarps parts of about equal count (part w starts at the first n0 whose first record lies at or after the
+// w/kTsWarps point of the tile's range).
+__global__ void ts_tiles_kernel(GeomParams P, int R, int kb, const long long* __restrict__ rec_off,
+                                const int2* __restrict__ rkey, const int* __restrict__ n0_off,
+                                uint32_t* __restrict__ crange, int* __restrict__ split, int* __restrict__ wmax)
+{
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (long long)P.K * ntile) return;
+    const int k = (int)(wid / ntile), t = (int)(wid - (long long)k * ntile);
+    const long long base = rec_off[k];
+    const int* no = n0_off + (size_t)k * (P.M + 1);
+    const int n_lo = t * kTsTile, n_hi = min((t + 1) * kTsTile, P.M);
+    const int r0 = no[n_lo], r1 = no[n_hi];
+    int glo = P.G, ghi = -1;
+    for (int r = r0 + lane; r < r1; r += 32) {
+        const int trow = (rkey[base + r].y >> 1) & 0xfff;
+        const int gi = trow / R;
+        glo = min(glo, gi);
+        ghi = max(ghi, min(gi + 1, P.G - 1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        glo = min(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+        ghi = max(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+    }
+    if (lane == 0) {
+        uint32_t v = 0;
+        if (ghi >= glo) {
+            const int c_lo = (glo * R) & ~15;
+            const int c_hi = min(kb, ((ghi + 1) * R + 15) & ~15);
+            v = (uint32_t)c_lo | (uint32_t)c_hi << 16;
+            atomicMax(wmax, c_hi - c_lo);
+        }
+        crange[wid] = v;
+    }
+    if (lane <= kTsWarps) {
+        int s = r1;
+        if (lane == 0) s = r0;
+        else if (lane < kTsWarps) {
+            const long long target = r0 + ((long long)(r1 - r0) * lane) / kTsWarps;
+            int lo = n_lo, hi = n_hi;                    // first n0 in [n_lo, n_hi] with no[n0] >= target
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (no[mid] < target) lo = mid + 1;
+                else hi = mid;
+            }
+            s = no[lo];
+        }
+        split[wid * kTsSplit + lane] = s;
+    }
+}
+
+// Tables of the tensor-core A x for a geometry with records: the n0 offsets, the A-scan order, the per-tile
+// column ranges and warp parts, and the table operand (FP32 form: two FP16 parts of the table scaled by
+// 2^texp; BF16 form: the BF16 table); cudaErrorNotSupported keeps the CUDA-core A x.
+cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    if (!g->d_rec_key || g->n_records <= 0) return cudaErrorNotSupported;
+    Tf4Layout L{};
+    for (int kw : {512, 448, 384, 320, 256, 224, 192, 160, 128, 96, 64}) {
+        L = tf4_layout(P, kw);
+        if (L.ok) break;
+    }
+    if (!L.ok) return cudaErrorNotSupported;
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    // A-scans by decreasing record count
+    std::vector<long long> roff((size_t)P.K + 1);
+    cudaError_t e = cudaMemcpy(roff.data(), g->d_rec_off, sizeof(long long) * (P.K + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    std::vector<int> order(P.K);
+    for (int k = 0; k < P.K; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return roff[a + 1] - roff[a] > roff[b + 1] - roff[b]; });
+    int *d_n0 = nullptr, *d_ord = nullptr, *d_ctr = nullptr, *d_sp = nullptr, *d_w = nullptr;
+    uint32_t* d_cr = nullptr;
+    uint4* d_b = nullptr;
+    e = cudaMalloc((void**)&d_n0, sizeof(int) * (size_t)P.K * (P.M + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ord, sizeof(int) * (size_t)P.K);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_cr, sizeof(uint32_t) * (size_t)P.K * ntile);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_sp, sizeof(int) * (size_t)P.K * ntile * kTsSplit);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_w, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(d_ord, order.data(), sizeof(int) * (size_t)P.K, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_w, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        const long long n = (long long)P.K * (P.M + 1);
+        ts_n0_off_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(P, g->d_rec_off, g->d_rec_key, d_n0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const long long threads = (long long)P.K * ntile * 32;
+        ts_tiles_kernel<<<(int)((threads + 255) / 256), 256, 0, st>>>(P, L.R, L.kb, g->d_rec_off, g->d_rec_key, d_n0,
+                                                                      d_cr, d_sp, d_w);
+        e = cudaGetLastError();
+    }
+    int wmax = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&wmax, d_w, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_w);
+    if (e == cudaSuccess && wmax > L.kwmax) e = cudaErrorNotSupported;   // a tile reaches too many planes
+    // table operand: row m (tap), column plane * R + phase (K-major)
+    if (e == cudaSuccess) {
+        const int nq = P.Q * P.Tw + 1;
+        const size_t part = (size_t)L.ntap * L.kb;
+        std::vector<uint16_t> img((size_t)L.parts * part, 0);
+        if (P.precision == MBIR_PREC_BF16) {
+            L.texp = 0;
+            for (int gpl = 0; gpl < P.G; ++gpl)
+                for (int ph = 0; ph < L.R; ++ph)
+                    for (int m = 0; m < P.Tw; ++m) {
+                        const __nv_bfloat16 v = __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
+                        img[kmajor_offset(m, gpl * L.R + ph, L.kb) / 2] = *reinterpret_cast<const uint16_t*>(&v);
+                    }
+        } else {
+            // the FP32 kernel table times 2^texp (largest magnitude into [2^14, 2^15)), split t = t1 + t2
+            float tmax = 0.0f;
+            for (size_t i = 0; i < (size_t)P.G * nq; ++i) tmax = std::max(tmax, std::fabs((float)g->tab_host[i]));
+            int ex = 0;
+            std::frexp(tmax, &ex);
+            L.texp = tmax > 0.0f ? std::min(15 - ex, 126) : 0;
+            for (int gpl = 0; gpl < P.G; ++gpl)
+                for (int ph = 0; ph < L.R; ++ph)
+                    for (int m = 0; m < P.Tw; ++m) {
+                        const float t = std::ldexp((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph], L.texp);
+                        const __half p1 = __float2half_rn(t);
+                        const __half p2 = __float2half_rn(t - __half2float(p1));
+                        const size_t o = kmajor_offset(m, gpl * L.R + ph, L.kb) / 2;
+                        img[o] = *reinterpret_cast<const uint16_t*>(&p1);
+                        img[part + o] = *reinterpret_cast<const uint16_t*>(&p2);
+                    }
+        }
+        e = cudaMalloc((void**)&d_b, L.bbytes);
+        if (e == cudaSuccess) e = cudaMemcpy(d_b, img.data(), L.bbytes, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        void* ptrs[] = {d_n0, d_ord, d_ctr, d_cr, d_sp, d_b};
+        for (void* p : ptrs) cudaFree(p);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
+    }
+    g->tf4 = L;
+    g->d_tf_n0off = d_n0;
+    g->d_tf_order = d_ord;
+    g->d_tf_counter = d_ctr;
+    g->d_tf4_bop = d_b;
+    g->d_tf4_crange = d_cr;
+    g->d_tf4_split = d_sp;
+    g->bytes += L.bbytes + sizeof(int) * ((size_t)P.K * (P.M + 1) + P.K + 1) +
+                sizeof(int) * (size_t)P.K * ntile * (kTsSplit + 1);
+    return cudaSuccess;
+}
+
+cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
+                               cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const Tf4Layout& L = g->tf4;
+    const bool bf = P.precision == MBIR_PREC_BF16;
+    auto kern = bf ? fwd_tcs_kernel<true> : fwd_tcs_kernel<false>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tf_counter, 0, sizeof(int), st);
+    if (ce != cudaSuccess) return ce;
+    const int grid = std::max(1, std::min(g->n_sm, P.K));
+    const void* tab = bf ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
+    TsView V{P, L, g->d_tf4_bop, tab, g->d_rec_off, g->d_tf4_crange, g->d_tf4_split, g->d_rec_key, g->d_rec_w,
+             g->d_tf_order, x, yf ? (void*)yf : (void*)yb, yf ? 0 : 1, stride, g->d_tf_counter};
+    kern<<<grid, kTsThreads, L.smem, st>>>(V, g->d_status);
+    return cudaGetLastError();
+}
+
+}  // namespace mbir

@@ -1,0 +1,365 @@
+// A x on the tensor cores, streaming each tile's records (FP32 and BF16
+// storage forms), shared by the single-request kernel (tc_fwd_stream.cu)
+// and the batched engine (engine.cu).
+//
+// Eq. 13 with the bilinear pulse table, grouped by first tap n0: for a tile of
+// 128 values of n0 of one A-scan,
+//     S[n0][col] = sum over the tile's pairs of their weight on table column col times x_v,
+//     U (128 x taps) = S T,   y[n0 + 1 + m] += U[n0][m],
+// with columns col = plane * (Q + 1) + phase (every tap of a pair shares one
+// table phase, so this regrouping is exact).
+//
+// Records: an A-scan's records are sorted by n0 and, within an n0, by table
+// row (plane * (Q + 1) + lower phase) and pixel, so a tile's records are one
+// contiguous range and records of one S cell are adjacent.  At set-up each
+// tile's range is cut at n0 boundaries into 16 parts of about equal record
+// count, one per warp, so no two warps add into the same row of S.  A warp
+// streams its part 32 records at a time (coalesced, four loads in flight, the
+// next tile's first loads issued while the current tile is multiplied), sums
+// the contributions of equal (n0, table row) with a segmented warp scan, and
+// the last record of each run adds its four bilinear corners into S with plain
+// read-modify-writes: within one instruction the cells are distinct, and the
+// four corners go in four instructions.  No atomics: the sums run in a fixed
+// order and every output bit is reproducible.
+//
+// The records of a tile reach a few neighbouring attenuation planes, one
+// column range [c_lo, c_hi) found per tile at set-up: only that range is held,
+// converted and multiplied.  S goes to tensor memory as the MMA's A operand
+// (row n0 in lane n0).  FP32 form: S scaled by the power of two that brings
+// the sum of the tile's absolute corner contributions (a bound of every |S|)
+// below 2^15 and split into two FP16 parts, the table likewise (scale fixed
+// per geometry): the three products S1 T1 + S1 T2 + S2 T1 (the dropped S2 T2
+// is below 2^-22 of the result).  BF16 form: S rounded once to BF16 against
+// the BF16 table, one product.  The table operand stays resident in shared
+// memory.  A tile's products are read back after the next tile's records have
+// been scattered, so they overlap the scatter; each warp sums the
+// anti-diagonals of its 32-row x (taps / 4)-column block of U with shuffles,
+// and the sixteen blocks are added per output sample in a fixed order.
+#pragma once
+
+#include "tc_apply.cuh"
+
+namespace mbir {
+
+constexpr int kTsThreads = 512;     // 16 warps: four per tensor-memory lane quarter
+constexpr int kTsWarps = kTsThreads / 32;
+constexpr int kTsTile = 128;        // n0 values per tile (MMA M)
+constexpr int kTsSplit = kTsWarps + 1;   // record offsets per tile: the warps' part boundaries
+constexpr uint32_t kTsCols = 512;   // tensor memory: A operand in [0, 256), the product at 256
+constexpr uint32_t kTsDCol = 256;
+constexpr int kTsPart = 64;         // anti-diagonal sums per warp block (32 + taps / 4 - 1 <= 63)
+static_assert(kTsThreads == kTcThreads, "the engine runs the adjoint and A x pools with one block size");
+
+struct TsView {
+    GeomParams P;
+    Tf4Layout T;
+    const uint4* bop;            // table operand image
+    const void* tab;             // kernel table, float2 (FP32) or __nv_bfloat162 (BF16): the tau = t0 tap
+    const long long* rec_off;
+    const uint32_t* crange;      // per (A-scan, tile): c_lo | c_hi << 16
+    const int* split;            // per (A-scan, tile): kTsSplit record offsets from the A-scan's first record
+    const int2* rkey;
+    const float4* rw;
+    const int* order;            // A-scans by decreasing record count
+    const float* x;
+    void* y;                     // float, or __nv_bfloat16 when y_bf16; row stride out_stride
+    int y_bf16;
+    int out_stride;
+    int* counter;
+};
+
+__device__ __forceinline__ float ts_pow2(int e) { return __int_as_float((e + 127) << 23); }
+
+// Power-of-two exponent that brings a bound m below 2^15 (0 for m = 0).
+__device__ __forceinline__ int ts_bound_exponent(float m)
+{
+    if (!(m > 0.0f)) return 0;
+    int ex = 0;
+    frexpf(m, &ex);
+    return min(15 - ex, 126);
+}
+
+// Drains the A x items (A-scans, largest first) of V.  The shared-memory
+// header (offset 0: MMA barrier, 8: tensor-memory address, 16: item slot, 20:
+// abort flag, 32: table copy barrier) is initialised and kTsCols columns of
+// tensor memory are allocated by the caller; mphase / bphase are the parities
+// of the two barriers.  Returns false when a bounded wait gave up.
+template <bool BF16>
+__device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char* smem, uint32_t tmem,
+                                                 uint32_t& mphase, uint32_t& bphase, int* status)
+{
+    const GeomParams& P = V.P;
+    const Tf4Layout& T = V.T;
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    volatile int* next = reinterpret_cast<volatile int*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    float* wsum = reinterpret_cast<float*>(smem + 64);
+    int* tsp = reinterpret_cast<int*>(smem + T.off_rs);             // this A-scan's part boundaries
+    uint32_t* tcr = reinterpret_cast<uint32_t*>(tsp + ntile * kTsSplit);
+    float* part = reinterpret_cast<float*>(smem + T.off_part);
+    unsigned char* sB = smem + T.off_b;
+    float* sS = reinterpret_cast<float*>(smem + T.off_s);
+    float* sY = reinterpret_cast<float*>(smem + T.off_y);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = T.R, S = table_stride(P.Tw4);
+    const float invR = 1.0f / (float)R;
+    const int2* __restrict__ rkey = V.rkey;
+    const float4* __restrict__ rw = V.rw;
+    const float* __restrict__ xg = V.x;
+    const uint32_t tA = tmem, tD = tmem + kTsDCol;
+    const int KA = T.kwmax / 2;                        // tensor-memory columns of one part of A
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t full = 0xffffffffu;
+
+    // the table operand; S cleared (a previous pool may have used another row stride)
+    if (tid == 0) {
+        mbar_arrive_expect_tx(smem_u32(smem + 32), (uint32_t)T.bbytes);
+        bulk_g2s(smem_u32(sB), V.bop, (uint32_t)T.bbytes, smem_u32(smem + 32));
+    }
+    for (int i = tid; i < kTsTile * T.astride; i += blockDim.x) sS[i] = 0.0f;
+    if (!mbar_wait_bounded(smem_u32(smem + 32), bphase, status)) *abort_flag = 1;
+    bphase ^= 1u;
+    __syncthreads();
+
+    const uint32_t idesc = BF16 ? umma_idesc_bf16(kTsTile, T.ntap) : umma_idesc_f16(kTsTile, T.ntap);
+    const uint32_t bpart = (uint32_t)(T.ntap * T.kb * 2), sboB = (uint32_t)(T.kb / 8) * 128;
+    const int cq = T.ntap / 4;                          // columns of a warp's block of U
+    const int qd = warp & 3, pb = warp >> 2;            // lane quarter and column block of this warp
+    const float it = ts_pow2(-T.texp);
+
+    // record batches in flight: slot s holds batch b = s (mod 4) of this warp's part of the tile
+    int2 kq[4];
+    float4 wq[4];
+    float xq[4];
+
+    // Products of tile tp (scale exponent se) in tensor memory -> y: wait for them, sum the anti-diagonals of
+    // each warp's block with shuffles (lane l: block offsets l and l + 32), then the blocks in a fixed order.
+    auto epilogue = [&](int tp, int se) {
+        if (!mbar_wait_bounded(smem_u32(smem), mphase, status)) *abort_flag = 1;
+        mphase ^= 1u;
+        tc_fence_after();
+        const float i0 = ts_pow2(-se);
+        float lo = 0.0f, hi = 0.0f;
+        for (int c = 0; c < cq; c += 4) {
+            float v[4];
+            tmem_ld4(tD + lane_base + (uint32_t)(pb * cq + c), v);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int d = c + j;                              // column within the block
+                const float u = __shfl_sync(full, (v[j] * i0) * it, (lane - d) & 31);
+                if (lane >= d) lo += u;
+                else hi += u;
+            }
+        }
+        part[warp * kTsPart + lane] = lo;
+        part[warp * kTsPart + 32 + lane] = hi;
+        tc_fence_before();
+        __syncthreads();
+        for (int o = tid; o < kTsTile + T.ntap - 1; o += blockDim.x) {
+            float acc = 0.0f;
+            for (int w = 0; w < kTsWarps; ++w) {
+                const int r = o - ((w & 3) * 32 + (w >> 2) * cq);
+                if (r >= 0 && r < 32 + cq - 1) acc += part[w * kTsPart + r];
+            }
+            sY[tp * kTsTile + 1 + o] += acc;
+        }
+    };
+
+    while (!*abort_flag) {
+        if (tid == 0) *next = atomicAdd(V.counter, 1);
+        __syncthreads();
+        const int idx = *next;
+        if (idx >= P.K) break;
+        const int k = __ldg(V.order + idx);
+        const long long base = __ldg(V.rec_off + k);
+        {
+            const int* sp = V.split + (size_t)k * ntile * kTsSplit;
+            const uint32_t* cr = V.crange + (size_t)k * ntile;
+            for (int i = tid; i < ntile * kTsSplit; i += blockDim.x) tsp[i] = __ldg(sp + i);
+            for (int i = tid; i < ntile; i += blockDim.x) tcr[i] = __ldg(cr + i);
+            for (int i = tid; i < T.ylen; i += blockDim.x) sY[i] = 0.0f;
+        }
+        __syncthreads();
+
+        // this warp's part [wa, wb) of tile t's records and its batches of 32
+        int wa = 0, wb = 0, nb = 0;
+        auto warp_range = [&](int t) {
+            wa = tsp[t * kTsSplit + warp];
+            wb = tsp[t * kTsSplit + warp + 1];
+            nb = (wb - wa + 31) >> 5;
+        };
+        auto issue = [&](int2& kk, float4& ww, int b) {
+            const int rec = wa + 32 * b + lane;
+            if (b < nb && rec < wb) {
+                kk = __ldg(rkey + base + rec);
+                ww = __ldg(rw + base + rec);
+            } else {
+                kk = make_int2(0, -1);                   // n0 field negative: not a record
+                ww = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        warp_range(0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) issue(kq[s], wq[s], s);
+
+        int pend = -1, pend_se = 0;                      // tile whose products wait in tensor memory
+        for (int t = 0; t < ntile; ++t) {
+            const int ts = t * kTsTile;
+            const bool live = tsp[t * kTsSplit + kTsWarps] > tsp[t * kTsSplit];
+            if (live) {
+                // ---- scatter: batches b = 0 .. nb-1, slot b & 3, x one batch ahead
+                float* Sb = sS - (int)(tcr[t] & 0xffffu);
+                float bsum = 0.0f;
+                xq[0] = kq[0].y >= 0 ? __ldg(xg + kq[0].x) : 0.0f;
+                for (int b0 = 0; b0 < nb; b0 += 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int b = b0 + u;
+                        if (b >= nb) break;
+                        if (b + 1 < nb) {
+                            const int2 kn = kq[(u + 1) & 3];
+                            xq[(u + 1) & 3] = kn.y >= 0 ? __ldg(xg + kn.x) : 0.0f;
+                        }
+                        const int2 kk = kq[u];
+                        const float4 w = wq[u];
+                        const float xv = xq[u];
+                        const bool valid = kk.y >= 0;
+                        const int n0r = valid ? (kk.y >> kRecShift) - ts : 0;
+                        const int trow = valid ? (kk.y >> 1) & 0xfff : 0;
+                        float c0 = w.x * xv, c1 = w.y * xv, c2 = w.z * xv, c3 = w.w * xv;
+                        bsum += (fabsf(c0) + fabsf(c1)) + (fabsf(c2) + fabsf(c3));
+                        // equal (n0, table row) are adjacent lanes: segmented inclusive sums over them
+                        const int key = valid ? (n0r << 12) | trow : 0x40000000 + lane;
+                        // (every lane takes part in every shuffle: none of them sits behind a condition)
+                        const int kup = __shfl_up_sync(full, key, 1);
+                        const int kdn = __shfl_down_sync(full, key, 1);
+                        if (__any_sync(full, lane > 0 && kup == key)) {
+#pragma unroll
+                            for (int d = 1; d < 32; d <<= 1) {
+                                const int kd = __shfl_up_sync(full, key, d);
+                                const float a0 = __shfl_up_sync(full, c0, d), a1 = __shfl_up_sync(full, c1, d);
+                                const float a2 = __shfl_up_sync(full, c2, d), a3 = __shfl_up_sync(full, c3, d);
+                                if (lane >= d && kd == key) {
+                                    c0 += a0;
+                                    c1 += a1;
+                                    c2 += a2;
+                                    c3 += a3;
+                                }
+                            }
+                        }
+                        const bool writer = valid && (lane == 31 || kdn != key);
+                        const int gi = (int)(((float)trow + 0.5f) * invR);
+                        const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
+                        float* row = Sb + n0r * T.astride;
+                        // the four corners in four steps: within a step the writers' cells are distinct
+                        if (writer) row[trow] += c0;
+                        __syncwarp();
+                        if (writer) row[c1col] += c1;
+                        __syncwarp();
+                        if (writer) row[trow + 1] += c2;
+                        __syncwarp();
+                        if (writer) row[c1col + 1] += c3;
+                        __syncwarp();
+                        // tau = t0 exactly (rare): the last tap of the upper phase row lies outside the window;
+                        // one lane after another
+                        uint32_t fm = __ballot_sync(full, valid && (kk.y & 1));
+                        while (fm) {
+                            if (lane == __ffs(fm) - 1) {
+                                const size_t ti = ((size_t)gi * R + (trow - gi * R) + 1) * S + P.Tw - 1;
+                                float2 tl;
+                                if (BF16) tl = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(V.tab) + ti));
+                                else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
+                                sY[ts + n0r + P.Tw] -= xv * (w.z * tl.x + w.w * tl.y);
+                            }
+                            __syncwarp();
+                            fm &= fm - 1;
+                        }
+                        issue(kq[u], wq[u], b + 4);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(full, bsum, o);
+                if (lane == 0) wsum[warp] = bsum;
+            }
+            // the next tile's first batches load while this tile is converted and multiplied
+            if (t + 1 < ntile) {
+                warp_range(t + 1);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) issue(kq[s], wq[s], s);
+            }
+            if (!live) continue;
+            __syncthreads();                             // every record of the tile is in S
+            // ---- the previous tile's products -> y (they ran during this tile's scatter)
+            if (pend >= 0) epilogue(pend, pend_se);
+            if (*abort_flag) break;
+            // ---- S -> A operand in tensor memory, S cleared as read
+            int se = 0;
+            if (!BF16) {
+                float tb = 0.0f;
+                for (int w = 0; w < kTsWarps; ++w) tb += wsum[w];
+                se = ts_bound_exponent(tb);
+            }
+            const float scl = ts_pow2(se);
+            const uint32_t crt = tcr[t];
+            const int c_lo = (int)(crt & 0xffffu), kw = (int)(crt >> 16) - c_lo;
+            {
+                float* srow = sS + (qd * 32 + lane) * T.astride;
+                for (int g8 = pb; g8 < kw / 8; g8 += 4) {
+                    float4* sp = reinterpret_cast<float4*>(srow + 8 * g8);
+                    const float4 v0 = sp[0], v1 = sp[1];
+                    sp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    sp[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (BF16) {
+                        const __nv_bfloat162 p0 = __floats2bfloat162_rn(v0.x, v0.y), p1 = __floats2bfloat162_rn(v0.z, v0.w);
+                        const __nv_bfloat162 p2 = __floats2bfloat162_rn(v1.x, v1.y), p3 = __floats2bfloat162_rn(v1.z, v1.w);
+                        const uint4 hv = make_uint4(*reinterpret_cast<const uint32_t*>(&p0),
+                                                    *reinterpret_cast<const uint32_t*>(&p1),
+                                                    *reinterpret_cast<const uint32_t*>(&p2),
+                                                    *reinterpret_cast<const uint32_t*>(&p3));
+                        tmem_st4(tA + lane_base + (uint32_t)(4 * g8), hv);
+                    } else {
+                        uint4 hv, lv;
+                        split2h_pair(v0.x * scl, v0.y * scl, hv.x, lv.x);
+                        split2h_pair(v0.z * scl, v0.w * scl, hv.y, lv.y);
+                        split2h_pair(v1.x * scl, v1.y * scl, hv.z, lv.z);
+                        split2h_pair(v1.z * scl, v1.w * scl, hv.w, lv.w);
+                        tmem_st4(tA + lane_base + (uint32_t)(4 * g8), hv);
+                        tmem_st4(tA + lane_base + (uint32_t)(KA + 4 * g8), lv);
+                    }
+                }
+                tmem_wait_st();
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t b0 = smem_u32(sB) + (uint32_t)(c_lo / 8) * 128;
+                for (int s = 0; s < kw / 16; ++s) {
+                    umma_f16_ta(tD, tA + 8 * s, umma_desc(b0 + 256 * s, 128, sboB), idesc, s > 0);
+                    if (!BF16) {
+                        // hi x lo, lo x hi
+                        umma_f16_ta(tD, tA + 8 * s, umma_desc(b0 + bpart + 256 * s, 128, sboB), idesc, true);
+                        umma_f16_ta(tD, tA + KA + 8 * s, umma_desc(b0 + 256 * s, 128, sboB), idesc, true);
+                    }
+                }
+                umma_commit(smem_u32(smem));
+            }
+            pend = t;
+            pend_se = se;
+        }
+        if (pend >= 0 && !*abort_flag) epilogue(pend, pend_se);
+        __syncthreads();
+        if (*abort_flag) break;
+        if (V.y_bf16) {
+            __nv_bfloat16* yo = reinterpret_cast<__nv_bfloat16*>(V.y) + (size_t)k * V.out_stride;
+            for (int n = tid; n < V.out_stride; n += blockDim.x) yo[n] = __float2bfloat16_rn(n < P.M ? sY[n] : 0.0f);
+        } else {
+            float* yo = reinterpret_cast<float*>(V.y) + (size_t)k * V.out_stride;
+            for (int n = tid; n < V.out_stride; n += blockDim.x) yo[n] = n < P.M ? sY[n] : 0.0f;
+        }
+        __syncthreads();
+    }
+    return !*abort_flag;
+}
+
+}  // namespace mbir
