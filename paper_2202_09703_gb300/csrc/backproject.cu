@@ -277,6 +277,7 @@ cudaError_t launch_backproject(const mbir_geometry* g, const float* e_pad, const
                                cudaStream_t st)
 {
     const bool bf = g->P.precision == MBIR_PREC_BF16;
+    if (g->d_tb4_bop) return launch_backproject_tcs(g, e_pad, e_bf, b, st);
     if (bf && g->d_tc_bop) return launch_backproject_tc(g, e_bf, b, st);
     if (!bf && g->d_tc3_bop) return launch_backproject_tc32(g, e_pad, b, st);
     if (g->P.mode == MBIR_MODE_TAB)

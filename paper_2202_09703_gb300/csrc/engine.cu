@@ -101,7 +101,10 @@ struct ReqDesc {
     const uint32_t* tc_dest;
     const long long* tc_pixoff;
     float* tc_contrib;     // this request's contributions (pixel-major)
-    // tensor-core A x (tcs != 0)
+    // tensor-core A^T and A x of tc_stream.cuh (tcb, tcs != 0)
+    int tcb;
+    Tb4Layout tb4l;
+    const uint4* tb4_bop;
     int tcs;
     Tf4Layout tf4l;
     const uint4* tf4_bop;
@@ -417,6 +420,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc_kernel(EngLists L)
         }
     }
     tc_header_release(smem, tmem, kTcCols);
+}
+
+// A^T e on the tensor cores (FP32 or BF16 form, tc_stream.cuh) over every active request
+template <bool BF16>
+__global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, kTsCols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
+    uint32_t mphase = 0, bphase = 0;
+    const int nreq = L.counts[0];
+    if (nreq > 0) {
+        const int r0 = L.start[blockIdx.x] % nreq;
+        for (int t = 0; t < nreq; ++t) {
+            const int rq = (r0 + t) % nreq;
+            const ReqDesc& R = L.desc[rq];
+            const int nitems = R.P.K * ((R.P.M + kTsTile - 1) / kTsTile);
+            if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
+            const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
+            const void* e = BF16 ? (const void*)R.ebf : (const void*)R.e;
+            const TbView V{R.P, R.tb4l, R.tb4_bop, tab, e, R.rec_off, R.tc_tile, R.tf4_crange, R.rkey, R.rw,
+                           R.tc_dest, R.tc_contrib, L.pool + 2 * rq + 1};
+            if (!tcs_adjoint_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
+            __syncthreads();
+        }
+    }
+    tc_header_release(smem, tmem, kTsCols);
 }
 
 // A^T e of the FP32 form on the tensor cores (two-part FP16 split) over every
@@ -779,6 +810,9 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.tc_dest = g->d_tc_dest;
     d.tc_pixoff = g->d_tc_pixoff;
     d.tc_contrib = r->contrib;
+    d.tcb = g->d_tb4_bop ? 1 : 0;
+    d.tb4l = g->tb4;
+    d.tb4_bop = g->d_tb4_bop;
     d.tcs = g->d_tf4_bop ? 1 : 0;
     d.tf4l = g->tf4;
     d.tf4_bop = g->d_tf4_bop;
@@ -901,12 +935,16 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 }
 
 // One MAP iteration of every active request, as launched inside the graph.
-cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cudaStream_t st)
+cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, bool tcb, cudaStream_t st)
 {
     const int G = E->n_sm, SG = E->n_sm * 8;
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
     if (e != cudaSuccess) return e;
-    if (tc && bf16) {
+    if (tc && tcb) {
+        if (bf16) eng_bwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[3], st>>>(E->L);
+        else eng_bwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[3], st>>>(E->L);
+        eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
+    } else if (tc && bf16) {
         eng_bwd_tc_kernel<<<G, kTcThreads, E->smem_tc[0], st>>>(E->L);
         eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
     } else if (tc) {
@@ -952,6 +990,8 @@ int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e != cudaSuccess) { delete E; return MBIR_ERR_CUDA; }
     *out = E;
@@ -1061,17 +1101,20 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
     bool tcf = true;                     // tensor-core A x when every request has its tables
+    bool tcb = true;                     // streamed tensor-core A^T likewise
     for (Request* r : E->sel) {
         if (!r->contrib) tc = false;
         if (!r->g->d_tf4_bop) tcf = false;
+        if (!r->g->d_tb4_bop) tcb = false;
     }
-    const int gtc = (int)tc + 2 * (int)tcf;
+    const int gtc = (int)tc + 2 * (int)tcf + 4 * (int)tcb;
     size_t smem_tc[4] = {1024, 1024, 1024, 1024};
     for (Request* r : E->active) {
         const mbir_geometry* g = r->g;
         if (g->d_tc_bop) smem_tc[0] = std::max(smem_tc[0], g->tc.smem);
         if (g->d_tc3_bop) smem_tc[1] = std::max(smem_tc[1], g->tc3.smem);
         if (g->d_tf4_bop) smem_tc[2] = std::max(smem_tc[2], g->tf4.smem);
+        if (g->d_tb4_bop) smem_tc[3] = std::max(smem_tc[3], g->tb4.smem);
     }
     const bool smem_changed = !std::equal(smem_tc, smem_tc + 4, E->smem_tc);
     if (grew || smem_changed || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != gtc) {
@@ -1081,7 +1124,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         cudaGraph_t graph;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, tcf, cs);
+        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, tcf, tcb, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&E->graph, graph, 0);

@@ -351,6 +351,21 @@ struct Tf4Layout {
     bool ok;
 };
 
+// Layout of the tensor-core A^T (tc_stream.cuh): the table operand resident in shared memory, the
+// residual windows of the current and the next item, the correlation tile of kwmax columns; the residual's
+// Hankel tile goes to tensor memory as the MMA's A operand.
+struct Tb4Layout {
+    int parts;             // 2: FP32 form (two FP16 parts), 1: BF16 form
+    int R, kb, ntap;       // as Tf4Layout
+    int kwmax;             // widest column range of a tile that the correlation tile holds (multiple of 16)
+    int cstride;           // FP32 row stride of the correlation tile (floats, 4 mod 32)
+    int ewin;              // floats of one residual window (128 + taps, padded)
+    int texp;              // FP32 form: table operand = table x 2^texp
+    size_t bbytes;         // bytes of the table operand (table rows x taps, K-major)
+    size_t off_e, off_b, off_c, smem;
+    bool ok;
+};
+
 struct mbir_geometry {
     int device;
     mbir::GeomParams P;
@@ -431,6 +446,10 @@ struct mbir_geometry {
     uint4* d_tf4_bop;      // table operand (taps x columns plane * (Q + 1) + phase, K-major; FP32: two parts)
     uint32_t* d_tf4_crange;// per (A-scan, tile of 128 n0): first | end column << 16 of the planes its records reach
     int* d_tf4_split;      // per (A-scan, tile): the 17 boundaries of the warps' parts (record offsets)
+    int tf4_wmax;          // widest column range of a tile
+    // tensor-core A^T (see tc_stream.cuh); uses the tile offsets, slots and contributions of build_tc_adjoint
+    Tb4Layout tb4;
+    uint4* d_tb4_bop;      // table operand (table rows plane * (Q + 1) + phase x taps, K-major; FP32: two parts)
     long long n_records;
     // |A_v|^2 per pixel for the coordinate descent (computed on its first call)
     float* w_colnorm;
@@ -497,6 +516,10 @@ cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e
 cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, float* b, cudaStream_t st);
 Tf4Layout tf4_layout(const GeomParams& P, int kwmax);
 cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st);
+Tb4Layout tb4_layout(const GeomParams& P, int kwmax);
+cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st);
+cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
+                                   cudaStream_t st);
 cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
                                cudaStream_t st);
 cudaError_t launch_column_norms(const mbir_geometry* g, float* out, cudaStream_t st);

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "tc_apply.cuh"
+#include "tc_stream.cuh"
 
 namespace mbir {
 
@@ -337,6 +338,125 @@ cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, 
     Tc3View V{P, L, g->d_tc3_bop, g->d_tab, e_pad, g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_tile, g->d_tc3_prange,
               g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
     bwd_tc32_kernel<<<grid, kTcThreads, L.smem, st>>>(V, g->d_status);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return ce;
+    const int N = P.W * P.H;
+    bwd_tc_reduce_kernel<<<std::max(1, std::min((N + 7) / 8, 152 * 16)), 256, 0, st>>>(N, g->d_tc_pixoff,
+                                                                                     g->w_tc_contrib, b);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Streamed tensor-core A^T (tcs_adjoint_pool): layout, table operand, launch.
+// ---------------------------------------------------------------------------
+Tb4Layout tb4_layout(const GeomParams& P, int kwmax)
+{
+    Tb4Layout L{};
+    const bool bf = P.precision == MBIR_PREC_BF16;
+    L.parts = bf ? 1 : 2;
+    L.R = P.Q + 1;
+    L.kb = (P.G * L.R + 15) & ~15;
+    L.ntap = (P.Tw + 15) & ~15;
+    L.kwmax = std::min(std::min(kwmax, 256), L.kb);
+    L.cstride = ((L.kwmax + 31) & ~31) + 4;            // 4 mod 32: the read-back rows hit distinct banks
+    L.ewin = (kTsTile + L.ntap + 31) & ~31;
+    L.bbytes = (size_t)L.parts * L.kb * L.ntap * 2;
+    L.off_e = 128;
+    L.off_b = (L.off_e + (size_t)2 * L.ewin * 4 + 1023) & ~(size_t)1023;
+    L.off_c = (L.off_b + L.bbytes + 1023) & ~(size_t)1023;
+    L.smem = L.off_c + (size_t)kTsTile * L.cstride * 4;
+    L.ok = L.R >= 2 && L.ntap <= 128 && L.kwmax >= 16 && L.kwmax % 16 == 0 && 128 + L.kwmax <= (int)kTsCols &&
+           kTsTile + L.ntap <= kTsThreads && L.smem <= 227 * 1024 && L.bbytes < (1u << 20) &&
+           P.G * L.R <= 4096;
+    return L;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kTsThreads, 1) bwd_tcs_kernel(TbView V, int* __restrict__ status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    tc_header_init(smem, kTsCols);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
+    uint32_t mphase = 0, bphase = 0;
+    tcs_adjoint_pool<BF16>(V, smem, tmem, mphase, bphase, status);
+    tc_header_release(smem, tmem, kTsCols);
+}
+
+// Table operand of the streamed A^T (rows plane * (Q + 1) + phase, columns taps; FP32 form: the table times
+// 2^texp split into two FP16 parts, BF16 form: the stored BF16 table), for a geometry whose records, tile
+// offsets and contribution slots (build_tc_adjoint) and per-tile column ranges (build_tc_forward_stream) are
+// present; cudaErrorNotSupported keeps the other adjoints.
+cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st)
+{
+    (void)st;
+    const GeomParams& P = g->P;
+    if (!g->d_tc_tile || !g->d_tc_dest || !g->w_tc_contrib || !g->d_tf4_crange || !g->d_tc_counter)
+        return cudaErrorNotSupported;
+    Tb4Layout L{};
+    for (int kw : {256, 224, 192, 160, 128, 96, 64}) {
+        L = tb4_layout(P, kw);
+        if (L.ok) break;
+    }
+    if (!L.ok || g->tf4_wmax > L.kwmax) return cudaErrorNotSupported;
+    const int nq = P.Q * P.Tw + 1;
+    const size_t part = (size_t)L.kb * L.ntap;
+    std::vector<uint16_t> img((size_t)L.parts * part, 0);
+    if (P.precision == MBIR_PREC_BF16) {
+        L.texp = 0;
+        for (int gpl = 0; gpl < P.G; ++gpl)
+            for (int ph = 0; ph < L.R; ++ph)
+                for (int m = 0; m < P.Tw; ++m) {
+                    const __nv_bfloat16 v = __float2bfloat16_rn((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
+                    img[kmajor_offset(gpl * L.R + ph, m, L.ntap) / 2] = *reinterpret_cast<const uint16_t*>(&v);
+                }
+    } else {
+        float tmax = 0.0f;
+        for (size_t i = 0; i < (size_t)P.G * nq; ++i) tmax = std::max(tmax, std::fabs((float)g->tab_host[i]));
+        int ex = 0;
+        std::frexp(tmax, &ex);
+        L.texp = tmax > 0.0f ? std::min(15 - ex, 126) : 0;
+        for (int gpl = 0; gpl < P.G; ++gpl)
+            for (int ph = 0; ph < L.R; ++ph)
+                for (int m = 0; m < P.Tw; ++m) {
+                    const float t = std::ldexp((float)g->tab_host[(size_t)gpl * nq + m * P.Q + ph], L.texp);
+                    const __half p1 = __float2half_rn(t);
+                    const __half p2 = __float2half_rn(t - __half2float(p1));
+                    const size_t o = kmajor_offset(gpl * L.R + ph, m, L.ntap) / 2;
+                    img[o] = *reinterpret_cast<const uint16_t*>(&p1);
+                    img[part + o] = *reinterpret_cast<const uint16_t*>(&p2);
+                }
+    }
+    uint4* d_b = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_b, L.bbytes);
+    if (e == cudaSuccess) e = cudaMemcpy(d_b, img.data(), L.bbytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_b);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
+    }
+    g->tb4 = L;
+    g->d_tb4_bop = d_b;
+    g->bytes += L.bbytes;
+    return cudaSuccess;
+}
+
+cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
+                                   cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const Tb4Layout& L = g->tb4;
+    const bool bf = P.precision == MBIR_PREC_BF16;
+    auto kern = bf ? bwd_tcs_kernel<true> : bwd_tcs_kernel<false>;
+    cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tc_counter, 0, sizeof(int), st);
+    if (ce != cudaSuccess) return ce;
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    const int grid = std::max(1, std::min(g->n_sm, P.K * ntile));
+    const void* tab = bf ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
+    const void* e = bf ? (const void*)e_bf : (const void*)e_pad;
+    TbView V{P, L, g->d_tb4_bop, tab, e, g->d_rec_off, g->d_tc_tile, g->d_tf4_crange, g->d_rec_key, g->d_rec_w,
+             g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
+    kern<<<grid, kTsThreads, L.smem, st>>>(V, g->d_status);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
     const int N = P.W * P.H;

@@ -74,6 +74,12 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint4& v)
                  : "memory");
 }
 
+// 2 consecutive 32-bit columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t a, uint32_t b)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(a), "r"(b) : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // The mbarrier completes once the MMAs this thread issued before have finished.

@@ -214,6 +214,7 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
     g->d_tf4_bop = d_b;
     g->d_tf4_crange = d_cr;
     g->d_tf4_split = d_sp;
+    g->tf4_wmax = wmax;
     g->bytes += L.bbytes + sizeof(int) * ((size_t)P.K * (P.M + 1) + P.K + 1) +
                 sizeof(int) * (size_t)P.K * ntile * (kTsSplit + 1);
     return cudaSuccess;

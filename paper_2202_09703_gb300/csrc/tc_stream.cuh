@@ -362,4 +362,254 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
     return !*abort_flag;
 }
 
+// ---------------------------------------------------------------------------
+// A^T r on the tensor cores (adjoint of eq. 13): per item (A-scan, tile of 128
+// first-tap samples n0), every tap of a pair shares one table phase, so
+//     C[n0][row] = sum_m e[n0 + 1 + m] T[row][m]
+// is one matrix product of the residual's Hankel tile H[n][m] = e[ts + 1 + n + m]
+// (128 x taps, in tensor memory as the A operand) and the table rows the tile's
+// records reach (one column range, the B operand resident in shared memory);
+// each record then combines four values of C with its bilinear weights (less
+// the tau = t0 tap of flagged records) and writes one contribution to its slot
+// in pixel-major order; a reduction kernel sums each pixel's contributions in
+// A-scan order.  FP32 form: the window scaled by the power of two that brings
+// its largest magnitude into [2^14, 2^15) and split into two FP16 parts, the
+// table likewise: three products.  BF16 form: the stored BF16 residual and
+// table, one product.  The products of the next item run while the current
+// item's records are processed.
+struct TbView {
+    GeomParams P;
+    Tb4Layout T;
+    const uint4* bop;            // table operand image
+    const void* tab;             // kernel table, float2 (FP32) or __nv_bfloat162 (BF16): the tau = t0 tap
+    const void* e;               // residual K x Mp: float (FP32) or __nv_bfloat16 (BF16), zero tail
+    const long long* rec_off;
+    const int* tile_off;         // first record of every tile, K x (ntile + 1)
+    const uint32_t* crange;      // per (A-scan, tile): c_lo | c_hi << 16
+    const int2* rkey;
+    const float4* rw;
+    const uint32_t* dest;        // record -> slot in pixel-major order
+    float* contrib;
+    int* counter;
+};
+
+constexpr int kTbUnroll = 4;     // records in flight per thread
+
+// Drains the A^T items of V (header as for tcs_forward_pool; kTsCols tensor-memory columns).
+template <bool BF16>
+__device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char* smem, uint32_t tmem,
+                                                 uint32_t& mphase, uint32_t& bphase, int* status)
+{
+    const GeomParams& P = V.P;
+    const Tb4Layout& T = V.T;
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    const int nitems = P.K * ntile;
+    volatile int* next = reinterpret_cast<volatile int*>(smem + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 20);
+    float* wmax = reinterpret_cast<float*>(smem + 64);
+    float* sE0 = reinterpret_cast<float*>(smem + T.off_e);
+    unsigned char* sB = smem + T.off_b;
+    float* sC = reinterpret_cast<float*>(smem + T.off_c);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = T.R, S = table_stride(P.Tw4);
+    const float invR = 1.0f / (float)R;
+    const int2* __restrict__ rkey = V.rkey;
+    const float4* __restrict__ rw = V.rw;
+    const uint32_t* __restrict__ dest = V.dest;
+    float* __restrict__ contrib = V.contrib;
+    const uint32_t tA = tmem, tD = tmem + 128;
+    const int HA = T.ntap / 2;                          // tensor-memory columns of one part of H
+    const int qd = warp & 3, pb = warp >> 2;
+    const int cq = T.ntap / 4;                          // taps of H converted per thread
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    const uint32_t full = 0xffffffffu;
+    const int W = kTsTile + T.ntap;                     // window samples e[ts + 1 .. ts + W]
+    const uint32_t sboB = (uint32_t)(T.ntap / 8) * 128, bpart = (uint32_t)(T.kb * T.ntap * 2);
+    const float it = ts_pow2(-T.texp);
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(smem_u32(smem + 32), (uint32_t)T.bbytes);
+        bulk_g2s(smem_u32(sB), V.bop, (uint32_t)T.bbytes, smem_u32(smem + 32));
+        *next = atomicAdd(V.counter, 1);
+    }
+    if (!mbar_wait_bounded(smem_u32(smem + 32), bphase, status)) *abort_flag = 1;
+    bphase ^= 1u;
+    __syncthreads();
+
+    auto load_e = [&](int item) -> float {
+        const int k = item / ntile, t = item - k * ntile;
+        const int n = t * kTsTile + 1 + tid;
+        if (tid >= W || n >= P.Mp) return 0.0f;
+        if (BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(V.e)[(size_t)k * P.Mp + n]);
+        return reinterpret_cast<const float*>(V.e)[(size_t)k * P.Mp + n];
+    };
+    // the window of an item: staged, its warps' maxima published (the scale needs a barrier)
+    auto stage = [&](float ew, float* sE) {
+        if (tid < W) sE[tid] = ew;
+        float mx = fabsf(ew);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+        if (lane == 0) wmax[warp] = mx;
+    };
+    auto window_exponent = [&]() -> int {
+        if (BF16) return 0;
+        float m = 0.0f;
+        for (int w = 0; w < kTsWarps; ++w) m = fmaxf(m, wmax[w]);
+        return ts_bound_exponent(m);
+    };
+    // H of an item into tensor memory: row n (lane), taps [pb cq, pb cq + cq), H[n][m] = 2^se e[ts + 1 + n + m]
+    auto convert_h = [&](const float* sE, int se) {
+        const float scl = ts_pow2(se);
+        const int n = qd * 32 + lane;
+        for (int m = pb * cq; m < pb * cq + cq; m += 4) {
+            const float a0 = sE[n + m] * scl, a1 = sE[n + m + 1] * scl, a2 = sE[n + m + 2] * scl,
+                        a3 = sE[n + m + 3] * scl;
+            if (BF16) {
+                const __nv_bfloat162 p0 = __floats2bfloat162_rn(a0, a1), p1 = __floats2bfloat162_rn(a2, a3);
+                tmem_st2(tA + lane_base + (uint32_t)(m / 2), *reinterpret_cast<const uint32_t*>(&p0),
+                         *reinterpret_cast<const uint32_t*>(&p1));
+            } else {
+                uint32_t h0, l0, h1, l1;
+                split2h_pair(a0, a1, h0, l0);
+                split2h_pair(a2, a3, h1, l1);
+                tmem_st2(tA + lane_base + (uint32_t)(m / 2), h0, h1);
+                tmem_st2(tA + lane_base + (uint32_t)(HA + m / 2), l0, l1);
+            }
+        }
+        tmem_wait_st();
+    };
+    auto issue_mma = [&](int item) {
+        const uint32_t cr = __ldg(V.crange + item);
+        const int c_lo = (int)(cr & 0xffffu), kw = (int)(cr >> 16) - c_lo;
+        tc_fence_after();
+        const uint32_t idesc = BF16 ? umma_idesc_bf16(kTsTile, kw) : umma_idesc_f16(kTsTile, kw);
+        const uint32_t b0 = smem_u32(sB) + (uint32_t)(c_lo / 8) * sboB;
+        for (int s = 0; s < T.ntap / 16; ++s) {
+            umma_f16_ta(tD, tA + 8 * s, umma_desc(b0 + 256 * s, 128, sboB), idesc, s > 0);
+            if (!BF16) {
+                umma_f16_ta(tD, tA + 8 * s, umma_desc(b0 + bpart + 256 * s, 128, sboB), idesc, true);
+                umma_f16_ta(tD, tA + HA + 8 * s, umma_desc(b0 + 256 * s, 128, sboB), idesc, true);
+            }
+        }
+        umma_commit(smem_u32(smem));
+    };
+
+    int cur = *next;
+    if (cur >= nitems) return !*abort_flag;
+    // first item: window, scale, H, products
+    int cbuf = 0;
+    stage(load_e(cur), sE0);
+    __syncthreads();
+    if (tid == 0) *next = atomicAdd(V.counter, 1);
+    int cse = window_exponent();
+    uint32_t live_cur = __ldg(V.crange + cur);           // a tile without records has an empty range
+    if (live_cur) convert_h(sE0, cse);
+    tc_fence_before();
+    __syncthreads();
+    int nxt = *next;
+    if (tid == 0 && live_cur) issue_mma(cur);
+    while (!*abort_flag) {
+        const int kc = cur / ntile, tc = cur - kc * ntile;
+        const long long base = __ldg(V.rec_off + kc);
+        const int r0 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc);
+        const int r1 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc + 1);
+        // the first records of this item and the next item's window load during the products
+        int2 kb_[kTbUnroll];
+        float4 wb_[kTbUnroll];
+        uint32_t db_[kTbUnroll];
+#pragma unroll
+        for (int u = 0; u < kTbUnroll; ++u) {
+            const int r = r0 + u * kTsThreads + tid;
+            if (r < r1) {
+                kb_[u] = __ldg(rkey + base + r);
+                wb_[u] = __ldg(rw + base + r);
+                db_[u] = __ldg(dest + base + r);
+            }
+        }
+        const float ew = nxt < nitems ? load_e(nxt) : 0.0f;
+        float* sEc = sE0 + cbuf * T.ewin;
+        float* sEn = sE0 + (cbuf ^ 1) * T.ewin;
+        // ---- C of the current item -> shared memory (scaled back)
+        const int c_lo = (int)(live_cur & 0xffffu), kw = (int)(live_cur >> 16) - c_lo;
+        if (live_cur) {
+            if (!mbar_wait_bounded(smem_u32(smem), mphase, status)) *abort_flag = 1;
+            mphase ^= 1u;
+            tc_fence_after();
+            const float i0 = ts_pow2(-cse);
+            const int cw = kw / 4, row = qd * 32 + lane;
+            float* crow = sC + row * T.cstride;
+            for (int c = pb * cw; c < pb * cw + cw; c += 4) {
+                float v[4];
+                tmem_ld4(tD + lane_base + (uint32_t)c, v);
+                *reinterpret_cast<float4*>(crow + c) =
+                    make_float4((v[0] * i0) * it, (v[1] * i0) * it, (v[2] * i0) * it, (v[3] * i0) * it);
+            }
+        }
+        if (nxt < nitems) stage(ew, sEn);
+        tc_fence_before();
+        __syncthreads();                                  // C ready; the next window staged
+        if (tid == 0) *next = atomicAdd(V.counter, 1);
+        // ---- the next item's H and products, issued before this item's records
+        int nse = 0;
+        uint32_t live_nxt = 0;
+        if (nxt < nitems) {
+            nse = window_exponent();
+            live_nxt = __ldg(V.crange + nxt);
+            if (live_nxt) convert_h(sEn, nse);
+        }
+        tc_fence_before();
+        __syncthreads();                                  // H of the next item in tensor memory
+        const int nn = *next;
+        if (tid == 0 && live_nxt) issue_mma(nxt);
+        // ---- the current item's records: four values of C each, one contribution per record
+        if (live_cur) {
+            const int ts = tc * kTsTile;
+            const float* Cb = sC - c_lo;
+            for (int rb = r0; rb < r1; rb += kTbUnroll * kTsThreads) {
+                if (rb > r0) {
+#pragma unroll
+                    for (int u = 0; u < kTbUnroll; ++u) {
+                        const int r = rb + u * kTsThreads + tid;
+                        if (r < r1) {
+                            kb_[u] = __ldg(rkey + base + r);
+                            wb_[u] = __ldg(rw + base + r);
+                            db_[u] = __ldg(dest + base + r);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kTbUnroll; ++u) {
+                    const int r = rb + u * kTsThreads + tid;
+                    if (r >= r1) continue;
+                    const int n0r = (kb_[u].y >> kRecShift) - ts, trow = (kb_[u].y >> 1) & 0xfff;
+                    const int gi = (int)(((float)trow + 0.5f) * invR);
+                    const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
+                    const float* cr = Cb + n0r * T.cstride;
+                    float v = wb_[u].x * cr[trow];
+                    v = fmaf(wb_[u].y, cr[c1col], v);
+                    v = fmaf(wb_[u].z, cr[trow + 1], v);
+                    v = fmaf(wb_[u].w, cr[c1col + 1], v);
+                    if (kb_[u].y & 1) {
+                        // tau = t0 exactly: the last tap of the upper phase row lies outside the window
+                        const size_t ti = ((size_t)gi * R + (trow - gi * R) + 1) * S + P.Tw - 1;
+                        float2 tl;
+                        if (BF16) tl = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(V.tab) + ti));
+                        else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
+                        v -= (wb_[u].z * tl.x + wb_[u].w * tl.y) * sEc[n0r + P.Tw - 1];
+                    }
+                    contrib[db_[u]] = v;
+                }
+            }
+        }
+        __syncthreads();                                  // C and this window are free
+        if (nxt >= nitems) break;
+        cur = nxt;
+        nxt = nn;
+        cbuf ^= 1;
+        cse = nse;
+        live_cur = live_nxt;
+    }
+    return !*abort_flag;
+}
+
 }  // namespace mbir
