@@ -73,17 +73,21 @@ def parse():
     return ap.parse_args()
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if none of the
-    kernel's source files changed since the capture (else None)."""
+def measured_traffic(kernel: str, pairs: float):
+    """DRAM bytes per launch from the committed ncu summary (a capture of a
+    smaller workload, scaled to this one by its active pairs: the record
+    stream is the traffic), if none of the kernel's source files changed
+    since the capture (else None)."""
     try:
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             if line.startswith("#") or not line.strip():
                 continue
-            name, srcs, sha, rd, wr = line.split()[:5]
-            if name.startswith(kernel):
-                return float(rd) + float(wr) if source_hash(srcs) == sha else None
-    except OSError:
+            name, srcs, sha, rd, wr, cap_pairs = line.split()[:6]
+            if name == kernel:
+                if source_hash(srcs) != sha:
+                    return None
+                return (float(rd) + float(wr)) * pairs / float(cap_pairs)
+    except (OSError, ValueError):
         return None
     return None
 
@@ -397,12 +401,13 @@ def run_gpu(args):
     tc_dom = bool(geo.info.forward_tensor_cores if dom == "forward" else geo.info.adjoint_tensor_cores)
     if tc_dom:
         rec_bytes = 12.0 * pairs + algo_bytes
-        name = "fwd_tc32_kernel" if dom == "forward" else "bwd_tc32_kernel"
+        name = "fwd_tcs_kernel" if dom == "forward" else "bwd_tcs_kernel"
         roofline = {"bound": "hbm", "resource": "HBM: the TAB record stream",
                     "kernel": name, "achieved": rec_bytes / (dom_ms * 1e-3) / 1e9,
                     "peak": hbm_peak, "unit": "GB/s", "frac": rec_bytes / (dom_ms * 1e-3) / 1e9 / hbm_peak,
-                    "traffic": measured_traffic(name),
-                    "traffic_note": "DRAM read+write bytes per launch (ncu), null if the kernel changed since",
+                    "traffic": measured_traffic(name, pairs),
+                    "traffic_note": "DRAM read+write bytes per launch: ncu capture of the 256x512 workload scaled "
+                                    "by active pairs; null if the kernel changed since",
                     "peak_source": f"hbm_gbs ({src})", "algorithmic_bytes_per_launch": rec_bytes,
                     "bytes_per_pair_minimum": 12, "active_pairs": pairs, "taps_per_launch": taps,
                     "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
