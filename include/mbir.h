@@ -117,20 +117,23 @@ typedef struct {
 } mbir_geometry_desc;
 
 /* TAB mode normally also stores every A-scan's active pairs as records
- * sorted by first tap sample (the system matrix of Section 3, about 24 bytes
- * per active pair) so that A x streams them; this flag keeps the on-the-fly
- * record path of A x instead (less memory, slower). */
+ * sorted by first tap sample, then table row and pixel (the system matrix of
+ * Section 3, 24 bytes per active pair) so that A x and A^T stream them; this
+ * flag keeps the on-the-fly record path of A x instead (less memory, slower). */
 #define MBIR_FLAG_NO_RECORDS 1
 
-/* BF16 precision with records normally applies A and A^T on the tensor
- * cores.  A^T: per A-scan and 128-sample tile, the correlation of the stored
- * residual with every stored table row is one BF16 matrix product with FP32
- * accumulation (an exact rewriting of the adjoint of eq. 13, every tap of a
- * pair sharing one table phase), and each pair then combines four of its
- * values.  A x: per A-scan and tile of 128 first-tap samples, the pairs'
- * weights times x are summed per (sample, table row) in FP32, rounded once to
- * BF16, multiplied by the table on the tensor cores and added along the
- * product's anti-diagonals.  This flag keeps the CUDA-core kernels instead. */
+/* With records, A and A^T normally run on the tensor cores (both storage
+ * forms).  Every tap of a pair shares one table phase (eq. 13 with the
+ * bilinear table), so per A-scan and tile of 128 first-tap samples n0:
+ *   A x: the pairs' weights times x are summed per (n0, table row), the sums
+ *        multiplied by the table on the tensor cores and added along the
+ *        product's anti-diagonals;
+ *   A^T: the correlation of the residual with the table rows is one matrix
+ *        product, and each pair combines four of its values.
+ * FP32 form: operands scaled by powers of two and split into two FP16 parts
+ * (three products, FP32 accuracy); BF16 form: the stored BF16 residual and
+ * table, the A x sums rounded once to BF16.  FP32 accumulation throughout;
+ * outputs are bitwise reproducible.  This flag keeps the CUDA-core kernels. */
 #define MBIR_FLAG_NO_TENSOR_CORES 2
 
 /* QGGMRF prior (eq. 15-17) and the noise sigma of eq. 2.
@@ -160,11 +163,12 @@ typedef struct {
     int mode;                    /* resolved mbir_mode (OTF or TAB) */
     int precision;
     int64_t device_bytes;        /* tables + workspace held by the handle */
-    int forward_window_spans;    /* TAB records: 32-sample spans per A x work unit (timed at creation), else 0 */
-    double forward_window_ms[3]; /* the A x times measured for windows of 1, 2 and 4 spans (0 if not timed) */
-    int adjoint_groups;          /* transmitter groups of the A^T r work items */
-    int adjoint_tensor_cores;    /* 1 if A^T runs on the tensor cores (BF16 form, see MBIR_FLAG_NO_TENSOR_CORES) */
-    int forward_tensor_cores;    /* 1 if A x runs on the tensor cores (BF16 form) */
+    int forward_window_spans;    /* TAB records: 32-sample spans per work unit of the CUDA-core A x, else 0 */
+    double forward_window_ms[3]; /* CUDA-core A x times for windows of 1, 2 and 4 spans, measured at creation
+                                  * when that kernel is the geometry's A x (0 otherwise) */
+    int adjoint_groups;          /* transmitter groups of the CUDA-core A^T r work items */
+    int adjoint_tensor_cores;    /* 1 if A^T runs on the tensor cores (see MBIR_FLAG_NO_TENSOR_CORES) */
+    int forward_tensor_cores;    /* 1 if A x runs on the tensor cores */
 } mbir_geometry_info;
 
 typedef struct mbir_geometry mbir_geometry;
@@ -191,8 +195,8 @@ size_t mbir_geometry_bytes(const mbir_geometry* g);
 
 int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info);
 
-/* Override the A x window chosen at creation (TAB records only): every warp of
- * the A x launch then covers `spans` consecutive 32-sample spans (1, 2 or 4).
+/* Override the window of the CUDA-core A x (TAB records only): every warp of
+ * that kernel then covers `spans` consecutive 32-sample spans (1, 2 or 4).
  * A tuning control with no counterpart in the paper; the output bits do not
  * depend on it.  Synchronises the device; the handle must not be in use by
  * another call or an engine.  Errors: MBIR_ERR_INVALID_ARG (other values),

@@ -6,16 +6,18 @@
 // requests from device-side work lists that the host rewrites between steps,
 // so the graph is captured once and replayed as requests come and go
 // (continuous batching):
-//   A^T e   persistent, two tile workers per CTA; each request's own work
-//           items (pixel tile x transmitter group, longest first) form a pool
-//           drained through a per-request counter.  A CTA starts at the
-//           request its share of the total cost falls on and walks on through
-//           the others until every pool is empty, loading a request's pulse
+//   A^T e   persistent; each request's own work items form a pool drained
+//           through a per-request counter (tensor cores: (A-scan, tile) items
+//           of tcs_adjoint_pool, then the per-pixel reduction; CUDA cores:
+//           pixel tile x transmitter group, longest first).  A CTA starts at
+//           the request its share of the total cost falls on and walks on
+//           through the others until every pool is empty, loading a request's
 //           table only when it joins that request's pool
 //   grad    prior gradient + FP64 partials per (request, pixel block)
 //   dir     Polak-Ribiere+ scalars per request, then directions + curvature
-//   A d     persistent span gather over each request's sorted records, spans
-//           largest first, pools and CTA placement as for A^T e
+//   A d     persistent over each request's sorted records (tensor cores:
+//           A-scans of tcs_forward_pool, largest first; CUDA cores: span
+//           windows, largest first), pools and CTA placement as for A^T e
 //   P q     direct-arrival projection per (request, A-scan) with FP64 norms
 //   step    majorize-minimize step per request; x and e updated
 // The apply kernels run the same per-item and per-span code as the

@@ -264,6 +264,21 @@ cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_b
     if (e == cudaSuccess) e = cudaMalloc((void**)&g->d_win_counter, sizeof(int));
     if (e != cudaSuccess) return e;
     g->bytes += sizeof(int);
+    // two spans per warp until tune_forward_window times the candidates (only when this kernel is the A x)
+    std::vector<int> order, cost;
+    window_order(runs, P.K, nspan, 2, &order, &cost);
+    return install_window(g, 2, order, cost);
+}
+
+// Times the CUDA-core A x windows (1, 2, 4 spans) once and keeps the fastest.
+cudaError_t tune_forward_window(mbir_geometry* g, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    if (!g->d_runs) return cudaSuccess;
+    const int nspan = (P.M + 31) / 32;
+    std::vector<int2> runs((size_t)P.K * nspan);
+    cudaError_t e = cudaMemcpy(runs.data(), g->d_runs, sizeof(int2) * runs.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
     return tune_window(g, runs, st);
 }
 

@@ -545,6 +545,11 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
             if (ce == cudaErrorNotSupported) ce = cudaSuccess;  // keep the per-half tensor-core A^T
             if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
         }
+        // the CUDA-core A x's window is tuned only when that kernel is the geometry's A x
+        if (g->d_rec_key && !g->d_tf4_bop) {
+            ce = mbir::tune_forward_window(g, st);
+            if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
+        }
     }
     // set-up of the allocation-free adjoint for this device (a no-op for geometries it does not take)
     ce = mbir::noalloc_prepare(g);

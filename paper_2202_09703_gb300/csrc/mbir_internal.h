@@ -497,6 +497,7 @@ cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, long long n, cu
 void compute_msq(const mbir_geometry* g, const mbir_prior* pr, float* out);
 cudaError_t launch_count_taps(const mbir_geometry* g, unsigned long long* d_out, cudaStream_t st);
 cudaError_t build_sorted_records(mbir_geometry* g, cudaStream_t st, size_t cap_bytes);
+cudaError_t tune_forward_window(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_forward_sorted(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,
                                   cudaStream_t st);
 size_t backproject_smem(const mbir_geometry* g);

@@ -18,9 +18,10 @@
 // next tile's first loads issued while the current tile is multiplied), sums
 // the contributions of equal (n0, table row) with a segmented warp scan, and
 // the last record of each run adds its four bilinear corners into S with plain
-// read-modify-writes: within one instruction the cells are distinct, and the
-// four corners go in four instructions.  No atomics: the sums run in a fixed
-// order and every output bit is reproducible.
+// read-modify-writes: within one instruction the cells are distinct, the four
+// corners go in four steps, and each row of S belongs to one warp.  No
+// atomics: every cell's additions happen in a fixed order and every output bit
+// is reproducible.
 //
 // The records of a tile reach a few neighbouring attenuation planes, one
 // column range [c_lo, c_hi) found per tile at set-up: only that range is held,
@@ -234,7 +235,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         const int kup = __shfl_up_sync(full, key, 1);
                         const int kdn = __shfl_down_sync(full, key, 1);
                         if (__any_sync(full, lane > 0 && kup == key)) {
-#pragma unroll
+                            // Hillis-Steele steps until no run reaches further back (runs are short)
                             for (int d = 1; d < 32; d <<= 1) {
                                 const int kd = __shfl_up_sync(full, key, d);
                                 const float a0 = __shfl_up_sync(full, c0, d), a1 = __shfl_up_sync(full, c1, d);
@@ -245,13 +246,16 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                                     c2 += a2;
                                     c3 += a3;
                                 }
+                                const int k2 = __shfl_up_sync(full, key, min(2 * d, 31));
+                                if (!__any_sync(full, lane >= 2 * d && k2 == key)) break;
                             }
                         }
+                        // the last record of each run adds its corners, one corner per step: within a step the
+                        // writers' cells are distinct and the rows belong to this warp alone
                         const bool writer = valid && (lane == 31 || kdn != key);
                         const int gi = (int)(((float)trow + 0.5f) * invR);
                         const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
                         float* row = Sb + n0r * T.astride;
-                        // the four corners in four steps: within a step the writers' cells are distinct
                         if (writer) row[trow] += c0;
                         __syncwarp();
                         if (writer) row[c1col] += c1;
@@ -393,7 +397,28 @@ struct TbView {
     int* counter;
 };
 
-constexpr int kTbUnroll = 4;     // records in flight per thread
+constexpr int kTbUnroll = 4;     // records per thread in one batch (two batches in flight)
+
+// A batch of records held in registers: records rb + u * kTsThreads + tid, u < kTbUnroll.
+struct TbBatch {
+    int2 key[kTbUnroll];
+    float4 w[kTbUnroll];
+    uint32_t dst[kTbUnroll];
+};
+
+__device__ __forceinline__ void tb_load(TbBatch& b, const int2* __restrict__ rkey, const float4* __restrict__ rw,
+                                        const uint32_t* __restrict__ dest, long long base, int rb, int r1, int tid)
+{
+#pragma unroll
+    for (int u = 0; u < kTbUnroll; ++u) {
+        const int r = rb + u * kTsThreads + tid;
+        if (r < r1) {
+            b.key[u] = __ldg(rkey + base + r);
+            b.w[u] = __ldg(rw + base + r);
+            b.dst[u] = __ldg(dest + base + r);
+        }
+    }
+}
 
 // Drains the A^T items of V (header as for tcs_forward_pool; kTsCols tensor-memory columns).
 template <bool BF16>
@@ -514,18 +539,8 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         const int r0 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc);
         const int r1 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc + 1);
         // the first records of this item and the next item's window load during the products
-        int2 kb_[kTbUnroll];
-        float4 wb_[kTbUnroll];
-        uint32_t db_[kTbUnroll];
-#pragma unroll
-        for (int u = 0; u < kTbUnroll; ++u) {
-            const int r = r0 + u * kTsThreads + tid;
-            if (r < r1) {
-                kb_[u] = __ldg(rkey + base + r);
-                wb_[u] = __ldg(rw + base + r);
-                db_[u] = __ldg(dest + base + r);
-            }
-        }
+        TbBatch ba, bb;
+        tb_load(ba, rkey, rw, dest, base, r0, r1, tid);
         const float ew = nxt < nitems ? load_e(nxt) : 0.0f;
         float* sEc = sE0 + cbuf * T.ewin;
         float* sEn = sE0 + (cbuf ^ 1) * T.ewin;
@@ -561,44 +576,42 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         __syncthreads();                                  // H of the next item in tensor memory
         const int nn = *next;
         if (tid == 0 && live_nxt) issue_mma(nxt);
-        // ---- the current item's records: four values of C each, one contribution per record
+        // ---- the current item's records: four values of C each, one contribution per record; the next
+        // batch loads while one is combined
         if (live_cur) {
             const int ts = tc * kTsTile;
             const float* Cb = sC - c_lo;
-            for (int rb = r0; rb < r1; rb += kTbUnroll * kTsThreads) {
-                if (rb > r0) {
-#pragma unroll
-                    for (int u = 0; u < kTbUnroll; ++u) {
-                        const int r = rb + u * kTsThreads + tid;
-                        if (r < r1) {
-                            kb_[u] = __ldg(rkey + base + r);
-                            wb_[u] = __ldg(rw + base + r);
-                            db_[u] = __ldg(dest + base + r);
-                        }
-                    }
-                }
+            auto run = [&](const TbBatch& bt, int rb) {
 #pragma unroll
                 for (int u = 0; u < kTbUnroll; ++u) {
                     const int r = rb + u * kTsThreads + tid;
                     if (r >= r1) continue;
-                    const int n0r = (kb_[u].y >> kRecShift) - ts, trow = (kb_[u].y >> 1) & 0xfff;
+                    const int n0r = (bt.key[u].y >> kRecShift) - ts, trow = (bt.key[u].y >> 1) & 0xfff;
                     const int gi = (int)(((float)trow + 0.5f) * invR);
                     const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
                     const float* cr = Cb + n0r * T.cstride;
-                    float v = wb_[u].x * cr[trow];
-                    v = fmaf(wb_[u].y, cr[c1col], v);
-                    v = fmaf(wb_[u].z, cr[trow + 1], v);
-                    v = fmaf(wb_[u].w, cr[c1col + 1], v);
-                    if (kb_[u].y & 1) {
+                    float v = bt.w[u].x * cr[trow];
+                    v = fmaf(bt.w[u].y, cr[c1col], v);
+                    v = fmaf(bt.w[u].z, cr[trow + 1], v);
+                    v = fmaf(bt.w[u].w, cr[c1col + 1], v);
+                    if (bt.key[u].y & 1) {
                         // tau = t0 exactly: the last tap of the upper phase row lies outside the window
                         const size_t ti = ((size_t)gi * R + (trow - gi * R) + 1) * S + P.Tw - 1;
                         float2 tl;
                         if (BF16) tl = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(V.tab) + ti));
                         else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
-                        v -= (wb_[u].z * tl.x + wb_[u].w * tl.y) * sEc[n0r + P.Tw - 1];
+                        v -= (bt.w[u].z * tl.x + bt.w[u].w * tl.y) * sEc[n0r + P.Tw - 1];
                     }
-                    contrib[db_[u]] = v;
+                    contrib[bt.dst[u]] = v;
                 }
+            };
+            constexpr int kStep = kTbUnroll * kTsThreads;
+            for (int rb = r0; rb < r1; rb += 2 * kStep) {
+                if (rb + kStep < r1) tb_load(bb, rkey, rw, dest, base, rb + kStep, r1, tid);
+                run(ba, rb);
+                if (rb + kStep >= r1) break;
+                if (rb + 2 * kStep < r1) tb_load(ba, rkey, rw, dest, base, rb + 2 * kStep, r1, tid);
+                run(bb, rb + kStep);
             }
         }
         __syncthreads();                                  // C and this window are free
