@@ -278,8 +278,6 @@ cudaError_t launch_backproject(const mbir_geometry* g, const float* e_pad, const
 {
     const bool bf = g->P.precision == MBIR_PREC_BF16;
     if (g->d_tb4_bop) return launch_backproject_tcs(g, e_pad, e_bf, b, st);
-    if (bf && g->d_tc_bop) return launch_backproject_tc(g, e_bf, b, st);
-    if (!bf && g->d_tc3_bop) return launch_backproject_tc32(g, e_pad, b, st);
     if (g->P.mode == MBIR_MODE_TAB)
         return bf ? launch_bwd_nl<kModeTAB, true>(g, e_bf, b, st) : launch_bwd_nl<kModeTAB, false>(g, e_pad, b, st);
     return bf ? launch_bwd_nl<kModeOTF, true>(g, e_bf, b, st) : launch_bwd_nl<kModeOTF, false>(g, e_pad, b, st);

@@ -91,14 +91,8 @@ struct ReqDesc {
     int nwin;              // K x windows of `sub` 32-sample spans
     int sub;
     int nblk;              // pixel blocks of kRedThreads
-    // tensor-core pools of the BF16 form (tc != 0)
+    // tensor-core A^T tables (tc != 0: the contribution buffer is allocated)
     int tc;
-    int tc32;              // FP32 tensor-core adjoint pool available
-    Tc3Layout tc3l;
-    const uint4* tc3_bop;
-    const uint2* tc3_prange;
-    TcLayout tcl;
-    const uint4* tc_bop;
     const int* tc_tile;
     const uint32_t* tc_dest;
     const long long* tc_pixoff;
@@ -396,34 +390,6 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
     }
 }
 
-// A^T e of the BF16 form on the tensor cores over every active request: the
-// CTA walks the requests from its start, draining each one's (A-scan, tile)
-// pool with the single-request pool function.
-__global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc_kernel(EngLists L)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    tc_header_init(smem, kTcCols);
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
-    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
-    uint32_t phase = 0;
-    const int nreq = L.counts[0];
-    if (nreq > 0) {
-        const int r0 = L.start[blockIdx.x] % nreq;
-        for (int t = 0; t < nreq; ++t) {
-            const int rq = (r0 + t) % nreq;
-            const ReqDesc& R = L.desc[rq];
-            const int nitems = R.P.K * ((R.P.M + kTcTile - 1) / kTcTile);
-            if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
-            const TcAdjView V{R.P, R.tcl, R.tc_bop, R.tab_bf, R.ebf, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc3_prange,
-                              R.tc_dest,
-                              R.tc_contrib, L.pool + 2 * rq + 1};
-            if (!tc_adjoint_pool(V, smem, tmem, phase, R.D.status)) break;
-            __syncthreads();
-        }
-    }
-    tc_header_release(smem, tmem, kTcCols);
-}
-
 // A^T e on the tensor cores (FP32 or BF16 form, tc_stream.cuh) over every active request
 template <bool BF16>
 __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
@@ -450,32 +416,6 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
         }
     }
     tc_header_release(smem, tmem, kTsCols);
-}
-
-// A^T e of the FP32 form on the tensor cores (two-part FP16 split) over every
-// active request, with the single-request pool function
-__global__ void __launch_bounds__(kTcThreads, 1) eng_bwd_tc32_kernel(EngLists L)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    tc_header_init(smem, 256);
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
-    volatile int* flag = reinterpret_cast<volatile int*>(smem + 24);
-    uint32_t phase = 0, bphase = 0;
-    const int nreq = L.counts[0];
-    if (nreq > 0) {
-        const int r0 = L.start[blockIdx.x] % nreq;
-        for (int t = 0; t < nreq; ++t) {
-            const int rq = (r0 + t) % nreq;
-            const ReqDesc& R = L.desc[rq];
-            const int nitems = R.P.K * ((R.P.M + kTcTile - 1) / kTcTile);
-            if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
-            const Tc3View V{R.P, R.tc3l, R.tc3_bop, R.tab, R.e, R.rec_off, R.rkey, R.rw, R.tc_tile, R.tc3_prange, R.tc_dest,
-                            R.tc_contrib, L.pool + 2 * rq + 1};
-            if (!tc_adjoint32_pool(V, smem, tmem, phase, bphase, R.D.status)) break;
-            __syncthreads();
-        }
-    }
-    tc_header_release(smem, tmem, 256);
 }
 
 // b = each pixel's contributions summed in A-scan order (the single-request
@@ -642,7 +582,7 @@ size_t request_bytes(const mbir_geometry* g, int ngroups)
     size_t b = 2 * KMp * 4 + 6 * N * 4 + (size_t)ngroups * N * 4 + (size_t)P.H * 4 + S_COUNT * 8 +
                (4 * nblk + P.K + 8) * 8;
     if (P.precision == MBIR_PREC_BF16) b += KMp * 2;
-    if (g->d_tc_bop || g->d_tc3_bop) b += (size_t)g->n_records * 4;   // tensor-core adjoint contributions
+    if (g->d_tb4_bop) b += (size_t)g->n_records * 4;   // tensor-core adjoint contributions
     return b;
 }
 
@@ -667,7 +607,7 @@ struct mbir_engine {
     size_t smem_bwd = 0, smem_fwd = 0;
     // dynamic shared memory of the tensor-core kernels as captured: the largest layout among the
     // admitted requests, not the 227 KB maximum, so that the rest of each SM's 256 KB stays L1
-    size_t smem_tc[4] = {0, 0, 0, 0};    // bwd BF16, bwd FP32, fwd BF16, fwd FP32
+    size_t smem_tc[2] = {0, 0};          // tensor-core A x, A^T
     // host mirrors
     std::vector<ReqDesc> h_desc;
 };
@@ -737,7 +677,7 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     AL(r->sc, (size_t)S_COUNT);
     AL(r->part, (size_t)4 * r->nblk + P.K + 8);
     if (P.precision == MBIR_PREC_BF16) AL(r->ebf, KMp);
-    if (g->d_tc_bop || g->d_tc3_bop) AL(r->contrib, (size_t)g->n_records);
+    if (g->d_tb4_bop) AL(r->contrib, (size_t)g->n_records);
 #undef AL
     if (e != cudaSuccess) { free_request_state(r, st); return e == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA; }
     r->msq_host.resize(P.H);
@@ -801,13 +741,7 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.nwin = (int)g->n_win;
     d.sub = g->fwd_sub;
     d.nblk = r->nblk;
-    d.tc = g->d_tc_bop ? 1 : 0;
-    d.tc32 = g->d_tc3_bop ? 1 : 0;
-    d.tc3l = g->tc3;
-    d.tc3_bop = g->d_tc3_bop;
-    d.tc3_prange = g->d_tc3_prange;
-    d.tcl = g->tc;
-    d.tc_bop = g->d_tc_bop;
+    d.tc = g->d_tb4_bop ? 1 : 0;
     d.tc_tile = g->d_tc_tile;
     d.tc_dest = g->d_tc_dest;
     d.tc_pixoff = g->d_tc_pixoff;
@@ -937,20 +871,14 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 }
 
 // One MAP iteration of every active request, as launched inside the graph.
-cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, bool tcb, cudaStream_t st)
+cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cudaStream_t st)
 {
     const int G = E->n_sm, SG = E->n_sm * 8;
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
     if (e != cudaSuccess) return e;
-    if (tc && tcb) {
-        if (bf16) eng_bwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[3], st>>>(E->L);
-        else eng_bwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[3], st>>>(E->L);
-        eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
-    } else if (tc && bf16) {
-        eng_bwd_tc_kernel<<<G, kTcThreads, E->smem_tc[0], st>>>(E->L);
-        eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
-    } else if (tc) {
-        eng_bwd_tc32_kernel<<<G, kTcThreads, E->smem_tc[1], st>>>(E->L);
+    if (tc) {
+        if (bf16) eng_bwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[1], st>>>(E->L);
+        else eng_bwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[1], st>>>(E->L);
         eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
     } else {
         if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
@@ -960,8 +888,8 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, bool
     eng_grad_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     eng_findir_kernel<<<G, kRedThreads, 0, st>>>(E->L);
     eng_dir_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
-    if (tcf && bf16) eng_fwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[2], st>>>(E->L);
-    else if (tcf) eng_fwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[2], st>>>(E->L);
+    if (tcf && bf16) eng_fwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[0], st>>>(E->L);
+    else if (tcf) eng_fwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[0], st>>>(E->L);
     else if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     else eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     eng_proj_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
@@ -989,8 +917,6 @@ int mbir_engine_create(size_t budget_bytes, int max_active, mbir_engine** out)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_bwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E->smem_fwd);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_fwd_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eng_bwd_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEngSmem);
@@ -1099,34 +1025,30 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;
     const bool bf16 = E->sel[0]->g->P.precision == MBIR_PREC_BF16;
-    bool tc = true;                      // tensor-core pools when every request of the step has them
+    bool tc = true;                      // tensor-core A^T when every request of the step has its tables
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
-    bool tcf = true;                     // tensor-core A x when every request has its tables
-    bool tcb = true;                     // streamed tensor-core A^T likewise
+    bool tcf = true;                     // tensor-core A x likewise
     for (Request* r : E->sel) {
         if (!r->contrib) tc = false;
         if (!r->g->d_tf4_bop) tcf = false;
-        if (!r->g->d_tb4_bop) tcb = false;
     }
-    const int gtc = (int)tc + 2 * (int)tcf + 4 * (int)tcb;
-    size_t smem_tc[4] = {1024, 1024, 1024, 1024};
+    const int gtc = (int)tc + 2 * (int)tcf;
+    size_t smem_tc[2] = {1024, 1024};
     for (Request* r : E->active) {
         const mbir_geometry* g = r->g;
-        if (g->d_tc_bop) smem_tc[0] = std::max(smem_tc[0], g->tc.smem);
-        if (g->d_tc3_bop) smem_tc[1] = std::max(smem_tc[1], g->tc3.smem);
-        if (g->d_tf4_bop) smem_tc[2] = std::max(smem_tc[2], g->tf4.smem);
-        if (g->d_tb4_bop) smem_tc[3] = std::max(smem_tc[3], g->tb4.smem);
+        if (g->d_tf4_bop) smem_tc[0] = std::max(smem_tc[0], g->tf4.smem);
+        if (g->d_tb4_bop) smem_tc[1] = std::max(smem_tc[1], g->tb4.smem);
     }
-    const bool smem_changed = !std::equal(smem_tc, smem_tc + 4, E->smem_tc);
+    const bool smem_changed = !std::equal(smem_tc, smem_tc + 2, E->smem_tc);
     if (grew || smem_changed || !E->graph || E->graph_bf16 != (int)bf16 || E->graph_tc != gtc) {
-        std::copy(smem_tc, smem_tc + 4, E->smem_tc);
+        std::copy(smem_tc, smem_tc + 2, E->smem_tc);
         if (E->graph) { cudaGraphExecDestroy(E->graph); E->graph = nullptr; }
         cudaStream_t cs;
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         cudaGraph_t graph;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, tcf, tcb, cs);
+        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, tcf, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&E->graph, graph, 0);

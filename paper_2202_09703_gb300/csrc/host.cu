@@ -173,9 +173,9 @@ void free_geometry(mbir_geometry* g)
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
                     g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
                     g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_win_order, g->d_win_counter,
-                    g->d_bwd_counter, g->d_tc_bop, g->d_tc_tile, g->d_tc_pixoff, g->d_tc_dest, g->w_tc_contrib,
-                    g->d_tc_counter, g->d_tf_n0off, g->d_tf_order, g->d_tf_counter, g->d_tc3_bop, g->w_colnorm,
-                    g->d_tc3_prange, g->d_tf4_bop, g->d_tf4_crange, g->d_tf4_split, g->d_tb4_bop};
+                    g->d_bwd_counter, g->d_tc_tile, g->d_tc_pixoff, g->d_tc_dest, g->w_tc_contrib,
+                    g->d_tc_counter, g->d_tf_n0off, g->d_tf_order, g->d_tf_counter, g->w_colnorm,
+                    g->d_tf4_bop, g->d_tf4_crange, g->d_tf4_split, g->d_tb4_bop};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::free_icd_lists(g);
     if (g->icd_stream) cudaStreamDestroy((cudaStream_t)g->icd_stream);
@@ -542,7 +542,10 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
             if (ce == cudaErrorNotSupported) ce = cudaSuccess;  // keep the CUDA-core A x
             if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
             ce = mbir::build_tc_adjoint_stream(g, st);
-            if (ce == cudaErrorNotSupported) ce = cudaSuccess;  // keep the per-half tensor-core A^T
+            if (ce == cudaErrorNotSupported) {                  // keep the CUDA-core A^T
+                mbir::free_tc_adjoint(g);
+                ce = cudaSuccess;
+            }
             if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
         }
         // the CUDA-core A x's window is tuned only when that kernel is the geometry's A x
@@ -590,7 +593,7 @@ int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info)
     info->forward_window_spans = g->d_rec_key ? g->fwd_sub : 0;
     for (int c = 0; c < 3; ++c) info->forward_window_ms[c] = g->fwd_tune_ms[c];
     info->adjoint_groups = g->n_groups;
-    info->adjoint_tensor_cores = (g->d_tb4_bop || g->d_tc_bop || g->d_tc3_bop) ? 1 : 0;
+    info->adjoint_tensor_cores = g->d_tb4_bop ? 1 : 0;
     info->forward_tensor_cores = g->d_tf4_bop ? 1 : 0;
     return MBIR_OK;
 }

@@ -308,33 +308,6 @@ struct GeomDev;
 }  // namespace mbir
 
 // The geometry handle (opaque in the C ABI).
-// Shared-memory and tensor-memory layout of the tensor-core adjoint (BF16 form).
-struct TcLayout {
-    int kpad;              // taps rounded up to the MMA K step (16)
-    int ncols, npad;       // table rows G (Q + 1), rounded up to 16
-    int nchunk0, nchunk1;  // MMA N of the two column chunks
-    int cstride;           // row stride of the shared correlation tile (floats)
-    size_t off_h, off_b, off_e, off_c, smem;
-    bool ok;
-};
-
-// Layout of the FP32 tensor-core adjoint: the residual window and the table
-// are each scaled by a power of two and split into two FP16 parts; table rows
-// are taken in two phase-aligned halves (phases [0, phsplit] and [phsplit, Q])
-// whose operands both stay resident, with one half's correlation tile at a time.
-struct Tc3Layout {
-    int kpad;              // taps rounded up to 16
-    int phsplit;           // phase where the halves meet (shared by both)
-    int pstride;           // phases per plane in a half's rows: row = plane * pstride + phase offset
-    int nrows[2];          // table rows of each half (multiples of 16)
-    int nmax;              // larger of the two
-    int cstride;           // row stride of the shared correlation tile (floats)
-    size_t bhalf[2];       // bytes of each half's two-part FP16 operand image (both resident)
-    int texp;              // table scale: operand = table x 2^texp (largest magnitude in [2^14, 2^15))
-    size_t off_h, off_b, off_e, off_c, smem;
-    bool ok;
-};
-
 // Layout of the tensor-core A x (tc_stream.cuh): the table operand resident in shared memory, an FP32 sum
 // tile of kwmax columns, the output row; the sums go to tensor memory as the MMA's A operand.
 struct Tf4Layout {
@@ -426,18 +399,12 @@ struct mbir_geometry {
     int* h_win_cost;       // host copy: records per window (K x windows), for work partitioning
     float* h_tvert;        // host copy: vertical two-way time per image row (samples)
     int* d_win_counter;    // work counter of the A x launch
-    // tensor-core adjoint of the BF16 form (see tc_adjoint.cu)
-    TcLayout tc;
-    uint4* d_tc_bop;       // table operand image (rows x taps, K-major)
+    // tensor-core A^T (see tc_adjoint.cu, tc_stream.cuh)
     int* d_tc_tile;        // first record of every 128-sample tile, K x (tiles + 1)
     long long* d_tc_pixoff;// pixel-major record offsets, N + 1
     uint32_t* d_tc_dest;   // record's place in pixel-major order (A-scan order within a pixel)
     float* w_tc_contrib;   // one contribution per record, pixel-major
     int* d_tc_counter;
-    Tc3Layout tc3;
-    uint4* d_tc3_bop;      // FP32 adjoint: both halves' two-part FP16 table operand images
-    uint2* d_tc3_prange;   // tensor-core adjoints: per (A-scan, tile) and row half (FP32 form; the BF16 form
-                           // uses .x for the whole tile), lowest | highest plane << 16
     // tensor-core A x (see tc_stream.cuh, tc_fwd_stream.cu)
     int* d_tf_n0off;       // first record of every sample n0, K x (M + 1)
     int* d_tf_order;       // A-scans by decreasing record count
@@ -510,11 +477,8 @@ cudaError_t load_backproject_partials(const mbir_geometry* g);
 cudaError_t load_pad_rows();
 cudaError_t noalloc_prepare(const mbir_geometry* g);
 size_t forward_smem(const mbir_geometry* g, int* cb_out);
-TcLayout tc_layout(const GeomParams& P);
-Tc3Layout tc3_layout(const GeomParams& P);
 cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st);
-cudaError_t launch_backproject_tc(const mbir_geometry* g, const __nv_bfloat16* e_bf, float* b, cudaStream_t st);
-cudaError_t launch_backproject_tc32(const mbir_geometry* g, const float* e_pad, float* b, cudaStream_t st);
+void free_tc_adjoint(mbir_geometry* g);
 Tf4Layout tf4_layout(const GeomParams& P, int kwmax);
 cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st);
 Tb4Layout tb4_layout(const GeomParams& P, int kwmax);
