@@ -86,6 +86,22 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         : "memory");
 }
 
+// Prefetch [p, p + bytes) of global memory into L2 (bulk, fire and forget): the start is rounded down and
+// the end down to 16-byte bounds (the range never leaves the caller's array, whose allocation starts on a
+// 256-byte bound), cut into 32 KB pieces, piece i issued by lane i of the calling warp (pieces past 32 are
+// dropped).
+__device__ __forceinline__ void prefetch_l2_range(const void* p, size_t bytes, int lane)
+{
+    if (bytes == 0) return;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
+    const uintptr_t z = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
+    const uintptr_t q = a + (uintptr_t)lane * 32768;
+    if (q < z) {
+        const uint32_t n = (uint32_t)((z - q) < 32768 ? (z - q) : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
+    }
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;

@@ -95,8 +95,8 @@ struct ReqDesc {
     int tc;
     const int* tc_tile;
     const uint32_t* tc_dest;
-    const long long* tc_pixoff;
-    float* tc_contrib;     // this request's contributions (pixel-major)
+    const int* tc_goff;
+    float* tc_contrib;     // this request's contributions (per transmitter group, pixel-major)
     // tensor-core A^T and A x of tc_stream.cuh (tcb, tcs != 0)
     int tcb;
     Tb4Layout tb4l;
@@ -418,30 +418,19 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
     tc_header_release(smem, tmem, kTsCols);
 }
 
-// b = each pixel's contributions summed in A-scan order (the single-request
-// reduction's arithmetic: warp per pixel, lane-strided Neumaier, fixed tree).
-// Warps stride over every (pixel block, pixel) slot of the step, so a step of
-// small requests still spreads one pixel per warp over the whole grid.
+// b = each pixel's contributions summed over every active request, with the single-request reduction
+// (tcs_reduce_pixels: 32 pixels per warp, one per lane); warps stride over every (pixel block, 32-pixel
+// chunk) slot of the step.
 __global__ void eng_bwd_tc_reduce_kernel(EngLists L)
 {
-    const long long nt = (long long)L.counts[1] * kRedThreads;
-    const int lane = threadIdx.x & 31;
+    constexpr int kChunks = kRedThreads / 32;
+    const long long nt = (long long)L.counts[1] * kChunks;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += nw) {
-        const int2 rb = L.pixblk[t / kRedThreads];
+        const int2 rb = L.pixblk[t / kChunks];
         const ReqDesc& R = L.desc[rb.x];
-        const int v = rb.y * kRedThreads + (int)(t % kRedThreads);
-        if (v >= R.P.W * R.P.H) continue;
-        const long long* pix_off = R.tc_pixoff;
-        const float* contrib = R.tc_contrib;
-        float* b = R.b;
-        const long long a = pix_off[v], z = pix_off[v + 1];
-        float s = 0.0f, c = 0.0f;
-        for (long long j = a + lane; j < z; j += 32) neumaier_add(s, c, contrib[j]);
-        s += c;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) b[v] = s;
+        const int v0 = rb.y * kRedThreads + (int)(t % kChunks) * 32;
+        tcs_reduce_pixels(v0, R.P.W * R.P.H, R.P.n_tx, R.P.n_rx, R.rec_off, R.tc_goff, R.tc_contrib, R.b);
     }
 }
 
@@ -744,7 +733,7 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.tc = g->d_tb4_bop ? 1 : 0;
     d.tc_tile = g->d_tc_tile;
     d.tc_dest = g->d_tc_dest;
-    d.tc_pixoff = g->d_tc_pixoff;
+    d.tc_goff = g->d_tc_goff;
     d.tc_contrib = r->contrib;
     d.tcb = g->d_tb4_bop ? 1 : 0;
     d.tb4l = g->tb4;

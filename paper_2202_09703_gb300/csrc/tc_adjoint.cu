@@ -1,8 +1,11 @@
 // Tables of the tensor-core A^T (tcs_adjoint_pool, tc_stream.cuh): the first
-// record of every tile, each record's slot in pixel-major order, the
-// per-pixel reduction of the record contributions, the table operand and the
-// launch.  A pixel has at most one record per A-scan; its contributions are
-// summed in A-scan order by one warp, so the result is reproducible.
+// record of every tile, each record's slot for its contribution, the
+// per-pixel reduction of the contributions, the table operand and the launch.
+// Slots are grouped by transmitter position (the n_rx A-scans of one position
+// are consecutive) and pixel-major inside a group, A-scans in order: the
+// contributions of one group, written close together in time, fill whole
+// sectors before they leave L2, and a pixel's contributions are summed group
+// after group in A-scan order, so the result is reproducible.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -11,42 +14,67 @@
 
 namespace mbir {
 
-// b_v = sum of pixel v's contributions in A-scan order: one warp per pixel,
-// lanes sum strided subsets (Neumaier), combined by a fixed shuffle tree.
-__global__ void bwd_tc_reduce_kernel(int N, const long long* __restrict__ pix_off, const float* __restrict__ contrib,
+// b = each pixel's contributions summed (tcs_reduce_pixels), one pixel per lane.
+__global__ void bwd_tc_reduce_kernel(int N, int n_tx, int n_rx, const long long* __restrict__ rec_off,
+                                     const int* __restrict__ goff, const float* __restrict__ contrib,
                                      float* __restrict__ b)
 {
-    const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int v = w0; v < N; v += nw) {
-        const long long a = __ldg(pix_off + v), z = __ldg(pix_off + v + 1);
-        float s = 0.0f, c = 0.0f;
-        for (long long j = a + lane; j < z; j += 32) neumaier_add(s, c, __ldg(contrib + j));
-        s += c;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) b[v] = s;
-    }
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < N; w += nw)
+        tcs_reduce_pixels(w * 32, N, n_tx, n_rx, rec_off, goff, contrib, b);
 }
 
-// per-pixel record counts (integer atomics: order-independent)
-__global__ void tc_pix_count_kernel(long long nrec, const int2* __restrict__ rkey, int* __restrict__ cnt)
+// cnt[v] += 1 for the records [a, z) of one A-scan (a pixel has at most one record per A-scan)
+__global__ void tc_gcount_kernel(long long a, long long z, const int2* __restrict__ rkey, int* __restrict__ cnt)
 {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrec; r += (long long)gridDim.x * blockDim.x)
-        atomicAdd(cnt + rkey[r].x, 1);
+    const long long r = a + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (r < z) cnt[rkey[r].x] += 1;
 }
 
-// place of each record of A-scan k in pixel-major order (A-scans one after
-// the other: a pixel has at most one record per A-scan, so no collisions)
-__global__ void tc_dest_kernel(long long a, long long z, const int2* __restrict__ rkey,
-                               const long long* __restrict__ pix_off, int* __restrict__ cursor,
-                               uint32_t* __restrict__ dest)
+// off[v] = cnt[0] + ... + cnt[v - 1] for v = 0 .. N (one block): chunks of consecutive pixels per thread, the
+// chunk sums scanned across the block
+__global__ void tc_gscan_kernel(const int* __restrict__ cnt, int N, int* __restrict__ off)
+{
+    __shared__ int ws[32];
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int chunk = (N + nt - 1) / nt, v0 = min(tid * chunk, N), v1 = min(v0 + chunk, N);
+    int sum = 0;
+    for (int v = v0; v < v1; ++v) sum += cnt[v];
+    // exclusive scan of the chunk sums: warp inclusive scan, then the warps' totals
+    int inc = sum;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, d);
+        if ((tid & 31) >= d) inc += t;
+    }
+    if ((tid & 31) == 31) ws[tid >> 5] = inc;
+    __syncthreads();
+    if (tid < 32) {
+        int x = tid < (nt >> 5) ? ws[tid] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, d);
+            if (tid >= d) x += t;
+        }
+        ws[tid] = x;
+    }
+    __syncthreads();
+    int run = inc - sum + ((tid >> 5) > 0 ? ws[(tid >> 5) - 1] : 0);
+    for (int v = v0; v < v1; ++v) {
+        off[v] = run;
+        run += cnt[v];
+    }
+    if (tid == nt - 1) off[N] = run;
+}
+
+// slot of each record of one A-scan of group g: the group's pixel-major offset of its pixel plus the
+// pixel's records already placed in the group (A-scans in order)
+__global__ void tc_gdest_kernel(long long a, long long z, long long gbase, const int2* __restrict__ rkey,
+                                const int* __restrict__ off, int* __restrict__ cursor, uint32_t* __restrict__ dest)
 {
     const long long r = a + blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r < z) {
         const int v = rkey[r].x;
         const int c = cursor[v];
-        dest[r] = (uint32_t)(pix_off[v] + c);
+        dest[r] = (uint32_t)(gbase + off[v] + c);
         cursor[v] = c + 1;
     }
 }
@@ -79,58 +107,63 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
     int* d_cnt = nullptr;
     int* d_tile = nullptr;
-    long long* d_poff = nullptr;
+    int* d_goff = nullptr;
     uint32_t* d_dest = nullptr;
     float* d_contrib = nullptr;
     int* d_ctr = nullptr;
+    const size_t gstride = (size_t)N + 1;
     cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int) * (size_t)N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_tile, sizeof(int) * (size_t)P.K * (ntile + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_poff, sizeof(long long) * ((size_t)N + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_goff, sizeof(int) * gstride * P.n_tx);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_dest, sizeof(uint32_t) * (size_t)g->n_records);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_contrib, sizeof(float) * (size_t)g->n_records);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctr, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)N, st);
     if (e == cudaSuccess) {
-        const long long nrec = g->n_records;
-        tc_pix_count_kernel<<<(int)std::min<long long>((nrec + 255) / 256, 152LL * 64), 256, 0, st>>>(nrec, g->d_rec_key,
-                                                                                                      d_cnt);
         const long long items = (long long)P.K * (ntile + 1);
         tc_tile_off_kernel<<<(int)((items + 255) / 256), 256, 0, st>>>(P, ntile, g->d_rec_off, g->d_rec_key, d_tile);
         e = cudaGetLastError();
     }
-    std::vector<int> cnt(N);
-    std::vector<long long> poff((size_t)N + 1, 0), roff((size_t)P.K + 1);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, st);
+    std::vector<long long> roff((size_t)P.K + 1);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(roff.data(), g->d_rec_off, sizeof(long long) * (P.K + 1), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) {
-        for (int v = 0; v < N; ++v) poff[v + 1] = poff[v] + cnt[v];
-        e = cudaMemcpy(d_poff, poff.data(), sizeof(long long) * ((size_t)N + 1), cudaMemcpyHostToDevice);
-    }
-    // destinations: A-scans one after the other, a cursor per pixel
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)N, st);
-    for (int k = 0; k < P.K && e == cudaSuccess; ++k) {
-        const long long a = roff[k], z = roff[k + 1];
-        if (z > a) {
-            tc_dest_kernel<<<(int)((z - a + 255) / 256), 256, 0, st>>>(a, z, g->d_rec_key, d_poff, d_cnt, d_dest);
+    // per transmitter position: pixel counts, their offsets, then the slots with a cursor per pixel
+    for (int gi = 0; gi < P.n_tx && e == cudaSuccess; ++gi) {
+        int* off = d_goff + gstride * gi;
+        const int k0 = gi * P.n_rx, k1 = k0 + P.n_rx;
+        e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)N, st);
+        for (int k = k0; k < k1 && e == cudaSuccess; ++k)
+            if (roff[k + 1] > roff[k]) {
+                tc_gcount_kernel<<<(int)((roff[k + 1] - roff[k] + 255) / 256), 256, 0, st>>>(roff[k], roff[k + 1],
+                                                                                            g->d_rec_key, d_cnt);
+                e = cudaGetLastError();
+            }
+        if (e == cudaSuccess) {
+            tc_gscan_kernel<<<1, 1024, 0, st>>>(d_cnt, N, off);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)N, st);
+        for (int k = k0; k < k1 && e == cudaSuccess; ++k)
+            if (roff[k + 1] > roff[k]) {
+                tc_gdest_kernel<<<(int)((roff[k + 1] - roff[k] + 255) / 256), 256, 0, st>>>(
+                    roff[k], roff[k + 1], roff[k0], g->d_rec_key, off, d_cnt, d_dest);
+                e = cudaGetLastError();
+            }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_cnt);
     if (e != cudaSuccess) {
-        void* ptrs[] = {d_tile, d_poff, d_dest, d_contrib, d_ctr};
+        void* ptrs[] = {d_tile, d_goff, d_dest, d_contrib, d_ctr};
         for (void* p : ptrs) cudaFree(p);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
     g->d_tc_tile = d_tile;
-    g->d_tc_pixoff = d_poff;
+    g->d_tc_goff = d_goff;
     g->d_tc_dest = d_dest;
     g->w_tc_contrib = d_contrib;
     g->d_tc_counter = d_ctr;
-    g->bytes += sizeof(int) * ((size_t)P.K * (ntile + 1) + 1) + sizeof(long long) * ((size_t)N + 1) +
+    g->bytes += sizeof(int) * ((size_t)P.K * (ntile + 1) + 1 + gstride * P.n_tx) +
                 (sizeof(uint32_t) + sizeof(float)) * (size_t)g->n_records;
     return cudaSuccess;
 }
@@ -138,11 +171,11 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
 // The tables above, freed when the tensor-core A^T is not used after all.
 void free_tc_adjoint(mbir_geometry* g)
 {
-    void* ptrs[] = {g->d_tc_tile, g->d_tc_pixoff, g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
+    void* ptrs[] = {g->d_tc_tile, g->d_tc_goff, g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     g->d_tc_tile = nullptr;
-    g->d_tc_pixoff = nullptr;
+    g->d_tc_goff = nullptr;
     g->d_tc_dest = nullptr;
     g->w_tc_contrib = nullptr;
     g->d_tc_counter = nullptr;
@@ -262,8 +295,8 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
     const int N = P.W * P.H;
-    bwd_tc_reduce_kernel<<<std::max(1, std::min((N + 7) / 8, 152 * 16)), 256, 0, st>>>(N, g->d_tc_pixoff,
-                                                                                     g->w_tc_contrib, b);
+    bwd_tc_reduce_kernel<<<std::max(1, std::min((N + 255) / 256, g->n_sm * 16)), 256, 0, st>>>(
+        N, P.n_tx, P.n_rx, g->d_rec_off, g->d_tc_goff, g->w_tc_contrib, b);
     return cudaGetLastError();
 }
 

@@ -207,6 +207,12 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
         for (int t = 0; t < ntile; ++t) {
             const int ts = t * kTsTile;
             const bool live = tsp[t * kTsSplit + kTsWarps] > tsp[t * kTsSplit];
+            if (t + 1 < ntile) {
+                // this warp's part of the next tile into L2 while this tile is scattered
+                const int pa = tsp[(t + 1) * kTsSplit + warp], pz = tsp[(t + 1) * kTsSplit + warp + 1];
+                prefetch_l2_range(rkey + base + pa, (size_t)(pz - pa) * sizeof(int2), lane);
+                prefetch_l2_range(rw + base + pa, (size_t)(pz - pa) * sizeof(float4), lane);
+            }
             if (live) {
                 // ---- scatter: batches b = 0 .. nb-1, slot b & 3, x one batch ahead
                 float* Sb = sS - (int)(tcr[t] & 0xffffu);
@@ -375,8 +381,8 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
 // records reach (one column range, the B operand resident in shared memory);
 // each record then combines four values of C with its bilinear weights (less
 // the tau = t0 tap of flagged records) and writes one contribution to its slot
-// in pixel-major order; a reduction kernel sums each pixel's contributions in
-// A-scan order.  FP32 form: the window scaled by the power of two that brings
+// (grouped by transmitter position, pixel-major inside a group); a reduction
+// kernel sums each pixel's contributions in A-scan order.  FP32 form: the window scaled by the power of two that brings
 // its largest magnitude into [2^14, 2^15) and split into two FP16 parts, the
 // table likewise: three products.  BF16 form: the stored BF16 residual and
 // table, one product.  The products of the next item run while the current
@@ -392,7 +398,7 @@ struct TbView {
     const uint32_t* crange;      // per (A-scan, tile): c_lo | c_hi << 16
     const int2* rkey;
     const float4* rw;
-    const uint32_t* dest;        // record -> slot in pixel-major order
+    const uint32_t* dest;        // record -> slot (group of its transmitter position, then pixel)
     float* contrib;
     int* counter;
 };
@@ -503,8 +509,9 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         }
         tmem_wait_st();
     };
+    auto crange_of = [&](int item) -> uint32_t { return __ldg(V.crange + item); };
     auto issue_mma = [&](int item) {
-        const uint32_t cr = __ldg(V.crange + item);
+        const uint32_t cr = crange_of(item);
         const int c_lo = (int)(cr & 0xffffu), kw = (int)(cr >> 16) - c_lo;
         tc_fence_after();
         const uint32_t idesc = BF16 ? umma_idesc_bf16(kTsTile, kw) : umma_idesc_f16(kTsTile, kw);
@@ -527,7 +534,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
     __syncthreads();
     if (tid == 0) *next = atomicAdd(V.counter, 1);
     int cse = window_exponent();
-    uint32_t live_cur = __ldg(V.crange + cur);           // a tile without records has an empty range
+    uint32_t live_cur = crange_of(cur);                  // a tile without records has an empty range
     if (live_cur) convert_h(sE0, cse);
     tc_fence_before();
     __syncthreads();
@@ -569,7 +576,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         uint32_t live_nxt = 0;
         if (nxt < nitems) {
             nse = window_exponent();
-            live_nxt = __ldg(V.crange + nxt);
+            live_nxt = crange_of(nxt);
             if (live_nxt) convert_h(sEn, nse);
         }
         tc_fence_before();
@@ -623,6 +630,25 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         live_cur = live_nxt;
     }
     return !*abort_flag;
+}
+
+// b[v] for the pixels v0 .. v0 + 31 (lane = pixel) of one geometry: the pixel's contributions group after
+// group (transmitter positions in order; group g's slots start at the first record of its first A-scan and
+// are pixel-major, goff[g (N + 1) + v] the pixel's offset), A-scans in order within a group, Neumaier sums.
+__device__ __forceinline__ void tcs_reduce_pixels(int v0, int N, int n_tx, int n_rx, const long long* __restrict__ rec_off,
+                                                  const int* __restrict__ goff, const float* __restrict__ contrib,
+                                                  float* __restrict__ b)
+{
+    const int v = v0 + (threadIdx.x & 31);
+    if (v >= N) return;
+    float s = 0.0f, c = 0.0f;
+    for (int g = 0; g < n_tx; ++g) {
+        const int* o = goff + (size_t)g * ((size_t)N + 1);
+        const long long gb = __ldg(rec_off + (size_t)g * n_rx);
+        const int a = __ldg(o + v), z = __ldg(o + v + 1);
+        for (int j = a; j < z; ++j) neumaier_add(s, c, __ldg(contrib + gb + j));
+    }
+    b[v] = s + c;
 }
 
 }  // namespace mbir
