@@ -174,7 +174,7 @@ void free_geometry(mbir_geometry* g)
                     g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
                     g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_win_order, g->d_win_counter,
                     g->d_bwd_counter, g->d_tc_tile, g->d_tc_goff, g->d_tc_dest, g->w_tc_contrib,
-                    g->d_tc_counter, g->d_tf_n0off, g->d_tf_order, g->d_tf_counter, g->w_colnorm,
+                    g->d_tc_counter, g->d_tf_order, g->d_tf_counter, g->w_colnorm,
                     g->d_tf4_bop, g->d_tf4_crange, g->d_tf4_split, g->d_tb4_bop};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::free_icd_lists(g);
@@ -535,11 +535,12 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
         if (ce == cudaErrorNotSupported) ce = cudaSuccess;     // keep the on-the-fly record path
         if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
         if (g->d_rec_key && !(d->flags & MBIR_FLAG_NO_TENSOR_CORES)) {
-            ce = mbir::build_tc_adjoint(g, st);
-            if (ce == cudaErrorNotSupported) ce = cudaSuccess;  // keep the CUDA-core adjoint
-            if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
+            // A x first: it leaves the records in its kernel's order, on which the adjoint's slots are built
             ce = mbir::build_tc_forward_stream(g, st);
             if (ce == cudaErrorNotSupported) ce = cudaSuccess;  // keep the CUDA-core A x
+            if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
+            ce = mbir::build_tc_adjoint(g, st);
+            if (ce == cudaErrorNotSupported) ce = cudaSuccess;  // keep the CUDA-core adjoint
             if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
             ce = mbir::build_tc_adjoint_stream(g, st);
             if (ce == cudaErrorNotSupported) {                  // keep the CUDA-core A^T

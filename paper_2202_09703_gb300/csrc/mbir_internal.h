@@ -406,7 +406,6 @@ struct mbir_geometry {
     float* w_tc_contrib;   // one contribution per record, pixel-major
     int* d_tc_counter;
     // tensor-core A x (see tc_stream.cuh, tc_fwd_stream.cu)
-    int* d_tf_n0off;       // first record of every sample n0, K x (M + 1)
     int* d_tf_order;       // A-scans by decreasing record count
     int* d_tf_counter;
     Tf4Layout tf4;

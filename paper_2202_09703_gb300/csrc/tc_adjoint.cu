@@ -97,8 +97,8 @@ __global__ void tc_tile_off_kernel(GeomParams P, int ntile, const long long* __r
     tile_off[i] = lo;
 }
 
-// First record of every tile, each record's slot in pixel-major order (A-scans one after the other) and
-// the contribution buffer of the tensor-core A^T; cudaErrorNotSupported keeps the CUDA-core adjoint.
+// First record of every tile, each record's slot (per transmitter position, pixel-major, A-scans in order)
+// and the contribution buffer of the tensor-core A^T; cudaErrorNotSupported keeps the CUDA-core adjoint.
 cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
 {
     const GeomParams& P = g->P;

@@ -117,8 +117,74 @@ __global__ void ts_tiles_kernel(GeomParams P, int R, int kb, const long long* __
     }
 }
 
-// Tables of the tensor-core A x for a geometry with records: the n0 offsets, the A-scan order, the per-tile
-// column ranges and warp parts, and the table operand (FP32 form: two FP16 parts of the table scaled by
+// The records of every warp part interleaved: batch b (stored positions 32 b .. 32 b + 31 of the part) takes
+// the part's sorted records b, b + q, b + 2 q, ... (q = its length / 32; the first length % 32 lanes hold
+// one more), so records of one (n0, table row), adjacent in sorted order, seldom share a batch, and where
+// they do they sit in adjacent lanes as the segmented sums require.  The sorted records of A-scans
+// k0 .. k0 + gridDim.x / ntile - 1 come from a copy whose first record is record src0.
+__global__ void ts_interleave_kernel(GeomParams P, int k0, const long long* __restrict__ rec_off,
+                                     const int* __restrict__ split, long long src0, const int2* __restrict__ tkey,
+                                     const float4* __restrict__ tw, int2* __restrict__ key, float4* __restrict__ w)
+{
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    const int k = k0 + (int)(blockIdx.x / ntile), t = (int)(blockIdx.x % ntile);
+    const int* sp = split + ((size_t)k * ntile + t) * kTsSplit;
+    const long long base = rec_off[k];
+    for (int p = 0; p < kTsWarps; ++p) {
+        const int a = sp[p], len = sp[p + 1] - a;
+        const int q = len >> 5, r = len & 31;
+        for (int s = threadIdx.x; s < len; s += blockDim.x) {
+            const int l = s & 31, o = l * q + min(l, r) + (s >> 5);
+            key[base + a + s] = tkey[base + a + o - src0];
+            w[base + a + s] = tw[base + a + o - src0];
+        }
+    }
+}
+
+// Interleaves the records of every warp part (ts_interleave_kernel) through a temporary copy of up to about
+// 256 MB of A-scans at a time; without room for the copy the records keep their sorted order, which the
+// kernel takes as well.
+static cudaError_t interleave_records(mbir_geometry* g, const std::vector<long long>& roff, const int* d_sp,
+                                      cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    long long cap = ((long long)256 << 20) / (long long)(sizeof(int2) + sizeof(float4));
+    for (int k = 0; k < P.K; ++k) cap = std::max(cap, roff[k + 1] - roff[k]);
+    cap = std::min(cap, g->n_records);
+    int2* tkey = nullptr;
+    float4* tw = nullptr;
+    if (cudaMalloc((void**)&tkey, sizeof(int2) * (size_t)cap) != cudaSuccess ||
+        cudaMalloc((void**)&tw, sizeof(float4) * (size_t)cap) != cudaSuccess) {
+        cudaFree(tkey);
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int k0 = 0; k0 < P.K && e == cudaSuccess;) {
+        int k1 = k0 + 1;
+        while (k1 < P.K && roff[k1 + 1] - roff[k0] <= cap) ++k1;
+        const size_t n = (size_t)(roff[k1] - roff[k0]);
+        if (n > 0) {
+            e = cudaMemcpyAsync(tkey, g->d_rec_key + roff[k0], sizeof(int2) * n, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(tw, g->d_rec_w + roff[k0], sizeof(float4) * n, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) {
+                ts_interleave_kernel<<<(k1 - k0) * ntile, 256, 0, st>>>(P, k0, g->d_rec_off, d_sp, roff[k0], tkey, tw,
+                                                                        g->d_rec_key, g->d_rec_w);
+                e = cudaGetLastError();
+            }
+        }
+        k0 = k1;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tkey);
+    cudaFree(tw);
+    return e;
+}
+
+// Tables of the tensor-core A x for a geometry with records: the A-scan order, the per-tile column ranges and
+// warp parts (from the first record of every n0), the table operand (FP32 form: two FP16 parts of the table scaled by
 // 2^texp; BF16 form: the BF16 table); cudaErrorNotSupported keeps the CUDA-core A x.
 cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
 {
@@ -201,22 +267,23 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
         e = cudaMalloc((void**)&d_b, L.bbytes);
         if (e == cudaSuccess) e = cudaMemcpy(d_b, img.data(), L.bbytes, cudaMemcpyHostToDevice);
     }
+    // last: from here on the records are in the kernel's order (the CUDA-core A x's span runs no longer hold)
+    if (e == cudaSuccess) e = interleave_records(g, roff, d_sp, st);
     if (e != cudaSuccess) {
         void* ptrs[] = {d_n0, d_ord, d_ctr, d_cr, d_sp, d_b};
         for (void* p : ptrs) cudaFree(p);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
+    cudaFree(d_n0);
     g->tf4 = L;
-    g->d_tf_n0off = d_n0;
     g->d_tf_order = d_ord;
     g->d_tf_counter = d_ctr;
     g->d_tf4_bop = d_b;
     g->d_tf4_crange = d_cr;
     g->d_tf4_split = d_sp;
     g->tf4_wmax = wmax;
-    g->bytes += L.bbytes + sizeof(int) * ((size_t)P.K * (P.M + 1) + P.K + 1) +
-                sizeof(int) * (size_t)P.K * ntile * (kTsSplit + 1);
+    g->bytes += L.bbytes + sizeof(int) * ((size_t)P.K + 1) + sizeof(int) * (size_t)P.K * ntile * (kTsSplit + 1);
     return cudaSuccess;
 }
 
