@@ -117,9 +117,9 @@ typedef struct {
 } mbir_geometry_desc;
 
 /* TAB mode normally also stores every A-scan's active pairs as records
- * sorted by first tap sample, then table row and pixel (the system matrix of
- * Section 3, 24 bytes per active pair) so that A x and A^T stream them; this
- * flag keeps the on-the-fly record path of A x instead (less memory, slower). */
+ * grouped by first tap sample (the system matrix of Section 3, 24 bytes per
+ * active pair) so that A x and A^T stream them; this flag keeps the
+ * on-the-fly record path of A x instead (less memory, slower). */
 #define MBIR_FLAG_NO_RECORDS 1
 
 /* With records, A and A^T normally run on the tensor cores (both storage
@@ -129,10 +129,14 @@ typedef struct {
  *        multiplied by the table on the tensor cores and added along the
  *        product's anti-diagonals;
  *   A^T: the correlation of the residual with the table rows is one matrix
- *        product, and each pair combines four of its values.
+ *        product, and each pair combines four of its values into one
+ *        contribution, which is rounded to a 64-bit fixed-point grid (one
+ *        power-of-two scale per call, from max |e| and bounds of the weights
+ *        and the table) and added to its pixel's integer sum; the exact sum is
+ *        rounded once to FP32 (a non-finite residual gives NaN).
  * FP32 form: operands scaled by powers of two and split into two FP16 parts
  * (three products, FP32 accuracy); BF16 form: the stored BF16 residual and
- * table, the A x sums rounded once to BF16.  FP32 accumulation throughout;
+ * table, the A x sums rounded once to BF16.  FP32 accumulation otherwise;
  * outputs are bitwise reproducible.  This flag keeps the CUDA-core kernels. */
 #define MBIR_FLAG_NO_TENSOR_CORES 2
 

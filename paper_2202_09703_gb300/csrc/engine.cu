@@ -7,8 +7,9 @@
 // so the graph is captured once and replayed as requests come and go
 // (continuous batching):
 //   A^T e   persistent; each request's own work items form a pool drained
-//           through a per-request counter (tensor cores: (A-scan, tile) items
-//           of tcs_adjoint_pool, then the per-pixel reduction; CUDA cores:
+//           through a per-request counter (tensor cores: max |e| per request,
+//           the (A-scan, tile) items of tcs_adjoint_pool into fixed-point
+//           sums, then the sums into b; CUDA cores:
 //           pixel tile x transmitter group, longest first).  A CTA starts at
 //           the request its share of the total cost falls on and walks on
 //           through the others until every pool is empty, loading a request's
@@ -23,7 +24,8 @@
 // The apply kernels run the same per-item and per-span code as the
 // single-request kernels, on the geometry's own work decomposition.
 // Each request's arithmetic depends only on its own data and its own fixed
-// work decomposition, so a result is bitwise the same alone and in any mix.
+// work decomposition (the tensor-core A^T sums are integer, so their order
+// does not matter), so a result is bitwise the same alone and in any mix.
 // Admission is by device memory: a request is admitted when its state fits
 // the engine's byte budget; state is allocated with stream-ordered
 // cudaMallocAsync and released with cudaFreeAsync when the request retires.
@@ -91,12 +93,11 @@ struct ReqDesc {
     int nwin;              // K x windows of `sub` 32-sample spans
     int sub;
     int nblk;              // pixel blocks of kRedThreads
-    // tensor-core A^T tables (tc != 0: the contribution buffer is allocated)
+    // tensor-core A^T tables (tc != 0: the accumulators are allocated)
     int tc;
     const int* tc_tile;
-    const uint32_t* tc_dest;
-    const int* tc_goff;
-    float* tc_contrib;     // this request's contributions (per transmitter group, pixel-major)
+    unsigned long long* tc_acc;   // this request's per-pixel fixed-point sums (zero between steps)
+    float tc_bound;        // the geometry's scale bound of those sums
     // tensor-core A^T and A x of tc_stream.cuh (tcb, tcs != 0)
     int tcb;
     Tb4Layout tb4l;
@@ -112,7 +113,7 @@ struct ReqDesc {
 
 struct EngLists {
     ReqDesc* desc;
-    int* pool;             // per request: next A d span, next A^T e item (zeroed every step)
+    int* pool;             // per request: next A d span, next A^T e item, bits of max |e| (zeroed every step)
     int* start;            // per CTA: first request of A^T e [0, G), of A d [G, 2G)
     int2* pixblk;          // {req, pixel block}
     int2* rowblk;          // {req, A-scan}
@@ -139,7 +140,7 @@ __device__ __forceinline__ void eng_layout(const GeomParams& P, size_t* tab_byte
 // work; the answer is the same for every thread of the CTA.
 __device__ __forceinline__ bool eng_pool_live(const int* pool, int rq, int slot, int total, volatile int* flag)
 {
-    if (threadIdx.x == 0) *flag = *reinterpret_cast<const volatile int*>(pool + 2 * rq + slot) < total;
+    if (threadIdx.x == 0) *flag = *reinterpret_cast<const volatile int*>(pool + 3 * rq + slot) < total;
     __syncthreads();
     const bool live = *flag != 0;
     __syncthreads();
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_bwd_kernel(EngLists L)
         E* ering = reinterpret_cast<E*>(smem + kEngHdr + tab_bytes + (size_t)h * nst * ebytes);
         const E* e_g = BF16 ? (const E*)(const void*)R.ebf : (const E*)(const void*)R.e;
         for (;;) {
-            if (ht == 0) flags[2 + h] = atomicAdd(L.pool + 2 * rq + 1, 1);
+            if (ht == 0) flags[2 + h] = atomicAdd(L.pool + 3 * rq + 1, 1);
             worker_barrier(h);
             const int it = flags[2 + h];
             worker_barrier(h);
@@ -383,9 +384,9 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
             cur = rq;
             __syncthreads();
         }
-        if (R.sub == 1) eng_fwd_pool<BF16, 1>(R, L.pool + 2 * rq, tab, lane, sr, sw);
-        else if (R.sub == 2) eng_fwd_pool<BF16, 2>(R, L.pool + 2 * rq, tab, lane, sr, sw);
-        else eng_fwd_pool<BF16, 4>(R, L.pool + 2 * rq, tab, lane, sr, sw);
+        if (R.sub == 1) eng_fwd_pool<BF16, 1>(R, L.pool + 3 * rq, tab, lane, sr, sw);
+        else if (R.sub == 2) eng_fwd_pool<BF16, 2>(R, L.pool + 3 * rq, tab, lane, sr, sw);
+        else eng_fwd_pool<BF16, 4>(R, L.pool + 3 * rq, tab, lane, sr, sw);
         __syncthreads();                 // every warp is done before the table is replaced
     }
 }
@@ -410,7 +411,8 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
             const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
             const void* e = BF16 ? (const void*)R.ebf : (const void*)R.e;
             const TbView V{R.P, R.tb4l, R.tb4_bop, tab, e, R.rec_off, R.tc_tile, R.tf4_crange, R.rkey, R.rw,
-                           R.tc_dest, R.tc_contrib, L.pool + 2 * rq + 1};
+                           R.tc_acc, reinterpret_cast<const unsigned int*>(L.pool + 3 * rq + 2), R.tc_bound,
+                           L.pool + 3 * rq + 1};
             if (!tcs_adjoint_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
             __syncthreads();
         }
@@ -418,19 +420,41 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
     tc_header_release(smem, tmem, kTsCols);
 }
 
-// b = each pixel's contributions summed over every active request, with the single-request reduction
-// (tcs_reduce_pixels: 32 pixels per warp, one per lane); warps stride over every (pixel block, 32-pixel
-// chunk) slot of the step.
-__global__ void eng_bwd_tc_reduce_kernel(EngLists L)
+// bits of max |e| of every active request (the scale of its fixed-point A^T sums): block per (request,
+// A-scan) row, atomically into the request's pool word
+template <bool BF16>
+__global__ void eng_emax_kernel(EngLists L)
 {
-    constexpr int kChunks = kRedThreads / 32;
-    const long long nt = (long long)L.counts[1] * kChunks;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += nw) {
-        const int2 rb = L.pixblk[t / kChunks];
+    const int nb = L.counts[2];
+    for (int bb = blockIdx.x; bb < nb; bb += gridDim.x) {
+        const int2 rk = L.rowblk[bb];
+        const ReqDesc& R = L.desc[rk.x];
+        const int Mp = R.P.Mp;
+        unsigned int m = 0;
+        for (int n = threadIdx.x; n < Mp; n += blockDim.x) {
+            const float v = BF16 ? __bfloat162float(R.ebf[(size_t)rk.y * Mp + n]) : R.e[(size_t)rk.y * Mp + n];
+            m = max(m, __float_as_uint(fabsf(v)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<unsigned int*>(L.pool + 3 * rk.x + 2), m);
+    }
+}
+
+// b of every active request from its fixed-point sums (tcs_finish_pixel), which are cleared for the next
+// step; block per (request, pixel block)
+__global__ void eng_bwd_tc_finish_kernel(EngLists L)
+{
+    const int nb = L.counts[1];
+    for (int bb = blockIdx.x; bb < nb; bb += gridDim.x) {
+        const int2 rb = L.pixblk[bb];
         const ReqDesc& R = L.desc[rb.x];
-        const int v0 = rb.y * kRedThreads + (int)(t % kChunks) * 32;
-        tcs_reduce_pixels(v0, R.P.W * R.P.H, R.P.n_tx, R.P.n_rx, R.rec_off, R.tc_goff, R.tc_contrib, R.b);
+        const int v = rb.y * kRedThreads + threadIdx.x;
+        if (v < R.P.W * R.P.H) {
+            const unsigned int eb = *reinterpret_cast<const unsigned int*>(L.pool + 3 * rb.x + 2);
+            R.b[v] = tcs_finish_pixel(R.tc_acc[v], eb, R.tc_bound);
+            R.tc_acc[v] = 0ull;
+        }
     }
 }
 
@@ -452,7 +476,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_fwd_tcs_kernel(EngLists L)
             if (!eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
             const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
             const TsView V{R.P, R.tf4l, R.tf4_bop, tab, R.rec_off, R.tf4_crange, R.tf4_split, R.rkey, R.rw,
-                           R.tf_order, dnew_of(R), R.q, 0, R.P.Mp, L.pool + 2 * rq};
+                           R.tf_order, dnew_of(R), R.q, 0, R.P.Mp, L.pool + 3 * rq};
             if (!tcs_forward_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
             __syncthreads();
         }
@@ -556,7 +580,8 @@ struct Request {
     double waited = 0;      // work of the steps that ran while this request was passed over
     double bwd_est = -1, fwd_est = -1;   // the geometry's A^T e and A d cost estimates (summed once)
     float *e = nullptr, *q = nullptr, *b = nullptr, *grad = nullptr, *gprev = nullptr, *d0 = nullptr,
-          *d1 = nullptr, *bpart = nullptr, *msq = nullptr, *contrib = nullptr;
+          *d1 = nullptr, *bpart = nullptr, *msq = nullptr;
+    unsigned long long* acc = nullptr;   // tensor-core A^T: per-pixel fixed-point sums
     __nv_bfloat16* ebf = nullptr;
     double *sc = nullptr, *part = nullptr;
     std::vector<float> msq_host;
@@ -571,7 +596,7 @@ size_t request_bytes(const mbir_geometry* g, int ngroups)
     size_t b = 2 * KMp * 4 + 6 * N * 4 + (size_t)ngroups * N * 4 + (size_t)P.H * 4 + S_COUNT * 8 +
                (4 * nblk + P.K + 8) * 8;
     if (P.precision == MBIR_PREC_BF16) b += KMp * 2;
-    if (g->d_tb4_bop) b += (size_t)g->n_records * 4;   // tensor-core adjoint contributions
+    if (g->d_tb4_bop) b += N * 8;   // tensor-core adjoint accumulators
     return b;
 }
 
@@ -637,10 +662,11 @@ std::vector<int> balance(const std::vector<double>& cost, int parts)
 void free_request_state(Request* r, cudaStream_t st)
 {
     void* ptrs[] = {r->e, r->q, r->b, r->grad, r->gprev, r->d0, r->d1, r->bpart, r->msq, r->ebf, r->sc, r->part,
-                    r->contrib};
+                    r->acc};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, st);
-    r->e = r->q = r->b = r->grad = r->gprev = r->d0 = r->d1 = r->bpart = r->msq = r->contrib = nullptr;
+    r->e = r->q = r->b = r->grad = r->gprev = r->d0 = r->d1 = r->bpart = r->msq = nullptr;
+    r->acc = nullptr;
     r->ebf = nullptr;
     r->sc = r->part = nullptr;
 }
@@ -666,7 +692,7 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     AL(r->sc, (size_t)S_COUNT);
     AL(r->part, (size_t)4 * r->nblk + P.K + 8);
     if (P.precision == MBIR_PREC_BF16) AL(r->ebf, KMp);
-    if (g->d_tb4_bop) AL(r->contrib, (size_t)g->n_records);
+    if (g->d_tb4_bop) AL(r->acc, N);
 #undef AL
     if (e != cudaSuccess) { free_request_state(r, st); return e == cudaErrorMemoryAllocation ? MBIR_ERR_OOM : MBIR_ERR_CUDA; }
     r->msq_host.resize(P.H);
@@ -674,6 +700,7 @@ int admit(mbir_engine* E, Request* r, cudaStream_t st)
     e = cudaMemcpyAsync(r->msq, r->msq_host.data(), sizeof(float) * P.H, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->sc, 0, sizeof(double) * S_COUNT, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->gprev, 0, sizeof(float) * N, st);
+    if (e == cudaSuccess && r->acc) e = cudaMemsetAsync(r->acc, 0, sizeof(unsigned long long) * N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d0, 0, sizeof(float) * N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d1, 0, sizeof(float) * N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->x, 0, sizeof(float) * N, st);
@@ -732,9 +759,8 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.nblk = r->nblk;
     d.tc = g->d_tb4_bop ? 1 : 0;
     d.tc_tile = g->d_tc_tile;
-    d.tc_dest = g->d_tc_dest;
-    d.tc_goff = g->d_tc_goff;
-    d.tc_contrib = r->contrib;
+    d.tc_acc = r->acc;
+    d.tc_bound = g->tc_bound;
     d.tcb = g->d_tb4_bop ? 1 : 0;
     d.tb4l = g->tb4;
     d.tb4_bop = g->d_tb4_bop;
@@ -835,7 +861,7 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
     start.insert(start.end(), fstart.begin(), fstart.end());
     cudaError_t e = cudaSuccess;
     e = ensure_cap(&E->L.desc, &E->cap_desc, E->sel.size(), grew);
-    if (e == cudaSuccess) e = ensure_cap(&E->L.pool, &E->cap_pool, 2 * E->cap_desc, grew);
+    if (e == cudaSuccess) e = ensure_cap(&E->L.pool, &E->cap_pool, 3 * E->cap_desc, grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.pixblk, &E->cap_pix, pix.size(), grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.rowblk, &E->cap_row, rows.size(), grew);
     if (e == cudaSuccess) e = ensure_cap(&E->L.upd, &E->cap_upd, upd.size(), grew);
@@ -866,9 +892,11 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cuda
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
     if (e != cudaSuccess) return e;
     if (tc) {
+        if (bf16) eng_emax_kernel<true><<<SG, kRedThreads, 0, st>>>(E->L);
+        else eng_emax_kernel<false><<<SG, kRedThreads, 0, st>>>(E->L);
         if (bf16) eng_bwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[1], st>>>(E->L);
         else eng_bwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[1], st>>>(E->L);
-        eng_bwd_tc_reduce_kernel<<<2 * SG, kRedThreads, 0, st>>>(E->L);
+        eng_bwd_tc_finish_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     } else {
         if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
         else eng_bwd_kernel<false><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
@@ -1019,7 +1047,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
     bool tcf = true;                     // tensor-core A x likewise
     for (Request* r : E->sel) {
-        if (!r->contrib) tc = false;
+        if (!r->acc) tc = false;
         if (!r->g->d_tf4_bop) tcf = false;
     }
     const int gtc = (int)tc + 2 * (int)tcf;

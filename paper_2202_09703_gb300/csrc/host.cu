@@ -173,7 +173,7 @@ void free_geometry(mbir_geometry* g)
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
                     g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
                     g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_win_order, g->d_win_counter,
-                    g->d_bwd_counter, g->d_tc_tile, g->d_tc_goff, g->d_tc_dest, g->w_tc_contrib,
+                    g->d_bwd_counter, g->d_tc_tile, g->w_tc_acc,
                     g->d_tc_counter, g->d_tf_order, g->d_tf_counter, g->w_colnorm,
                     g->d_tf4_bop, g->d_tf4_crange, g->d_tf4_split, g->d_tb4_bop};
     for (void* p : ptrs) if (p) cudaFree(p);

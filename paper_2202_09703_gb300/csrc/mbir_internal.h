@@ -401,9 +401,8 @@ struct mbir_geometry {
     int* d_win_counter;    // work counter of the A x launch
     // tensor-core A^T (see tc_adjoint.cu, tc_stream.cuh)
     int* d_tc_tile;        // first record of every 128-sample tile, K x (tiles + 1)
-    int* d_tc_goff;        // per transmitter position g: pixel-major offsets of its slots, n_tx x (N + 1)
-    uint32_t* d_tc_dest;   // record's slot: its group's pixel-major place (A-scan order within a pixel)
-    float* w_tc_contrib;   // one contribution per record, pixel-major
+    unsigned long long* w_tc_acc;   // per pixel: fixed-point sum, N + 1 (the last word: bits of max |e|)
+    float tc_bound;        // scale bound of the fixed-point sums (build_tc_adjoint)
     int* d_tc_counter;
     // tensor-core A x (see tc_stream.cuh, tc_fwd_stream.cu)
     int* d_tf_order;       // A-scans by decreasing record count

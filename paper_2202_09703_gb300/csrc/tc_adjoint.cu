@@ -1,85 +1,60 @@
 // Tables of the tensor-core A^T (tcs_adjoint_pool, tc_stream.cuh): the first
-// record of every tile, each record's slot for its contribution, the
-// per-pixel reduction of the contributions, the table operand and the launch.
-// Slots are grouped by transmitter position (the n_rx A-scans of one position
-// are consecutive) and pixel-major inside a group, A-scans in order: the
-// contributions of one group, written close together in time, fill whole
-// sectors before they leave L2, and a pixel's contributions are summed group
-// after group in A-scan order, so the result is reproducible.
+// record of every tile, the per-pixel fixed-point accumulators and the bound
+// that sets their scale, the table operand, and the launch: max |e| of the
+// residual, the pool (one integer addition per record into its pixel's sum),
+// then the sums turned into FP32.  Integer addition is associative, so the
+// result does not depend on which CTA adds what when: it is reproducible bit
+// for bit.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "tc_stream.cuh"
 
 namespace mbir {
 
-// b = each pixel's contributions summed (tcs_reduce_pixels), one pixel per lane.
-__global__ void bwd_tc_reduce_kernel(int N, int n_tx, int n_rx, const long long* __restrict__ rec_off,
-                                     const int* __restrict__ goff, const float* __restrict__ contrib,
-                                     float* __restrict__ b)
+// *emax = bits of max |e| over n values (non-negative floats order as their bits; a non-finite value
+// gives bits >= 0x7f800000).
+template <typename T>
+__global__ void tc_emax_kernel(const T* __restrict__ e, long long n, unsigned int* __restrict__ emax)
 {
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < N; w += nw)
-        tcs_reduce_pixels(w * 32, N, n_tx, n_rx, rec_off, goff, contrib, b);
+    unsigned int m = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float v;
+        if constexpr (sizeof(T) == 2) v = __bfloat162float(e[i]);
+        else v = e[i];
+        m = max(m, __float_as_uint(fabsf(v)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(emax, m);
 }
 
-// cnt[v] += 1 for the records [a, z) of one A-scan (a pixel has at most one record per A-scan)
-__global__ void tc_gcount_kernel(long long a, long long z, const int2* __restrict__ rkey, int* __restrict__ cnt)
+// b[v] from the fixed-point sums (tcs_finish_pixel)
+__global__ void tc_finish_kernel(int N, const unsigned long long* __restrict__ acc,
+                                 const unsigned int* __restrict__ emax, float bound, float* __restrict__ b)
 {
-    const long long r = a + blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r < z) cnt[rkey[r].x] += 1;
+    const unsigned int eb = *emax;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x)
+        b[v] = tcs_finish_pixel(acc[v], eb, bound);
 }
 
-// off[v] = cnt[0] + ... + cnt[v - 1] for v = 0 .. N (one block): chunks of consecutive pixels per thread, the
-// chunk sums scanned across the block
-__global__ void tc_gscan_kernel(const int* __restrict__ cnt, int N, int* __restrict__ off)
+// *wmax = bits of the largest sum of a record's four weights' magnitudes
+__global__ void tc_wmax_kernel(const float4* __restrict__ rw, long long n, unsigned int* __restrict__ wmax)
 {
-    __shared__ int ws[32];
-    const int nt = blockDim.x, tid = threadIdx.x;
-    const int chunk = (N + nt - 1) / nt, v0 = min(tid * chunk, N), v1 = min(v0 + chunk, N);
-    int sum = 0;
-    for (int v = v0; v < v1; ++v) sum += cnt[v];
-    // exclusive scan of the chunk sums: warp inclusive scan, then the warps' totals
-    int inc = sum;
-    for (int d = 1; d < 32; d <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, inc, d);
-        if ((tid & 31) >= d) inc += t;
+    unsigned int m = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float4 w = rw[i];
+        m = max(m, __float_as_uint((fabsf(w.x) + fabsf(w.y)) + (fabsf(w.z) + fabsf(w.w))));
     }
-    if ((tid & 31) == 31) ws[tid >> 5] = inc;
-    __syncthreads();
-    if (tid < 32) {
-        int x = tid < (nt >> 5) ? ws[tid] : 0;
-        for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, x, d);
-            if (tid >= d) x += t;
-        }
-        ws[tid] = x;
-    }
-    __syncthreads();
-    int run = inc - sum + ((tid >> 5) > 0 ? ws[(tid >> 5) - 1] : 0);
-    for (int v = v0; v < v1; ++v) {
-        off[v] = run;
-        run += cnt[v];
-    }
-    if (tid == nt - 1) off[N] = run;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(wmax, m);
 }
 
-// slot of each record of one A-scan of group g: the group's pixel-major offset of its pixel plus the
-// pixel's records already placed in the group (A-scans in order)
-__global__ void tc_gdest_kernel(long long a, long long z, long long gbase, const int2* __restrict__ rkey,
-                                const int* __restrict__ off, int* __restrict__ cursor, uint32_t* __restrict__ dest)
-{
-    const long long r = a + blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (r < z) {
-        const int v = rkey[r].x;
-        const int c = cursor[v];
-        dest[r] = (uint32_t)(gbase + off[v] + c);
-        cursor[v] = c + 1;
-    }
-}
-
-// first record of every 128-sample tile of every A-scan (records sorted by n0)
+// first record of every 128-sample tile of every A-scan (records grouped by tile, n0 ascending from tile to
+// tile)
 __global__ void tc_tile_off_kernel(GeomParams P, int ntile, const long long* __restrict__ rec_off,
                                    const int2* __restrict__ rkey, int* __restrict__ tile_off)
 {
@@ -97,87 +72,75 @@ __global__ void tc_tile_off_kernel(GeomParams P, int ntile, const long long* __r
     tile_off[i] = lo;
 }
 
-// First record of every tile, each record's slot (per transmitter position, pixel-major, A-scans in order)
-// and the contribution buffer of the tensor-core A^T; cudaErrorNotSupported keeps the CUDA-core adjoint.
+// First record of every tile, the per-pixel accumulators (N sums and the max |e| word after them, zeroed)
+// and the bound of the fixed-point scale: K x the largest record weight sum x (the largest table row sum
+// of |T| + the largest |T|, for the tau = t0 tap), doubled for the rounding of the products;
+// cudaErrorNotSupported keeps the CUDA-core adjoint.
 cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
 {
     const GeomParams& P = g->P;
-    if (!g->d_rec_key || g->n_records <= 0 || g->n_records >= (1LL << 32)) return cudaErrorNotSupported;
+    if (!g->d_rec_key || g->n_records <= 0) return cudaErrorNotSupported;
     const int N = P.W * P.H;
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
-    int* d_cnt = nullptr;
     int* d_tile = nullptr;
-    int* d_goff = nullptr;
-    uint32_t* d_dest = nullptr;
-    float* d_contrib = nullptr;
+    unsigned long long* d_acc = nullptr;
     int* d_ctr = nullptr;
-    const size_t gstride = (size_t)N + 1;
-    cudaError_t e = cudaMalloc((void**)&d_cnt, sizeof(int) * (size_t)N);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_tile, sizeof(int) * (size_t)P.K * (ntile + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_goff, sizeof(int) * gstride * P.n_tx);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_dest, sizeof(uint32_t) * (size_t)g->n_records);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_contrib, sizeof(float) * (size_t)g->n_records);
+    cudaError_t e = cudaMalloc((void**)&d_tile, sizeof(int) * (size_t)P.K * (ntile + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_acc, sizeof(unsigned long long) * ((size_t)N + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long) * ((size_t)N + 1), st);
     if (e == cudaSuccess) {
         const long long items = (long long)P.K * (ntile + 1);
         tc_tile_off_kernel<<<(int)((items + 255) / 256), 256, 0, st>>>(P, ntile, g->d_rec_off, g->d_rec_key, d_tile);
         e = cudaGetLastError();
     }
-    std::vector<long long> roff((size_t)P.K + 1);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(roff.data(), g->d_rec_off, sizeof(long long) * (P.K + 1), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    // per transmitter position: pixel counts, their offsets, then the slots with a cursor per pixel
-    for (int gi = 0; gi < P.n_tx && e == cudaSuccess; ++gi) {
-        int* off = d_goff + gstride * gi;
-        const int k0 = gi * P.n_rx, k1 = k0 + P.n_rx;
-        e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)N, st);
-        for (int k = k0; k < k1 && e == cudaSuccess; ++k)
-            if (roff[k + 1] > roff[k]) {
-                tc_gcount_kernel<<<(int)((roff[k + 1] - roff[k] + 255) / 256), 256, 0, st>>>(roff[k], roff[k + 1],
-                                                                                            g->d_rec_key, d_cnt);
-                e = cudaGetLastError();
-            }
-        if (e == cudaSuccess) {
-            tc_gscan_kernel<<<1, 1024, 0, st>>>(d_cnt, N, off);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * (size_t)N, st);
-        for (int k = k0; k < k1 && e == cudaSuccess; ++k)
-            if (roff[k + 1] > roff[k]) {
-                tc_gdest_kernel<<<(int)((roff[k + 1] - roff[k] + 255) / 256), 256, 0, st>>>(
-                    roff[k], roff[k + 1], roff[k0], g->d_rec_key, off, d_cnt, d_dest);
-                e = cudaGetLastError();
-            }
+    unsigned int wbits = 0;
+    if (e == cudaSuccess) {
+        unsigned int* d_wmax = reinterpret_cast<unsigned int*>(d_acc + N);
+        tc_wmax_kernel<<<std::max(1, g->n_sm * 8), 256, 0, st>>>(g->d_rec_w, g->n_records, d_wmax);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&wbits, d_wmax, sizeof(wbits), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_wmax, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d_cnt);
+    double tsum = 0.0, tmax = 0.0;
+    const int nq = P.Q * P.Tw + 1;
+    for (int gpl = 0; gpl < P.G; ++gpl)
+        for (int ph = 0; ph <= P.Q; ++ph) {
+            double rs = 0.0;
+            for (int m = 0; m < P.Tw; ++m) {
+                const double t = std::fabs((double)g->tab_host[(size_t)gpl * nq + m * P.Q + ph]);
+                rs += t;
+                tmax = std::max(tmax, t);
+            }
+            tsum = std::max(tsum, rs);
+        }
+    float wmax = 0.0f;
+    std::memcpy(&wmax, &wbits, sizeof(wmax));
+    const double bound = 2.0 * P.K * (double)wmax * (tsum + tmax);
+    if (e == cudaSuccess && !(bound > 0.0 && bound < 1e30)) e = cudaErrorNotSupported;
     if (e != cudaSuccess) {
-        void* ptrs[] = {d_tile, d_goff, d_dest, d_contrib, d_ctr};
+        void* ptrs[] = {d_tile, d_acc, d_ctr};
         for (void* p : ptrs) cudaFree(p);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
     g->d_tc_tile = d_tile;
-    g->d_tc_goff = d_goff;
-    g->d_tc_dest = d_dest;
-    g->w_tc_contrib = d_contrib;
+    g->w_tc_acc = d_acc;
     g->d_tc_counter = d_ctr;
-    g->bytes += sizeof(int) * ((size_t)P.K * (ntile + 1) + 1 + gstride * P.n_tx) +
-                (sizeof(uint32_t) + sizeof(float)) * (size_t)g->n_records;
+    g->tc_bound = (float)bound;
+    g->bytes += sizeof(int) * ((size_t)P.K * (ntile + 1) + 1) + sizeof(unsigned long long) * ((size_t)N + 1);
     return cudaSuccess;
 }
 
 // The tables above, freed when the tensor-core A^T is not used after all.
 void free_tc_adjoint(mbir_geometry* g)
 {
-    void* ptrs[] = {g->d_tc_tile, g->d_tc_goff, g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
+    void* ptrs[] = {g->d_tc_tile, g->w_tc_acc, g->d_tc_counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     g->d_tc_tile = nullptr;
-    g->d_tc_goff = nullptr;
-    g->d_tc_dest = nullptr;
-    g->w_tc_contrib = nullptr;
+    g->w_tc_acc = nullptr;
     g->d_tc_counter = nullptr;
 }
 
@@ -219,13 +182,13 @@ __global__ void __launch_bounds__(kTsThreads, 1) bwd_tcs_kernel(TbView V, int* _
 
 // Table operand of the streamed A^T (rows plane * (Q + 1) + phase, columns taps; FP32 form: the table times
 // 2^texp split into two FP16 parts, BF16 form: the stored BF16 table), for a geometry whose records, tile
-// offsets and contribution slots (build_tc_adjoint) and per-tile column ranges (build_tc_forward_stream) are
+// offsets and accumulators (build_tc_adjoint) and per-tile column ranges (build_tc_forward_stream) are
 // present; cudaErrorNotSupported keeps the other adjoints.
 cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st)
 {
     (void)st;
     const GeomParams& P = g->P;
-    if (!g->d_tc_tile || !g->d_tc_dest || !g->w_tc_contrib || !g->d_tf4_crange || !g->d_tc_counter)
+    if (!g->d_tc_tile || !g->w_tc_acc || !g->d_tf4_crange || !g->d_tc_counter)
         return cudaErrorNotSupported;
     Tb4Layout L{};
     for (int kw : {256, 224, 192, 160, 128, 96, 64}) {
@@ -289,14 +252,23 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     const int grid = std::max(1, std::min(g->n_sm, P.K * ntile));
     const void* tab = bf ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
     const void* e = bf ? (const void*)e_bf : (const void*)e_pad;
+    const int N = P.W * P.H;
+    unsigned int* emax = reinterpret_cast<unsigned int*>(g->w_tc_acc + N);
+    ce = cudaMemsetAsync(g->w_tc_acc, 0, sizeof(unsigned long long) * ((size_t)N + 1), st);
+    if (ce != cudaSuccess) return ce;
+    const long long ne = (long long)P.K * P.Mp;
+    const int eg = (int)std::max(1LL, std::min((ne + 255) / 256, (long long)g->n_sm * 8));
+    if (bf) tc_emax_kernel<__nv_bfloat16><<<eg, 256, 0, st>>>(e_bf, ne, emax);
+    else tc_emax_kernel<float><<<eg, 256, 0, st>>>(e_pad, ne, emax);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return ce;
     TbView V{P, L, g->d_tb4_bop, tab, e, g->d_rec_off, g->d_tc_tile, g->d_tf4_crange, g->d_rec_key, g->d_rec_w,
-             g->d_tc_dest, g->w_tc_contrib, g->d_tc_counter};
+             g->w_tc_acc, emax, g->tc_bound, g->d_tc_counter};
     kern<<<grid, kTsThreads, L.smem, st>>>(V, g->d_status);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
-    const int N = P.W * P.H;
-    bwd_tc_reduce_kernel<<<std::max(1, std::min((N + 255) / 256, g->n_sm * 16)), 256, 0, st>>>(
-        N, P.n_tx, P.n_rx, g->d_rec_off, g->d_tc_goff, g->w_tc_contrib, b);
+    tc_finish_kernel<<<std::max(1, std::min((N + 255) / 256, g->n_sm * 8)), 256, 0, st>>>(N, g->w_tc_acc, emax,
+                                                                                           g->tc_bound, b);
     return cudaGetLastError();
 }
 

@@ -380,13 +380,15 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
 // (128 x taps, in tensor memory as the A operand) and the table rows the tile's
 // records reach (one column range, the B operand resident in shared memory);
 // each record then combines four values of C with its bilinear weights (less
-// the tau = t0 tap of flagged records) and writes one contribution to its slot
-// (grouped by transmitter position, pixel-major inside a group); a reduction
-// kernel sums each pixel's contributions in A-scan order.  FP32 form: the window scaled by the power of two that brings
-// its largest magnitude into [2^14, 2^15) and split into two FP16 parts, the
-// table likewise: three products.  BF16 form: the stored BF16 residual and
-// table, one product.  The products of the next item run while the current
-// item's records are processed.
+// the tau = t0 tap of flagged records) into one contribution v and adds it to
+// its pixel's 64-bit fixed-point accumulator: round(v 2^s) by an integer atomic
+// (one scale 2^s per apply, tc_fixed_exponent), so the sum is exact and its
+// value does not depend on the order of the additions; a last kernel turns the
+// sums into FP32 (tcs_finish_pixel).  FP32 form: the window scaled by the power
+// of two that brings its largest magnitude into [2^14, 2^15) and split into two
+// FP16 parts, the table likewise: three products.  BF16 form: the stored BF16
+// residual and table, one product.  The products of the next item run while the
+// current item's records are processed.
 struct TbView {
     GeomParams P;
     Tb4Layout T;
@@ -398,22 +400,42 @@ struct TbView {
     const uint32_t* crange;      // per (A-scan, tile): c_lo | c_hi << 16
     const int2* rkey;
     const float4* rw;
-    const uint32_t* dest;        // record -> slot (group of its transmitter position, then pixel)
-    float* contrib;
+    unsigned long long* acc;     // per pixel: the fixed-point sum (zero on entry)
+    const unsigned int* emax;    // bits of max |e| over the residual (tc_emax)
+    float bound;                 // K x max record weight sum x (max table row sum of |T| + max |T|), doubled
     int* counter;
 };
 
 constexpr int kTbUnroll = 4;     // records per thread in one batch (two batches in flight)
 
+// Scale exponent s of the adjoint's fixed-point sums: every contribution is at most bound / K x max|e| in
+// magnitude and a pixel has at most one per A-scan, so with s = 61 - (exponents of bound and max|e|) no
+// partial sum reaches 2^61.  Clamped to [-126, 126] (2^s and 2^-s normal floats); 0 for a zero residual.
+__device__ __forceinline__ int tc_fixed_exponent(unsigned int emax_bits, float bound)
+{
+    const float em = __uint_as_float(emax_bits);
+    if (!(em > 0.0f) || !(em <= 3.4e38f)) return 0;
+    int e1 = 0, e2 = 0;
+    frexpf(em, &e1);
+    frexpf(bound, &e2);
+    return min(max(61 - e1 - e2, -126), 126);
+}
+
+// b[v] from its fixed-point sum (one rounding to FP32); NaN when the residual held a non-finite value.
+__device__ __forceinline__ float tcs_finish_pixel(unsigned long long a, unsigned int emax_bits, float bound)
+{
+    if (emax_bits >= 0x7f800000u) return __uint_as_float(0x7fc00000u);
+    return __ll2float_rn((long long)a) * ts_pow2(-tc_fixed_exponent(emax_bits, bound));
+}
+
 // A batch of records held in registers: records rb + u * kTsThreads + tid, u < kTbUnroll.
 struct TbBatch {
     int2 key[kTbUnroll];
     float4 w[kTbUnroll];
-    uint32_t dst[kTbUnroll];
 };
 
 __device__ __forceinline__ void tb_load(TbBatch& b, const int2* __restrict__ rkey, const float4* __restrict__ rw,
-                                        const uint32_t* __restrict__ dest, long long base, int rb, int r1, int tid)
+                                        long long base, int rb, int r1, int tid)
 {
 #pragma unroll
     for (int u = 0; u < kTbUnroll; ++u) {
@@ -421,7 +443,6 @@ __device__ __forceinline__ void tb_load(TbBatch& b, const int2* __restrict__ rke
         if (r < r1) {
             b.key[u] = __ldg(rkey + base + r);
             b.w[u] = __ldg(rw + base + r);
-            b.dst[u] = __ldg(dest + base + r);
         }
     }
 }
@@ -446,8 +467,8 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
     const float invR = 1.0f / (float)R;
     const int2* __restrict__ rkey = V.rkey;
     const float4* __restrict__ rw = V.rw;
-    const uint32_t* __restrict__ dest = V.dest;
-    float* __restrict__ contrib = V.contrib;
+    unsigned long long* __restrict__ acc = V.acc;
+    const float fsc = ts_pow2(tc_fixed_exponent(*V.emax, V.bound));
     const uint32_t tA = tmem, tD = tmem + 128;
     const int HA = T.ntap / 2;                          // tensor-memory columns of one part of H
     const int qd = warp & 3, pb = warp >> 2;
@@ -547,7 +568,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         const int r1 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc + 1);
         // the first records of this item and the next item's window load during the products
         TbBatch ba, bb;
-        tb_load(ba, rkey, rw, dest, base, r0, r1, tid);
+        tb_load(ba, rkey, rw, base, r0, r1, tid);
         const float ew = nxt < nitems ? load_e(nxt) : 0.0f;
         float* sEc = sE0 + cbuf * T.ewin;
         float* sEn = sE0 + (cbuf ^ 1) * T.ewin;
@@ -583,8 +604,8 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         __syncthreads();                                  // H of the next item in tensor memory
         const int nn = *next;
         if (tid == 0 && live_nxt) issue_mma(nxt);
-        // ---- the current item's records: four values of C each, one contribution per record; the next
-        // batch loads while one is combined
+        // ---- the current item's records: four values of C each, one fixed-point addition per record; the
+        // next batch loads while one is combined
         if (live_cur) {
             const int ts = tc * kTsTile;
             const float* Cb = sC - c_lo;
@@ -609,15 +630,15 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
                         else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
                         v -= (bt.w[u].z * tl.x + bt.w[u].w * tl.y) * sEc[n0r + P.Tw - 1];
                     }
-                    contrib[bt.dst[u]] = v;
+                    atomicAdd(acc + bt.key[u].x, (unsigned long long)__float2ll_rn(v * fsc));
                 }
             };
             constexpr int kStep = kTbUnroll * kTsThreads;
             for (int rb = r0; rb < r1; rb += 2 * kStep) {
-                if (rb + kStep < r1) tb_load(bb, rkey, rw, dest, base, rb + kStep, r1, tid);
+                if (rb + kStep < r1) tb_load(bb, rkey, rw, base, rb + kStep, r1, tid);
                 run(ba, rb);
                 if (rb + kStep >= r1) break;
-                if (rb + 2 * kStep < r1) tb_load(ba, rkey, rw, dest, base, rb + 2 * kStep, r1, tid);
+                if (rb + 2 * kStep < r1) tb_load(ba, rkey, rw, base, rb + 2 * kStep, r1, tid);
                 run(bb, rb + kStep);
             }
         }
@@ -630,25 +651,6 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         live_cur = live_nxt;
     }
     return !*abort_flag;
-}
-
-// b[v] for the pixels v0 .. v0 + 31 (lane = pixel) of one geometry: the pixel's contributions group after
-// group (transmitter positions in order; group g's slots start at the first record of its first A-scan and
-// are pixel-major, goff[g (N + 1) + v] the pixel's offset), A-scans in order within a group, Neumaier sums.
-__device__ __forceinline__ void tcs_reduce_pixels(int v0, int N, int n_tx, int n_rx, const long long* __restrict__ rec_off,
-                                                  const int* __restrict__ goff, const float* __restrict__ contrib,
-                                                  float* __restrict__ b)
-{
-    const int v = v0 + (threadIdx.x & 31);
-    if (v >= N) return;
-    float s = 0.0f, c = 0.0f;
-    for (int g = 0; g < n_tx; ++g) {
-        const int* o = goff + (size_t)g * ((size_t)N + 1);
-        const long long gb = __ldg(rec_off + (size_t)g * n_rx);
-        const int a = __ldg(o + v), z = __ldg(o + v + 1);
-        for (int j = a; j < z; ++j) neumaier_add(s, c, __ldg(contrib + gb + j));
-    }
-    b[v] = s + c;
 }
 
 }  // namespace mbir
