@@ -7,6 +7,8 @@
 namespace mbir {
 
 constexpr int kRecShift = 13;                     // record key: n0 << 13 | table row << 1 | flag0
+constexpr int kRecPixel = 0x7fffffff;             // record pixel field: pixel index (bit 31: a batch mark of the
+                                                  // tensor-core A x, set at its set-up)
 
 // Copies a pulse table (tab_bytes, a multiple of 16) into shared memory.
 __device__ __forceinline__ void load_table_smem(void* dst, const void* src, size_t tab_bytes, int tid, int nthreads)

@@ -9,16 +9,18 @@
 //   A^T e   persistent; each request's own work items form a pool drained
 //           through a per-request counter (tensor cores: max |e| per request,
 //           the (A-scan, tile) items of tcs_adjoint_pool into fixed-point
-//           sums, then the sums into b; CUDA cores:
-//           pixel tile x transmitter group, longest first).  A CTA starts at
+//           sums, then the sums into b; CUDA cores: pixel tile x
+//           transmitter group, longest first; a step with both kinds of
+//           request launches both, each taking its own).  A CTA starts at
 //           the request its share of the total cost falls on and walks on
 //           through the others until every pool is empty, loading a request's
 //           table only when it joins that request's pool
 //   grad    prior gradient + FP64 partials per (request, pixel block)
 //   dir     Polak-Ribiere+ scalars per request, then directions + curvature
-//   A d     persistent over each request's sorted records (tensor cores:
-//           A-scans of tcs_forward_pool, largest first; CUDA cores: span
-//           windows, largest first), pools and CTA placement as for A^T e
+//   A d     persistent over each request's records (tensor cores: A-scans
+//           of tcs_forward_pool, largest first; CUDA cores: span windows,
+//           largest first; a step with both kinds of request launches both
+//           kernels, each taking its own), pools and CTA placement as for A^T e
 //   P q     direct-arrival projection per (request, A-scan) with FP64 norms
 //   step    majorize-minimize step per request; x and e updated
 // The apply kernels run the same per-item and per-span code as the
@@ -173,7 +175,8 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_bwd_kernel(EngLists L)
     for (int t = 0; t < nreq; ++t) {
         const int rq = (r0 + t) % nreq;
         const ReqDesc& R = L.desc[rq];
-        if (!eng_pool_live(L.pool, rq, 1, R.n_items, flags + 4)) continue;
+        // requests with the tensor-core A^T are eng_bwd_tcs_kernel's
+        if (R.tc || !eng_pool_live(L.pool, rq, 1, R.n_items, flags + 4)) continue;
         const GeomParams& P = R.P;
         size_t tab_bytes, ebytes;
         int nst;
@@ -208,6 +211,7 @@ __global__ void eng_bwd_reduce_kernel(EngLists L)
     for (int bb = blockIdx.x; bb < nb; bb += gridDim.x) {
         const int2 rb = L.pixblk[bb];
         const ReqDesc& R = L.desc[rb.x];
+        if (R.tc) continue;
         const GeomParams& P = R.P;
         const int N = P.W * P.H;
         const int v = rb.y * kRedThreads + threadIdx.x;
@@ -375,7 +379,8 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
     for (int t = 0; t < nreq; ++t) {
         const int rq = (r0 + t) % nreq;
         const ReqDesc& R = L.desc[rq];
-        if (!eng_pool_live(L.pool, rq, 0, R.nwin, flag)) continue;
+        // requests with the tensor-core A x (their records are in that kernel's order) are eng_fwd_tcs_kernel's
+        if (R.tcs || !eng_pool_live(L.pool, rq, 0, R.nwin, flag)) continue;
         const GeomParams& P = R.P;
         if (rq != cur) {
             const size_t tab_bytes =
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
             const int rq = (r0 + t) % nreq;
             const ReqDesc& R = L.desc[rq];
             const int nitems = R.P.K * ((R.P.M + kTsTile - 1) / kTsTile);
-            if (!eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
+            if (!R.tc || !eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
             const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
             const void* e = BF16 ? (const void*)R.ebf : (const void*)R.e;
             const TbView V{R.P, R.tb4l, R.tb4_bop, tab, e, R.rec_off, R.tc_tile, R.tf4_crange, R.rkey, R.rw,
@@ -429,6 +434,7 @@ __global__ void eng_emax_kernel(EngLists L)
     for (int bb = blockIdx.x; bb < nb; bb += gridDim.x) {
         const int2 rk = L.rowblk[bb];
         const ReqDesc& R = L.desc[rk.x];
+        if (!R.tc) continue;
         const int Mp = R.P.Mp;
         unsigned int m = 0;
         for (int n = threadIdx.x; n < Mp; n += blockDim.x) {
@@ -450,7 +456,7 @@ __global__ void eng_bwd_tc_finish_kernel(EngLists L)
         const int2 rb = L.pixblk[bb];
         const ReqDesc& R = L.desc[rb.x];
         const int v = rb.y * kRedThreads + threadIdx.x;
-        if (v < R.P.W * R.P.H) {
+        if (R.tc && v < R.P.W * R.P.H) {
             const unsigned int eb = *reinterpret_cast<const unsigned int*>(L.pool + 3 * rb.x + 2);
             R.b[v] = tcs_finish_pixel(R.tc_acc[v], eb, R.tc_bound);
             R.tc_acc[v] = 0ull;
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_fwd_tcs_kernel(EngLists L)
         for (int t = 0; t < nreq; ++t) {
             const int rq = (r0 + t) % nreq;
             const ReqDesc& R = L.desc[rq];
-            if (!eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
+            if (!R.tcs || !eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
             const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
             const TsView V{R.P, R.tf4l, R.tf4_bop, tab, R.rec_off, R.tf4_crange, R.tf4_split, R.rkey, R.rw,
                            R.tf_order, dnew_of(R), R.q, 0, R.P.Mp, L.pool + 3 * rq};
@@ -886,18 +892,21 @@ int rebuild_lists(mbir_engine* E, cudaStream_t st, bool* grew)
 }
 
 // One MAP iteration of every active request, as launched inside the graph.
-cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cudaStream_t st)
+// tcb / ccb: some requests have the tensor-core A^T / some do not; tcf / ccf likewise for A x.  Each kernel
+// takes only the requests of its kind, so a request runs the same kernels alone and in any mix.
+cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tcb, bool ccb, bool tcf, bool ccf, cudaStream_t st)
 {
     const int G = E->n_sm, SG = E->n_sm * 8;
     cudaError_t e = cudaMemsetAsync(E->L.pool, 0, sizeof(int) * E->cap_pool, st);
     if (e != cudaSuccess) return e;
-    if (tc) {
+    if (tcb) {
         if (bf16) eng_emax_kernel<true><<<SG, kRedThreads, 0, st>>>(E->L);
         else eng_emax_kernel<false><<<SG, kRedThreads, 0, st>>>(E->L);
         if (bf16) eng_bwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[1], st>>>(E->L);
         else eng_bwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[1], st>>>(E->L);
         eng_bwd_tc_finish_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
-    } else {
+    }
+    if (ccb) {
         if (bf16) eng_bwd_kernel<true><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
         else eng_bwd_kernel<false><<<G, kEngThreads, E->smem_bwd, st>>>(E->L);
         eng_bwd_reduce_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
@@ -907,8 +916,8 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tc, bool tcf, cuda
     eng_dir_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     if (tcf && bf16) eng_fwd_tcs_kernel<true><<<G, kTsThreads, E->smem_tc[0], st>>>(E->L);
     else if (tcf) eng_fwd_tcs_kernel<false><<<G, kTsThreads, E->smem_tc[0], st>>>(E->L);
-    else if (bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
-    else eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
+    if (ccf && bf16) eng_fwd_kernel<true><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
+    else if (ccf) eng_fwd_kernel<false><<<G, kEngThreads, E->smem_fwd, st>>>(E->L);
     eng_proj_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     eng_finstep_kernel<<<G, kRedThreads, 0, st>>>(E->L);
     eng_update_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
@@ -1042,15 +1051,16 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return MBIR_ERR_CUDA;
     const bool bf16 = E->sel[0]->g->P.precision == MBIR_PREC_BF16;
-    bool tc = true;                      // tensor-core A^T when every request of the step has its tables
     for (Request* r : E->active)
         if ((r->g->P.precision == MBIR_PREC_BF16) != bf16) return MBIR_ERR_UNSUPPORTED;
-    bool tcf = true;                     // tensor-core A x likewise
+    bool tcb = false, ccb = false, tcf = false, ccf = false;   // requests with / without each tensor-core apply
     for (Request* r : E->sel) {
-        if (!r->acc) tc = false;
-        if (!r->g->d_tf4_bop) tcf = false;
+        if (r->acc) tcb = true;
+        else ccb = true;
+        if (r->g->d_tf4_bop) tcf = true;
+        else ccf = true;
     }
-    const int gtc = (int)tc + 2 * (int)tcf;
+    const int gtc = (int)tcb + 2 * (int)ccb + 4 * (int)tcf + 8 * (int)ccf;
     size_t smem_tc[2] = {1024, 1024};
     for (Request* r : E->active) {
         const mbir_geometry* g = r->g;
@@ -1065,7 +1075,7 @@ int mbir_engine_step(mbir_engine* E, void* stream, int* n_active, int* n_queued)
         cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         cudaGraph_t graph;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tc, tcf, cs);
+        if (e == cudaSuccess) e = enqueue_iteration(E, bf16, tcb, ccb, tcf, ccf, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&E->graph, graph, 0);

@@ -141,6 +141,50 @@ __global__ void ts_interleave_kernel(GeomParams P, int k0, const long long* __re
     }
 }
 
+// Marks every batch of 32 records (per warp part, as the kernel reads them) whose lanes' four corner cells
+// (n0, table row), (n0, next plane's row), (n0, row + 1), (n0, next plane's row + 1) are all distinct between
+// lanes: bit 31 of the pixel field of the batch's first record.  Such a batch has no equal keys, so the
+// kernel adds its corners without the segmented sums and in one step.  Warp per batch, blocks per
+// (A-scan, tile).
+__global__ void ts_batch_flag_kernel(GeomParams P, int R, const long long* __restrict__ rec_off,
+                                     const int* __restrict__ split, int2* __restrict__ key)
+{
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    const int k = (int)(blockIdx.x / ntile), t = (int)(blockIdx.x % ntile);
+    const int* sp = split + ((size_t)k * ntile + t) * kTsSplit;
+    const long long base = rec_off[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t full = 0xffffffffu;
+    for (int p = 0; p < kTsWarps; ++p) {
+        const int a = sp[p], z = sp[p + 1];
+        for (int b = a + 32 * warp; b < z; b += 32 * nw) {
+            const int r = b + lane;
+            int c[4];
+            if (r < z) {
+                const int y = key[base + r].y;
+                const int n0 = y >> kRecShift, trow = (y >> 1) & 0xfff, gi = trow / R;
+                const int c1 = min(gi + 1, P.G - 1) * R + (trow - gi * R);
+                c[0] = (n0 << 13) | trow;
+                c[1] = (n0 << 13) | c1;
+                c[2] = c[0] + 1;
+                c[3] = c[1] + 1;
+            } else {
+                c[0] = c[1] = c[2] = c[3] = -1 - lane;       // matches nothing
+            }
+            bool clash = false;
+            for (int d = 1; d < 32; ++d) {
+                const int src = (lane + d) & 31;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int o = __shfl_sync(full, c[j], src);
+                    clash |= (o == c[0]) | (o == c[1]) | (o == c[2]) | (o == c[3]);
+                }
+            }
+            if (!__any_sync(full, clash) && lane == 0) key[base + b].x |= (int)0x80000000;
+        }
+    }
+}
+
 // Interleaves the records of every warp part (ts_interleave_kernel) through a temporary copy of up to about
 // 256 MB of A-scans at a time; without room for the copy the records keep their sorted order, which the
 // kernel takes as well.
@@ -267,8 +311,14 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
         e = cudaMalloc((void**)&d_b, L.bbytes);
         if (e == cudaSuccess) e = cudaMemcpy(d_b, img.data(), L.bbytes, cudaMemcpyHostToDevice);
     }
-    // last: from here on the records are in the kernel's order (the CUDA-core A x's span runs no longer hold)
+    // last: from here on the records are in the kernel's order and carry its batch marks (the CUDA-core A x's
+    // span runs no longer hold)
     if (e == cudaSuccess) e = interleave_records(g, roff, d_sp, st);
+    if (e == cudaSuccess) {
+        ts_batch_flag_kernel<<<P.K * ntile, 256, 0, st>>>(P, L.R, g->d_rec_off, d_sp, g->d_rec_key);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) {
         void* ptrs[] = {d_n0, d_ord, d_ctr, d_cr, d_sp, d_b};
         for (void* p : ptrs) cudaFree(p);

@@ -217,7 +217,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                 // ---- scatter: batches b = 0 .. nb-1, slot b & 3, x one batch ahead
                 float* Sb = sS - (int)(tcr[t] & 0xffffu);
                 float bsum = 0.0f;
-                xq[0] = kq[0].y >= 0 ? __ldg(xg + kq[0].x) : 0.0f;
+                xq[0] = kq[0].y >= 0 ? __ldg(xg + (kq[0].x & kRecPixel)) : 0.0f;
                 for (int b0 = 0; b0 < nb; b0 += 4) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -225,7 +225,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         if (b >= nb) break;
                         if (b + 1 < nb) {
                             const int2 kn = kq[(u + 1) & 3];
-                            xq[(u + 1) & 3] = kn.y >= 0 ? __ldg(xg + kn.x) : 0.0f;
+                            xq[(u + 1) & 3] = kn.y >= 0 ? __ldg(xg + (kn.x & kRecPixel)) : 0.0f;
                         }
                         const int2 kk = kq[u];
                         const float4 w = wq[u];
@@ -235,11 +235,36 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         const int trow = valid ? (kk.y >> 1) & 0xfff : 0;
                         float c0 = w.x * xv, c1 = w.y * xv, c2 = w.z * xv, c3 = w.w * xv;
                         bsum += (fabsf(c0) + fabsf(c1)) + (fabsf(c2) + fabsf(c3));
+                        const int gi = (int)(((float)trow + 0.5f) * invR);
+                        const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
+                        float* row = Sb + n0r * T.astride;
+                        // a marked batch (first record's pixel field negative): every corner cell is its lane's
+                        // alone, so the four read-modify-writes are independent (the last plane's two pairs of
+                        // equal cells are merged first)
+                        const bool one_step = __shfl_sync(full, kk.x, 0) < 0;
                         // equal (n0, table row) are adjacent lanes: segmented inclusive sums over them
                         const int key = valid ? (n0r << 12) | trow : 0x40000000 + lane;
                         // (every lane takes part in every shuffle: none of them sits behind a condition)
                         const int kup = __shfl_up_sync(full, key, 1);
                         const int kdn = __shfl_down_sync(full, key, 1);
+                        if (one_step) {
+                            if (valid) {
+                                const bool dup = c1col == trow;
+                                if (dup) {
+                                    c0 += c1;
+                                    c2 += c3;
+                                }
+                                const float s0 = row[trow], s2 = row[trow + 1];
+                                const float s1 = dup ? 0.0f : row[c1col], s3 = dup ? 0.0f : row[c1col + 1];
+                                row[trow] = s0 + c0;
+                                row[trow + 1] = s2 + c2;
+                                if (!dup) {
+                                    row[c1col] = s1 + c1;
+                                    row[c1col + 1] = s3 + c3;
+                                }
+                            }
+                            __syncwarp();
+                        } else {
                         if (__any_sync(full, lane > 0 && kup == key)) {
                             // Hillis-Steele steps until no run reaches further back (runs are short)
                             for (int d = 1; d < 32; d <<= 1) {
@@ -259,9 +284,6 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         // the last record of each run adds its corners, one corner per step: within a step the
                         // writers' cells are distinct and the rows belong to this warp alone
                         const bool writer = valid && (lane == 31 || kdn != key);
-                        const int gi = (int)(((float)trow + 0.5f) * invR);
-                        const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
-                        float* row = Sb + n0r * T.astride;
                         if (writer) row[trow] += c0;
                         __syncwarp();
                         if (writer) row[c1col] += c1;
@@ -270,6 +292,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         __syncwarp();
                         if (writer) row[c1col + 1] += c3;
                         __syncwarp();
+                        }
                         // tau = t0 exactly (rare): the last tap of the upper phase row lies outside the window;
                         // one lane after another
                         uint32_t fm = __ballot_sync(full, valid && (kk.y & 1));
@@ -630,7 +653,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
                         else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
                         v -= (bt.w[u].z * tl.x + bt.w[u].w * tl.y) * sEc[n0r + P.Tw - 1];
                     }
-                    atomicAdd(acc + bt.key[u].x, (unsigned long long)__float2ll_rn(v * fsc));
+                    atomicAdd(acc + (bt.key[u].x & kRecPixel), (unsigned long long)__float2ll_rn(v * fsc));
                 }
             };
             constexpr int kStep = kTbUnroll * kTsThreads;

@@ -92,6 +92,29 @@ def test_engine_result_is_identical_alone_and_in_a_mix(problems):
         assert np.array_equal(a, x.cpu().numpy())
 
 
+def test_engine_mixes_tensor_core_and_cuda_core_geometries(problems):
+    """One step holding a request whose geometry runs A on the tensor cores (records in that kernel's
+    order) and one whose geometry keeps the CUDA-core kernels: each A d kernel takes its own requests, and
+    each result equals its single-request reconstruction bit for bit."""
+    s0, geo0, y0, sig0, _, _ = problems[0]
+    s1, _, y1, sig1, _, _ = problems[1]
+    geo1 = M.Geometry(s1, mode="tab", tensor_cores=False)
+    assert geo0.info.forward_tensor_cores == 1 and geo1.info.forward_tensor_cores == 0
+    n0, n1 = 6, 5
+    x0 = torch.empty(s0.N, device=DEV)
+    x1 = torch.empty(s1.N, device=DEV)
+    eng = M.Engine(1 << 30)
+    t0 = eng.submit(geo0, y0, sig0, n0, x0)
+    t1 = eng.submit(geo1, y1, sig1, n1, x1)
+    eng.run_until_idle()
+    torch.cuda.synchronize()
+    assert eng.poll(t0) == M.Engine.DONE and eng.poll(t1) == M.Engine.DONE
+    assert np.array_equal(x0.cpu().numpy(), single(geo0, y0, sig0, n0)[0])
+    assert np.array_equal(x1.cpu().numpy(), single(geo1, y1, sig1, n1)[0])
+    eng.close()
+    geo1.close()
+
+
 def test_admission_waits_for_memory_and_refuses_oversize(problems):
     s, geo, y, sig, _, _ = problems[0]
     x1 = torch.empty(s.N, device=DEV)
