@@ -422,9 +422,11 @@ def run_gpu(args):
                     "algorithmic_bytes_per_launch": smem_bytes, "taps_per_launch": taps, "active_pairs": pairs,
                     "forward_ms": fwd_ms, "backproject_ms": bwd_ms}
 
-    # per iteration: A^T r and its reduction, prior gradient, PR+ scalars, direction, A x, projection, step,
-    # update; per reconstruction one projection of y first
-    launches = args.steps * (9 * scene.n_iter + 1)
+    # per iteration: A^T r (tensor cores: max |e|, the pool, the fixed-point sums into b; CUDA cores: the
+    # partial images and their reduction), prior gradient, PR+ scalars, direction, A x, projection, step,
+    # update; per reconstruction the projection of y and the residual's sum of squares first
+    per_iter = (3 if geo.info.adjoint_tensor_cores else 2) + 7
+    launches = args.steps * (per_iter * scene.n_iter + 2)
 
     out = {"metric": "recons/s", "value": value, "unit": "recons/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
