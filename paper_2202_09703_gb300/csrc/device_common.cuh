@@ -102,6 +102,14 @@ __device__ __forceinline__ void prefetch_l2_range(const void* p, size_t bytes, i
     }
 }
 
+// *p += v in global memory as a reduction that returns nothing: the address is taken into the global window
+// explicitly, so a pointer read from memory (a generic pointer to the compiler) still gets the
+// fire-and-forget form rather than an atomic that waits for the old value.
+__device__ __forceinline__ void red_add_global_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;

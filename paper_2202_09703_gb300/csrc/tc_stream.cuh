@@ -429,7 +429,7 @@ struct TbView {
     int* counter;
 };
 
-constexpr int kTbUnroll = 4;     // records per thread in one batch (two batches in flight)
+constexpr int kTbUnroll = 4;     // records per thread in one batch (two batches in flight), by default
 
 // Scale exponent s of the adjoint's fixed-point sums: every contribution is at most bound / K x max|e| in
 // magnitude and a pixel has at most one per A-scan, so with s = 61 - (exponents of bound and max|e|) no
@@ -451,17 +451,19 @@ __device__ __forceinline__ float tcs_finish_pixel(unsigned long long a, unsigned
     return __ll2float_rn((long long)a) * ts_pow2(-tc_fixed_exponent(emax_bits, bound));
 }
 
-// A batch of records held in registers: records rb + u * kTsThreads + tid, u < kTbUnroll.
+// A batch of records held in registers: records rb + u * kTsThreads + tid, u < U.
+template <int U>
 struct TbBatch {
-    int2 key[kTbUnroll];
-    float4 w[kTbUnroll];
+    int2 key[U];
+    float4 w[U];
 };
 
-__device__ __forceinline__ void tb_load(TbBatch& b, const int2* __restrict__ rkey, const float4* __restrict__ rw,
+template <int U>
+__device__ __forceinline__ void tb_load(TbBatch<U>& b, const int2* __restrict__ rkey, const float4* __restrict__ rw,
                                         long long base, int rb, int r1, int tid)
 {
 #pragma unroll
-    for (int u = 0; u < kTbUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
         const int r = rb + u * kTsThreads + tid;
         if (r < r1) {
             b.key[u] = __ldg(rkey + base + r);
@@ -471,7 +473,7 @@ __device__ __forceinline__ void tb_load(TbBatch& b, const int2* __restrict__ rke
 }
 
 // Drains the A^T items of V (header as for tcs_forward_pool; kTsCols tensor-memory columns).
-template <bool BF16>
+template <bool BF16, int U = kTbUnroll>
 __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char* smem, uint32_t tmem,
                                                  uint32_t& mphase, uint32_t& bphase, int* status)
 {
@@ -590,7 +592,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         const int r0 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc);
         const int r1 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc + 1);
         // the first records of this item and the next item's window load during the products
-        TbBatch ba, bb;
+        TbBatch<U> ba, bb;
         tb_load(ba, rkey, rw, base, r0, r1, tid);
         const float ew = nxt < nitems ? load_e(nxt) : 0.0f;
         float* sEc = sE0 + cbuf * T.ewin;
@@ -632,9 +634,9 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         if (live_cur) {
             const int ts = tc * kTsTile;
             const float* Cb = sC - c_lo;
-            auto run = [&](const TbBatch& bt, int rb) {
+            auto run = [&](const TbBatch<U>& bt, int rb) {
 #pragma unroll
-                for (int u = 0; u < kTbUnroll; ++u) {
+                for (int u = 0; u < U; ++u) {
                     const int r = rb + u * kTsThreads + tid;
                     if (r >= r1) continue;
                     const int n0r = (bt.key[u].y >> kRecShift) - ts, trow = (bt.key[u].y >> 1) & 0xfff;
@@ -653,10 +655,10 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
                         else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
                         v -= (bt.w[u].z * tl.x + bt.w[u].w * tl.y) * sEc[n0r + P.Tw - 1];
                     }
-                    atomicAdd(acc + (bt.key[u].x & kRecPixel), (unsigned long long)__float2ll_rn(v * fsc));
+                    red_add_global_u64(acc + (bt.key[u].x & kRecPixel), (unsigned long long)__float2ll_rn(v * fsc));
                 }
             };
-            constexpr int kStep = kTbUnroll * kTsThreads;
+            constexpr int kStep = U * kTsThreads;
             for (int rb = r0; rb < r1; rb += 2 * kStep) {
                 if (rb + kStep < r1) tb_load(bb, rkey, rw, base, rb + kStep, r1, tid);
                 run(ba, rb);
