@@ -175,7 +175,7 @@ void free_geometry(mbir_geometry* g)
                     g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_win_order, g->d_win_counter,
                     g->d_bwd_counter, g->d_tc_tile, g->w_tc_acc,
                     g->d_tc_counter, g->d_tf_order, g->d_tf_counter, g->w_colnorm,
-                    g->d_tf4_bop, g->d_tf4_crange, g->d_tf4_split, g->d_tb4_bop};
+                    g->d_tf4_bop, g->d_tf4_crange, g->d_tf4_split, g->d_tb4_bop, g->d_tf_view, g->d_tb_view};
     for (void* p : ptrs) if (p) cudaFree(p);
     mbir::free_icd_lists(g);
     if (g->icd_stream) cudaStreamDestroy((cudaStream_t)g->icd_stream);

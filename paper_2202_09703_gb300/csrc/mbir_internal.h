@@ -305,6 +305,8 @@ __device__ __forceinline__ Pair make_pair(const GeomParams& P, const Leg& tx, co
 
 // Host-side launchers (apply.cu / map.cu)
 struct GeomDev;
+struct TsView;             // tensor-core apply views (tc_stream.cuh)
+struct TbView;
 }  // namespace mbir
 
 // The geometry handle (opaque in the C ABI).
@@ -405,6 +407,8 @@ struct mbir_geometry {
     float tc_bound;        // scale bound of the fixed-point sums (build_tc_adjoint)
     int* d_tc_counter;
     // tensor-core A x (see tc_stream.cuh, tc_fwd_stream.cu)
+    mbir::TsView* d_tf_view;   // fwd_tcs_kernel's view without the per-call fields (device memory)
+    mbir::TbView* d_tb_view;   // bwd_tcs_kernel's view without the residual (device memory)
     int* d_tf_order;       // A-scans by decreasing record count
     int* d_tf_counter;
     Tf4Layout tf4;

@@ -169,13 +169,19 @@ Tb4Layout tb4_layout(const GeomParams& P, int kwmax)
     return L;
 }
 
+// The view is read from device memory (written at set-up) with the residual as a parameter, as for the
+// tensor-core A x (fwd_tcs_kernel).
 template <bool BF16>
-__global__ void __launch_bounds__(kTsThreads, 1) bwd_tcs_kernel(TbView V, int* __restrict__ status)
+__global__ void __launch_bounds__(kTsThreads, 1)
+    bwd_tcs_kernel(const TbView* __restrict__ base, const void* e, int* __restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     tc_header_init(smem, kTsCols);
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + 8);
     uint32_t mphase = 0, bphase = 0;
+    TbView V = *base;
+    asm volatile("" : "+l"(e));
+    V.e = e;
     tcs_adjoint_pool<BF16>(V, smem, tmem, mphase, bphase, status);
     tc_header_release(smem, tmem, kTsCols);
 }
@@ -225,15 +231,28 @@ cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st)
                 }
     }
     uint4* d_b = nullptr;
+    TbView* d_view = nullptr;
     cudaError_t e = cudaMalloc((void**)&d_b, L.bbytes);
     if (e == cudaSuccess) e = cudaMemcpy(d_b, img.data(), L.bbytes, cudaMemcpyHostToDevice);
+    // the kernel's view without the residual
+    if (e == cudaSuccess) {
+        const int N = P.W * P.H;
+        const void* tab = P.precision == MBIR_PREC_BF16 ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
+        const TbView V{P, L, d_b, tab, nullptr, g->d_rec_off, g->d_tc_tile, g->d_tf4_crange, g->d_rec_key,
+                       g->d_rec_w, g->w_tc_acc, reinterpret_cast<const unsigned int*>(g->w_tc_acc + N),
+                       g->tc_bound, g->d_tc_counter};
+        e = cudaMalloc((void**)&d_view, sizeof(TbView));
+        if (e == cudaSuccess) e = cudaMemcpy(d_view, &V, sizeof(TbView), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(d_b);
+        cudaFree(d_view);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
     g->tb4 = L;
     g->d_tb4_bop = d_b;
+    g->d_tb_view = d_view;
     g->bytes += L.bbytes;
     return cudaSuccess;
 }
@@ -262,9 +281,7 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     else tc_emax_kernel<float><<<eg, 256, 0, st>>>(e_pad, ne, emax);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
-    TbView V{P, L, g->d_tb4_bop, tab, e, g->d_rec_off, g->d_tc_tile, g->d_tf4_crange, g->d_rec_key, g->d_rec_w,
-             g->w_tc_acc, emax, g->tc_bound, g->d_tc_counter};
-    kern<<<grid, kTsThreads, L.smem, st>>>(V, g->d_status);
+    kern<<<grid, kTsThreads, L.smem, st>>>(g->d_tb_view, e, g->d_status);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
     tc_finish_kernel<<<std::max(1, std::min((N + 255) / 256, g->n_sm * 8)), 256, 0, st>>>(N, g->w_tc_acc, emax,
