@@ -409,7 +409,9 @@ def run_gpu(args):
                     "traffic_note": "DRAM read+write bytes per launch: ncu capture of the 256x512 workload scaled "
                                     "by active pairs; null if the kernel changed since",
                     "peak_source": f"hbm_gbs ({src})", "algorithmic_bytes_per_launch": rec_bytes,
-                    "bytes_per_pair_minimum": 12, "active_pairs": pairs, "taps_per_launch": taps,
+                    "bytes_per_pair_minimum": 12,
+                    "bytes_per_pair_stored": geo.info.record_bytes / max(geo.info.n_records, 1), "active_pairs": pairs,
+                    "taps_per_launch": taps,
                     "forward_ms": fwd_ms, "backproject_ms": bwd_ms,
                     "forward_frac": (12.0 * pairs + algo_bytes) / (fwd_ms * 1e-3) / 1e9 / hbm_peak,
                     "backproject_frac": (12.0 * pairs + algo_bytes) / (bwd_ms * 1e-3) / 1e9 / hbm_peak}
@@ -475,6 +477,7 @@ def run_extras(args, M, S, torch, np, scene, geo, y, sigma, x_true, x_fp32, flus
     fwd, bwd = apply_times(torch, geo, scene, dev)
     ex["fp32_apply_ms"] = {"forward": fwd, "backproject": bwd}
     ex["fp32_geometry_bytes"] = geo.nbytes
+    ex["fp32_record_bytes_per_pair"] = geo.info.record_bytes / max(geo.info.n_records, 1)
     geo.close()                                  # the headline's tables go before the next geometries
     torch.cuda.empty_cache()
     # BF16 storage form: same data rounded to BF16, same sigma
@@ -483,6 +486,7 @@ def run_extras(args, M, S, torch, np, scene, geo, y, sigma, x_true, x_fp32, flus
     torch.cuda.synchronize()
     g16_ms = 1e3 * (time.perf_counter() - t0)
     ex["bf16_geometry_bytes"] = g16.nbytes
+    ex["bf16_record_bytes_per_pair"] = g16.info.record_bytes / max(g16.info.n_records, 1)
     x16 = torch.empty(scene.N, dtype=torch.float32, device=dev)
     lat16 = timed_reconstructions(torch, g16, y.to(torch.bfloat16), sigma, scene.n_iter, x16, steps, 1, flush,
                                   stream)

@@ -167,12 +167,15 @@ typedef struct {
     int mode;                    /* resolved mbir_mode (OTF or TAB) */
     int precision;
     int64_t device_bytes;        /* tables + workspace held by the handle */
-    int forward_window_spans;    /* TAB records: 32-sample spans per work unit of the CUDA-core A x, else 0 */
+    int forward_window_spans;    /* sorted TAB records (CUDA-core A x): 32-sample spans per work unit, else 0 */
     double forward_window_ms[3]; /* CUDA-core A x times for windows of 1, 2 and 4 spans, measured at creation
                                   * when that kernel is the geometry's A x (0 otherwise) */
     int adjoint_groups;          /* transmitter groups of the CUDA-core A^T r work items */
     int adjoint_tensor_cores;    /* 1 if A^T runs on the tensor cores (see MBIR_FLAG_NO_TENSOR_CORES) */
     int forward_tensor_cores;    /* 1 if A x runs on the tensor cores */
+    int64_t n_records;           /* TAB records: active (pixel, A-scan) pairs held, else 0 */
+    int64_t record_bytes;        /* bytes of the record list as held: 24 per pair sorted (CUDA-core A x),
+                                  * 16 (FP32 form) or 12 (BF16 form) packed for the tensor cores */
 } mbir_geometry_info;
 
 typedef struct mbir_geometry mbir_geometry;
@@ -204,7 +207,9 @@ int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info);
  * A tuning control with no counterpart in the paper; the output bits do not
  * depend on it.  Synchronises the device; the handle must not be in use by
  * another call or an engine.  Errors: MBIR_ERR_INVALID_ARG (other values),
- * MBIR_ERR_UNSUPPORTED (no record list), MBIR_ERR_OOM, MBIR_ERR_CUDA. */
+ * MBIR_ERR_UNSUPPORTED (no sorted record list: OTF mode, or a geometry whose
+ * A x runs on the tensor cores, which keeps only the packed records),
+ * MBIR_ERR_OOM, MBIR_ERR_CUDA. */
 int mbir_set_forward_window(mbir_geometry* g, int spans);
 
 /* y = A x (eq. 11-13 summed over voxels).  x_dev: N floats.  y_dev: K x M,

@@ -10,6 +10,20 @@ constexpr int kRecShift = 13;                     // record key: n0 << 13 | tabl
 constexpr int kRecPixel = 0x7fffffff;             // record pixel field: pixel index (bit 31: a batch mark of the
                                                   // tensor-core A x, set at its set-up)
 
+// The pair of A-scan k and pixel v in TAB mode (legs from the table, eq. 4-6 and 12): true when it is
+// active, i.e. its weight is non-zero and its first tap n0 + 1 lies inside the record.
+__device__ __forceinline__ bool tab_pair(const GeomParams& P, const DevPtrs& D, int k, int v, Pair& pr)
+{
+    const int row = v / P.W, col = v - row * P.W;
+    const RowInfo ri = load_row(D.rows, row);
+    if (!(ri.tvert < (float)(P.M - 1))) return false;
+    const int i = k / P.n_rx;
+    const Leg tx = get_leg<1, kModeTAB>(P, D, ri, row, col, __ldg(D.txpos + i));
+    const Leg rx = get_leg<1, kModeTAB>(P, D, ri, row, col, __ldg(D.rxpos + k));
+    pr = make_pair(P, tx, rx, ri.tau);
+    return pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M;
+}
+
 // Copies a pulse table (tab_bytes, a multiple of 16) into shared memory.
 __device__ __forceinline__ void load_table_smem(void* dst, const void* src, size_t tab_bytes, int tid, int nthreads)
 {

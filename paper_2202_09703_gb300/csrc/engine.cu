@@ -68,8 +68,10 @@ struct ReqDesc {
     const float2* tab;
     const __nv_bfloat162* tab_bf;
     const long long* rec_off;
-    const int2* rkey;
+    const int2* rkey;      // sorted records (CUDA-core A d)
     const float4* rw;
+    const uint2* tkey;     // packed records (tensor-core applies)
+    const void* tw;
     const int2* runs;
     const float* direct;
     const float* dinv;
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
             if (!R.tc || !eng_pool_live(L.pool, rq, 1, nitems, flag)) continue;
             const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
             const void* e = BF16 ? (const void*)R.ebf : (const void*)R.e;
-            const TbView V{R.P, R.tb4l, R.tb4_bop, tab, e, R.rec_off, R.tc_tile, R.tf4_crange, R.rkey, R.rw,
+            const TbView V{R.P, R.tb4l, R.tb4_bop, tab, e, R.rec_off, R.tc_tile, R.tf4_crange, R.tkey, R.tw,
                            R.tc_acc, reinterpret_cast<const unsigned int*>(L.pool + 3 * rq + 2), R.tc_bound,
                            L.pool + 3 * rq + 1};
             if (!tcs_adjoint_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_fwd_tcs_kernel(EngLists L)
             const ReqDesc& R = L.desc[rq];
             if (!R.tcs || !eng_pool_live(L.pool, rq, 0, R.P.K, flag)) continue;
             const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
-            const TsView V{R.P, R.tf4l, R.tf4_bop, tab, R.rec_off, R.tf4_crange, R.tf4_split, R.rkey, R.rw,
+            const TsView V{R.P, R.tf4l, R.tf4_bop, tab, R.rec_off, R.tf4_crange, R.tf4_split, R.tkey, R.tw,
                            R.tf_order, dnew_of(R), R.q, 0, R.P.Mp, L.pool + 3 * rq};
             if (!tcs_forward_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
             __syncthreads();
@@ -738,6 +740,8 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.rec_off = g->d_rec_off;
     d.rkey = g->d_rec_key;
     d.rw = g->d_rec_w;
+    d.tkey = g->d_tc_key;
+    d.tw = g->d_tc_w;
     d.runs = g->d_runs;
     d.direct = g->d_direct;
     d.dinv = g->d_dinv;
@@ -973,7 +977,7 @@ int mbir_engine_submit(mbir_engine* E, const mbir_geometry* g, const void* y_dev
                        float* x_dev, float* g_dev, int64_t* ticket)
 {
     if (!E || !g || !y_dev || !x_dev || !ticket || n_iter < 1 || !prior_is_valid(pr)) return MBIR_ERR_INVALID_ARG;
-    if (g->P.mode != MBIR_MODE_TAB || !g->d_rec_key || !g->h_win_cost) return MBIR_ERR_UNSUPPORTED;
+    if (g->P.mode != MBIR_MODE_TAB || !(g->d_rec_key || g->d_tc_key) || !g->h_win_cost) return MBIR_ERR_UNSUPPORTED;
     const size_t tsz = g->P.precision == MBIR_PREC_BF16 ? 4 : 8;
     const size_t tab = ((size_t)g->P.Gt * (g->P.Q + 1) * table_stride(g->P.Tw4) * tsz + 127) & ~(size_t)127;
     const size_t eb = ((size_t)g->P.Mp * (g->P.precision == MBIR_PREC_BF16 ? 2 : 4) + 127) & ~(size_t)127;

@@ -34,16 +34,9 @@ struct RecPair {
 __device__ __forceinline__ RecPair tab_record(const GeomParams& P, const DevPtrs& D, int k, int v)
 {
     RecPair o;
-    o.act = false;
-    const int row = v / P.W, col = v - row * P.W;
-    const RowInfo ri = load_row(D.rows, row);
-    if (!(ri.tvert < (float)(P.M - 1))) return o;
-    const int i = k / P.n_rx;
-    const Leg tx = get_leg<1, kModeTAB>(P, D, ri, row, col, __ldg(D.txpos + i));
-    const Leg rx = get_leg<1, kModeTAB>(P, D, ri, row, col, __ldg(D.rxpos + k));
-    const Pair pr = make_pair(P, tx, rx, ri.tau);
-    if (!(pr.w != 0.0f && pr.n0 >= 0 && pr.n0 + 1 < P.M)) return o;
-    o.act = true;
+    Pair pr;
+    o.act = tab_pair(P, D, k, v, pr);
+    if (!o.act) return o;
     o.n0 = pr.n0;
     o.trow = pr.gi * (P.Q + 1) + pr.r;
     o.flag = pr.flag0 ? 1 : 0;

@@ -172,7 +172,7 @@ void free_geometry(mbir_geometry* g)
                     g->d_legs, g->d_hidx, g->d_direct, g->d_dinv, g->d_status, g->w_e, g->w_q,
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
                     g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
-                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_runs, g->d_win_order, g->d_win_counter,
+                    g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_key, g->d_tc_w, g->d_runs, g->d_win_order, g->d_win_counter,
                     g->d_bwd_counter, g->d_tc_tile, g->w_tc_acc,
                     g->d_tc_counter, g->d_tf_order, g->d_tf_counter, g->w_colnorm,
                     g->d_tf4_bop, g->d_tf4_crange, g->d_tf4_split, g->d_tb4_bop, g->d_tf_view, g->d_tb_view};
@@ -596,6 +596,11 @@ int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info)
     info->adjoint_groups = g->n_groups;
     info->adjoint_tensor_cores = g->d_tb4_bop ? 1 : 0;
     info->forward_tensor_cores = g->d_tf4_bop ? 1 : 0;
+    const bool has_rec = g->d_rec_key || g->d_tc_key;
+    info->n_records = has_rec ? g->n_records : 0;
+    const size_t per = g->d_tc_key ? sizeof(uint2) + (g->P.precision == MBIR_PREC_BF16 ? 4 : 8)
+                                   : sizeof(int2) + sizeof(float4);
+    info->record_bytes = has_rec ? (int64_t)(per * (size_t)g->n_records) : 0;
     return MBIR_OK;
 }
 

@@ -152,7 +152,7 @@ cudaError_t build_icd_lists(mbir_geometry* g, int s, cudaStream_t st)
     g->bytes += g->icd_bytes;
     g->icd_s = s;
     // per-colour record lists up to 64 x 64 colours (their span bounds grow with the colour count)
-    if (g->d_rec_key && nc <= 4096) {
+    if ((g->d_rec_key || g->d_tc_key) && nc <= 4096) {
         e = build_colour_records(g, s, st);
         if (e == cudaSuccess) g->bytes += g->icd_rec_bytes;
         else if (e == cudaErrorMemoryAllocation) {

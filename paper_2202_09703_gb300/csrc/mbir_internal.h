@@ -389,10 +389,13 @@ struct mbir_geometry {
     int* d_bwd_counter;    // work counter of the A^T r launch
     float* h_bwd_cost;     // host copy: estimated A^T r cost per (16-row tile, 32-column tile, Tx position)
     int bwd_ntc;           // 32-column tiles per row of tiles
-    // TAB-mode A x records sorted by first tap sample (see forward_tab.cu)
+    // TAB-mode A x records sorted by first tap sample (see forward_tab.cu); with the tensor-core applies the
+    // sorted records are replaced by their packed form (tc_apply.cuh), on the same per-A-scan offsets
     long long* d_rec_off;
     int2* d_rec_key;
     float4* d_rec_w;
+    uint2* d_tc_key;       // packed records: keys
+    void* d_tc_w;          // and weights (uint2 in the FP32 form, uint32 in the BF16 form)
     int2* d_runs;
     int fwd_sub;           // 32-sample spans per A x window (autotuned)
     double fwd_tune_ms[3]; // measured A x times of windows of 1, 2, 4 spans

@@ -40,14 +40,13 @@ __global__ void tc_finish_kernel(int N, const unsigned long long* __restrict__ a
         b[v] = tcs_finish_pixel(acc[v], eb, bound);
 }
 
-// *wmax = bits of the largest sum of a record's four weights' magnitudes
-__global__ void tc_wmax_kernel(const float4* __restrict__ rw, long long n, unsigned int* __restrict__ wmax)
+// *wmax = bits of the largest record weight w (the four bilinear corners are non-negative and sum to w)
+template <typename WT>
+__global__ void tc_wmax_kernel(const WT* __restrict__ rw, long long n, unsigned int* __restrict__ wmax)
 {
     unsigned int m = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float4 w = rw[i];
-        m = max(m, __float_as_uint((fabsf(w.x) + fabsf(w.y)) + (fabsf(w.z) + fabsf(w.w))));
-    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(tc_rec_w(rw[i]))));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m) atomicMax(wmax, m);
@@ -56,7 +55,7 @@ __global__ void tc_wmax_kernel(const float4* __restrict__ rw, long long n, unsig
 // first record of every 128-sample tile of every A-scan (records grouped by tile, n0 ascending from tile to
 // tile)
 __global__ void tc_tile_off_kernel(GeomParams P, int ntile, const long long* __restrict__ rec_off,
-                                   const int2* __restrict__ rkey, int* __restrict__ tile_off)
+                                   const uint2* __restrict__ rkey, int* __restrict__ tile_off)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)P.K * (ntile + 1)) return;
@@ -66,20 +65,20 @@ __global__ void tc_tile_off_kernel(GeomParams P, int ntile, const long long* __r
     const int target = t * kTsTile;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if ((rkey[base + mid].y >> kRecShift) < target) lo = mid + 1;
+        if (tc_rec_n0(rkey[base + mid]) < target) lo = mid + 1;
         else hi = mid;
     }
     tile_off[i] = lo;
 }
 
 // First record of every tile, the per-pixel accumulators (N sums and the max |e| word after them, zeroed)
-// and the bound of the fixed-point scale: K x the largest record weight sum x (the largest table row sum
+// and the bound of the fixed-point scale: K x the largest record weight w x (the largest table row sum
 // of |T| + the largest |T|, for the tau = t0 tap), doubled for the rounding of the products;
 // cudaErrorNotSupported keeps the CUDA-core adjoint.
 cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
 {
     const GeomParams& P = g->P;
-    if (!g->d_rec_key || g->n_records <= 0) return cudaErrorNotSupported;
+    if (!g->d_tc_key || g->n_records <= 0) return cudaErrorNotSupported;
     const int N = P.W * P.H;
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
     int* d_tile = nullptr;
@@ -91,13 +90,18 @@ cudaError_t build_tc_adjoint(mbir_geometry* g, cudaStream_t st)
     if (e == cudaSuccess) e = cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long) * ((size_t)N + 1), st);
     if (e == cudaSuccess) {
         const long long items = (long long)P.K * (ntile + 1);
-        tc_tile_off_kernel<<<(int)((items + 255) / 256), 256, 0, st>>>(P, ntile, g->d_rec_off, g->d_rec_key, d_tile);
+        tc_tile_off_kernel<<<(int)((items + 255) / 256), 256, 0, st>>>(P, ntile, g->d_rec_off, g->d_tc_key, d_tile);
         e = cudaGetLastError();
     }
     unsigned int wbits = 0;
     if (e == cudaSuccess) {
         unsigned int* d_wmax = reinterpret_cast<unsigned int*>(d_acc + N);
-        tc_wmax_kernel<<<std::max(1, g->n_sm * 8), 256, 0, st>>>(g->d_rec_w, g->n_records, d_wmax);
+        if (P.precision == MBIR_PREC_BF16)
+            tc_wmax_kernel<<<std::max(1, g->n_sm * 8), 256, 0, st>>>(reinterpret_cast<const uint32_t*>(g->d_tc_w),
+                                                                     g->n_records, d_wmax);
+        else
+            tc_wmax_kernel<<<std::max(1, g->n_sm * 8), 256, 0, st>>>(reinterpret_cast<const uint2*>(g->d_tc_w),
+                                                                     g->n_records, d_wmax);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&wbits, d_wmax, sizeof(wbits), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_wmax, 0, sizeof(unsigned long long), st);
@@ -238,8 +242,8 @@ cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st)
     if (e == cudaSuccess) {
         const int N = P.W * P.H;
         const void* tab = P.precision == MBIR_PREC_BF16 ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
-        const TbView V{P, L, d_b, tab, nullptr, g->d_rec_off, g->d_tc_tile, g->d_tf4_crange, g->d_rec_key,
-                       g->d_rec_w, g->w_tc_acc, reinterpret_cast<const unsigned int*>(g->w_tc_acc + N),
+        const TbView V{P, L, d_b, tab, nullptr, g->d_rec_off, g->d_tc_tile, g->d_tf4_crange, g->d_tc_key,
+                       g->d_tc_w, g->w_tc_acc, reinterpret_cast<const unsigned int*>(g->w_tc_acc + N),
                        g->tc_bound, g->d_tc_counter};
         e = cudaMalloc((void**)&d_view, sizeof(TbView));
         if (e == cudaSuccess) e = cudaMemcpy(d_view, &V, sizeof(TbView), cudaMemcpyHostToDevice);

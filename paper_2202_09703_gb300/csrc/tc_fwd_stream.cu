@@ -29,7 +29,8 @@ Tf4Layout tf4_layout(const GeomParams& P, int kwmax)
     L.smem = L.off_y + (size_t)L.ylen * 4;
     L.ok = L.R >= 2 && L.ntap <= 128 && L.ntap / 4 <= 32 && L.kwmax >= 16 && L.kwmax % 16 == 0 &&
            L.parts * L.kwmax / 2 <= (int)kTsDCol && L.smem <= 227 * 1024 && L.bbytes < (1u << 20) &&
-           P.G * L.R <= 4096 && (long long)P.K * (P.M + 1) < (1LL << 31);
+           P.G * L.R <= kTcMaxRows && P.M <= kTcMaxSamples && (long long)P.W * P.H <= kTcMaxPixels &&
+           (long long)P.K * (P.M + 1) < (1LL << 31);
     return L;
 }
 
@@ -128,42 +129,55 @@ __global__ void ts_tiles_kernel(GeomParams P, int R, int kb, const long long* __
     }
 }
 
-// The records of every warp part interleaved: batch b (stored positions 32 b .. 32 b + 31 of the part) takes
-// the part's sorted records b, b + q, b + 2 q, ... (q = its length / 32; the first length % 32 lanes hold
-// one more), so records of one (n0, table row), adjacent in sorted order, seldom share a batch, and where
-// they do they sit in adjacent lanes as the segmented sums require.  The sorted records of A-scans
-// k0 .. k0 + gridDim.x / ntile - 1 come from a copy whose first record is record src0.
-__global__ void ts_interleave_kernel(GeomParams P, int k0, const long long* __restrict__ rec_off,
-                                     const int* __restrict__ split, long long src0, const int2* __restrict__ tkey,
-                                     const float4* __restrict__ tw, int2* __restrict__ key, float4* __restrict__ w)
-{
-    const int ntile = (P.M + kTsTile - 1) / kTsTile;
-    const int k = k0 + (int)(blockIdx.x / ntile), t = (int)(blockIdx.x % ntile);
-    const int* sp = split + ((size_t)k * ntile + t) * kTsSplit;
-    const long long base = rec_off[k];
-    for (int p = 0; p < kTsWarps; ++p) {
-        const int a = sp[p], len = sp[p + 1] - a;
-        const int q = len >> 5, r = len & 31;
-        for (int s = threadIdx.x; s < len; s += blockDim.x) {
-            const int l = s & 31, o = l * q + min(l, r) + (s >> 5);
-            key[base + a + s] = tkey[base + a + o - src0];
-            w[base + a + s] = tw[base + a + o - src0];
-        }
-    }
-}
-
-// Marks every batch of 32 records (per warp part, as the kernel reads them) whose lanes' four corner cells
-// (n0, table row), (n0, next plane's row), (n0, row + 1), (n0, next plane's row + 1) are all distinct between
-// lanes: bit 31 of the pixel field of the batch's first record.  Such a batch has no equal keys, so the
-// kernel adds its corners without the segmented sums and in one step.  Warp per batch, blocks per
-// (A-scan, tile).
-__global__ void ts_batch_flag_kernel(GeomParams P, int R, const long long* __restrict__ rec_off,
-                                     const int* __restrict__ split, int2* __restrict__ key)
+// The records of every warp part interleaved and packed (tc_apply.cuh): batch b of a part (stored positions
+// 32 b .. 32 b + 31) takes the part's sorted records b, b + q, b + 2 q, ... (q = its length / 32; the first
+// length % 32 lanes hold one more), so records of one (n0, table row), adjacent in sorted order, seldom share
+// a batch, and where they do they sit in adjacent lanes as the segmented sums require.  Each record's pair
+// quantities are evaluated again from the legs, as when the records were sorted (tab_pair), so the packed
+// fractions come from the delay and attenuation coordinates themselves.  Block per (A-scan, tile).
+template <bool BF16>
+__global__ void ts_pack_kernel(GeomParams P, DevPtrs D, const long long* __restrict__ rec_off,
+                               const int* __restrict__ split, const int2* __restrict__ skey,
+                               uint2* __restrict__ key, typename TcW<BF16>::type* __restrict__ w)
 {
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
     const int k = (int)(blockIdx.x / ntile), t = (int)(blockIdx.x % ntile);
     const int* sp = split + ((size_t)k * ntile + t) * kTsSplit;
     const long long base = rec_off[k];
+    const int R = P.Q + 1;
+    for (int p = 0; p < kTsWarps; ++p) {
+        const int a = sp[p], len = sp[p + 1] - a;
+        const int q = len >> 5, r = len & 31;
+        for (int s = threadIdx.x; s < len; s += blockDim.x) {
+            const int l = s & 31, o = l * q + min(l, r) + (s >> 5);
+            const int v = skey[base + a + o].x & kRecPixel;
+            Pair pr;
+            typename TcW<BF16>::type pw;
+            if (tab_pair(P, D, k, v, pr)) {
+                key[base + a + s] = tc_pack_key(v, pr.gi * R + pr.r, pr);
+                tc_pack_w(pr, pw);
+            } else {
+                // (not reached: the record was made from the same active pair) a zero-weight record
+                key[base + a + s] = make_uint2((uint32_t)v, (uint32_t)(t * kTsTile) << kTcN0Shift);
+                pw = typename TcW<BF16>::type{};
+            }
+            w[base + a + s] = pw;
+        }
+    }
+}
+
+// Marks every batch of 32 records (per warp part, as the kernel reads them) whose lanes' four corner cells
+// (n0, row), (n0, row + dR), (n0, row + 1), (n0, row + dR + 1) are all distinct between lanes: bit 31 of
+// key.x of the batch's first record.  Such a batch has no equal keys, so the kernel adds its corners without
+// the segmented sums and in one step.  Warp per batch, blocks per (A-scan, tile).
+__global__ void ts_batch_flag_kernel(GeomParams P, int R, const long long* __restrict__ rec_off,
+                                     const int* __restrict__ split, uint2* __restrict__ key)
+{
+    const int ntile = (P.M + kTsTile - 1) / kTsTile;
+    const int k = (int)(blockIdx.x / ntile), t = (int)(blockIdx.x % ntile);
+    const int* sp = split + ((size_t)k * ntile + t) * kTsSplit;
+    const long long base = rec_off[k];
+    const int dR = P.G > 1 ? R : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t full = 0xffffffffu;
     for (int p = 0; p < kTsWarps; ++p) {
@@ -172,11 +186,10 @@ __global__ void ts_batch_flag_kernel(GeomParams P, int R, const long long* __res
             const int r = b + lane;
             int c[4];
             if (r < z) {
-                const int y = key[base + r].y;
-                const int n0 = y >> kRecShift, trow = (y >> 1) & 0xfff, gi = trow / R;
-                const int c1 = min(gi + 1, P.G - 1) * R + (trow - gi * R);
+                const uint2 kk = key[base + r];
+                const int n0 = tc_rec_n0(kk), trow = tc_rec_row(kk);
                 c[0] = (n0 << 13) | trow;
-                c[1] = (n0 << 13) | c1;
+                c[1] = (n0 << 13) | (trow + dR);
                 c[2] = c[0] + 1;
                 c[3] = c[1] + 1;
             } else {
@@ -191,51 +204,9 @@ __global__ void ts_batch_flag_kernel(GeomParams P, int R, const long long* __res
                     clash |= (o == c[0]) | (o == c[1]) | (o == c[2]) | (o == c[3]);
                 }
             }
-            if (!__any_sync(full, clash) && lane == 0) key[base + b].x |= (int)0x80000000;
+            if (!__any_sync(full, clash) && lane == 0) key[base + b].x |= kTcMark;
         }
     }
-}
-
-// Interleaves the records of every warp part (ts_interleave_kernel) through a temporary copy of up to about
-// 256 MB of A-scans at a time; without room for the copy the records keep their sorted order, which the
-// kernel takes as well.
-static cudaError_t interleave_records(mbir_geometry* g, const std::vector<long long>& roff, const int* d_sp,
-                                      cudaStream_t st)
-{
-    const GeomParams& P = g->P;
-    const int ntile = (P.M + kTsTile - 1) / kTsTile;
-    long long cap = ((long long)256 << 20) / (long long)(sizeof(int2) + sizeof(float4));
-    for (int k = 0; k < P.K; ++k) cap = std::max(cap, roff[k + 1] - roff[k]);
-    cap = std::min(cap, g->n_records);
-    int2* tkey = nullptr;
-    float4* tw = nullptr;
-    if (cudaMalloc((void**)&tkey, sizeof(int2) * (size_t)cap) != cudaSuccess ||
-        cudaMalloc((void**)&tw, sizeof(float4) * (size_t)cap) != cudaSuccess) {
-        cudaFree(tkey);
-        cudaGetLastError();
-        return cudaSuccess;
-    }
-    cudaError_t e = cudaSuccess;
-    for (int k0 = 0; k0 < P.K && e == cudaSuccess;) {
-        int k1 = k0 + 1;
-        while (k1 < P.K && roff[k1 + 1] - roff[k0] <= cap) ++k1;
-        const size_t n = (size_t)(roff[k1] - roff[k0]);
-        if (n > 0) {
-            e = cudaMemcpyAsync(tkey, g->d_rec_key + roff[k0], sizeof(int2) * n, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(tw, g->d_rec_w + roff[k0], sizeof(float4) * n, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess) {
-                ts_interleave_kernel<<<(k1 - k0) * ntile, 256, 0, st>>>(P, k0, g->d_rec_off, d_sp, roff[k0], tkey, tw,
-                                                                        g->d_rec_key, g->d_rec_w);
-                e = cudaGetLastError();
-            }
-        }
-        k0 = k1;
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(tkey);
-    cudaFree(tw);
-    return e;
 }
 
 // Tables of the tensor-core A x for a geometry with records: the A-scan order, the per-tile column ranges and
@@ -322,29 +293,54 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
         e = cudaMalloc((void**)&d_b, L.bbytes);
         if (e == cudaSuccess) e = cudaMemcpy(d_b, img.data(), L.bbytes, cudaMemcpyHostToDevice);
     }
-    // the kernel's view without the per-call fields
-    TsView* d_view = nullptr;
+    // the packed records (16 B per pair in the FP32 form, 12 B in the BF16 form), interleaved within every warp
+    // part and carrying the batch marks; the sorted records stay intact until these exist, so a failure here
+    // leaves the CUDA-core A x usable
+    const bool bf = P.precision == MBIR_PREC_BF16;
+    const size_t wsz = bf ? sizeof(uint32_t) : sizeof(uint2);
+    const size_t nrec = (size_t)std::max<long long>(g->n_records, 1);
+    uint2* d_key = nullptr;
+    void* d_pw = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_key, sizeof(uint2) * nrec);
+    if (e == cudaSuccess) e = cudaMalloc(&d_pw, wsz * nrec);
     if (e == cudaSuccess) {
-        const void* tab = P.precision == MBIR_PREC_BF16 ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
-        const TsView V{P, L, d_b, tab, g->d_rec_off, d_cr, d_sp, g->d_rec_key, g->d_rec_w, d_ord, nullptr, nullptr, 0,
-                       0, d_ctr};
-        e = cudaMalloc((void**)&d_view, sizeof(TsView));
-        if (e == cudaSuccess) e = cudaMemcpy(d_view, &V, sizeof(TsView), cudaMemcpyHostToDevice);
+        const DevPtrs D = dev_ptrs(g);
+        if (bf)
+            ts_pack_kernel<true><<<P.K * ntile, 256, 0, st>>>(P, D, g->d_rec_off, d_sp, g->d_rec_key, d_key,
+                                                              reinterpret_cast<uint32_t*>(d_pw));
+        else
+            ts_pack_kernel<false><<<P.K * ntile, 256, 0, st>>>(P, D, g->d_rec_off, d_sp, g->d_rec_key, d_key,
+                                                               reinterpret_cast<uint2*>(d_pw));
+        e = cudaGetLastError();
     }
-    // last: from here on the records are in the kernel's order and carry its batch marks (the CUDA-core A x's
-    // span runs no longer hold)
-    if (e == cudaSuccess) e = interleave_records(g, roff, d_sp, st);
     if (e == cudaSuccess) {
-        ts_batch_flag_kernel<<<P.K * ntile, 256, 0, st>>>(P, L.R, g->d_rec_off, d_sp, g->d_rec_key);
+        ts_batch_flag_kernel<<<P.K * ntile, 256, 0, st>>>(P, L.R, g->d_rec_off, d_sp, d_key);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
+    // the kernel's view without the per-call fields
+    TsView* d_view = nullptr;
+    if (e == cudaSuccess) {
+        const void* tab = bf ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
+        const TsView V{P, L, d_b, tab, g->d_rec_off, d_cr, d_sp, d_key, d_pw, d_ord, nullptr, nullptr, 0, 0, d_ctr};
+        e = cudaMalloc((void**)&d_view, sizeof(TsView));
+        if (e == cudaSuccess) e = cudaMemcpy(d_view, &V, sizeof(TsView), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
-        void* ptrs[] = {d_n0, d_ord, d_ctr, d_cr, d_sp, d_b, d_view};
+        void* ptrs[] = {d_n0, d_ord, d_ctr, d_cr, d_sp, d_b, d_view, d_key, d_pw};
         for (void* p : ptrs) cudaFree(p);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? cudaErrorNotSupported : e;
     }
+    // the sorted records are not read again (the CUDA-core A x no longer runs for this geometry)
+    cudaFree(g->d_rec_key);
+    cudaFree(g->d_rec_w);
+    g->d_rec_key = nullptr;
+    g->d_rec_w = nullptr;
+    g->bytes -= (sizeof(int2) + sizeof(float4)) * nrec;
+    g->bytes += (sizeof(uint2) + wsz) * nrec;
+    g->d_tc_key = d_key;
+    g->d_tc_w = d_pw;
     cudaFree(d_n0);
     g->d_tf_view = d_view;
     g->tf4 = L;

@@ -49,6 +49,15 @@ constexpr int kTsSplit = kTsWarps + 1;   // record offsets per tile: the warps' 
 constexpr uint32_t kTsCols = 512;   // tensor memory: A operand in [0, 256), the product at 256
 constexpr uint32_t kTsDCol = 256;
 constexpr int kTsPart = 64;         // anti-diagonal sums per warp block (32 + taps / 4 - 1 <= 63)
+#ifndef MBIR_TS_RING
+#define MBIR_TS_RING 4
+#endif
+#ifndef MBIR_TS_XAHEAD
+#define MBIR_TS_XAHEAD 1
+#endif
+constexpr int kTsRing = MBIR_TS_RING;      // record batches of a warp in flight (A x)
+constexpr int kTsXAhead = MBIR_TS_XAHEAD;  // batches between an x gather and its use (< kTsRing)
+static_assert(kTsXAhead >= 1 && kTsXAhead < kTsRing, "x is gathered from records already in the ring");
 static_assert(kTsThreads == kTcThreads, "the engine runs the adjoint and A x pools with one block size");
 
 struct TsView {
@@ -59,8 +68,8 @@ struct TsView {
     const long long* rec_off;
     const uint32_t* crange;      // per (A-scan, tile): c_lo | c_hi << 16
     const int* split;            // per (A-scan, tile): kTsSplit record offsets from the A-scan's first record
-    const int2* rkey;
-    const float4* rw;
+    const uint2* rkey;           // packed records (tc_apply.cuh): keys
+    const void* rw;              // and weights, uint2 (FP32 form) or uint32 (BF16 form)
     const int* order;            // A-scans by decreasing record count
     const float* x;
     void* y;                     // float, or __nv_bfloat16 when y_bf16; row stride out_stride
@@ -102,10 +111,11 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
     float* sS = reinterpret_cast<float*>(smem + T.off_s);
     float* sY = reinterpret_cast<float*>(smem + T.off_y);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    using WT = typename TcW<BF16>::type;
     const int R = T.R, S = table_stride(P.Tw4);
-    const float invR = 1.0f / (float)R;
-    const int2* __restrict__ rkey = V.rkey;
-    const float4* __restrict__ rw = V.rw;
+    const int dR = P.G > 1 ? R : 0;                    // columns from a table row to the next plane's
+    const uint2* __restrict__ rkey = V.rkey;
+    const WT* __restrict__ rw = reinterpret_cast<const WT*>(V.rw);
     const float* __restrict__ xg = V.x;
     const uint32_t tA = tmem, tD = tmem + kTsDCol;
     const int KA = T.kwmax / 2;                        // tensor-memory columns of one part of A
@@ -128,10 +138,10 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
     const int qd = warp & 3, pb = warp >> 2;            // lane quarter and column block of this warp
     const float it = ts_pow2(-T.texp);
 
-    // record batches in flight: slot s holds batch b = s (mod 4) of this warp's part of the tile
-    int2 kq[4];
-    float4 wq[4];
-    float xq[4];
+    // record batches in flight: slot s holds batch b = s (mod kTsRing) of this warp's part of the tile
+    uint2 kq[kTsRing];
+    WT wq[kTsRing];
+    float xq[kTsRing];
 
     // Products of tile tp (scale exponent se) in tensor memory -> y: wait for them, sum the anti-diagonals of
     // each warp's block with shuffles (lane l: block offsets l and l + 32), then the blocks in a fixed order.
@@ -189,19 +199,19 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
             wb = tsp[t * kTsSplit + warp + 1];
             nb = (wb - wa + 31) >> 5;
         };
-        auto issue = [&](int2& kk, float4& ww, int b) {
+        auto issue = [&](uint2& kk, WT& ww, int b) {
             const int rec = wa + 32 * b + lane;
             if (b < nb && rec < wb) {
                 kk = __ldg(rkey + base + rec);
                 ww = __ldg(rw + base + rec);
             } else {
-                kk = make_int2(0, -1);                   // n0 field negative: not a record
-                ww = make_float4(0.f, 0.f, 0.f, 0.f);
+                kk = make_uint2(0u, kTcNone);            // not a record: weight zero
+                ww = WT{};
             }
         };
         warp_range(0);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) issue(kq[s], wq[s], s);
+        for (int s = 0; s < kTsRing; ++s) issue(kq[s], wq[s], s);
 
         int pend = -1, pend_se = 0;                      // tile whose products wait in tensor memory
         for (int t = 0; t < ntile; ++t) {
@@ -211,60 +221,62 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                 // this warp's part of the next tile into L2 while this tile is scattered
                 const int pa = tsp[(t + 1) * kTsSplit + warp], pz = tsp[(t + 1) * kTsSplit + warp + 1];
                 prefetch_l2_range(rkey + base + pa, (size_t)(pz - pa) * sizeof(int2), lane);
-                prefetch_l2_range(rw + base + pa, (size_t)(pz - pa) * sizeof(float4), lane);
+                prefetch_l2_range(rw + base + pa, (size_t)(pz - pa) * sizeof(WT), lane);
             }
             if (live) {
-                // ---- scatter: batches b = 0 .. nb-1, slot b & 3, x one batch ahead
+                // ---- scatter: batches b = 0 .. nb-1, slot b mod kTsRing
                 float* Sb = sS - (int)(tcr[t] & 0xffffu);
                 float bsum = 0.0f;
-                xq[0] = kq[0].y >= 0 ? __ldg(xg + (kq[0].x & kRecPixel)) : 0.0f;
-                for (int b0 = 0; b0 < nb; b0 += 4) {
+                // x gathered kTsXAhead batches ahead of its use, the records kTsRing batches ahead
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                for (int s = 0; s < kTsXAhead; ++s)
+                    xq[s] = kq[s].y != kTcNone ? __ldg(xg + (kq[s].x & kTcPixelMask)) : 0.0f;
+                for (int b0 = 0; b0 < nb; b0 += kTsRing) {
+#pragma unroll
+                    for (int u = 0; u < kTsRing; ++u) {
                         const int b = b0 + u;
                         if (b >= nb) break;
-                        if (b + 1 < nb) {
-                            const int2 kn = kq[(u + 1) & 3];
-                            xq[(u + 1) & 3] = kn.y >= 0 ? __ldg(xg + (kn.x & kRecPixel)) : 0.0f;
+                        if (b + kTsXAhead < nb) {
+                            const int sn = (u + kTsXAhead) % kTsRing;
+                            xq[sn] = kq[sn].y != kTcNone ? __ldg(xg + (kq[sn].x & kTcPixelMask)) : 0.0f;
                         }
-                        const int2 kk = kq[u];
-                        const float4 w = wq[u];
-                        const float xv = xq[u];
-                        const bool valid = kk.y >= 0;
-                        const int n0r = valid ? (kk.y >> kRecShift) - ts : 0;
-                        const int trow = valid ? (kk.y >> 1) & 0xfff : 0;
-                        float c0 = w.x * xv, c1 = w.y * xv, c2 = w.z * xv, c3 = w.w * xv;
-                        bsum += (fabsf(c0) + fabsf(c1)) + (fabsf(c2) + fabsf(c3));
-                        const int gi = (int)(((float)trow + 0.5f) * invR);
-                        const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
+                        const uint2 kk = kq[u];
+                        const bool valid = kk.y != kTcNone;
+                        const int n0r = valid ? tc_rec_n0(kk) - ts : 0;
+                        const int trow = valid ? tc_rec_row(kk) : 0;
+                        // the four bilinear corners times x (zero for a lane without a record)
+                        const float wx = tc_rec_w(wq[u]) * xq[u], psi = tc_rec_psi(wq[u]);
+                        const float ca = wx * tc_rec_fa(kk), cb = wx - ca;
+                        float c1 = ca * psi, c3 = cb * psi;
+                        float c0 = ca - c1, c2 = cb - c3;
+                        bsum += fabsf(wx);                       // the corners' magnitudes sum to |w x|
+                        const int c1col = trow + dR;
                         float* row = Sb + n0r * T.astride;
-                        // a marked batch (first record's pixel field negative): every corner cell is its lane's
-                        // alone, so the four read-modify-writes are independent (the last plane's two pairs of
-                        // equal cells are merged first)
-                        const bool one_step = __shfl_sync(full, kk.x, 0) < 0;
-                        // equal (n0, table row) are adjacent lanes: segmented inclusive sums over them
-                        const int key = valid ? (n0r << 12) | trow : 0x40000000 + lane;
-                        // (every lane takes part in every shuffle: none of them sits behind a condition)
-                        const int kup = __shfl_up_sync(full, key, 1);
-                        const int kdn = __shfl_down_sync(full, key, 1);
+                        // a marked batch (first record's key.x with bit 31 set): every corner cell is its lane's
+                        // alone, so the four read-modify-writes are independent (with one attenuation plane the
+                        // two pairs of equal cells are merged first)
+                        const bool one_step = (int)__shfl_sync(full, kk.x, 0) < 0;
                         if (one_step) {
                             if (valid) {
-                                const bool dup = c1col == trow;
-                                if (dup) {
-                                    c0 += c1;
-                                    c2 += c3;
-                                }
-                                const float s0 = row[trow], s2 = row[trow + 1];
-                                const float s1 = dup ? 0.0f : row[c1col], s3 = dup ? 0.0f : row[c1col + 1];
-                                row[trow] = s0 + c0;
-                                row[trow + 1] = s2 + c2;
-                                if (!dup) {
+                                if (dR == 0) {
+                                    row[trow] += c0 + c1;
+                                    row[trow + 1] += c2 + c3;
+                                } else {
+                                    const float s0 = row[trow], s2 = row[trow + 1];
+                                    const float s1 = row[c1col], s3 = row[c1col + 1];
+                                    row[trow] = s0 + c0;
+                                    row[trow + 1] = s2 + c2;
                                     row[c1col] = s1 + c1;
                                     row[c1col + 1] = s3 + c3;
                                 }
                             }
                             __syncwarp();
                         } else {
+                        // equal (n0, table row) are adjacent lanes: segmented inclusive sums over them (one_step
+                        // is the same for the whole warp, so every lane takes part in every shuffle)
+                        const int key = valid ? (n0r << 12) | trow : 0x40000000 + lane;
+                        const int kup = __shfl_up_sync(full, key, 1);
+                        const int kdn = __shfl_down_sync(full, key, 1);
                         if (__any_sync(full, lane > 0 && kup == key)) {
                             // Hillis-Steele steps until no run reaches further back (runs are short)
                             for (int d = 1; d < 32; d <<= 1) {
@@ -295,19 +307,19 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         }
                         // tau = t0 exactly (rare): the last tap of the upper phase row lies outside the window;
                         // one lane after another
-                        uint32_t fm = __ballot_sync(full, valid && (kk.y & 1));
+                        uint32_t fm = __ballot_sync(full, valid && (kk.y & kTcFlag0));
                         while (fm) {
                             if (lane == __ffs(fm) - 1) {
-                                const size_t ti = ((size_t)gi * R + (trow - gi * R) + 1) * S + P.Tw - 1;
+                                const size_t ti = (size_t)(trow + 1) * S + P.Tw - 1;
                                 float2 tl;
                                 if (BF16) tl = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(V.tab) + ti));
                                 else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
-                                sY[ts + n0r + P.Tw] -= xv * (w.z * tl.x + w.w * tl.y);
+                                sY[ts + n0r + P.Tw] -= cb * fmaf(psi, tl.y - tl.x, tl.x);
                             }
                             __syncwarp();
                             fm &= fm - 1;
                         }
-                        issue(kq[u], wq[u], b + 4);
+                        issue(kq[u], wq[u], b + kTsRing);
                     }
                 }
 #pragma unroll
@@ -318,7 +330,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
             if (t + 1 < ntile) {
                 warp_range(t + 1);
 #pragma unroll
-                for (int s = 0; s < 4; ++s) issue(kq[s], wq[s], s);
+                for (int s = 0; s < kTsRing; ++s) issue(kq[s], wq[s], s);
             }
             if (!live) continue;
             __syncthreads();                             // every record of the tile is in S
@@ -421,15 +433,18 @@ struct TbView {
     const long long* rec_off;
     const int* tile_off;         // first record of every tile, K x (ntile + 1)
     const uint32_t* crange;      // per (A-scan, tile): c_lo | c_hi << 16
-    const int2* rkey;
-    const float4* rw;
+    const uint2* rkey;           // packed records (tc_apply.cuh): keys
+    const void* rw;              // and weights, uint2 (FP32 form) or uint32 (BF16 form)
     unsigned long long* acc;     // per pixel: the fixed-point sum (zero on entry)
     const unsigned int* emax;    // bits of max |e| over the residual (tc_emax)
-    float bound;                 // K x max record weight sum x (max table row sum of |T| + max |T|), doubled
+    float bound;                 // K x max record weight x (max table row sum of |T| + max |T|), doubled
     int* counter;
 };
 
-constexpr int kTbUnroll = 4;     // records per thread in one batch (two batches in flight), by default
+#ifndef MBIR_TB_UNROLL
+#define MBIR_TB_UNROLL 6
+#endif
+constexpr int kTbUnroll = MBIR_TB_UNROLL;  // records per thread in one batch (two batches in flight), by default
 
 // Scale exponent s of the adjoint's fixed-point sums: every contribution is at most bound / K x max|e| in
 // magnitude and a pixel has at most one per A-scan, so with s = 61 - (exponents of bound and max|e|) no
@@ -452,14 +467,14 @@ __device__ __forceinline__ float tcs_finish_pixel(unsigned long long a, unsigned
 }
 
 // A batch of records held in registers: records rb + u * kTsThreads + tid, u < U.
-template <int U>
+template <int U, typename WT>
 struct TbBatch {
-    int2 key[U];
-    float4 w[U];
+    uint2 key[U];
+    WT w[U];
 };
 
-template <int U>
-__device__ __forceinline__ void tb_load(TbBatch<U>& b, const int2* __restrict__ rkey, const float4* __restrict__ rw,
+template <int U, typename WT>
+__device__ __forceinline__ void tb_load(TbBatch<U, WT>& b, const uint2* __restrict__ rkey, const WT* __restrict__ rw,
                                         long long base, int rb, int r1, int tid)
 {
 #pragma unroll
@@ -488,10 +503,11 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
     unsigned char* sB = smem + T.off_b;
     float* sC = reinterpret_cast<float*>(smem + T.off_c);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    using WT = typename TcW<BF16>::type;
     const int R = T.R, S = table_stride(P.Tw4);
-    const float invR = 1.0f / (float)R;
-    const int2* __restrict__ rkey = V.rkey;
-    const float4* __restrict__ rw = V.rw;
+    const int dR = P.G > 1 ? R : 0;                    // columns from a table row to the next plane's
+    const uint2* __restrict__ rkey = V.rkey;
+    const WT* __restrict__ rw = reinterpret_cast<const WT*>(V.rw);
     unsigned long long* __restrict__ acc = V.acc;
     const float fsc = ts_pow2(tc_fixed_exponent(*V.emax, V.bound));
     const uint32_t tA = tmem, tD = tmem + 128;
@@ -592,7 +608,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         const int r0 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc);
         const int r1 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc + 1);
         // the first records of this item and the next item's window load during the products
-        TbBatch<U> ba, bb;
+        TbBatch<U, WT> ba, bb;
         tb_load(ba, rkey, rw, base, r0, r1, tid);
         const float ew = nxt < nitems ? load_e(nxt) : 0.0f;
         float* sEc = sE0 + cbuf * T.ewin;
@@ -634,28 +650,29 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         if (live_cur) {
             const int ts = tc * kTsTile;
             const float* Cb = sC - c_lo;
-            auto run = [&](const TbBatch<U>& bt, int rb) {
+            auto run = [&](const TbBatch<U, WT>& bt, int rb) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int r = rb + u * kTsThreads + tid;
                     if (r >= r1) continue;
-                    const int n0r = (bt.key[u].y >> kRecShift) - ts, trow = (bt.key[u].y >> 1) & 0xfff;
-                    const int gi = (int)(((float)trow + 0.5f) * invR);
-                    const int c1col = min(gi + 1, P.G - 1) * R + (trow - gi * R);
+                    const uint2 kk = bt.key[u];
+                    const int n0r = tc_rec_n0(kk) - ts, trow = tc_rec_row(kk);
                     const float* cr = Cb + n0r * T.cstride;
-                    float v = bt.w[u].x * cr[trow];
-                    v = fmaf(bt.w[u].y, cr[c1col], v);
-                    v = fmaf(bt.w[u].z, cr[trow + 1], v);
-                    v = fmaf(bt.w[u].w, cr[c1col + 1], v);
-                    if (bt.key[u].y & 1) {
+                    const float fa = tc_rec_fa(kk), psi = tc_rec_psi(bt.w[u]);
+                    // bilinear in the attenuation plane (psi), then in the phase (fa)
+                    const float c00 = cr[trow], c10 = cr[trow + dR], c01 = cr[trow + 1], c11 = cr[trow + dR + 1];
+                    const float a0 = fmaf(psi, c10 - c00, c00), a1 = fmaf(psi, c11 - c01, c01);
+                    float v = fmaf(fa, a0 - a1, a1);
+                    if (kk.y & kTcFlag0) {
                         // tau = t0 exactly: the last tap of the upper phase row lies outside the window
-                        const size_t ti = ((size_t)gi * R + (trow - gi * R) + 1) * S + P.Tw - 1;
+                        const size_t ti = (size_t)(trow + 1) * S + P.Tw - 1;
                         float2 tl;
                         if (BF16) tl = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(V.tab) + ti));
                         else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
-                        v -= (bt.w[u].z * tl.x + bt.w[u].w * tl.y) * sEc[n0r + P.Tw - 1];
+                        v -= (1.0f - fa) * fmaf(psi, tl.y - tl.x, tl.x) * sEc[n0r + P.Tw - 1];
                     }
-                    red_add_global_u64(acc + (bt.key[u].x & kRecPixel), (unsigned long long)__float2ll_rn(v * fsc));
+                    v *= tc_rec_w(bt.w[u]);
+                    red_add_global_u64(acc + (kk.x & kTcPixelMask), (unsigned long long)__float2ll_rn(v * fsc));
                 }
             };
             constexpr int kStep = U * kTsThreads;

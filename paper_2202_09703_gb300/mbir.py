@@ -72,7 +72,8 @@ class Info(C.Structure):
                 ("gamma_max_s", C.c_double), ("mode", C.c_int), ("precision", C.c_int),
                 ("device_bytes", C.c_int64), ("forward_window_spans", C.c_int),
                 ("forward_window_ms", C.c_double * 3), ("adjoint_groups", C.c_int),
-                ("adjoint_tensor_cores", C.c_int), ("forward_tensor_cores", C.c_int)]
+                ("adjoint_tensor_cores", C.c_int), ("forward_tensor_cores", C.c_int),
+                ("n_records", C.c_int64), ("record_bytes", C.c_int64)]
 
 
 _lib = None

@@ -196,7 +196,10 @@ def test_forward_window_does_not_change_output_bits():
 def test_bf16_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn):
     """BF16 form: A^T on the tensor cores (per-tile correlation GEMM + four
     corners per pair) against the CUDA-core adjoint on the same stored BF16
-    residual and table, and against the FP64 oracle."""
+    residual and table, and against the FP64 oracle.  The tensor-core form
+    reads its pair weights from the 12 B packed records (w rounded to FP16,
+    2^-12 relative), the CUDA-core adjoint from the legs in FP32: their
+    difference is at that level, far inside the BF16 form's oracle bound."""
     s = scene_fn().copy(precision="bf16")
     tc = make_geo(s, "tab")
     cc = make_geo(s, "tab", tensor_cores=False)
@@ -205,9 +208,9 @@ def test_bf16_tensor_core_adjoint_matches_cuda_core_adjoint_and_oracle(scene_fn)
     for seed in (31, 32):
         r = S.random_vector(s.K * s.M, seed)
         b_tc, b_cc = gpu_backproject(tc, r), gpu_backproject(cc, r)
-        assert rel_l2(b_tc, b_cc) <= 1e-5
+        assert rel_l2(b_tc, b_cc) <= 1e-3
         assert rel_l2(b_tc, plan.backproject(r)) <= 1e-2
-    # reproducible: the per-pixel sums run in a fixed order
+    # reproducible: the per-pixel fixed-point sums do not depend on the order of the additions
     assert np.array_equal(gpu_backproject(tc, r), b_tc)
 
 
@@ -329,6 +332,21 @@ def test_bf16_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn)
         assert rel_l2(y_tc, y_cc) <= 5e-3
         assert rel_l2(y_tc, plan.forward(x)) <= 1e-2
     assert np.array_equal(gpu_forward(tc, x), y_tc)
+
+
+@pytest.mark.parametrize("precision,per_pair", [("fp32", 16), ("bf16", 12)])
+def test_tensor_core_records_are_packed(precision, per_pair):
+    """The tensor-core forms keep only the packed records: 16 B per active
+    pair in the FP32 form and 12 B in the BF16 form, against 24 B per pair
+    for the sorted records of the CUDA-core A x; one record per active pair."""
+    s = S.cfg0().copy(precision=precision)
+    tc = make_geo(s, "tab")
+    cc = make_geo(s, "tab", tensor_cores=False)
+    assert tc.info.forward_tensor_cores == 1 and cc.info.forward_tensor_cores == 0
+    pairs, _ = tc.count_taps()
+    assert tc.info.n_records == cc.info.n_records == pairs > 0
+    assert tc.info.record_bytes == per_pair * pairs
+    assert cc.info.record_bytes == 24 * pairs
 
 
 def test_otf_and_tab_modes_agree():
