@@ -102,6 +102,27 @@ __device__ __forceinline__ void prefetch_l2_range(const void* p, size_t bytes, i
     }
 }
 
+// Read-only loads with an L1 eviction hint: streamed data read once (L1::no_allocate keeps it from pushing
+// reused lines out of the L1), and gathered data that is read again (L1::evict_last).
+__device__ __forceinline__ uint2 ldg_stream(const uint2* p)
+{
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ldg_stream(const uint32_t* p)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ldg_keep(const float* p)
+{
+    float v;
+    asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // *p += v in global memory as a reduction that returns nothing: the address is taken into the global window
 // explicitly, so a pointer read from memory (a generic pointer to the compiler) still gets the
 // fire-and-forget form rather than an atomic that waits for the old value.

@@ -320,7 +320,7 @@ struct Tf4Layout {
     int kwmax;             // widest column range of a tile that the sum tile holds (multiple of 16)
     int astride;           // FP32 row stride of the sums (floats, 4 mod 32)
     int texp;              // FP32 form: table operand = table x 2^texp (largest magnitude in [2^14, 2^15))
-    int ylen;              // output window (floats)
+    int ylen;              // output samples held in shared memory (a ring)
     size_t bbytes;         // bytes of the table operand
     size_t off_part, off_rs, off_b, off_s, off_y, smem;
     bool ok;

@@ -206,6 +206,10 @@ cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st)
         if (L.ok) break;
     }
     if (!L.ok || g->tf4_wmax > L.kwmax) return cudaErrorNotSupported;
+    {
+        const Tb4Layout Lt = tb4_layout(P, std::max(g->tf4_wmax, 16));   // no wider than the widest tile
+        if (Lt.ok) L = Lt;
+    }
     const int nq = P.Q * P.Tw + 1;
     const size_t part = (size_t)L.kb * L.ntap;
     std::vector<uint16_t> img((size_t)L.parts * part, 0);

@@ -24,7 +24,7 @@ Tf4Layout tf4_layout(const GeomParams& P, int kwmax)
     L.off_rs = L.off_part + (size_t)kTsWarps * kTsPart * 4;   // per A-scan: part boundaries, column ranges
     L.off_b = (L.off_rs + (size_t)ntile * (kTsSplit + 1) * 4 + 1023) & ~(size_t)1023;
     L.off_s = (L.off_b + L.bbytes + 1023) & ~(size_t)1023;
-    L.ylen = ntile * kTsTile + L.ntap + 2;
+    L.ylen = kTsYRing;
     L.off_y = L.off_s + (size_t)kTsTile * L.astride * 4;
     L.smem = L.off_y + (size_t)L.ylen * 4;
     L.ok = L.R >= 2 && L.ntap <= 128 && L.ntap / 4 <= 32 && L.kwmax >= 16 && L.kwmax % 16 == 0 &&
@@ -259,6 +259,12 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_w);
     if (e == cudaSuccess && wmax > L.kwmax) e = cudaErrorNotSupported;   // a tile reaches too many planes
+    if (e == cudaSuccess) {
+        // the sum tile as wide as the widest tile's column range (a multiple of 16), no wider: the shared
+        // memory left over goes to the L1, which keeps the gathered x
+        const Tf4Layout Lt = tf4_layout(P, std::max(wmax, 16));
+        if (Lt.ok) L = Lt;
+    }
     // table operand: row m (tap), column plane * R + phase (K-major)
     if (e == cudaSuccess) {
         const int nq = P.Q * P.Tw + 1;

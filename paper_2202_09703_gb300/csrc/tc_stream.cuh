@@ -49,13 +49,32 @@ constexpr int kTsSplit = kTsWarps + 1;   // record offsets per tile: the warps' 
 constexpr uint32_t kTsCols = 512;   // tensor memory: A operand in [0, 256), the product at 256
 constexpr uint32_t kTsDCol = 256;
 constexpr int kTsPart = 64;         // anti-diagonal sums per warp block (32 + taps / 4 - 1 <= 63)
+constexpr int kTsYRing = 512;       // output samples held in shared memory, a ring indexed by sample mod 512
 #ifndef MBIR_TS_RING
 #define MBIR_TS_RING 4
 #endif
 #ifndef MBIR_TS_XAHEAD
 #define MBIR_TS_XAHEAD 1
 #endif
+#ifndef MBIR_TS_LDHINT
+#define MBIR_TS_LDHINT 2
+#endif
 constexpr int kTsRing = MBIR_TS_RING;      // record batches of a warp in flight (A x)
+// A x loads: 0 plain read-only loads; 1 records bypass the L1; 2 as 1, and x is kept in the L1 (512x1024 FP32
+// A x: 12.6 ms with plain loads, 11.5 ms with 1 or 2; the adjoint's record loads were slower with the hint)
+constexpr int kTsLdHint = MBIR_TS_LDHINT;
+
+template <typename T>
+__device__ __forceinline__ T ld_rec(const T* p)
+{
+    if constexpr (kTsLdHint >= 1) return ldg_stream(p);
+    else return __ldg(p);
+}
+__device__ __forceinline__ float ld_x(const float* p)
+{
+    if constexpr (kTsLdHint >= 2) return ldg_keep(p);
+    else return __ldg(p);
+}
 constexpr int kTsXAhead = MBIR_TS_XAHEAD;  // batches between an x gather and its use (< kTsRing)
 static_assert(kTsXAhead >= 1 && kTsXAhead < kTsRing, "x is gathered from records already in the ring");
 static_assert(kTsThreads == kTcThreads, "the engine runs the adjoint and A x pools with one block size");
@@ -172,8 +191,28 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                 const int r = o - ((w & 3) * 32 + (w >> 2) * cq);
                 if (r >= 0 && r < 32 + cq - 1) acc += part[w * kTsPart + r];
             }
-            sY[tp * kTsTile + 1 + o] += acc;
+            sY[(tp * kTsTile + 1 + o) & (kTsYRing - 1)] += acc;
         }
+    };
+    // Output samples [flushed, upto) are final: written to y and their ring slots cleared.  Every sample not
+    // yet flushed lies in [clo, clo + 383] (a tile's products reach 127 + taps samples past its start, the
+    // tau = t0 taps of the next tile 255 + Tw), so a ring of 512 holds them without overlap; samples outside
+    // that range are zero.
+    size_t yrow = 0;                                    // this A-scan's first output element
+    int flushed = 0;
+    auto flush = [&](int upto, int clo) {
+        const int hi = min(upto, V.out_stride);
+        for (int n = flushed + tid; n < hi; n += blockDim.x) {
+            float v = 0.0f;
+            if (n >= clo && n < clo + kTsYRing) {
+                v = sY[n & (kTsYRing - 1)];
+                sY[n & (kTsYRing - 1)] = 0.0f;
+            }
+            if (n >= P.M) v = 0.0f;
+            if (V.y_bf16) reinterpret_cast<__nv_bfloat16*>(V.y)[yrow + n] = __float2bfloat16_rn(v);
+            else reinterpret_cast<float*>(V.y)[yrow + n] = v;
+        }
+        flushed = max(flushed, upto);
     };
 
     while (!*abort_flag) {
@@ -188,8 +227,10 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
             const uint32_t* cr = V.crange + (size_t)k * ntile;
             for (int i = tid; i < ntile * kTsSplit; i += blockDim.x) tsp[i] = __ldg(sp + i);
             for (int i = tid; i < ntile; i += blockDim.x) tcr[i] = __ldg(cr + i);
-            for (int i = tid; i < T.ylen; i += blockDim.x) sY[i] = 0.0f;
+            for (int i = tid; i < kTsYRing; i += blockDim.x) sY[i] = 0.0f;
         }
+        yrow = (size_t)k * V.out_stride;
+        flushed = 0;
         __syncthreads();
 
         // this warp's part [wa, wb) of tile t's records and its batches of 32
@@ -202,8 +243,8 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
         auto issue = [&](uint2& kk, WT& ww, int b) {
             const int rec = wa + 32 * b + lane;
             if (b < nb && rec < wb) {
-                kk = __ldg(rkey + base + rec);
-                ww = __ldg(rw + base + rec);
+                kk = ld_rec(rkey + base + rec);
+                ww = ld_rec(rw + base + rec);
             } else {
                 kk = make_uint2(0u, kTcNone);            // not a record: weight zero
                 ww = WT{};
@@ -223,6 +264,18 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                 prefetch_l2_range(rkey + base + pa, (size_t)(pz - pa) * sizeof(int2), lane);
                 prefetch_l2_range(rw + base + pa, (size_t)(pz - pa) * sizeof(WT), lane);
             }
+            if (live && pend >= 0 && t > pend + 1) {
+                // tiles without records lie between the pending tile and this one: finish the pending tile and
+                // flush every sample before this tile's first, so that this tile's writes cannot meet older
+                // samples in the ring
+                __syncthreads();
+                epilogue(pend, pend_se);
+                __syncthreads();
+                flush(t * kTsTile + 1, pend * kTsTile + 1);
+                __syncthreads();
+                pend = -1;
+                if (*abort_flag) break;
+            }
             if (live) {
                 // ---- scatter: batches b = 0 .. nb-1, slot b mod kTsRing
                 float* Sb = sS - (int)(tcr[t] & 0xffffu);
@@ -230,7 +283,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                 // x gathered kTsXAhead batches ahead of its use, the records kTsRing batches ahead
 #pragma unroll
                 for (int s = 0; s < kTsXAhead; ++s)
-                    xq[s] = kq[s].y != kTcNone ? __ldg(xg + (kq[s].x & kTcPixelMask)) : 0.0f;
+                    xq[s] = kq[s].y != kTcNone ? ld_x(xg + (kq[s].x & kTcPixelMask)) : 0.0f;
                 for (int b0 = 0; b0 < nb; b0 += kTsRing) {
 #pragma unroll
                     for (int u = 0; u < kTsRing; ++u) {
@@ -238,7 +291,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         if (b >= nb) break;
                         if (b + kTsXAhead < nb) {
                             const int sn = (u + kTsXAhead) % kTsRing;
-                            xq[sn] = kq[sn].y != kTcNone ? __ldg(xg + (kq[sn].x & kTcPixelMask)) : 0.0f;
+                            xq[sn] = kq[sn].y != kTcNone ? ld_x(xg + (kq[sn].x & kTcPixelMask)) : 0.0f;
                         }
                         const uint2 kk = kq[u];
                         const bool valid = kk.y != kTcNone;
@@ -314,7 +367,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                                 float2 tl;
                                 if (BF16) tl = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(V.tab) + ti));
                                 else tl = __ldg(reinterpret_cast<const float2*>(V.tab) + ti);
-                                sY[ts + n0r + P.Tw] -= cb * fmaf(psi, tl.y - tl.x, tl.x);
+                                sY[(ts + n0r + P.Tw) & (kTsYRing - 1)] -= cb * fmaf(psi, tl.y - tl.x, tl.x);
                             }
                             __syncwarp();
                             fm &= fm - 1;
@@ -334,8 +387,13 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
             }
             if (!live) continue;
             __syncthreads();                             // every record of the tile is in S
-            // ---- the previous tile's products -> y (they ran during this tile's scatter)
-            if (pend >= 0) epilogue(pend, pend_se);
+            // ---- the previous tile's products -> y (they ran during this tile's scatter); the samples before
+            // this tile's first are then final
+            if (pend >= 0) {
+                epilogue(pend, pend_se);
+                __syncthreads();
+                flush((pend + 1) * kTsTile + 1, pend * kTsTile + 1);
+            }
             if (*abort_flag) break;
             // ---- S -> A operand in tensor memory, S cleared as read
             int se = 0;
@@ -395,13 +453,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
         if (pend >= 0 && !*abort_flag) epilogue(pend, pend_se);
         __syncthreads();
         if (*abort_flag) break;
-        if (V.y_bf16) {
-            __nv_bfloat16* yo = reinterpret_cast<__nv_bfloat16*>(V.y) + (size_t)k * V.out_stride;
-            for (int n = tid; n < V.out_stride; n += blockDim.x) yo[n] = __float2bfloat16_rn(n < P.M ? sY[n] : 0.0f);
-        } else {
-            float* yo = reinterpret_cast<float*>(V.y) + (size_t)k * V.out_stride;
-            for (int n = tid; n < V.out_stride; n += blockDim.x) yo[n] = n < P.M ? sY[n] : 0.0f;
-        }
+        flush(V.out_stride, pend >= 0 ? pend * kTsTile + 1 : V.out_stride);
         __syncthreads();
     }
     return !*abort_flag;

@@ -334,6 +334,40 @@ def test_bf16_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn)
     assert np.array_equal(gpu_forward(tc, x), y_tc)
 
 
+def _gapped_scene():
+    """Two columns of pixels 20 mm apart in water: consecutive rows' echoes
+    are some 250 samples apart, so every A-scan's 128-sample tiles with records
+    alternate with tiles without any (the first and the last ones empty too)."""
+    s = S.small_scene(n_layers=1, w=2, h=5, n_tx=2, n_rx=2, M=1500, name="tiny_gapped")
+    return s.copy(pitch=20e-3, tx_x=S.centred_positions(2, 2e-3, 20e-3))
+
+
+@pytest.mark.parametrize("precision,bound", [("fp32", 1e-6), ("bf16", 5e-3)])
+def test_tensor_core_applies_with_empty_tiles_between_records(precision, bound):
+    """The tensor-core A x holds its output in a ring of samples that it
+    flushes as tiles complete; tiles without records between tiles with
+    records take a separate path.  Both applies against the CUDA-core ones
+    and the oracle on a scene made of such gaps."""
+    s = _gapped_scene().copy(precision=precision)
+    tc = make_geo(s, "tab")
+    cc = make_geo(s, "tab", tensor_cores=False)
+    assert tc.info.forward_tensor_cores == 1 and tc.info.adjoint_tensor_cores == 1
+    plan = O.Plan(s)
+    n0 = np.array([[np.floor(plan.pair(v, k)[0] * s.fs) for v in range(s.N)] for k in range(s.K)])
+    for k in range(s.K):
+        live = set((n0[k] // 128).astype(int))
+        assert any(t not in live for t in range(min(live), max(live)))   # a gap between tiles with records
+    for seed in (2, 3):
+        x = S.random_vector(s.N, seed).reshape(s.img_h, s.img_w)
+        y_tc, y_cc = gpu_forward(tc, x), gpu_forward(cc, x)
+        assert rel_l2(y_tc, y_cc) <= bound
+        assert rel_l2(y_tc, plan.forward(x)) <= (1e-5 if precision == "fp32" else 1e-2)
+        r = S.random_vector(s.K * s.M, seed + 10)
+        b_tc = gpu_backproject(tc, r)
+        assert rel_l2(b_tc, gpu_backproject(cc, r)) <= (1e-6 if precision == "fp32" else 1e-3)
+        assert rel_l2(b_tc, plan.backproject(r)) <= (1e-5 if precision == "fp32" else 1e-2)
+
+
 @pytest.mark.parametrize("precision,per_pair", [("fp32", 16), ("bf16", 12)])
 def test_tensor_core_records_are_packed(precision, per_pair):
     """The tensor-core forms keep only the packed records: 16 B per active
