@@ -63,6 +63,8 @@ def parse():
                     help="headline only: skip the BF16 form, the 256x512 and OTF figures and the served stream")
     ap.add_argument("--served-requests", type=int, default=100, help="requests per rate of the served figure")
     ap.add_argument("--requests", type=int, default=0, help="requests for the batched / served workloads")
+    ap.add_argument("--rates", default="20,200", help="arrival rates (req/s) of --workload served")
+    ap.add_argument("--geometries", type=int, default=1, help="distinct scans per size class of --workload served")
     ap.add_argument("--source-hash", default="",
                     help="print the hash profiles/traffic.txt records for these comma-separated sources and exit")
     ap.add_argument("--scene", default="cfg1", choices=["cfg1", "cfg2"], help="workload of --apply-only")
@@ -206,16 +208,21 @@ def run_reference(args):
     from paper_2202_09703_gb300 import synth as S
     scene = S.cfg1() if args.workload == "cfg1" else S.cfg2().copy(precision="fp32")
     x_img = S.phantom(scene, 0)
-    times = []
+    times, walls = [], []
     desc, nth = "", 1
     for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         recon, desc, nth, _, _ = oracle_sample(scene, args.cpu_seconds / 3, x_img)
         if step >= args.warmup:
             times.append(recon)
+            walls.append(time.perf_counter() - t0)
     val = len(times) / sum(times)
     wl = "cfg1" if args.workload == "cfg1" else "cfg2"
+    # a step is one bounded sample of the workload (its wall time is ms_per_step); the value is the
+    # reconstructions per second that the samples extrapolate to
     out = {"impl": "reference", "metric": "recons/s", "value": val, "unit": "recons/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
+           "extrapolated_ms_per_recon": 1e3 * statistics.mean(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOADS[wl]},
            "cpu_baseline": {"value": val, "unit": "recons/s", "cores": nth, "kind": "oracle", "sample": desc},
@@ -436,6 +443,9 @@ def run_gpu(args):
            "config": {"workload": WORKLOADS[wl], "mode": geo.mode, "iterations": scene.n_iter,
                       "image": [scene.img_w, scene.img_h], "ascans": K, "samples": Mn,
                       "adjoint_groups": geo.info.adjoint_groups,
+                      "tensor_core_variants": {"forward": geo.info.tc_forward_variant,
+                                               "adjoint": geo.info.tc_adjoint_variant,
+                                               "timed_ms": [round(t, 4) for t in geo.info.tc_variant_ms]},
                       "l2": "flushed between steps (256 MB write); device time from CUDA events per step",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)),
@@ -639,30 +649,45 @@ def run_batched(args):
                       "higher_is_better": True, "data": "synthetic", "config": out}), flush=True)
 
 
-def served_measure(M, S, torch, np, dev, n, rates):
+def served_measure(M, S, torch, np, dev, n, rates, n_geo=1):
     """Poisson arrivals mixing the three workload sizes (64x64 / 256x512 / 512x1024 at 60/30/10 %), each a
     50-iteration reconstruction, served by the engine (admission capped at 120 GB) in FP32 and in the BF16
-    storage form, against a serial FIFO of FP32 mbir_reconstruct calls on the same GPU.  Latency runs from a
+    storage form, against a serial FIFO of FP32 mbir_reconstruct calls on the same GPU.  Each size class has
+    n_geo distinct scans (geometries with their own layer thicknesses and speeds, phantoms and noise), a
+    request drawing one of them, so admission sees different geometries' tables come and go.  Latency runs from a
     request's arrival to its completion seen by the host; image error against the phantom."""
-    classes = [S.cfg0(), S.cfg1(), S.cfg2().copy(precision="fp32")]
-    for c in classes:
-        c.n_iter = 50
-    pool = {ci: _synth_request(M, S, torch, c, ci, dev) for ci, c in enumerate(classes)}
+    base = [S.cfg0(), S.cfg1(), S.cfg2().copy(precision="fp32")]
+
+    def variant(c, v):
+        s_ = c.copy(name=f"{c.name}_v{v}")
+        for li, L in enumerate(s_.layers):            # +/- a few per cent per variant, layer by layer
+            f = 1.0 + 0.02 * ((v + li) % 3 - 1) * (1 if v else 0)
+            L.thickness *= f
+            L.speed *= 2.0 - f
+        s_.n_iter = 50
+        return s_
+
+    classes = [[variant(c, v) for v in range(n_geo)] for c in base]
+    pool = {(ci, v): _synth_request(M, S, torch, classes[ci][v], 10 * ci + v, dev)
+            for ci in range(3) for v in range(n_geo)}
     # the BF16 storage form of the same requests (same phantoms, noise and sigma)
-    pool_bf = {ci: _synth_request(M, S, torch, c, ci, dev, precision="bf16") for ci, c in enumerate(classes)}
-    truth = {ci: torch.as_tensor(S.phantom(c, ci).reshape(-1), dtype=torch.float32, device=dev)
-             for ci, c in enumerate(classes)}
+    pool_bf = {(ci, v): _synth_request(M, S, torch, classes[ci][v], 10 * ci + v, dev, precision="bf16")
+               for ci in range(3) for v in range(n_geo)}
+    truth = {(ci, v): torch.as_tensor(S.phantom(classes[ci][v], 10 * ci + v).reshape(-1), dtype=torch.float32,
+                                      device=dev) for ci in range(3) for v in range(n_geo)}
     rng = S.SplitMix64(4242)
     results = {}
     for rate in rates:
         u = rng.uniform(n)
-        kinds = np.where(u < 0.6, 0, np.where(u < 0.9, 1, 2))
+        cls = np.where(u < 0.6, 0, np.where(u < 0.9, 1, 2))
+        var = np.minimum((rng.uniform(n) * n_geo).astype(int), n_geo - 1)
+        kinds = [(int(c), int(v)) for c, v in zip(cls, var)]
         gaps = -np.log(1.0 - rng.uniform(n)) / rate
         arrive = np.cumsum(gaps)
-        res = {"mix": [int(np.sum(kinds == c)) for c in range(3)]}
+        res = {"mix": [int(np.sum(cls == c)) for c in range(3)]}
         for mode in ("engine", "engine_bf16", "serial"):
             src = pool_bf if mode == "engine_bf16" else pool
-            xs = [torch.empty(classes[k].N, device=dev) for k in kinds]
+            xs = [torch.empty(classes[k[0]][k[1]].N, device=dev) for k in kinds]
             done = [None] * n
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -674,7 +699,7 @@ def served_measure(M, S, torch, np, dev, n, rates):
                     now = time.perf_counter() - t0
                     while nxt < n and arrive[nxt] <= now:
                         geo, y, sig = src[kinds[nxt]]
-                        tickets[nxt] = eng.submit(geo, y, sig, classes[kinds[nxt]].n_iter, xs[nxt])
+                        tickets[nxt] = eng.submit(geo, y, sig, 50, xs[nxt])
                         nxt += 1
                     na, nq = eng.step()
                     for i, t in tickets.items():
@@ -691,7 +716,7 @@ def served_measure(M, S, torch, np, dev, n, rates):
                     if wait > 0:
                         time.sleep(wait)
                     geo, y, sig = pool[kinds[i]]
-                    geo.reconstruct(y, sig, classes[kinds[i]].n_iter, xs[i])
+                    geo.reconstruct(y, sig, 50, xs[i])
                     done[i] = time.perf_counter() - t0
             lat = np.array(done) - arrive
             torch.cuda.synchronize()
@@ -705,7 +730,7 @@ def served_measure(M, S, torch, np, dev, n, rates):
             geo.close()
     torch.cuda.empty_cache()
     return {"workload": f"served: {n} Poisson requests per rate, sizes 64x64 / 256x512 / 512x1024 at 60/30/10 %, "
-                        "50 iterations each", "rates": results}
+                        f"{n_geo} distinct scan(s) per size, 50 iterations each", "rates": results}
 
 
 def run_served(args):
@@ -717,8 +742,9 @@ def run_served(args):
     from paper_2202_09703_gb300 import mbir as M
     from paper_2202_09703_gb300 import synth as S
     dev = torch.device("cuda:0")
-    cfg = served_measure(M, S, torch, np, dev, args.requests or 100, (20.0, 200.0))
-    best = cfg["rates"]["200_req_per_s"]["engine_bf16"]["recons_per_s"]
+    rates = tuple(float(r) for r in args.rates.split(","))
+    cfg = served_measure(M, S, torch, np, dev, args.requests or 100, rates, args.geometries)
+    best = cfg["rates"][f"{rates[-1]:g}_req_per_s"]["engine_bf16"]["recons_per_s"]
     print(json.dumps({"metric": "recons/s", "value": best, "unit": "recons/s", "higher_is_better": True,
                       "data": "synthetic", "config": cfg}), flush=True)
 

@@ -176,6 +176,11 @@ typedef struct {
     int64_t n_records;           /* TAB records: active (pixel, A-scan) pairs held, else 0 */
     int64_t record_bytes;        /* bytes of the record list as held: 24 per pair sorted (CUDA-core A x),
                                   * 16 (FP32 form) or 12 (BF16 form) packed for the tensor cores */
+    int tc_forward_variant;      /* tensor-core A x variant in use: 0 record loads through the L1, 1 records
+                                  * past the L1 and the gathered image kept there */
+    int tc_adjoint_variant;      /* tensor-core A^T variant in use: 0 four, 1 six records per thread and batch */
+    double tc_variant_ms[4];     /* their times measured at creation (A x 0, 1, A^T 0, 1; 0 if not timed):
+                                  * each pool runs the faster of its two */
 } mbir_geometry_info;
 
 typedef struct mbir_geometry mbir_geometry;
@@ -211,6 +216,15 @@ int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info);
  * A x runs on the tensor cores, which keeps only the packed records),
  * MBIR_ERR_OOM, MBIR_ERR_CUDA. */
 int mbir_set_forward_window(mbir_geometry* g, int spans);
+
+/* Override the variants of the tensor-core A x and A^T that the geometry
+ * chose by timing at creation (see mbir_geometry_info): 0 or 1 each, -1
+ * keeps the current one.  A tuning control with no counterpart in the paper;
+ * the output bits do not depend on it.  The handle must not be in use by
+ * another call or an engine (an engine reads the variants when a request is
+ * admitted).  Errors: MBIR_ERR_INVALID_ARG (other values), MBIR_ERR_UNSUPPORTED
+ * (a variant given for an apply that does not run on the tensor cores). */
+int mbir_set_tensor_core_variants(mbir_geometry* g, int forward_variant, int adjoint_variant);
 
 /* y = A x (eq. 11-13 summed over voxels).  x_dev: N floats.  y_dev: K x M,
  * float (FP32) or bfloat16 (BF16 precision).  Every output sample is written

@@ -72,6 +72,7 @@ struct ReqDesc {
     const float4* rw;
     const uint2* tkey;     // packed records (tensor-core applies)
     const void* tw;
+    int fvar, bvar;        // the geometry's variants of the tensor-core A x and A^T pools
     const int2* runs;
     const float* direct;
     const float* dinv;
@@ -420,7 +421,9 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_bwd_tcs_kernel(EngLists L)
             const TbView V{R.P, R.tb4l, R.tb4_bop, tab, e, R.rec_off, R.tc_tile, R.tf4_crange, R.tkey, R.tw,
                            R.tc_acc, reinterpret_cast<const unsigned int*>(L.pool + 3 * rq + 2), R.tc_bound,
                            L.pool + 3 * rq + 1};
-            if (!tcs_adjoint_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
+            const bool ok = R.bvar ? tcs_adjoint_pool<BF16, 1>(V, smem, tmem, mphase, bphase, R.D.status)
+                                   : tcs_adjoint_pool<BF16, 0>(V, smem, tmem, mphase, bphase, R.D.status);
+            if (!ok) break;
             __syncthreads();
         }
     }
@@ -485,7 +488,9 @@ __global__ void __launch_bounds__(kTsThreads, 1) eng_fwd_tcs_kernel(EngLists L)
             const void* tab = BF16 ? (const void*)R.tab_bf : (const void*)R.tab;
             const TsView V{R.P, R.tf4l, R.tf4_bop, tab, R.rec_off, R.tf4_crange, R.tf4_split, R.tkey, R.tw,
                            R.tf_order, dnew_of(R), R.q, 0, R.P.Mp, L.pool + 3 * rq};
-            if (!tcs_forward_pool<BF16>(V, smem, tmem, mphase, bphase, R.D.status)) break;
+            const bool ok = R.fvar ? tcs_forward_pool<BF16, 1>(V, smem, tmem, mphase, bphase, R.D.status)
+                                   : tcs_forward_pool<BF16, 0>(V, smem, tmem, mphase, bphase, R.D.status);
+            if (!ok) break;
             __syncthreads();
         }
     }
@@ -742,6 +747,8 @@ void fill_desc(ReqDesc& d, const Request* r)
     d.rw = g->d_rec_w;
     d.tkey = g->d_tc_key;
     d.tw = g->d_tc_w;
+    d.fvar = g->tc_fvar;
+    d.bvar = g->tc_bvar;
     d.runs = g->d_runs;
     d.direct = g->d_direct;
     d.dinv = g->d_dinv;

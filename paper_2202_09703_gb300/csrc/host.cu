@@ -549,6 +549,11 @@ int mbir_create_geometry(const mbir_geometry_desc* d, void* stream, mbir_geometr
             }
             if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
         }
+        // the tensor-core pools' variants are chosen by timing them once
+        if (g->d_tf4_bop || g->d_tb4_bop) {
+            ce = mbir::tune_tc_applies(g, st);
+            if (ce != cudaSuccess) { free_geometry(g); return cuda_err(ce); }
+        }
         // the CUDA-core A x's window is tuned only when that kernel is the geometry's A x
         if (g->d_rec_key && !g->d_tf4_bop) {
             ce = mbir::tune_forward_window(g, st);
@@ -578,6 +583,16 @@ int mbir_destroy_geometry(mbir_geometry* g)
 
 size_t mbir_geometry_bytes(const mbir_geometry* g) { return g ? g->bytes : 0; }
 
+int mbir_set_tensor_core_variants(mbir_geometry* g, int forward_variant, int adjoint_variant)
+{
+    if (!g || forward_variant < -1 || forward_variant > 1 || adjoint_variant < -1 || adjoint_variant > 1)
+        return MBIR_ERR_INVALID_ARG;
+    if ((forward_variant >= 0 && !g->d_tf4_bop) || (adjoint_variant >= 0 && !g->d_tb4_bop)) return MBIR_ERR_UNSUPPORTED;
+    if (forward_variant >= 0) g->tc_fvar = forward_variant;
+    if (adjoint_variant >= 0) g->tc_bvar = adjoint_variant;
+    return MBIR_OK;
+}
+
 int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info)
 {
     if (!g || !info) return MBIR_ERR_INVALID_ARG;
@@ -601,6 +616,9 @@ int mbir_geometry_get_info(const mbir_geometry* g, mbir_geometry_info* info)
     const size_t per = g->d_tc_key ? sizeof(uint2) + (g->P.precision == MBIR_PREC_BF16 ? 4 : 8)
                                    : sizeof(int2) + sizeof(float4);
     info->record_bytes = has_rec ? (int64_t)(per * (size_t)g->n_records) : 0;
+    info->tc_forward_variant = g->tc_fvar;
+    info->tc_adjoint_variant = g->tc_bvar;
+    for (int c = 0; c < 4; ++c) info->tc_variant_ms[c] = g->tc_tune_ms[c];
     return MBIR_OK;
 }
 

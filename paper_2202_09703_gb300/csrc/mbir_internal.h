@@ -421,6 +421,8 @@ struct mbir_geometry {
     int tf4_wmax;          // widest column range of a tile
     // tensor-core A^T (see tc_stream.cuh); uses the tile offsets, slots and contributions of build_tc_adjoint
     Tb4Layout tb4;
+    int tc_fvar, tc_bvar;  // variants of the tensor-core A x and A^T pools (tc_stream.cuh), chosen by timing
+    double tc_tune_ms[4];  // their measured times: A x variant 0, 1, A^T variant 0, 1 (0 when not timed)
     uint4* d_tb4_bop;      // table operand (table rows plane * (Q + 1) + phase x taps, K-major; FP32: two parts)
     long long n_records;
     // |A_v|^2 per pixel for the coordinate descent (computed on its first call)
@@ -488,6 +490,7 @@ Tf4Layout tf4_layout(const GeomParams& P, int kwmax);
 cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st);
 Tb4Layout tb4_layout(const GeomParams& P, int kwmax);
 cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st);
+cudaError_t tune_tc_applies(mbir_geometry* g, cudaStream_t st);
 cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
                                    cudaStream_t st);
 cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,

@@ -175,7 +175,7 @@ Tb4Layout tb4_layout(const GeomParams& P, int kwmax)
 
 // The view is read from device memory (written at set-up) with the residual as a parameter, as for the
 // tensor-core A x (fwd_tcs_kernel).
-template <bool BF16>
+template <bool BF16, int BV>
 __global__ void __launch_bounds__(kTsThreads, 1)
     bwd_tcs_kernel(const TbView* __restrict__ base, const void* e, int* __restrict__ status)
 {
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kTsThreads, 1)
     TbView V = *base;
     asm volatile("" : "+l"(e));
     V.e = e;
-    tcs_adjoint_pool<BF16>(V, smem, tmem, mphase, bphase, status);
+    tcs_adjoint_pool<BF16, BV>(V, smem, tmem, mphase, bphase, status);
     tc_header_release(smem, tmem, kTsCols);
 }
 
@@ -271,7 +271,8 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     const GeomParams& P = g->P;
     const Tb4Layout& L = g->tb4;
     const bool bf = P.precision == MBIR_PREC_BF16;
-    auto kern = bf ? bwd_tcs_kernel<true> : bwd_tcs_kernel<false>;
+    auto kern = bf ? (g->tc_bvar ? bwd_tcs_kernel<true, 1> : bwd_tcs_kernel<true, 0>)
+                   : (g->tc_bvar ? bwd_tcs_kernel<false, 1> : bwd_tcs_kernel<false, 0>);
     cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tc_counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return ce;

@@ -37,7 +37,7 @@ Tf4Layout tf4_layout(const GeomParams& P, int kwmax)
 // The call-independent part of the view is read from device memory (written at set-up) and the per-call
 // fields come as parameters routed through registers: with every field register-resident the pool ran the
 // 512x1024 A x in 13.7 ms against 16.5 ms with the whole view read from the parameter space.
-template <bool BF16>
+template <bool BF16, int FV>
 __global__ void __launch_bounds__(kTsThreads, 1)
     fwd_tcs_kernel(const TsView* __restrict__ base, const float* x, void* y, int y_bf16, int out_stride,
                    int* __restrict__ status)
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kTsThreads, 1)
     V.y = y;
     V.y_bf16 = y_bf16;
     V.out_stride = out_stride;
-    tcs_forward_pool<BF16>(V, smem, tmem, mphase, bphase, status);
+    tcs_forward_pool<BF16, FV>(V, smem, tmem, mphase, bphase, status);
     tc_header_release(smem, tmem, kTsCols);
 }
 
@@ -366,7 +366,8 @@ cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf
     const GeomParams& P = g->P;
     const Tf4Layout& L = g->tf4;
     const bool bf = P.precision == MBIR_PREC_BF16;
-    auto kern = bf ? fwd_tcs_kernel<true> : fwd_tcs_kernel<false>;
+    auto kern = bf ? (g->tc_fvar ? fwd_tcs_kernel<true, 1> : fwd_tcs_kernel<true, 0>)
+                   : (g->tc_fvar ? fwd_tcs_kernel<false, 1> : fwd_tcs_kernel<false, 0>);
     cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tf_counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return ce;
@@ -374,6 +375,76 @@ cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf
     kern<<<grid, kTsThreads, L.smem, st>>>(g->d_tf_view, x, yf ? (void*)yf : (void*)yb, yf ? 0 : 1, stride,
                                            g->d_status);
     return cudaGetLastError();
+}
+
+}  // namespace mbir
+
+namespace mbir {
+
+// Times each variant of the tensor-core A x and A^T once on this geometry (x = 1, a constant residual; the
+// first run of each warms up) and keeps the fastest of each: the autotuner of the tensor-core pools.
+// Leaves g->tc_tune_ms with {A x variant 0, 1, A^T variant 0, 1} in ms.  Synchronous.
+cudaError_t tune_tc_applies(mbir_geometry* g, cudaStream_t st)
+{
+    const GeomParams& P = g->P;
+    const bool bf = P.precision == MBIR_PREC_BF16;
+    const size_t N = (size_t)P.W * P.H, KMp = (size_t)P.K * P.Mp;
+    float *x = nullptr, *y = nullptr, *b = nullptr, *e = nullptr;
+    __nv_bfloat16* ebf = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaMalloc((void**)&x, sizeof(float) * N);
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&b, sizeof(float) * N);
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&y, (bf ? 2 : 4) * (size_t)P.K * P.M);
+    if (ce == cudaSuccess && g->d_tb4_bop) {
+        if (bf) ce = cudaMalloc((void**)&ebf, sizeof(__nv_bfloat16) * KMp);
+        else ce = cudaMalloc((void**)&e, sizeof(float) * KMp);
+    }
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) {
+        std::vector<float> ones(std::max(N, KMp), 1.0f);
+        ce = cudaMemcpy(x, ones.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess && e) ce = cudaMemcpy(e, ones.data(), sizeof(float) * KMp, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess && ebf) {
+            std::vector<__nv_bfloat16> ob(KMp, __float2bfloat16_rn(1.0f));
+            ce = cudaMemcpy(ebf, ob.data(), sizeof(__nv_bfloat16) * KMp, cudaMemcpyHostToDevice);
+        }
+    }
+    auto timed = [&](auto&& launch, double& ms) -> cudaError_t {
+        float t = 0.0f;
+        cudaError_t r = cudaSuccess;
+        for (int rep = 0; rep < 2 && r == cudaSuccess; ++rep) {
+            r = cudaEventRecord(e0, st);
+            if (r == cudaSuccess) r = launch();
+            if (r == cudaSuccess) r = cudaEventRecord(e1, st);
+            if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+            if (r == cudaSuccess) r = cudaEventElapsedTime(&t, e0, e1);
+        }
+        ms = t;
+        return r;
+    };
+    const int keep_f = g->tc_fvar, keep_b = g->tc_bvar;
+    for (int v = 0; v < kTcVariants && ce == cudaSuccess && g->d_tf4_bop; ++v) {
+        g->tc_fvar = v;
+        ce = timed([&] { return launch_forward_tcs(g, x, bf ? nullptr : y, bf ? (__nv_bfloat16*)y : nullptr, P.M, st); },
+                   g->tc_tune_ms[v]);
+    }
+    for (int v = 0; v < kTcVariants && ce == cudaSuccess && g->d_tb4_bop; ++v) {
+        g->tc_bvar = v;
+        ce = timed([&] { return launch_backproject_tcs(g, e, ebf, b, st); }, g->tc_tune_ms[kTcVariants + v]);
+    }
+    g->tc_fvar = keep_f;
+    g->tc_bvar = keep_b;
+    if (ce == cudaSuccess && g->d_tf4_bop) g->tc_fvar = g->tc_tune_ms[1] < g->tc_tune_ms[0] ? 1 : 0;
+    if (ce == cudaSuccess && g->d_tb4_bop) g->tc_bvar = g->tc_tune_ms[3] < g->tc_tune_ms[2] ? 1 : 0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(b);
+    cudaFree(e);
+    cudaFree(ebf);
+    return ce;
 }
 
 }  // namespace mbir

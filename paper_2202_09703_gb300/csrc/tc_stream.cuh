@@ -56,23 +56,23 @@ constexpr int kTsYRing = 512;       // output samples held in shared memory, a r
 #ifndef MBIR_TS_XAHEAD
 #define MBIR_TS_XAHEAD 1
 #endif
-#ifndef MBIR_TS_LDHINT
-#define MBIR_TS_LDHINT 2
-#endif
 constexpr int kTsRing = MBIR_TS_RING;      // record batches of a warp in flight (A x)
-// A x loads: 0 plain read-only loads; 1 records bypass the L1; 2 as 1, and x is kept in the L1 (512x1024 FP32
-// A x: 12.6 ms with plain loads, 11.5 ms with 1 or 2; the adjoint's record loads were slower with the hint)
-constexpr int kTsLdHint = MBIR_TS_LDHINT;
 
-template <typename T>
+// Variants of the two pools, chosen per geometry by timing each once at set-up (tune_tc_applies):
+// A x: 0 plain read-only loads, 1 the records bypass the L1 and the gathered x is kept there (512x1024 FP32:
+// 12.6 against 11.5 ms; 256x512: 0.596 against 0.605 ms); A^T: 0 four, 1 six records per thread and batch
+// (512x1024: 8.5 against 8.3 ms).
+constexpr int kTcVariants = 2;
+template <int FV, typename T>
 __device__ __forceinline__ T ld_rec(const T* p)
 {
-    if constexpr (kTsLdHint >= 1) return ldg_stream(p);
+    if constexpr (FV == 1) return ldg_stream(p);
     else return __ldg(p);
 }
+template <int FV>
 __device__ __forceinline__ float ld_x(const float* p)
 {
-    if constexpr (kTsLdHint >= 2) return ldg_keep(p);
+    if constexpr (FV == 1) return ldg_keep(p);
     else return __ldg(p);
 }
 constexpr int kTsXAhead = MBIR_TS_XAHEAD;  // batches between an x gather and its use (< kTsRing)
@@ -113,7 +113,7 @@ __device__ __forceinline__ int ts_bound_exponent(float m)
 // abort flag, 32: table copy barrier) is initialised and kTsCols columns of
 // tensor memory are allocated by the caller; mphase / bphase are the parities
 // of the two barriers.  Returns false when a bounded wait gave up.
-template <bool BF16>
+template <bool BF16, int FV>
 __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char* smem, uint32_t tmem,
                                                  uint32_t& mphase, uint32_t& bphase, int* status)
 {
@@ -243,8 +243,8 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
         auto issue = [&](uint2& kk, WT& ww, int b) {
             const int rec = wa + 32 * b + lane;
             if (b < nb && rec < wb) {
-                kk = ld_rec(rkey + base + rec);
-                ww = ld_rec(rw + base + rec);
+                kk = ld_rec<FV>(rkey + base + rec);
+                ww = ld_rec<FV>(rw + base + rec);
             } else {
                 kk = make_uint2(0u, kTcNone);            // not a record: weight zero
                 ww = WT{};
@@ -283,7 +283,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                 // x gathered kTsXAhead batches ahead of its use, the records kTsRing batches ahead
 #pragma unroll
                 for (int s = 0; s < kTsXAhead; ++s)
-                    xq[s] = kq[s].y != kTcNone ? ld_x(xg + (kq[s].x & kTcPixelMask)) : 0.0f;
+                    xq[s] = kq[s].y != kTcNone ? ld_x<FV>(xg + (kq[s].x & kTcPixelMask)) : 0.0f;
                 for (int b0 = 0; b0 < nb; b0 += kTsRing) {
 #pragma unroll
                     for (int u = 0; u < kTsRing; ++u) {
@@ -291,7 +291,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
                         if (b >= nb) break;
                         if (b + kTsXAhead < nb) {
                             const int sn = (u + kTsXAhead) % kTsRing;
-                            xq[sn] = kq[sn].y != kTcNone ? ld_x(xg + (kq[sn].x & kTcPixelMask)) : 0.0f;
+                            xq[sn] = kq[sn].y != kTcNone ? ld_x<FV>(xg + (kq[sn].x & kTcPixelMask)) : 0.0f;
                         }
                         const uint2 kk = kq[u];
                         const bool valid = kk.y != kTcNone;
@@ -493,10 +493,8 @@ struct TbView {
     int* counter;
 };
 
-#ifndef MBIR_TB_UNROLL
-#define MBIR_TB_UNROLL 6
-#endif
-constexpr int kTbUnroll = MBIR_TB_UNROLL;  // records per thread in one batch (two batches in flight), by default
+// records per thread in one batch of the A^T pool (two batches in flight), per variant
+template <int BV> struct TbUnroll { static constexpr int value = BV == 1 ? 6 : 4; };
 
 // Scale exponent s of the adjoint's fixed-point sums: every contribution is at most bound / K x max|e| in
 // magnitude and a pixel has at most one per A-scan, so with s = 61 - (exponents of bound and max|e|) no
@@ -540,7 +538,7 @@ __device__ __forceinline__ void tb_load(TbBatch<U, WT>& b, const uint2* __restri
 }
 
 // Drains the A^T items of V (header as for tcs_forward_pool; kTsCols tensor-memory columns).
-template <bool BF16, int U = kTbUnroll>
+template <bool BF16, int BV, int U = TbUnroll<BV>::value>
 __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char* smem, uint32_t tmem,
                                                  uint32_t& mphase, uint32_t& bphase, int* status)
 {

@@ -73,7 +73,9 @@ class Info(C.Structure):
                 ("device_bytes", C.c_int64), ("forward_window_spans", C.c_int),
                 ("forward_window_ms", C.c_double * 3), ("adjoint_groups", C.c_int),
                 ("adjoint_tensor_cores", C.c_int), ("forward_tensor_cores", C.c_int),
-                ("n_records", C.c_int64), ("record_bytes", C.c_int64)]
+                ("n_records", C.c_int64), ("record_bytes", C.c_int64),
+                ("tc_forward_variant", C.c_int), ("tc_adjoint_variant", C.c_int),
+                ("tc_variant_ms", C.c_double * 4)]
 
 
 _lib = None
@@ -96,6 +98,7 @@ def lib(path: str | None = None):
         "mbir_destroy_geometry": [_V],
         "mbir_geometry_get_info": [_V, I],
         "mbir_set_forward_window": [_V, C.c_int],
+        "mbir_set_tensor_core_variants": [_V, C.c_int, C.c_int],
         "mbir_forward": [_V, _V, _V, _V],
         "mbir_backproject": [_V, _V, _V, _V],
         "mbir_project": [_V, _V, _V, _V, _V],
@@ -300,6 +303,12 @@ class Geometry:
     def set_forward_window(self, spans: int):
         """Override the autotuned A x window (1, 2 or 4 spans per warp)."""
         _check(self._lib.mbir_set_forward_window(self.h, int(spans)), "mbir_set_forward_window")
+        _check(self._lib.mbir_geometry_get_info(self.h, C.byref(self.info)), "mbir_geometry_get_info")
+
+    def set_tensor_core_variants(self, forward: int = -1, adjoint: int = -1):
+        """Override the timed choice of the tensor-core A x / A^T variants (0 or 1; -1 keeps)."""
+        _check(self._lib.mbir_set_tensor_core_variants(self.h, int(forward), int(adjoint)),
+               "mbir_set_tensor_core_variants")
         _check(self._lib.mbir_geometry_get_info(self.h, C.byref(self.info)), "mbir_geometry_get_info")
 
     def count_taps(self):

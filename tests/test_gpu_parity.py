@@ -334,6 +334,34 @@ def test_bf16_tensor_core_forward_matches_cuda_core_forward_and_oracle(scene_fn)
     assert np.array_equal(gpu_forward(tc, x), y_tc)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_tensor_core_variants_are_timed_and_give_the_same_bits(precision):
+    """At creation each tensor-core pool's two variants are timed once and
+    the faster one kept; every combination gives the same output bits."""
+    s = ragged_scene().copy(precision=precision)
+    geo = make_geo(s, "tab")
+    info = geo.info
+    ms = list(info.tc_variant_ms)
+    assert all(t > 0 for t in ms)
+    assert ms[info.tc_forward_variant] == min(ms[0], ms[1])
+    assert ms[2 + info.tc_adjoint_variant] == min(ms[2], ms[3])
+    x = S.phantom(s, 4)
+    r = S.random_vector(s.K * s.M, 44)
+    outs = []
+    for fv in (0, 1):
+        for bv in (0, 1):
+            geo.set_tensor_core_variants(fv, bv)
+            assert geo.info.tc_forward_variant == fv and geo.info.tc_adjoint_variant == bv
+            outs.append((gpu_forward(geo, x), gpu_backproject(geo, r)))
+    for y, b in outs[1:]:
+        assert np.array_equal(y, outs[0][0]) and np.array_equal(b, outs[0][1])
+    with pytest.raises(M.MbirError):
+        geo.set_tensor_core_variants(2, 0)
+    cc = make_geo(s, "tab", tensor_cores=False)
+    with pytest.raises(M.MbirError):
+        cc.set_tensor_core_variants(1, -1)
+
+
 def _gapped_scene():
     """Two columns of pixels 20 mm apart in water: consecutive rows' echoes
     are some 250 samples apart, so every A-scan's 128-sample tiles with records
