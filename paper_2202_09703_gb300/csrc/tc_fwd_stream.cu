@@ -21,8 +21,9 @@ Tf4Layout tf4_layout(const GeomParams& P, int kwmax)
     L.bbytes = (size_t)L.parts * L.ntap * L.kb * 2;
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
     L.off_part = 1024;                                 // anti-diagonal sums, 16 warps x 64 floats
-    L.off_rs = L.off_part + (size_t)kTsWarps * kTsPart * 4;   // per A-scan: part boundaries, column ranges
-    L.off_b = (L.off_rs + (size_t)ntile * (kTsSplit + 1) * 4 + 1023) & ~(size_t)1023;
+    const int nw = ts_warps(bf);
+    L.off_rs = L.off_part + (size_t)nw * kTsPart * 4;   // per A-scan: part boundaries, column ranges
+    L.off_b = (L.off_rs + (size_t)ntile * (nw + 2) * 4 + 1023) & ~(size_t)1023;
     L.off_s = (L.off_b + L.bbytes + 1023) & ~(size_t)1023;
     L.ylen = kTsYRing;
     L.off_y = L.off_s + (size_t)kTsTile * L.astride * 4;
@@ -38,7 +39,7 @@ Tf4Layout tf4_layout(const GeomParams& P, int kwmax)
 // fields come as parameters routed through registers: with every field register-resident the pool ran the
 // 512x1024 A x in 13.7 ms against 16.5 ms with the whole view read from the parameter space.
 template <bool BF16, int FV>
-__global__ void __launch_bounds__(kTsThreads, 1)
+__global__ void __launch_bounds__(TsShape<BF16>::threads, 1)
     fwd_tcs_kernel(const TsView* __restrict__ base, const float* x, void* y, int y_bf16, int out_stride,
                    int* __restrict__ status)
 {
@@ -75,9 +76,9 @@ __global__ void ts_n0_off_kernel(GeomParams P, const long long* __restrict__ rec
 
 // Per (A-scan, tile of 128 n0): the column range of the planes its records reach (warp per tile; the widest
 // range goes to *wmax) and the boundaries of the warps' parts: the tile's records cut at n0 boundaries into
-// kTsWarps parts of about equal count (part w starts at the first n0 whose first record lies at or after the
-// w/kTsWarps point of the tile's range).
-__global__ void ts_tiles_kernel(GeomParams P, int R, int kb, const long long* __restrict__ rec_off,
+// nw parts of about equal count (part w starts at the first n0 whose first record lies at or after the
+// w/nw point of the tile's range).
+__global__ void ts_tiles_kernel(GeomParams P, int R, int kb, int nw, const long long* __restrict__ rec_off,
                                 const int2* __restrict__ rkey, const int* __restrict__ n0_off,
                                 uint32_t* __restrict__ crange, int* __restrict__ split, int* __restrict__ wmax)
 {
@@ -112,11 +113,11 @@ __global__ void ts_tiles_kernel(GeomParams P, int R, int kb, const long long* __
         }
         crange[wid] = v;
     }
-    if (lane <= kTsWarps) {
+    if (lane <= nw) {
         int s = r1;
         if (lane == 0) s = r0;
-        else if (lane < kTsWarps) {
-            const long long target = r0 + ((long long)(r1 - r0) * lane) / kTsWarps;
+        else if (lane < nw) {
+            const long long target = r0 + ((long long)(r1 - r0) * lane) / nw;
             int lo = n_lo, hi = n_hi;                    // first n0 in [n_lo, n_hi] with no[n0] >= target
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
@@ -125,7 +126,7 @@ __global__ void ts_tiles_kernel(GeomParams P, int R, int kb, const long long* __
             }
             s = no[lo];
         }
-        split[wid * kTsSplit + lane] = s;
+        split[wid * (nw + 1) + lane] = s;
     }
 }
 
@@ -142,10 +143,11 @@ __global__ void ts_pack_kernel(GeomParams P, DevPtrs D, const long long* __restr
 {
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
     const int k = (int)(blockIdx.x / ntile), t = (int)(blockIdx.x % ntile);
-    const int* sp = split + ((size_t)k * ntile + t) * kTsSplit;
+    constexpr int nw = TsShape<BF16>::warps;
+    const int* sp = split + ((size_t)k * ntile + t) * (nw + 1);
     const long long base = rec_off[k];
     const int R = P.Q + 1;
-    for (int p = 0; p < kTsWarps; ++p) {
+    for (int p = 0; p < nw; ++p) {
         const int a = sp[p], len = sp[p + 1] - a;
         const int q = len >> 5, r = len & 31;
         for (int s = threadIdx.x; s < len; s += blockDim.x) {
@@ -170,17 +172,17 @@ __global__ void ts_pack_kernel(GeomParams P, DevPtrs D, const long long* __restr
 // (n0, row), (n0, row + dR), (n0, row + 1), (n0, row + dR + 1) are all distinct between lanes: bit 31 of
 // key.x of the batch's first record.  Such a batch has no equal keys, so the kernel adds its corners without
 // the segmented sums and in one step.  Warp per batch, blocks per (A-scan, tile).
-__global__ void ts_batch_flag_kernel(GeomParams P, int R, const long long* __restrict__ rec_off,
+__global__ void ts_batch_flag_kernel(GeomParams P, int R, int nparts, const long long* __restrict__ rec_off,
                                      const int* __restrict__ split, uint2* __restrict__ key)
 {
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
     const int k = (int)(blockIdx.x / ntile), t = (int)(blockIdx.x % ntile);
-    const int* sp = split + ((size_t)k * ntile + t) * kTsSplit;
+    const int* sp = split + ((size_t)k * ntile + t) * (nparts + 1);
     const long long base = rec_off[k];
     const int dR = P.G > 1 ? R : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t full = 0xffffffffu;
-    for (int p = 0; p < kTsWarps; ++p) {
+    for (int p = 0; p < nparts; ++p) {
         const int a = sp[p], z = sp[p + 1];
         for (int b = a + 32 * warp; b < z; b += 32 * nw) {
             const int r = b + lane;
@@ -238,7 +240,8 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ord, sizeof(int) * (size_t)P.K);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_ctr, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_cr, sizeof(uint32_t) * (size_t)P.K * ntile);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_sp, sizeof(int) * (size_t)P.K * ntile * kTsSplit);
+    const int nw = ts_warps(P.precision == MBIR_PREC_BF16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_sp, sizeof(int) * (size_t)P.K * ntile * (nw + 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d_w, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(d_ord, order.data(), sizeof(int) * (size_t)P.K, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_w, 0, sizeof(int), st);
@@ -250,7 +253,7 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
     }
     if (e == cudaSuccess) {
         const long long threads = (long long)P.K * ntile * 32;
-        ts_tiles_kernel<<<(int)((threads + 255) / 256), 256, 0, st>>>(P, L.R, L.kb, g->d_rec_off, g->d_rec_key, d_n0,
+        ts_tiles_kernel<<<(int)((threads + 255) / 256), 256, 0, st>>>(P, L.R, L.kb, nw, g->d_rec_off, g->d_rec_key, d_n0,
                                                                       d_cr, d_sp, d_w);
         e = cudaGetLastError();
     }
@@ -320,7 +323,7 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        ts_batch_flag_kernel<<<P.K * ntile, 256, 0, st>>>(P, L.R, g->d_rec_off, d_sp, d_key);
+        ts_batch_flag_kernel<<<P.K * ntile, 256, 0, st>>>(P, L.R, nw, g->d_rec_off, d_sp, d_key);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
@@ -356,7 +359,7 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st)
     g->d_tf4_crange = d_cr;
     g->d_tf4_split = d_sp;
     g->tf4_wmax = wmax;
-    g->bytes += L.bbytes + sizeof(int) * ((size_t)P.K + 1) + sizeof(int) * (size_t)P.K * ntile * (kTsSplit + 1);
+    g->bytes += L.bbytes + sizeof(int) * ((size_t)P.K + 1) + sizeof(int) * (size_t)P.K * ntile * (nw + 2);
     return cudaSuccess;
 }
 
@@ -372,7 +375,7 @@ cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf
     if (ce == cudaSuccess) ce = cudaMemsetAsync(g->d_tf_counter, 0, sizeof(int), st);
     if (ce != cudaSuccess) return ce;
     const int grid = std::max(1, std::min(g->n_sm, P.K));
-    kern<<<grid, kTsThreads, L.smem, st>>>(g->d_tf_view, x, yf ? (void*)yf : (void*)yb, yf ? 0 : 1, stride,
+    kern<<<grid, 32 * ts_warps(bf), L.smem, st>>>(g->d_tf_view, x, yf ? (void*)yf : (void*)yb, yf ? 0 : 1, stride,
                                            g->d_status);
     return cudaGetLastError();
 }

@@ -42,10 +42,28 @@
 
 namespace mbir {
 
-constexpr int kTsThreads = 512;     // 16 warps: four per tensor-memory lane quarter
-constexpr int kTsWarps = kTsThreads / 32;
+#ifndef MBIR_TS_WARPS_F32
+#define MBIR_TS_WARPS_F32 20
+#endif
+#ifndef MBIR_TS_WARPS_BF16
+#define MBIR_TS_WARPS_BF16 24
+#endif
+// A x: warps per CTA, one part of every tile each, by storage form (512x1024 A x with 16 / 20 / 24 / 28
+// warps: FP32 11.1 / 10.4 / 10.8 / 10.8 ms, BF16 10.5 / - / 9.1 / - ms)
+__host__ __device__ constexpr int ts_warps(bool bf16) { return bf16 ? MBIR_TS_WARPS_BF16 : MBIR_TS_WARPS_F32; }
+template <bool BF16>
+struct TsShape {
+    static constexpr int warps = ts_warps(BF16);
+    static constexpr int threads = 32 * warps;
+    static constexpr int split = warps + 1;         // record offsets per tile: the warps' part boundaries
+};
+constexpr int kTsEpiWarps = 16;     // A x epilogue: four warps per tensor-memory lane quarter read the product
+constexpr int kTbThreads = 512;     // A^T: 16 warps, four per tensor-memory lane quarter
+constexpr int kTbWarps = kTbThreads / 32;
 constexpr int kTsTile = 128;        // n0 values per tile (MMA M)
-constexpr int kTsSplit = kTsWarps + 1;   // record offsets per tile: the warps' part boundaries
+static_assert(ts_warps(false) % 4 == 0 && ts_warps(false) >= kTsEpiWarps && ts_warps(false) < 32 &&
+              ts_warps(true) % 4 == 0 && ts_warps(true) >= kTsEpiWarps && ts_warps(true) < 32,
+              "A x warps: 16..28, multiples of 4");
 constexpr uint32_t kTsCols = 512;   // tensor memory: A operand in [0, 256), the product at 256
 constexpr uint32_t kTsDCol = 256;
 constexpr int kTsPart = 64;         // anti-diagonal sums per warp block (32 + taps / 4 - 1 <= 63)
@@ -77,7 +95,7 @@ __device__ __forceinline__ float ld_x(const float* p)
 }
 constexpr int kTsXAhead = MBIR_TS_XAHEAD;  // batches between an x gather and its use (< kTsRing)
 static_assert(kTsXAhead >= 1 && kTsXAhead < kTsRing, "x is gathered from records already in the ring");
-static_assert(kTsThreads == kTcThreads, "the engine runs the adjoint and A x pools with one block size");
+static_assert(kTbThreads == kTcThreads, "the tensor-core header assumes the adjoint's block size");
 
 struct TsView {
     GeomParams P;
@@ -86,7 +104,7 @@ struct TsView {
     const void* tab;             // kernel table, float2 (FP32) or __nv_bfloat162 (BF16): the tau = t0 tap
     const long long* rec_off;
     const uint32_t* crange;      // per (A-scan, tile): c_lo | c_hi << 16
-    const int* split;            // per (A-scan, tile): kTsSplit record offsets from the A-scan's first record
+    const int* split;            // per (A-scan, tile): warps + 1 record offsets from the A-scan's first record
     const uint2* rkey;           // packed records (tc_apply.cuh): keys
     const void* rw;              // and weights, uint2 (FP32 form) or uint32 (BF16 form)
     const int* order;            // A-scans by decreasing record count
@@ -117,6 +135,8 @@ template <bool BF16, int FV>
 __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char* smem, uint32_t tmem,
                                                  uint32_t& mphase, uint32_t& bphase, int* status)
 {
+    constexpr int kTsWarps = TsShape<BF16>::warps;
+    constexpr int kTsSplit = TsShape<BF16>::split;
     const GeomParams& P = V.P;
     const Tf4Layout& T = V.T;
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
@@ -169,25 +189,27 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
         mphase ^= 1u;
         tc_fence_after();
         const float i0 = ts_pow2(-se);
-        float lo = 0.0f, hi = 0.0f;
-        for (int c = 0; c < cq; c += 4) {
-            float v[4];
-            tmem_ld4(tD + lane_base + (uint32_t)(pb * cq + c), v);
+        if (warp < kTsEpiWarps) {
+            float lo = 0.0f, hi = 0.0f;
+            for (int c = 0; c < cq; c += 4) {
+                float v[4];
+                tmem_ld4(tD + lane_base + (uint32_t)(pb * cq + c), v);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int d = c + j;                              // column within the block
-                const float u = __shfl_sync(full, (v[j] * i0) * it, (lane - d) & 31);
-                if (lane >= d) lo += u;
-                else hi += u;
+                for (int j = 0; j < 4; ++j) {
+                    const int d = c + j;                              // column within the block
+                    const float u = __shfl_sync(full, (v[j] * i0) * it, (lane - d) & 31);
+                    if (lane >= d) lo += u;
+                    else hi += u;
+                }
             }
+            part[warp * kTsPart + lane] = lo;
+            part[warp * kTsPart + 32 + lane] = hi;
         }
-        part[warp * kTsPart + lane] = lo;
-        part[warp * kTsPart + 32 + lane] = hi;
         tc_fence_before();
         __syncthreads();
         for (int o = tid; o < kTsTile + T.ntap - 1; o += blockDim.x) {
             float acc = 0.0f;
-            for (int w = 0; w < kTsWarps; ++w) {
+            for (int w = 0; w < kTsEpiWarps; ++w) {
                 const int r = o - ((w & 3) * 32 + (w >> 2) * cq);
                 if (r >= 0 && r < 32 + cq - 1) acc += part[w * kTsPart + r];
             }
@@ -407,7 +429,7 @@ __device__ __forceinline__ bool tcs_forward_pool(const TsView& V, unsigned char*
             const int c_lo = (int)(crt & 0xffffu), kw = (int)(crt >> 16) - c_lo;
             {
                 float* srow = sS + (qd * 32 + lane) * T.astride;
-                for (int g8 = pb; g8 < kw / 8; g8 += 4) {
+                for (int g8 = pb; g8 < kw / 8; g8 += kTsWarps / 4) {
                     float4* sp = reinterpret_cast<float4*>(srow + 8 * g8);
                     const float4 v0 = sp[0], v1 = sp[1];
                     sp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -516,7 +538,7 @@ __device__ __forceinline__ float tcs_finish_pixel(unsigned long long a, unsigned
     return __ll2float_rn((long long)a) * ts_pow2(-tc_fixed_exponent(emax_bits, bound));
 }
 
-// A batch of records held in registers: records rb + u * kTsThreads + tid, u < U.
+// A batch of records held in registers: records rb + u * kTbThreads + tid, u < U.
 template <int U, typename WT>
 struct TbBatch {
     uint2 key[U];
@@ -529,7 +551,7 @@ __device__ __forceinline__ void tb_load(TbBatch<U, WT>& b, const uint2* __restri
 {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int r = rb + u * kTsThreads + tid;
+        const int r = rb + u * kTbThreads + tid;
         if (r < r1) {
             b.key[u] = __ldg(rkey + base + r);
             b.w[u] = __ldg(rw + base + r);
@@ -597,7 +619,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
     auto window_exponent = [&]() -> int {
         if (BF16) return 0;
         float m = 0.0f;
-        for (int w = 0; w < kTsWarps; ++w) m = fmaxf(m, wmax[w]);
+        for (int w = 0; w < kTbWarps; ++w) m = fmaxf(m, wmax[w]);
         return ts_bound_exponent(m);
     };
     // H of an item into tensor memory: row n (lane), taps [pb cq, pb cq + cq), H[n][m] = 2^se e[ts + 1 + n + m]
@@ -703,7 +725,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
             auto run = [&](const TbBatch<U, WT>& bt, int rb) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int r = rb + u * kTsThreads + tid;
+                    const int r = rb + u * kTbThreads + tid;
                     if (r >= r1) continue;
                     const uint2 kk = bt.key[u];
                     const int n0r = tc_rec_n0(kk) - ts, trow = tc_rec_row(kk);
@@ -725,7 +747,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
                     red_add_global_u64(acc + (kk.x & kTcPixelMask), (unsigned long long)__float2ll_rn(v * fsc));
                 }
             };
-            constexpr int kStep = U * kTsThreads;
+            constexpr int kStep = U * kTbThreads;
             for (int rb = r0; rb < r1; rb += 2 * kStep) {
                 if (rb + kStep < r1) tb_load(bb, rkey, rw, base, rb + kStep, r1, tid);
                 run(ba, rb);
