@@ -604,7 +604,7 @@ def run_batched(args):
     from paper_2202_09703_gb300 import mbir as M
     from paper_2202_09703_gb300 import synth as S
     dev = torch.device("cuda:0")
-    n = args.requests or 48
+    n = args.requests or 96
     scenes = S.cfg3_scenes(n, seed=0)
     out = {"workload": f"batched: {n} uneven scenes (cfg3 recipe), 50 iterations each"}
     truth = [torch.as_tensor(S.phantom(sc, i).reshape(-1), dtype=torch.float32, device=dev)

@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) eng_fwd_kernel(EngLists L)
 
 // A^T e on the tensor cores (FP32 or BF16 form, tc_stream.cuh) over every active request
 template <bool BF16>
-__global__ void __launch_bounds__(kTbThreads, 1) eng_bwd_tcs_kernel(EngLists L)
+__global__ void __launch_bounds__(TbShape<BF16>::threads, 1) eng_bwd_tcs_kernel(EngLists L)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     tc_header_init(smem, kTsCols);
@@ -913,8 +913,8 @@ cudaError_t enqueue_iteration(mbir_engine* E, bool bf16, bool tcb, bool ccb, boo
     if (tcb) {
         if (bf16) eng_emax_kernel<true><<<SG, kRedThreads, 0, st>>>(E->L);
         else eng_emax_kernel<false><<<SG, kRedThreads, 0, st>>>(E->L);
-        if (bf16) eng_bwd_tcs_kernel<true><<<G, kTbThreads, E->smem_tc[1], st>>>(E->L);
-        else eng_bwd_tcs_kernel<false><<<G, kTbThreads, E->smem_tc[1], st>>>(E->L);
+        if (bf16) eng_bwd_tcs_kernel<true><<<G, TbShape<true>::threads, E->smem_tc[1], st>>>(E->L);
+        else eng_bwd_tcs_kernel<false><<<G, TbShape<false>::threads, E->smem_tc[1], st>>>(E->L);
         eng_bwd_tc_finish_kernel<<<SG, kRedThreads, 0, st>>>(E->L);
     }
     if (ccb) {

@@ -163,12 +163,12 @@ Tb4Layout tb4_layout(const GeomParams& P, int kwmax)
     L.cstride = ((L.kwmax + 31) & ~31) + 4;            // 4 mod 32: the read-back rows hit distinct banks
     L.ewin = (kTsTile + L.ntap + 31) & ~31;
     L.bbytes = (size_t)L.parts * L.kb * L.ntap * 2;
-    L.off_e = 128;
+    L.off_e = 256;                                     // after the header and the warps' maxima
     L.off_b = (L.off_e + (size_t)2 * L.ewin * 4 + 1023) & ~(size_t)1023;
     L.off_c = (L.off_b + L.bbytes + 1023) & ~(size_t)1023;
     L.smem = L.off_c + (size_t)kTsTile * L.cstride * 4;
     L.ok = L.R >= 2 && L.ntap <= 128 && L.kwmax >= 16 && L.kwmax % 16 == 0 && 128 + L.kwmax <= (int)kTsCols &&
-           kTsTile + L.ntap <= kTbThreads && L.smem <= 227 * 1024 && L.bbytes < (1u << 20) &&
+           kTsTile + L.ntap <= 32 * tb_warps(bf) && L.smem <= 227 * 1024 && L.bbytes < (1u << 20) &&
            P.G * L.R <= 4096;
     return L;
 }
@@ -176,7 +176,7 @@ Tb4Layout tb4_layout(const GeomParams& P, int kwmax)
 // The view is read from device memory (written at set-up) with the residual as a parameter, as for the
 // tensor-core A x (fwd_tcs_kernel).
 template <bool BF16, int BV>
-__global__ void __launch_bounds__(kTbThreads, 1)
+__global__ void __launch_bounds__(TbShape<BF16>::threads, 1)
     bwd_tcs_kernel(const TbView* __restrict__ base, const void* e, int* __restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -290,7 +290,7 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     else tc_emax_kernel<float><<<eg, 256, 0, st>>>(e_pad, ne, emax);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
-    kern<<<grid, kTbThreads, L.smem, st>>>(g->d_tb_view, e, g->d_status);
+    kern<<<grid, 32 * tb_warps(bf), L.smem, st>>>(g->d_tb_view, e, g->d_status);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
     tc_finish_kernel<<<std::max(1, std::min((N + 255) / 256, g->n_sm * 8)), 256, 0, st>>>(N, g->w_tc_acc, emax,

@@ -58,8 +58,23 @@ struct TsShape {
     static constexpr int split = warps + 1;         // record offsets per tile: the warps' part boundaries
 };
 constexpr int kTsEpiWarps = 16;     // A x epilogue: four warps per tensor-memory lane quarter read the product
-constexpr int kTbThreads = 512;     // A^T: 16 warps, four per tensor-memory lane quarter
-constexpr int kTbWarps = kTbThreads / 32;
+constexpr int kTbThreads = 512;     // the tensor-core header's reference block: 16 warps, four per lane quarter
+#ifndef MBIR_TB_WARPS_F32
+#define MBIR_TB_WARPS_F32 20
+#endif
+#ifndef MBIR_TB_WARPS_BF16
+#define MBIR_TB_WARPS_BF16 20
+#endif
+// A^T: warps per CTA by storage form (the record pass runs on all of them, the tensor-memory work on 16;
+// 512x1024 A^T with 16 / 20 / 24 warps: FP32 7.77 / 7.56 / 7.58 ms, BF16 7.14 / 7.08 / 7.11 ms)
+__host__ __device__ constexpr int tb_warps(bool bf16) { return bf16 ? MBIR_TB_WARPS_BF16 : MBIR_TB_WARPS_F32; }
+template <bool BF16>
+struct TbShape {
+    static constexpr int warps = tb_warps(BF16);
+    static constexpr int threads = 32 * warps;
+};
+static_assert(tb_warps(false) % 4 == 0 && tb_warps(false) >= 16 && tb_warps(false) <= 28 &&
+              tb_warps(true) % 4 == 0 && tb_warps(true) >= 16 && tb_warps(true) <= 28, "A^T warps: 16..28");
 constexpr int kTsTile = 128;        // n0 values per tile (MMA M)
 static_assert(ts_warps(false) % 4 == 0 && ts_warps(false) >= kTsEpiWarps && ts_warps(false) < 32 &&
               ts_warps(true) % 4 == 0 && ts_warps(true) >= kTsEpiWarps && ts_warps(true) < 32,
@@ -538,20 +553,20 @@ __device__ __forceinline__ float tcs_finish_pixel(unsigned long long a, unsigned
     return __ll2float_rn((long long)a) * ts_pow2(-tc_fixed_exponent(emax_bits, bound));
 }
 
-// A batch of records held in registers: records rb + u * kTbThreads + tid, u < U.
+// A batch of records held in registers: records rb + u * NT + tid, u < U (NT threads per CTA).
 template <int U, typename WT>
 struct TbBatch {
     uint2 key[U];
     WT w[U];
 };
 
-template <int U, typename WT>
+template <int NT, int U, typename WT>
 __device__ __forceinline__ void tb_load(TbBatch<U, WT>& b, const uint2* __restrict__ rkey, const WT* __restrict__ rw,
                                         long long base, int rb, int r1, int tid)
 {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int r = rb + u * kTbThreads + tid;
+        const int r = rb + u * NT + tid;
         if (r < r1) {
             b.key[u] = __ldg(rkey + base + r);
             b.w[u] = __ldg(rw + base + r);
@@ -564,6 +579,7 @@ template <bool BF16, int BV, int U = TbUnroll<BV>::value>
 __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char* smem, uint32_t tmem,
                                                  uint32_t& mphase, uint32_t& bphase, int* status)
 {
+    constexpr int NWB = TbShape<BF16>::warps, NTB = TbShape<BF16>::threads;
     const GeomParams& P = V.P;
     const Tb4Layout& T = V.T;
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
@@ -619,14 +635,14 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
     auto window_exponent = [&]() -> int {
         if (BF16) return 0;
         float m = 0.0f;
-        for (int w = 0; w < kTbWarps; ++w) m = fmaxf(m, wmax[w]);
+        for (int w = 0; w < NWB; ++w) m = fmaxf(m, wmax[w]);
         return ts_bound_exponent(m);
     };
     // H of an item into tensor memory: row n (lane), taps [pb cq, pb cq + cq), H[n][m] = 2^se e[ts + 1 + n + m]
     auto convert_h = [&](const float* sE, int se) {
         const float scl = ts_pow2(se);
         const int n = qd * 32 + lane;
-        for (int m = pb * cq; m < pb * cq + cq; m += 4) {
+        for (int m = pb * cq; m < pb * cq + cq && warp < 16; m += 4) {
             const float a0 = sE[n + m] * scl, a1 = sE[n + m + 1] * scl, a2 = sE[n + m + 2] * scl,
                         a3 = sE[n + m + 3] * scl;
             if (BF16) {
@@ -681,7 +697,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
         const int r1 = __ldg(V.tile_off + (size_t)kc * (ntile + 1) + tc + 1);
         // the first records of this item and the next item's window load during the products
         TbBatch<U, WT> ba, bb;
-        tb_load(ba, rkey, rw, base, r0, r1, tid);
+        tb_load<NTB>(ba, rkey, rw, base, r0, r1, tid);
         const float ew = nxt < nitems ? load_e(nxt) : 0.0f;
         float* sEc = sE0 + cbuf * T.ewin;
         float* sEn = sE0 + (cbuf ^ 1) * T.ewin;
@@ -694,7 +710,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
             const float i0 = ts_pow2(-cse);
             const int cw = kw / 4, row = qd * 32 + lane;
             float* crow = sC + row * T.cstride;
-            for (int c = pb * cw; c < pb * cw + cw; c += 4) {
+            for (int c = pb * cw; c < pb * cw + cw && warp < 16; c += 4) {
                 float v[4];
                 tmem_ld4(tD + lane_base + (uint32_t)c, v);
                 *reinterpret_cast<float4*>(crow + c) =
@@ -725,7 +741,7 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
             auto run = [&](const TbBatch<U, WT>& bt, int rb) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int r = rb + u * kTbThreads + tid;
+                    const int r = rb + u * NTB + tid;
                     if (r >= r1) continue;
                     const uint2 kk = bt.key[u];
                     const int n0r = tc_rec_n0(kk) - ts, trow = tc_rec_row(kk);
@@ -747,12 +763,12 @@ __device__ __forceinline__ bool tcs_adjoint_pool(const TbView& V, unsigned char*
                     red_add_global_u64(acc + (kk.x & kTcPixelMask), (unsigned long long)__float2ll_rn(v * fsc));
                 }
             };
-            constexpr int kStep = U * kTbThreads;
+            constexpr int kStep = U * NTB;
             for (int rb = r0; rb < r1; rb += 2 * kStep) {
-                if (rb + kStep < r1) tb_load(bb, rkey, rw, base, rb + kStep, r1, tid);
+                if (rb + kStep < r1) tb_load<NTB>(bb, rkey, rw, base, rb + kStep, r1, tid);
                 run(ba, rb);
                 if (rb + kStep >= r1) break;
-                if (rb + 2 * kStep < r1) tb_load(ba, rkey, rw, base, rb + 2 * kStep, r1, tid);
+                if (rb + 2 * kStep < r1) tb_load<NTB>(ba, rkey, rw, base, rb + 2 * kStep, r1, tid);
                 run(bb, rb + kStep);
             }
         }
