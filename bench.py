@@ -431,11 +431,12 @@ def run_gpu(args):
                     "algorithmic_bytes_per_launch": smem_bytes, "taps_per_launch": taps, "active_pairs": pairs,
                     "forward_ms": fwd_ms, "backproject_ms": bwd_ms}
 
-    # per iteration: A^T r (tensor cores: max |e|, the pool, the fixed-point sums into b; CUDA cores: the
-    # partial images and their reduction), prior gradient, PR+ scalars, direction, A x, projection, step,
-    # update; per reconstruction the projection of y and the residual's sum of squares first
-    per_iter = (3 if geo.info.adjoint_tensor_cores else 2) + 7
-    launches = args.steps * (per_iter * scene.n_iter + 2)
+    # per iteration: A^T r (tensor cores: the previous step's residual update with max |e|, the pool, the
+    # fixed-point sums into b; CUDA cores: the residual update, the partial images and their reduction), the
+    # prior stencil with the previous step's image update, PR+ scalars, direction, A x, projection, step; per
+    # reconstruction the projection of y and the residual's sum of squares first, the last image update after
+    per_iter = 3 + 6
+    launches = args.steps * (per_iter * scene.n_iter + 3)
 
     out = {"metric": "recons/s", "value": value, "unit": "recons/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,

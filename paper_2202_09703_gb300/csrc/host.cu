@@ -171,7 +171,7 @@ void free_geometry(mbir_geometry* g)
     void* ptrs[] = {g->d_rows, g->d_colx, g->d_pos, g->d_txpos, g->d_rxpos, g->d_tab, g->d_tab_bf16,
                     g->d_legs, g->d_hidx, g->d_direct, g->d_dinv, g->d_status, g->w_e, g->w_q,
                     g->w_b, g->w_grad, g->w_gprev, g->w_d, g->w_part, g->w_scal, g->w_ebf,
-                    g->w_msq, g->w_d2, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
+                    g->w_msq, g->w_d2, g->w_xalt, g->w_y, g->w_x, g->w_g, g->w_hist, g->d_items, g->w_bpart,
                     g->d_rec_off, g->d_rec_key, g->d_rec_w, g->d_tc_key, g->d_tc_w, g->d_runs, g->d_win_order, g->d_win_counter,
                     g->d_bwd_counter, g->d_tc_tile, g->w_tc_acc,
                     g->d_tc_counter, g->d_tf_order, g->d_tf_counter, g->w_colnorm,

@@ -17,19 +17,26 @@
 
 namespace mbir {
 
-// grad = -b/sigma^2 + grad R(x); partials of <g,g>, <g,gprev>, <g,dprev>
+// The MAP update and the prior stencil in one pass: with dupd given, x is first moved by the previous
+// iteration's step, x + alpha dupd (alpha = sc[S_ALPHA]), at the pixel and at its eight neighbours, and the
+// moved image is written to xout; then grad = -b/sigma^2 + grad R(x) at the moved image, with FP64 partials
+// of <g,g>, <g,gprev>, <g,dprev>.  Without dupd the image is taken as it is.
 __global__ void grad_kernel(GeomParams P, PriorParams pr, const float* __restrict__ x, const float* __restrict__ b,
                             const float* __restrict__ msq, const float* __restrict__ gprev,
                             const float* __restrict__ dprev, float* __restrict__ grad, double* __restrict__ part,
-                            int with_data)
+                            int with_data, const float* __restrict__ dupd, const double* __restrict__ sc,
+                            float* __restrict__ xout)
 {
     __shared__ double sh[32];
     const int N = P.W * P.H;
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const float a = dupd ? (float)sc[S_ALPHA] : 0.0f;
+    auto xat = [&](int u) { return dupd ? fmaf(a, dupd[u], x[u]) : x[u]; };   // the same rounding as update_kernel
     double a0 = 0, a1 = 0, a2 = 0;
     if (v < N) {
         const int r = v / P.W, c = v - r * P.W;
-        const float xs = x[v];
+        const float xs = xat(v);
+        if (dupd) xout[v] = xs;
         const float ms = msq[r];
         float gr = 0.0f;
 #pragma unroll
@@ -37,7 +44,7 @@ __global__ void grad_kernel(GeomParams P, PriorParams pr, const float* __restric
             const int r2 = r + c_nb_dr[t], c2 = c + c_nb_dc[t];
             if (r2 < 0 || r2 >= P.H || c2 < 0 || c2 >= P.W) continue;
             float dr;
-            qggmrf(pr, xs - x[r2 * P.W + c2], pr.sigma0 * ms * msq[r2], &dr, nullptr, nullptr);
+            qggmrf(pr, xs - xat(r2 * P.W + c2), pr.sigma0 * ms * msq[r2], &dr, nullptr, nullptr);
             gr += nb_weight(c_nb_dr[t], c_nb_dc[t]) * dr;
         }
         const float g = with_data ? -b[v] * pr.inv_s2 + gr : gr;
@@ -54,6 +61,14 @@ __global__ void grad_kernel(GeomParams P, PriorParams pr, const float* __restric
         part[3 * blockIdx.x + 1] = s1;
         part[3 * blockIdx.x + 2] = s2;
     }
+}
+
+// xout = xin + alpha d (alpha = sc[S_ALPHA]); in place when xout == xin
+__global__ void x_step_kernel(int N, const double* __restrict__ sc, const float* xin, const float* __restrict__ d,
+                              float* xout)
+{
+    const float a = (float)sc[S_ALPHA];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) xout[t] = fmaf(a, d[t], xin[t]);
 }
 
 // Polak-Ribiere+ coefficient with a descent restart
@@ -369,6 +384,7 @@ int ensure_workspace(mbir_geometry* g, int hist)
     CK(grow(&g->w_gprev, N, &B));
     CK(grow(&g->w_d, N, &B));
     CK(grow(&g->w_d2, N, &B));
+    CK(grow(&g->w_xalt, N, &B));
     CK(grow(&g->w_msq, (size_t)P.H, &B));
     g->part_len = std::max<size_t>(3 * nbpix, (size_t)P.K) + 4096;
     CK(grow(&g->w_part, g->part_len * 2, &B));
@@ -511,13 +527,29 @@ int reconstruct_core(mbir_geometry* g, const void* y_dev, int y_bf16, const mbir
     float* dnxt = g->w_d2;
     const int ublocks = (int)std::min<long long>((N + KMp + 255) / 256, 152LL * 32);
     const int cblocks = 152 * 4;
+    // The MAP update of an iteration's step is applied where the next iteration first reads it: e -= alpha q in
+    // the tensor-core adjoint's pass over e that finds max |e| (a pass of its own for the other adjoints), and
+    // x += alpha d in the prior stencil, which writes the moved image to the other of two buffers.  When the
+    // cost is recorded after every iteration, both are applied at the end of the iteration instead (the cost
+    // reads them); the arithmetic, and so every output bit, is the same either way.
+    const bool fuse = !want_cost;
+    float* xc = x;                                     // the current image
+    float* xo = g->w_xalt;                             // the other buffer of the fused stencil
+    bool pending = false;                              // a step waits to be applied
     for (int it = 0; it < n_iter; ++it) {
         prof_begin(g, 1, st);
-        CK(launch_backproject(g, g->w_e, ebf, g->w_b, st));
+        if (pending && g->d_tb4_bop) {
+            CK(launch_backproject_tcs_update(g, g->w_e, ebf, g->w_q, sc, S_ALPHA, g->w_b, st));
+        } else {
+            if (pending) update_kernel<<<ublocks, 256, 0, st>>>(0, KMp, sc, nullptr, nullptr, g->w_e, g->w_q, ebf);
+            CK(launch_backproject(g, g->w_e, ebf, g->w_b, st));
+        }
         prof_end(g, st);
-        grad_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, x, g->w_b, g->w_msq, g->w_gprev, dcur, g->w_grad, part, 1);
+        grad_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, xc, g->w_b, g->w_msq, g->w_gprev, dcur, g->w_grad, part, 1,
+                                                   pending ? dcur : nullptr, sc, xo);
+        if (pending) std::swap(xc, xo);
         finalize_dir_kernel<<<1, kRedThreads, 0, st>>>(part, nbpix, it, sc, g->w_hist + g->hist_len);
-        dir_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, x, g->w_grad, dcur, g->w_msq, sc, dnxt, g->w_gprev, part2);
+        dir_kernel<<<nbpix, kRedThreads, 0, st>>>(P, pp, xc, g->w_grad, dcur, g->w_msq, sc, dnxt, g->w_gprev, part2);
         CK(cudaGetLastError());
         prof_begin(g, 0, st);
         CK(launch_forward(g, dnxt, g->w_q, nullptr, P.Mp, st));
@@ -525,13 +557,20 @@ int reconstruct_core(mbir_geometry* g, const void* y_dev, int y_bf16, const mbir
         project_kernel<<<P.K, kRedThreads, 0, st>>>(P, g->w_q, 0, P.Mp, nullptr, 0, g->d_direct, g->d_dinv,
                                                     use_direct, g->w_q, P.Mp, nullptr, part);
         finalize_step_kernel<<<1, kRedThreads, 0, st>>>(part, P.K, part2, nbpix, pp.inv_s2, sc);
-        update_kernel<<<ublocks, 256, 0, st>>>(N, KMp, sc, x, dnxt, g->w_e, g->w_q, ebf);
-        if (want_cost) {
-            cost_part_kernel<<<cblocks, kRedThreads, 0, st>>>(P, pp, x, g->w_msq, g->w_e, KMp, part);
+        if (fuse) {
+            pending = true;
+        } else {
+            update_kernel<<<ublocks, 256, 0, st>>>(N, KMp, sc, xc, dnxt, g->w_e, g->w_q, ebf);
+            cost_part_kernel<<<cblocks, kRedThreads, 0, st>>>(P, pp, xc, g->w_msq, g->w_e, KMp, part);
             finalize_cost_kernel<<<1, kRedThreads, 0, st>>>(part, cblocks, it, sc, g->w_hist);
         }
         CK(cudaGetLastError());
         std::swap(dcur, dnxt);
+    }
+    if (pending) {
+        // the last step: x into the caller's buffer (the residual is not read again)
+        x_step_kernel<<<std::max(1, std::min((N + 255) / 256, 152 * 8)), 256, 0, st>>>(N, sc, xc, dcur, x);
+        CK(cudaGetLastError());
     }
     if (g_dev) {
         CK(launch_forward(g, x, g->w_q, nullptr, P.Mp, st));
@@ -812,7 +851,7 @@ int mbir_prior_gradient(const mbir_geometry* gc, const mbir_prior* pr, const flo
     const int nb = (N + kRedThreads - 1) / kRedThreads;
     CK(cudaMemsetAsync(g->w_gprev, 0, sizeof(float) * N, st));
     grad_kernel<<<nb, kRedThreads, 0, st>>>(g->P, prior_params(&tmp), x_dev, nullptr, g->w_msq, g->w_gprev,
-                                           g->w_gprev, out_dev, g->w_part, 0);
+                                           g->w_gprev, out_dev, g->w_part, 0, nullptr, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MBIR_OK : cerr_code(e);
 }

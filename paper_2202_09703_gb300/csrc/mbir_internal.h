@@ -372,6 +372,7 @@ struct mbir_geometry {
     size_t tab_len;
     float* w_msq;          // H: sqrt(m_s) of eq. 17 for the current prior
     float* w_d2;           // N: second direction buffer (ping-pong)
+    float* w_xalt;         // N: second image buffer of the fused update-and-prior stencil (ping-pong)
     float* w_y;            // K x M staging for host-buffer calls
     float* w_x;            // N staging for host-buffer calls
     float* w_g;            // K staging for host-buffer calls
@@ -491,6 +492,8 @@ cudaError_t build_tc_forward_stream(mbir_geometry* g, cudaStream_t st);
 Tb4Layout tb4_layout(const GeomParams& P, int kwmax);
 cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st);
 cudaError_t tune_tc_applies(mbir_geometry* g, cudaStream_t st);
+cudaError_t launch_backproject_tcs_update(const mbir_geometry* g, float* e, __nv_bfloat16* ebf, const float* q,
+                                          const double* sc, int alpha_slot, float* b, cudaStream_t st);
 cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
                                    cudaStream_t st);
 cudaError_t launch_forward_tcs(const mbir_geometry* g, const float* x, float* yf, __nv_bfloat16* yb, int stride,

@@ -31,6 +31,30 @@ __global__ void tc_emax_kernel(const T* __restrict__ e, long long n, unsigned in
     if ((threadIdx.x & 31) == 0 && m) atomicMax(emax, m);
 }
 
+// The residual's pending MAP update e -= alpha q (alpha = sc[alpha_slot], the previous iteration's step),
+// its BF16 copy when there is one, and *emax = bits of max |e| over the values the adjoint then reads (the
+// BF16 copy in the BF16 form): the update and the scale's pass over e in one.
+__global__ void tc_emax_update_kernel(float* __restrict__ e, __nv_bfloat16* __restrict__ ebf,
+                                      const float* __restrict__ q, const double* __restrict__ sc, int alpha_slot,
+                                      long long n, unsigned int* __restrict__ emax)
+{
+    const float a = (float)sc[alpha_slot];
+    unsigned int m = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float v = fmaf(-a, q[i], e[i]);
+        e[i] = v;
+        if (ebf) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            ebf[i] = h;
+            v = __bfloat162float(h);
+        }
+        m = max(m, __float_as_uint(fabsf(v)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(emax, m);
+}
+
 // b[v] from the fixed-point sums (tcs_finish_pixel)
 __global__ void tc_finish_kernel(int N, const unsigned long long* __restrict__ acc,
                                  const unsigned int* __restrict__ emax, float bound, float* __restrict__ b)
@@ -265,8 +289,9 @@ cudaError_t build_tc_adjoint_stream(mbir_geometry* g, cudaStream_t st)
     return cudaSuccess;
 }
 
-cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
-                                   cudaStream_t st)
+static cudaError_t launch_backproject_tcs_impl(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf,
+                                               float* b, float* e_upd, __nv_bfloat16* ebf_upd, const float* q,
+                                               const double* sc, int alpha_slot, cudaStream_t st)
 {
     const GeomParams& P = g->P;
     const Tb4Layout& L = g->tb4;
@@ -278,7 +303,6 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     if (ce != cudaSuccess) return ce;
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
     const int grid = std::max(1, std::min(g->n_sm, P.K * ntile));
-    const void* tab = bf ? (const void*)g->d_tab_bf16 : (const void*)g->d_tab;
     const void* e = bf ? (const void*)e_bf : (const void*)e_pad;
     const int N = P.W * P.H;
     unsigned int* emax = reinterpret_cast<unsigned int*>(g->w_tc_acc + N);
@@ -286,7 +310,8 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     if (ce != cudaSuccess) return ce;
     const long long ne = (long long)P.K * P.Mp;
     const int eg = (int)std::max(1LL, std::min((ne + 255) / 256, (long long)g->n_sm * 8));
-    if (bf) tc_emax_kernel<__nv_bfloat16><<<eg, 256, 0, st>>>(e_bf, ne, emax);
+    if (e_upd) tc_emax_update_kernel<<<eg, 256, 0, st>>>(e_upd, bf ? ebf_upd : nullptr, q, sc, alpha_slot, ne, emax);
+    else if (bf) tc_emax_kernel<__nv_bfloat16><<<eg, 256, 0, st>>>(e_bf, ne, emax);
     else tc_emax_kernel<float><<<eg, 256, 0, st>>>(e_pad, ne, emax);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return ce;
@@ -296,6 +321,20 @@ cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, c
     tc_finish_kernel<<<std::max(1, std::min((N + 255) / 256, g->n_sm * 8)), 256, 0, st>>>(N, g->w_tc_acc, emax,
                                                                                            g->tc_bound, b);
     return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_tcs(const mbir_geometry* g, const float* e_pad, const __nv_bfloat16* e_bf, float* b,
+                                   cudaStream_t st)
+{
+    return launch_backproject_tcs_impl(g, e_pad, e_bf, b, nullptr, nullptr, nullptr, nullptr, 0, st);
+}
+
+// A^T e after the residual's pending update e -= alpha q (e: K x Mp FP32, with its BF16 copy ebf in the BF16
+// form), the update done in the pass that finds max |e|.
+cudaError_t launch_backproject_tcs_update(const mbir_geometry* g, float* e, __nv_bfloat16* ebf, const float* q,
+                                          const double* sc, int alpha_slot, float* b, cudaStream_t st)
+{
+    return launch_backproject_tcs_impl(g, e, ebf, b, e, ebf, q, sc, alpha_slot, st);
 }
 
 }  // namespace mbir
