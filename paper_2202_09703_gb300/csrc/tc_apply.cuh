@@ -10,8 +10,6 @@
 
 namespace mbir {
 
-constexpr int kTcThreads = 512;      // 16 warps: four per tensor-memory lane quarter
-
 // Records of the tensor-core forms, packed once per geometry from the sorted records (ts_pack_kernel):
 //   key.x = pixel (bits 0-19) | table row (bits 20-30) | batch mark of the A x (bit 31)
 //   key.y = n0 (bits 19-31) | tau = t0 flag (bit 18) | fa x 2^18 (bits 0-17)

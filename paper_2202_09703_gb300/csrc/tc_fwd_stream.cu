@@ -20,7 +20,7 @@ Tf4Layout tf4_layout(const GeomParams& P, int kwmax)
     L.astride = ((L.kwmax + 31) & ~31) + 4;            // 4 mod 32: a warp's row reads hit distinct banks
     L.bbytes = (size_t)L.parts * L.ntap * L.kb * 2;
     const int ntile = (P.M + kTsTile - 1) / kTsTile;
-    L.off_part = 1024;                                 // anti-diagonal sums, 16 warps x 64 floats
+    L.off_part = 1024;                                 // the epilogue warps' anti-diagonal sums, 64 floats each
     const int nw = ts_warps(bf);
     L.off_rs = L.off_part + (size_t)nw * kTsPart * 4;   // per A-scan: part boundaries, column ranges
     L.off_b = (L.off_rs + (size_t)ntile * (nw + 2) * 4 + 1023) & ~(size_t)1023;

@@ -58,7 +58,6 @@ struct TsShape {
     static constexpr int split = warps + 1;         // record offsets per tile: the warps' part boundaries
 };
 constexpr int kTsEpiWarps = 16;     // A x epilogue: four warps per tensor-memory lane quarter read the product
-constexpr int kTbThreads = 512;     // the tensor-core header's reference block: 16 warps, four per lane quarter
 #ifndef MBIR_TB_WARPS_F32
 #define MBIR_TB_WARPS_F32 20
 #endif
@@ -112,7 +111,6 @@ __device__ __forceinline__ float ld_x(const float* p)
 // 512x1024 A x from 10.35 to 9.04 ms (FP32) and from 9.12 to 8.21 ms (BF16); with 16 warps one was better
 constexpr int kTsXAhead = MBIR_TS_XAHEAD;
 static_assert(kTsXAhead >= 1 && kTsXAhead < kTsRing, "x is gathered from records already in the ring");
-static_assert(kTbThreads == kTcThreads, "the tensor-core header assumes the adjoint's block size");
 
 struct TsView {
     GeomParams P;
