@@ -117,9 +117,11 @@ typedef struct {
 } mbir_geometry_desc;
 
 /* TAB mode normally also stores every A-scan's active pairs as records
- * grouped by first tap sample (the system matrix of Section 3, 24 bytes per
- * active pair) so that A x and A^T stream them; this flag keeps the
- * on-the-fly record path of A x instead (less memory, slower). */
+ * grouped by first tap sample (the system matrix of Section 3) so that A x
+ * and A^T stream them: 24 bytes per active pair for the CUDA-core kernels,
+ * packed to 16 (FP32 form) or 12 bytes (BF16 form) for the tensor-core ones;
+ * this flag keeps the on-the-fly record path of A x instead (less memory,
+ * slower). */
 #define MBIR_FLAG_NO_RECORDS 1
 
 /* With records, A and A^T normally run on the tensor cores (both storage
