@@ -227,6 +227,42 @@ def test_pulse_table_no_attenuation_is_the_pulse():
     assert np.max(np.abs(tab[0] - ref)) < 1e-12
 
 
+@pytest.mark.parametrize("cfg", ["cfg0", "cfg1"])
+def test_pulse_is_a_two_cycle_gaussian_burst(cfg):
+    """Eq. 9-10 reading: a Gaussian-modulated sinusoid whose envelope's full
+    width at half maximum is n_c = 2 carrier periods, centred in its window
+    of t0 = ceil(8 sigma fs) samples.  At the centre and one period either
+    side the carrier is 1, so the pulse is 1 and 1/2 there; half a period
+    out the carrier is -1 and the envelope exp(-(1/(2 f_c))^2 / (2 sigma^2))."""
+    s = S.CONFIGS[cfg]()
+    g = O.Geometry(s)
+    sigma = 2.0 / (2.0 * math.sqrt(2.0 * math.log(2.0)) * s.fc)
+    Tw = g.pulse_support()
+    assert Tw == math.ceil(8.0 * sigma * s.fs) == 68
+    tc = 0.5 * Tw / s.fs
+    assert abs(g.pulse(tc) - 1.0) < 1e-12
+    for sgn in (-1.0, 1.0):
+        assert abs(g.pulse(tc + sgn / s.fc) - 0.5) < 1e-12
+        half = tc + sgn / (2.0 * s.fc)
+        assert abs(g.pulse(half) + math.exp(-(0.5 / s.fc) ** 2 / (2.0 * sigma ** 2))) < 1e-12
+
+
+def test_gamma_max_is_twice_the_two_way_vertical_loss():
+    """The table's attenuation range (reading R10): twice the two-way loss of
+    the vertical path to the deepest pixel centre, i.e. four times the
+    one-way leg's gamma at zero offset (the leg's gamma is pinned against the
+    Fermat path above); zero, and a single plane, without attenuation."""
+    for s in (S.cfg0(), S.cfg1(), _scene_layers([1480.0, 3000.0, 4500.0], [2e-3, 1.5e-3, 3e-3],
+                                                  atten=[2.0, 30.0, 20.0], h=12)):
+        g = O.Geometry(s)
+        zb = s.z0 + (s.img_h - 0.5) * s.pitch
+        assert abs(g.gamma_max() - 4.0 * g.leg(0.0, zb)[1]) <= 1e-12 * g.gamma_max()
+        assert g.effective_G() == s.G > 1
+    s0 = S.cfg0().copy(layers=[S.Layer(10e-3, 1480, 0.0, 1000), S.Layer(10e-3, 5900, 0.0, 7850)])
+    g0 = O.Geometry(s0)
+    assert g0.gamma_max() == 0.0 and g0.effective_G() == 1
+
+
 def test_pulse_table_matches_faddeeva_closed_form():
     s = S.cfg1()
     g = O.Geometry(s)
