@@ -197,6 +197,27 @@ def test_transmission_two_way_normal_incidence():
     assert g.transmission(10e-3) == pytest.approx(t12 * t23, rel=1e-15)
 
 
+def test_transmission_conserves_energy_and_is_reciprocal():
+    """The two-way normal-incidence transmission through an interface is the
+    energy that is not reflected, 1 - R^2 with R = (Z2 - Z1) / (Z2 + Z1); it is
+    the same with the two media swapped, 1 between matched impedances, and
+    below 1 otherwise."""
+    def tau_below(layers, z):
+        s = _scene_layers([L[0] for L in layers], [L[1] for L in layers])
+        s.layers = [S.Layer(t, c, 0.0, rho) for (c, t, rho) in layers]
+        return O.Geometry(s).transmission(z)
+    a, b = (1480.0, 2e-3, 1000.0), (5900.0, 2e-3, 7850.0)
+    Za, Zb = a[0] * a[2], b[0] * b[2]
+    R = (Zb - Za) / (Zb + Za)
+    assert tau_below([a, b], 3e-3) == pytest.approx(1.0 - R * R, rel=1e-14)
+    assert tau_below([b, a], 3e-3) == pytest.approx(tau_below([a, b], 3e-3), rel=1e-14)
+    matched = (2960.0, 2e-3, 500.0)                       # same impedance as water (1480 x 1000)
+    assert tau_below([a, matched], 3e-3) == pytest.approx(1.0, rel=1e-14)
+    three = tau_below([a, b, (3000.0, 5e-3, 1900.0)], 5e-3)
+    R2 = (3000.0 * 1900.0 - Zb) / (3000.0 * 1900.0 + Zb)
+    assert three == pytest.approx((1.0 - R * R) * (1.0 - R2 * R2), rel=1e-14) and three < 1.0
+
+
 # --------------------------------------------------------------------------
 # pulse family (eq. 9-10)
 # --------------------------------------------------------------------------
